@@ -1,0 +1,254 @@
+"""Plain CPU oracle for Gaussian-kernel ridge regression on genotypes.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(the CUDA library and its binding) never imports it and shares no code with it.
+
+Everything here is the plain definition of what the method computes, in
+int64 / IEEE double:
+
+* Alg. 2 / Alg. 5 (Build with the Gaussian kernel): ``d_ij = sum_k (g_ik -
+  g_jk)^2`` term by term, ``K_ij = exp(-gamma d_ij)``.
+* Alg. 3 (Associate): Cholesky of ``K + alpha I`` and forward/backward
+  substitution for every phenotype column.
+* Alg. 4 (Predict): Build(gamma, T, G) then ``P_r = K_test W``.
+* The gradient of the held-out mean-squared error with respect to log gamma
+  and log lambda, from the adjoint closed form (the paper has no gradient;
+  the formula is derived in ``hyper_gradient``'s docstring).
+
+Pins (tests/test_oracle_*.py) tie each function to something other than
+itself: brute force on tiny inputs, the paper's 3x2 worked example, closed
+forms (gamma = 0, K = I, lambda -> infinity, min(i,j) Cholesky), invariants
+(symmetry, K_ii = 1, L L^T reconstruction, the predict identity) and central
+finite differences for the gradient.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "krr_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i8p = ctypes.POINTER(ctypes.c_int8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle into ``oracle/liboracle.so`` (gcc, OpenMP if available)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.oracle_num_threads.restype = ctypes.c_int
+            for name in ("oracle_sqdist_bruteforce", "oracle_sqdist_gram"):
+                f = getattr(lib, name)
+                f.restype = None
+                f.argtypes = [_i8p, ctypes.c_int64, ctypes.c_int64, _i8p, ctypes.c_int64,
+                              ctypes.c_int64, ctypes.c_int64, _i64p]
+            lib.oracle_gaussian_kernel.restype = None
+            lib.oracle_gaussian_kernel.argtypes = [_i64p, ctypes.c_int64, ctypes.c_double, _f64p]
+            lib.oracle_cholesky.restype = ctypes.c_int64
+            lib.oracle_cholesky.argtypes = [_f64p, ctypes.c_int64]
+            for name in ("oracle_forward_subst", "oracle_backward_subst"):
+                f = getattr(lib, name)
+                f.restype = None
+                f.argtypes = [_f64p, ctypes.c_int64, _f64p, ctypes.c_int64]
+            lib.oracle_matmul.restype = None
+            lib.oracle_matmul.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, _f64p,
+                                          ctypes.c_int64, _f64p]
+            lib.oracle_kernel_rows.restype = None
+            lib.oracle_kernel_rows.argtypes = [_i8p, ctypes.c_int64, _i64p, ctypes.c_int64, _i8p,
+                                               ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                               ctypes.c_double, _f64p]
+            _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """Threads the oracle's OpenMP loops use."""
+    return int(_load().oracle_num_threads())
+
+
+def _geno(g) -> np.ndarray:
+    g = np.ascontiguousarray(np.asarray(g), dtype=np.int8)
+    if g.ndim != 2:
+        raise ValueError("genotype matrix must be 2-D (patients x SNPs)")
+    return g
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+def sqdist(g1, g2=None, method: str = "bruteforce") -> np.ndarray:
+    """Squared Euclidean distances between the rows of ``g1`` and ``g2`` (int64).
+
+    ``method="bruteforce"`` sums ``(g1_ik - g2_jk)^2`` term by term (the
+    definition used by Alg. 5); ``method="gram"`` uses the norm-plus-Gram
+    identity of the paper's distance section (Sec. IV-B).  Both are exact.
+    """
+    a = _geno(g1)
+    b = a if g2 is None else _geno(g2)
+    if a.shape[1] != b.shape[1]:
+        raise ValueError("SNP counts differ")
+    out = np.empty((a.shape[0], b.shape[0]), dtype=np.int64)
+    fn = {"bruteforce": _load().oracle_sqdist_bruteforce, "gram": _load().oracle_sqdist_gram}[method]
+    fn(_ptr(a, _i8p), a.shape[0], a.shape[1], _ptr(b, _i8p), b.shape[0], b.shape[1], a.shape[1],
+       _ptr(out, _i64p))
+    return out
+
+
+def gaussian_kernel(d: np.ndarray, gamma: float) -> np.ndarray:
+    """Alg. 5, Gaussian branch: ``exp(-gamma * d)`` elementwise, in double."""
+    d = np.ascontiguousarray(d, dtype=np.int64)
+    out = np.empty(d.shape, dtype=np.float64)
+    _load().oracle_gaussian_kernel(_ptr(d, _i64p), d.size, float(gamma), _ptr(out, _f64p))
+    return out
+
+
+def build_kernel(gamma: float, g1, g2=None) -> np.ndarray:
+    """Alg. 2: ``K[i, j] = KernelMatrix('Gaussian', gamma, G1[i, :], G2[j, :])``."""
+    return gaussian_kernel(sqdist(g1, g2), gamma)
+
+
+class NotPositiveDefinite(ArithmeticError):
+    def __init__(self, column: int):
+        super().__init__(f"non-positive pivot at column {column}")
+        self.column = column
+
+
+def cholesky(a: np.ndarray) -> np.ndarray:
+    """Alg. 3 "Factorize": lower-triangular L with ``L L^T = a`` (double)."""
+    l = np.array(a, dtype=np.float64, order="C", copy=True)
+    n = l.shape[0]
+    if l.shape != (n, n):
+        raise ValueError("square matrix expected")
+    col = _load().oracle_cholesky(_ptr(l, _f64p), n)
+    if col >= 0:
+        raise NotPositiveDefinite(int(col))
+    return l
+
+
+def forward_subst(l: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Solve ``L Z = Y`` by forward substitution (Y is n x p)."""
+    l = np.ascontiguousarray(l, dtype=np.float64)
+    z = np.array(y, dtype=np.float64, order="C", copy=True).reshape(l.shape[0], -1)
+    _load().oracle_forward_subst(_ptr(l, _f64p), l.shape[0], _ptr(z, _f64p), z.shape[1])
+    return z
+
+
+def backward_subst(l: np.ndarray, z: np.ndarray) -> np.ndarray:
+    """Solve ``L^T X = Z`` by backward substitution (Z is n x p)."""
+    l = np.ascontiguousarray(l, dtype=np.float64)
+    x = np.array(z, dtype=np.float64, order="C", copy=True).reshape(l.shape[0], -1)
+    _load().oracle_backward_subst(_ptr(l, _f64p), l.shape[0], _ptr(x, _f64p), x.shape[1])
+    return x
+
+
+def matmul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Plain double product ``a @ b`` accumulated in index order."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64).reshape(a.shape[1], -1)
+    c = np.empty((a.shape[0], b.shape[1]), dtype=np.float64)
+    _load().oracle_matmul(_ptr(a, _f64p), a.shape[0], a.shape[1], _ptr(b, _f64p), b.shape[1],
+                          _ptr(c, _f64p))
+    return c
+
+
+def associate(alpha: float, k: np.ndarray, y: np.ndarray, return_factor: bool = False):
+    """Alg. 3: ``K~ = Factorize(K + alpha I)``; ``W = Solve(K~, P_h)``."""
+    a = np.array(k, dtype=np.float64, copy=True)
+    a[np.diag_indices_from(a)] += alpha
+    l = cholesky(a)
+    w = backward_subst(l, forward_subst(l, y))
+    return (w, l) if return_factor else w
+
+
+def predict(gamma: float, g, t, w: np.ndarray) -> np.ndarray:
+    """Alg. 4: ``K = Build(gamma, T, G)`` (N_P2 x N_P1), ``P_r = K W``."""
+    return matmul(build_kernel(gamma, t, g), w)
+
+
+def krr(gamma: float, alpha: float, g, y, t):
+    """Alg. 1: Build, Associate, Predict.  Returns (K, W, P_r)."""
+    k = build_kernel(gamma, g)
+    w = associate(alpha, k, y)
+    return k, w, predict(gamma, g, t, w)
+
+
+def kernel_rows(gamma: float, g1, rows, g2) -> np.ndarray:
+    """Rows ``rows`` of Build(gamma, G1, G2), each entry from the definition."""
+    a = _geno(g1)
+    b = _geno(g2)
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    out = np.empty((r.size, b.shape[0]), dtype=np.float64)
+    _load().oracle_kernel_rows(_ptr(a, _i8p), a.shape[1], _ptr(r, _i64p), r.size, _ptr(b, _i8p),
+                               b.shape[0], b.shape[1], a.shape[1], float(gamma), _ptr(out, _f64p))
+    return out
+
+
+def held_out_loss(gamma: float, lam: float, g, y, t, y_t) -> float:
+    """Held-out mean squared error ``||K_test A - Y_t||_F^2 / (N_t P)``, A from Alg. 3."""
+    w = associate(lam, build_kernel(gamma, g), y)
+    r = predict(gamma, g, t, w) - np.asarray(y_t, dtype=np.float64).reshape(len(t), -1)
+    return float((r * r).sum() / r.size)
+
+
+def hyper_gradient(gamma: float, lam: float, g, y, t, y_t):
+    """Gradient of the held-out MSE with respect to log gamma and log lambda.
+
+    With M = K + lambda I, A = M^-1 Y, Yhat = K_t A and
+    loss = ||Yhat - Y_t||_F^2 / (N_t P):
+
+    * G_p = dloss/dYhat = 2 (Yhat - Y_t) / (N_t P)
+    * B = dloss/dA = K_t^T G_p and Z = M^-1 B (M is symmetric)
+    * dA = -M^-1 dM A, so dloss = -<Z A^T, dM>.
+    * dM/dlambda = I:              dloss/dlog lambda = -lambda <Z, A>.
+    * dK/dgamma = -D (.) K, for K and for K_t:
+      dloss/dlog gamma = gamma * ( sum_ij D_ij K_ij (Z A^T)_ij
+                                   - sum_tj D_tj K_tj (G_p A^T)_tj ).
+
+    Returns (loss, dloss/dlog gamma, dloss/dlog lambda), all double.
+    """
+    g = _geno(g)
+    t = _geno(t)
+    y = np.asarray(y, dtype=np.float64).reshape(len(g), -1)
+    y_t = np.asarray(y_t, dtype=np.float64).reshape(len(t), -1)
+    d = sqdist(g)
+    k = gaussian_kernel(d, gamma)
+    a, l = associate(lam, k, y, return_factor=True)
+    d_t = sqdist(t, g)
+    k_t = gaussian_kernel(d_t, gamma)
+    yhat = matmul(k_t, a)
+    r = yhat - y_t
+    loss = float((r * r).sum() / r.size)
+    g_p = 2.0 * r / r.size
+    b = matmul(k_t.T, g_p)
+    z = backward_subst(l, forward_subst(l, b))
+    dlog_lam = -lam * float((z * a).sum())
+    za = matmul(z, a.T)
+    ga = matmul(g_p, a.T)
+    dgamma = float((d * k * za).sum()) - float((d_t * k_t * ga).sum())
+    return loss, gamma * dgamma, dlog_lam

@@ -1,0 +1,263 @@
+"""Pins for the CPU oracle: each check ties an oracle function to something
+other than itself (the paper's worked example, brute force on tiny inputs,
+closed forms, invariants, a library routine on a special case, finite
+differences).  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_01712_gb300 import inputs
+
+
+def _rand_geno(n, m, seed):
+    rng = np.random.default_rng(seed)
+    p = rng.uniform(0.05, 0.5, m)
+    return ((rng.random((n, m)) < p).astype(np.int8) + (rng.random((n, m)) < p)).astype(np.int8)
+
+
+def _golden(golden_dir):
+    rows = {}
+    with open(os.path.join(golden_dir, "worked_example_3x2.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            rows.setdefault(key, []).append([int(v) for v in vals])
+    return {k: np.array(v, dtype=np.int64) for k, v in rows.items()}
+
+
+# ---------------------------------------------------------------- distances
+
+def test_worked_example_3x2(golden_dir):
+    """Sec. IV-B worked example: 3 patients x 2 markers, hand-computed."""
+    gold = _golden(golden_dir)
+    patients = gold["G"].T.astype(np.int8)  # rows = patients a, b, c
+    assert np.array_equal(oracle.sqdist(patients), gold["DT"])
+    assert np.array_equal(oracle.sqdist(patients, method="gram"), gold["DT"])
+    # the identity the example walks through, term by term, on the golden numbers
+    assert np.array_equal(gold["D"] + gold["D"].T - 2 * gold["GTG"], gold["DT"])
+
+
+def test_bruteforce_equals_gram_identity():
+    for seed, (n1, n2, m) in enumerate([(1, 1, 1), (7, 5, 3), (33, 64, 300), (64, 17, 129)]):
+        a = _rand_geno(n1, m, seed)
+        b = _rand_geno(n2, m, seed + 100)
+        d1 = oracle.sqdist(a, b)
+        d2 = oracle.sqdist(a, b, method="gram")
+        assert np.array_equal(d1, d2)
+
+
+def test_distance_small_cases_by_hand():
+    # one SNP differing by 1, by 2; nothing differing
+    a = np.array([[0, 1, 2, 1]], dtype=np.int8)
+    b = np.array([[0, 2, 2, 1], [2, 1, 0, 1], [0, 1, 2, 1]], dtype=np.int8)
+    assert oracle.sqdist(a, b).tolist() == [[1, 8, 0]]
+
+
+def test_distance_extremes_and_symmetry():
+    m = 300
+    z = np.zeros((1, m), np.int8)
+    two = np.full((1, m), 2, np.int8)
+    assert oracle.sqdist(z, two)[0, 0] == 4 * m  # max-value case
+    g = _rand_geno(40, m, 3)
+    d = oracle.sqdist(g)
+    assert np.array_equal(d, d.T)
+    assert np.all(np.diag(d) == 0)
+    g[5] = g[9]
+    assert oracle.sqdist(g)[5, 9] == 0
+
+
+# ---------------------------------------------------------------- kernel
+
+def test_gaussian_kernel_values():
+    d = np.array([[0, 1, 3], [7, 100, 4]], dtype=np.int64)
+    k = oracle.gaussian_kernel(d, 0.25)
+    expect = [[1.0, math.exp(-0.25), math.exp(-0.75)], [math.exp(-1.75), math.exp(-25.0), math.exp(-1.0)]]
+    assert np.allclose(k, expect, rtol=1e-15, atol=0)
+
+
+def test_kernel_invariants_and_pd():
+    g = _rand_geno(48, 64, 4)
+    k = oracle.build_kernel(1 / 64, g)
+    assert np.allclose(k, k.T, rtol=0, atol=0)
+    assert np.all(np.diag(k) == 1.0)
+    assert np.all((k > 0) & (k <= 1))
+    # distinct rows -> Gaussian kernel is positive definite: Cholesky with lambda = 0
+    assert len({r.tobytes() for r in g}) == len(g)
+    l = oracle.cholesky(k)
+    assert np.all(np.diag(l) > 0)
+    # identical rows -> d = 0, K = 1, K singular: with rows 0 and 2 equal the
+    # third pivot is exactly 1 - 1 - 0 = 0 and the factorisation must fail
+    g2 = g[:3].copy()
+    g2[2] = g2[0]
+    k2 = oracle.build_kernel(1 / 64, g2)
+    assert k2[2, 0] == 1.0
+    with pytest.raises(oracle.NotPositiveDefinite) as e:
+        oracle.cholesky(k2)
+    assert e.value.column == 2
+
+
+# ---------------------------------------------------------------- factor
+
+def test_cholesky_min_matrix_closed_form():
+    # A_ij = min(i, j) (1-based) has the all-ones lower triangle as its factor
+    n = 9
+    i = np.arange(1, n + 1)
+    a = np.minimum.outer(i, i).astype(np.float64)
+    l = oracle.cholesky(a)
+    assert np.array_equal(l, np.tril(np.ones((n, n))))
+
+
+def test_cholesky_reconstruction_and_library():
+    rng = np.random.default_rng(5)
+    for n in (1, 2, 17, 128):
+        x = rng.standard_normal((n, n))
+        a = x @ x.T + n * np.eye(n)
+        l = oracle.cholesky(a)
+        assert np.array_equal(l, np.tril(l))
+        err = np.linalg.norm(l @ l.T - a) / np.linalg.norm(a)
+        assert err <= 10 * n * np.finfo(np.float64).eps
+        assert np.allclose(l, np.linalg.cholesky(a), rtol=1e-12, atol=1e-12)
+
+
+def test_cholesky_reports_first_bad_pivot():
+    a = np.diag([4.0, 1.0, -1.0, 2.0])
+    with pytest.raises(oracle.NotPositiveDefinite) as e:
+        oracle.cholesky(a)
+    assert e.value.column == 2
+
+
+# ---------------------------------------------------------------- solve
+
+def test_substitution_on_known_triangle():
+    l = np.array([[2.0, 0, 0], [1.0, 3.0, 0], [-1.0, 2.0, 4.0]])
+    x = np.array([[1.0, -2.0], [0.5, 3.0], [2.0, 1.0]])
+    y = l @ x
+    assert np.allclose(oracle.forward_subst(l, y), x, rtol=1e-15, atol=1e-15)
+    assert np.allclose(oracle.backward_subst(l, l.T @ x), x, rtol=1e-15, atol=1e-15)
+
+
+def test_solve_gamma_zero_sherman_morrison():
+    # gamma = 0: K = 1 1^T, A = (Y - 1 (1^T Y)/(lambda + N)) / lambda
+    g = _rand_geno(50, 20, 6)
+    y = np.random.default_rng(6).standard_normal((50, 3))
+    lam = 0.37
+    k = oracle.build_kernel(0.0, g)
+    assert np.all(k == 1.0)
+    a = oracle.associate(lam, k, y)
+    expect = (y - np.ones((50, 1)) * y.sum(0, keepdims=True) / (lam + 50)) / lam
+    assert np.allclose(a, expect, rtol=1e-10, atol=1e-12)
+
+
+def test_solve_large_gamma_identity_kernel():
+    g = _rand_geno(40, 30, 7)
+    assert len({r.tobytes() for r in g}) == len(g)
+    y = np.random.default_rng(7).standard_normal((40, 2))
+    lam = 0.1
+    k = oracle.build_kernel(1000.0, g)  # exp(-1000 d) underflows to 0 for d >= 1
+    assert np.array_equal(k, np.eye(40))
+    assert np.allclose(oracle.associate(lam, k, y), y / (1 + lam), rtol=1e-15, atol=0)
+
+
+def test_solve_lambda_to_infinity():
+    g = _rand_geno(60, 40, 8)
+    y = np.random.default_rng(8).standard_normal((60, 2))
+    k = oracle.build_kernel(1 / 40, g)
+    knorm = np.linalg.norm(k, 2)
+    for lam in (1e3, 1e6):
+        a = oracle.associate(lam, k, y)
+        assert np.linalg.norm(lam * a - y) / np.linalg.norm(y) <= knorm / lam
+
+
+def test_solve_matches_library_solve():
+    g = _rand_geno(64, 32, 9)
+    y = np.random.default_rng(9).standard_normal((64, 4))
+    k = oracle.build_kernel(1 / 32, g)
+    a = oracle.associate(0.1, k, y)
+    assert np.allclose(a, np.linalg.solve(k + 0.1 * np.eye(64), y), rtol=1e-9, atol=1e-9)
+
+
+# ---------------------------------------------------------------- predict
+
+def test_predict_identity_on_training_rows():
+    # predicting the training rows gives K A = Y - lambda A
+    g = _rand_geno(70, 50, 10)
+    y = np.random.default_rng(10).standard_normal((70, 3))
+    lam, gamma = 0.2, 1 / 50
+    _, a, pr = oracle.krr(gamma, lam, g, y, g)
+    assert np.allclose(pr, y - lam * a, rtol=1e-9, atol=1e-10)
+
+
+def test_predict_matmul_by_hand():
+    a = np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 6.0]])
+    b = np.array([[1.0, -1.0, 0.5], [2.0, 0.0, 1.0]])
+    assert np.array_equal(oracle.matmul(a, b), [[5.0, -1.0, 2.5], [11.0, -3.0, 5.5], [17.0, -5.0, 8.5]])
+
+
+def test_kernel_rows_match_full_build():
+    g = _rand_geno(30, 25, 11)
+    t = _rand_geno(12, 25, 12)
+    rows = np.array([0, 5, 11])
+    assert np.allclose(oracle.kernel_rows(0.05, t, rows, g), oracle.build_kernel(0.05, t, g)[rows],
+                       rtol=0, atol=0)
+
+
+# ---------------------------------------------------------------- gradient
+
+def test_gradient_matches_central_differences():
+    g = _rand_geno(80, 64, 13)
+    t = _rand_geno(24, 64, 14)
+    rng = np.random.default_rng(13)
+    y = rng.standard_normal((80, 2))
+    yt = rng.standard_normal((24, 2))
+    gamma, lam = 1 / 64, 0.1
+    loss, dlg, dll = oracle.hyper_gradient(gamma, lam, g, y, t, yt)
+    assert loss == pytest.approx(oracle.held_out_loss(gamma, lam, g, y, t, yt), rel=1e-12)
+    h = 1e-3
+    f = lambda lg, ll: oracle.held_out_loss(math.exp(lg), math.exp(ll), g, y, t, yt)
+    lg0, ll0 = math.log(gamma), math.log(lam)
+    fd_g = (f(lg0 + h, ll0) - f(lg0 - h, ll0)) / (2 * h)
+    fd_l = (f(lg0, ll0 + h) - f(lg0, ll0 - h)) / (2 * h)
+    assert dlg == pytest.approx(fd_g, rel=1e-5, abs=1e-12)
+    assert dll == pytest.approx(fd_l, rel=1e-5, abs=1e-12)
+
+
+def test_gradient_identity_kernel_closed_form():
+    # K = I, K_t selects training rows: Yhat = Y_sel / (1 + lambda)
+    g = _rand_geno(30, 40, 15)
+    sel = np.array([2, 7, 19, 21])
+    t = g[sel]
+    rng = np.random.default_rng(15)
+    y = rng.standard_normal((30, 2))
+    yt = rng.standard_normal((4, 2))
+    lam = 0.3
+    loss, dlg, dll = oracle.hyper_gradient(1000.0, lam, g, y, t, yt)
+    r = y[sel] / (1 + lam) - yt
+    assert loss == pytest.approx((r * r).sum() / r.size, rel=1e-14)
+    dl_dlam = (2 * r * (-y[sel] / (1 + lam) ** 2)).sum() / r.size
+    assert dll == pytest.approx(lam * dl_dlam, rel=1e-12)
+    assert dlg == 0.0
+
+
+# ---------------------------------------------------------------- inputs recipe
+
+def test_input_generator_recipe():
+    prob = inputs.problem(200, 300, 3, 50, seed=1)
+    g = prob["G"]
+    assert g.dtype == torch.int8 and g.shape == (200, 300)
+    assert set(torch.unique(g).tolist()) <= {0, 1, 2}
+    p = inputs.allele_freqs(300, 1)
+    assert float(p.min()) >= 0.05 and float(p.max()) <= 0.5
+    assert prob["Y"].shape == (200, 3) and prob["Yt"].shape == (50, 3)
+    assert prob["T"].shape == (50, 300)
+    # deterministic for a fixed seed
+    again = inputs.problem(200, 300, 3, 50, seed=1)
+    assert torch.equal(again["G"], g) and torch.equal(again["Y"], prob["Y"])
+    # mean genotype matches 2 p_j on a larger draw
+    big = inputs.genotypes(4000, 64, seed=2).double()
+    assert torch.allclose(big.mean(0), 2 * inputs.allele_freqs(64, 2), atol=0.08)
