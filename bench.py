@@ -1,0 +1,402 @@
+"""Benchmark of the KRR hot path on GB300: Build -> Factor -> Solve (+ refinement)
+-> Predict on synthetic genotypes, one JSON line on stdout.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c3|c2|c1]
+                    [--impl ours|reference] [--no-compare] [--no-e2e] [--no-cpu]
+
+A step is one pass of the whole path on resident inputs; value = algorithmic
+TOp/s of build + factor + solve (N(N+1)M + N^3/3 + 2N^2P) over the step time
+(predict is inside the step but not counted).  Under torchrun (N > 1) every
+rank runs an independent replica (the path has no data-path collective);
+value = all ranks' operations / the slowest rank's time.
+
+--impl reference times the CPU oracle (the method's plain FP64 definition) on
+this machine's host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KRR build+factor+solve TOp/s and s at N=131072: mixed vs FP32, rel err<=1e-4"
+CONFIGS = {
+    # name: (N, M, P, N_test, tile)
+    "c1": (2048, 512, 1, 512, 256),
+    "c2": (32768, 8192, 10, 4096, 1024),
+    "c3": (131072, 16384, 20, 4096, 1024),
+}
+LAMBDA = 0.1
+SEED = 2409017120
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "update_kernel_traffic.json")
+TC_SRC = os.path.join(ROOT, "paper_2409_01712_gb300", "csrc", "tc_gemm.cu")
+
+
+def metric_ops(n, m, p):
+    return n * (n + 1) * m + n ** 3 / 3.0 + 2.0 * n * n * p
+
+
+def workload_name(cfg):
+    n, m, p, nt, b = CONFIGS[cfg]
+    return (f"{cfg}: N={n} M={m} P={p} N_test={nt} tile={b} gamma=1/M lambda={LAMBDA}, "
+            f"genotypes Binomial(2,p_j) p_j~U(0.05,0.5), phenotypes 20 SNP-pair products + N(0,0.5)")
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def update_traffic():
+    """DRAM bytes per update launch from the committed ncu summary, if it was
+    taken on the current tensor-core source (else None)."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+        with open(TC_SRC, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        if rec.get("tc_gemm_sha256") != sha:
+            return None
+        return rec.get("bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample(cfg, n_sample, g_host=None, y_host=None):
+    """Times the oracle's build + factor + solve on the first n_sample rows."""
+    import oracle
+    from paper_2409_01712_gb300 import inputs
+
+    n, m, p, _, _ = CONFIGS[cfg]
+    if g_host is None:
+        prob = inputs.problem(n_sample, m, p, 1, seed=SEED)
+        g_host, y_host = prob["G"].numpy(), prob["Y"].numpy()
+    g = np.ascontiguousarray(g_host[:n_sample])
+    y = np.ascontiguousarray(y_host[:n_sample]).astype(np.float64)
+    t0 = time.perf_counter()
+    k = oracle.build_kernel(1.0 / m, g)
+    oracle.associate(LAMBDA, k, y)
+    dt = time.perf_counter() - t0
+    ops = metric_ops(n_sample, m, p)
+    return {"value": ops / dt / 1e12, "unit": "TOp/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {n_sample} rows of the {cfg} workload (M={m}, P={p}): brute-force "
+                      f"distances, FP64 Cholesky, substitution; {dt:.2f} s",
+            "seconds": dt}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cfg = args.config
+    n_sample = args.cpu_rows
+    times = []
+    res = None
+    for i in range(args.warmup + args.steps):
+        res = cpu_sample(cfg, n_sample)
+        if i >= args.warmup:
+            times.append(res["seconds"])
+    n, m, p, _, _ = CONFIGS[cfg]
+    ops = metric_ops(n_sample, m, p)
+    t = float(np.mean(times))
+    value = ops / t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TOp/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "sample_rows": n_sample},
+            "cpu_baseline": {"value": value, "unit": "TOp/s", "cores": res["cores"], "kind": "oracle",
+                             "sample": res["sample"]},
+            "e2e": {"value": value, "unit": "TOp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2409_01712_gb300 import KRR, inputs
+
+    world, rank, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    cfg = args.config
+    n, m, p, n_test, tile = CONFIGS[cfg]
+    gamma = 1.0 / m
+
+    prob = inputs.problem(n, m, p, n_test, seed=SEED + rank, device=dev)
+    g, y, t = prob["G"], prob["Y"], prob["T"]
+    torch.cuda.synchronize()
+    a_out = torch.empty((n, p), dtype=torch.float32, device=dev)
+    yt_out = torch.empty((n_test, p), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    model = KRR(tile=tile, mode=args.mode, stream=stream.cuda_stream)
+
+    def step():
+        model.build_kernel(g, gamma)
+        fi = model.factor(LAMBDA)
+        _, si = model.solve(y, out=a_out)
+        model.predict(t, a_out, out=yt_out)
+        return fi, si
+
+    for _ in range(args.warmup):
+        fi, si = step()
+    torch.cuda.synchronize()
+    model.set_profiling(True)
+    model.profile(reset=True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        infos.append(step())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = model.profile(reset=True)
+    model.set_profiling(False)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ops = metric_ops(n, m, p)
+    value = world * ops / (ms / 1e3) / 1e12
+    fi, si = infos[-1]
+
+    pk, pk_kind = peaks()
+    upd = prof["update"]
+    roof = None
+    if upd["count"] > 0 and upd["ms"] > 0:
+        ach = upd["flops"] / (upd["ms"] / 1e3) / 1e12
+        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
+        traffic = update_traffic() if args.mode == "mixed" else None
+        roof = {"bound": "tensor", "kernel": "tc_kernel<F16, OP_UPDATE> (trailing update)",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_source": f"{pk_kind}: bf16 dense sustained (FP16 dense runs at the same rate)",
+                "traffic": traffic, "launches": upd["count"],
+                "avg_launch_ms": upd["ms"] / upd["count"]}
+    phases = {k: {"ms_per_step": v["ms"] / args.steps, "count_per_step": v["count"] / args.steps}
+              for k, v in prof.items() if isinstance(v, dict) and v["count"] > 0}
+    for k, v in prof.items():
+        if isinstance(v, dict) and v["count"] > 0 and v["ms"] > 0:
+            if v["flops"] > 0:
+                phases[k]["tflops"] = v["flops"] / (v["ms"] / 1e3) / 1e12
+            if v["bytes"] > 0:
+                phases[k]["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "TOp/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "e4m3+f16 tensor, f32/f64 refine" if args.mode == "mixed" else "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(cfg), "mode": args.mode,
+                       "l2": "inputs larger than L2 (K tiles alone are "
+                             f"{(n // tile) * (n // tile + 1) // 2 * tile * tile * 4 / 1e9:.1f} GB)",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": int(prof["launches"]),
+            "clocks": clk,
+            "phases": phases,
+            "factor": {k: fi[k] for k in ("tiles_fp32", "tiles_fp16", "tiles_e4m3", "factor_bytes",
+                                          "min_pivot")},
+            "solve": {"iterations": si["iterations"], "rel_residual": si["rel_residual"],
+                      "converged": si["converged"]}}
+    if roof:
+        line["roofline"] = roof
+
+    # ---- e2e: the same step through host buffers (pinned), copies inside the timing
+    if not args.no_e2e:
+        gh = g.cpu().pin_memory()
+        yh = y.cpu().pin_memory()
+        th = t.cpu().pin_memory()
+        ah = torch.empty((n, p), dtype=torch.float32).pin_memory()
+        yth = torch.empty((n_test, p), dtype=torch.float32).pin_memory()
+
+        def step_host():
+            model.build_kernel(gh, gamma)
+            model.factor(LAMBDA)
+            model.solve(yh, out=ah)
+            model.predict(th, ah, out=yth)
+
+        step_host()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        w0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_host()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - w0) / args.steps
+        ems = max(e0.elapsed_time(e1) / args.steps, wall * 1e3)
+        if dist:
+            tt = torch.tensor([ems], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        h2d = n * m + n * p * 4 + n_test * m + n * p * 4
+        d2h = n * p * 4 + n_test * p * 4
+        line["e2e"] = {"value": world * ops / (ems / 1e3) / 1e12, "unit": "TOp/s", "ms_per_step": ems,
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- sampled accuracy check against the oracle (outside the timing)
+    if not args.no_cpu and rank == 0:
+        import oracle
+
+        a_host = a_out.double().cpu().numpy()
+        rows = np.random.default_rng(7).choice(n, size=args.check_rows, replace=False)
+        gh_np = g.cpu().numpy()
+        krows = oracle.kernel_rows(gamma, gh_np, rows, gh_np)
+        yh_np = y.double().cpu().numpy()
+        r = yh_np[rows] - (krows @ a_host + LAMBDA * a_host[rows])
+        line["accuracy"] = {"sampled_rows": int(args.check_rows),
+                            "rel_residual_fp64_oracle_rows": float(np.linalg.norm(r) / np.linalg.norm(yh_np[rows])),
+                            "rel_residual_device": si["rel_residual"]}
+
+    # ---- plain FP32 comparator: the same engine with every step in FP32 on CUDA cores
+    if not args.no_compare and args.mode == "mixed":
+        model.close()
+        del model
+        torch.cuda.empty_cache()
+        cmp_model = KRR(tile=tile, mode="fp32", stream=stream.cuda_stream)
+
+        def step32():
+            cmp_model.build_kernel(g, gamma)
+            cmp_model.factor(LAMBDA)
+            cmp_model.solve(y, out=a_out)
+            cmp_model.predict(t, a_out, out=yt_out)
+
+        torch.cuda.synchronize()
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        step32()
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1)
+        line["fp32_comparator"] = {"ms_per_step": cms, "value": ops / (cms / 1e3) / 1e12, "unit": "TOp/s",
+                                   "steps": 1, "speedup_mixed_over_fp32": cms / ms}
+        cmp_model.close()
+
+    # ---- CPU baseline: the oracle on this host's cores, bounded sample
+    if not args.no_cpu and rank == 0:
+        res = cpu_sample(cfg, args.cpu_rows, g.cpu().numpy(), y.cpu().numpy())
+        res.pop("seconds")
+        line["cpu_baseline"] = res
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--config", default="c3", choices=sorted(CONFIGS))
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "fp32"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparator step")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline and sampled check")
+    ap.add_argument("--cpu-rows", type=int, default=2048, help="rows of the oracle sample")
+    ap.add_argument("--check-rows", type=int, default=32, help="rows of the sampled oracle residual")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

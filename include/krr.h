@@ -1,0 +1,241 @@
+/*
+ * krr.h -- C ABI of the GB300 kernel ridge regression library (libkrr.so).
+ *
+ * The library runs the three phases of the paper's KRR driver (Alg. 1) on one
+ * GPU:  Build (Alg. 2 with the Gaussian kernel of Alg. 5), Associate (Alg. 3:
+ * factorise K + lambda I, solve for the weights) and Predict (Alg. 4).
+ *
+ * Conventions for every call:
+ *  - Every call returns a krr_status; nothing throws across this boundary.
+ *    On failure krr_last_error() returns a message for the context.
+ *  - Matrices are row-major with an explicit leading dimension (elements).
+ *    Sizes and leading dimensions are int64_t.
+ *  - Pointer arguments may point to device memory or to host memory (pageable
+ *    or pinned); the library tells them apart with cudaPointerGetAttributes
+ *    and stages host buffers through its own device buffers.  Caller buffers
+ *    are only borrowed for the duration of the call.
+ *  - The context owns every internal buffer (packed genotypes, norms, kernel
+ *    tiles, factor tiles, precision map) and frees them in krr_destroy().
+ *  - Work is issued on the stream given to krr_create().  A call that returns
+ *    host-visible results (info structs, host output buffers) synchronises
+ *    that stream before it returns.
+ *  - A context is not thread safe; use one context per host thread.
+ *
+ * Notation: N training patients, M SNPs, P phenotypes, N_t held-out patients,
+ * b tile edge, NT = ceil(N / b) tiles per side.
+ */
+#ifndef KRR_H
+#define KRR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum krr_status {
+    KRR_OK = 0,
+    KRR_EINVAL = 1,   /* bad argument: shape, leading dimension, gamma <= 0, NaN lambda */
+    KRR_ENOMEM = 2,   /* a device or pinned-host allocation failed */
+    KRR_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    KRR_ENOTPD = 4,   /* a pivot of the Cholesky factorisation was not positive */
+    KRR_ENOCONV = 5,  /* iterative refinement did not reach the requested residual */
+    KRR_ETIMEOUT = 6, /* a bounded device-side wait ran out */
+    KRR_ESTATE = 7    /* calls out of order (e.g. solve before factor) */
+} krr_status;
+
+typedef enum krr_mode {
+    /* Tensor-core path: exact distances on FP8 (E4M3) operands with FP32
+     * accumulation, adaptive per-tile precision of the factor (FP32 / FP16 /
+     * E4M3), FP16 tensor-core trailing updates, refinement to FP32 accuracy. */
+    KRR_MODE_MIXED = 0,
+    /* Plain FP32 on CUDA cores for every step: the comparison path. */
+    KRR_MODE_FP32 = 1
+} krr_mode;
+
+/* Tile precisions reported by krr_get_precision_map(). */
+enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_FP16 = 2, KRR_PREC_E4M3 = 3 };
+
+typedef struct krr_options {
+    int64_t tile;            /* b: tile edge, a multiple of 256 (default 1024) */
+    int32_t mode;            /* krr_mode (default KRR_MODE_MIXED) */
+    int32_t allow_fp8;       /* 1: E4M3 allowed for factor tiles (default 1) */
+    double eps;              /* adaptive-precision threshold (default 1e-4) */
+    double ir_tol;           /* refinement stops at ||R||_F / ||Y||_F <= ir_tol (default 1e-7) */
+    int32_t ir_max;          /* maximum refinement iterations (default 30; 0 = none) */
+    int32_t diag_fp64;       /* 1: diagonal-tile Cholesky in FP64, 0: FP32 (default 0) */
+    int64_t wait_budget_ns;  /* limit of every bounded device wait (default 2e9) */
+} krr_options;
+
+/* Per-call reports; valid when the call returns. */
+typedef struct krr_factor_info {
+    int64_t nt;              /* tiles per side */
+    int64_t tiles_fp32;      /* off-diagonal factor tiles stored FP32 */
+    int64_t tiles_fp16;      /* ... stored FP16 */
+    int64_t tiles_e4m3;      /* ... stored E4M3 */
+    int64_t factor_bytes;    /* bytes of the stored off-diagonal factor tiles */
+    int64_t bad_tile;        /* KRR_ENOTPD: diagonal tile of the first bad pivot, else -1 */
+    int64_t bad_column;      /* KRR_ENOTPD: global column of the first bad pivot, else -1 */
+    double min_pivot;        /* smallest diagonal entry of L */
+} krr_factor_info;
+
+typedef struct krr_solve_info {
+    int32_t iterations;      /* refinement iterations taken */
+    int32_t converged;       /* 1: ||R||_F / ||Y||_F <= ir_tol; 2: refinement stopped at the
+                                attainable floor (two successive steps that did not halve the
+                                residual); 0: no refinement or not converged */
+    double rel_residual;     /* final ||Y - (K + lambda I) A||_F / ||Y||_F */
+    double history[32];      /* relative residual after the first solve and each iteration */
+} krr_solve_info;
+
+typedef struct krr_ctx krr_ctx;
+
+/* Fills *opt with the defaults listed above. */
+void krr_default_options(krr_options *opt);
+
+/*
+ * Creates a context bound to the current CUDA device and to `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  opt may be NULL for
+ * the defaults.  Returns KRR_EINVAL for a tile edge that is not a positive
+ * multiple of 256 or an unknown mode.
+ */
+krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream);
+
+/*
+ * Phase 1, Build (Alg. 2 with the Gaussian kernel of Alg. 5, distance form of
+ * Sec. IV-B): K_ij = exp(-gamma * ||g_i - g_j||^2) over the lower-triangle
+ * tiles of K (i >= j tile-wise; diagonal tiles in full).
+ *   G     : n x m int8 genotypes, row-major with leading dimension ldg >= m,
+ *           values in {0, 1, 2} (other values give undefined results), host
+ *           or device.  Copied and packed; the caller may free it afterwards.
+ *   gamma : kernel bandwidth, > 0 and finite.
+ * Squared distances are exact integers (m <= 2^22).  Rows past n up to the
+ * tile multiple are padding with K = identity.
+ * Errors: KRR_EINVAL (n < 1, m < 1, m > 2^22, ldg < m, bad gamma), KRR_ENOMEM,
+ * KRR_ECUDA.  Invalidates any earlier factor.
+ */
+krr_status krr_build_kernel(krr_ctx *ctx, const int8_t *G, int64_t n, int64_t m, int64_t ldg,
+                            double gamma);
+
+/*
+ * Phase 2a (Alg. 3, Factorize): tile Cholesky L L^T = K + lambda I.
+ * Diagonal tiles are factorised in FP32 or FP64 (options.diag_fp64); each
+ * off-diagonal factor tile is stored in the lowest precision the adaptive
+ * rule allows (mixed mode) or in FP32 (fp32 mode).  K itself is kept for the
+ * refinement residual.
+ *   lambda : regularisation, finite (lambda >= 0).
+ *   info   : optional report (may be NULL).
+ * Errors: KRR_ESTATE (no kernel built), KRR_EINVAL, KRR_ENOTPD (info gives
+ * the tile and column), KRR_ECUDA.
+ */
+krr_status krr_factor(krr_ctx *ctx, double lambda, krr_factor_info *info);
+
+/*
+ * Phase 2b (Alg. 3, Solve): A = (K + lambda I)^-1 Y for p right-hand sides by
+ * forward and backward substitution with the factor, followed by iterative
+ * refinement (residual accumulated in FP64 against the FP32 kernel) in mixed
+ * mode.  The factor is reused across calls, so many phenotype sets can be
+ * solved against one factorisation.
+ *   Y : n x p FP32, leading dimension ldy >= p, host or device (read only).
+ *   A : n x p FP32 output, leading dimension lda >= p, host or device.
+ * Refinement stops when ||R||_F / ||Y||_F <= ir_tol or when two successive
+ * steps fail to halve it (the floor set by FP32 storage of K and A).
+ * Errors: KRR_ESTATE (no factor), KRR_EINVAL, KRR_ENOCONV (the residual grew
+ * above that of the first solve, or ir_max iterations passed; A holds the last
+ * iterate), KRR_ECUDA.
+ */
+krr_status krr_solve(krr_ctx *ctx, const float *Y, int64_t p, int64_t ldy, float *A, int64_t lda,
+                     krr_solve_info *info);
+
+/*
+ * Phase 3 (Alg. 4, Predict): Yt = K_test A with K_test = Build(gamma, T, G),
+ * the n_test x n test-by-training kernel, never stored: each distance tile is
+ * exponentiated and multiplied by the matching rows of A in one pass, and
+ * the per-tile partial products are summed in a fixed order.
+ *   T  : n_test x m int8 genotypes, leading dimension ldt >= m, host or device.
+ *   A  : n x p FP32 weights (from krr_solve), leading dimension lda >= p.
+ *   Yt : n_test x p FP32 output, leading dimension ldyt >= p.
+ * Errors: KRR_ESTATE (no kernel built), KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA.
+ */
+krr_status krr_predict(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt, const float *A,
+                       int64_t lda, int64_t p, float *Yt, int64_t ldyt);
+
+/*
+ * Copies the per-tile precision map of the current factor (the "mosaic" of
+ * the paper's adaptive-precision Cholesky) to host memory: map[i * nt + j]
+ * for tile row i >= tile column j holds a KRR_PREC_* value (diagonal tiles
+ * report their factorisation precision); entries above the diagonal are 255.
+ * map may be NULL to query nt only.  Errors: KRR_ESTATE (no factor),
+ * KRR_EINVAL (map_capacity < nt * nt).
+ */
+krr_status krr_get_precision_map(krr_ctx *ctx, uint8_t *map, int64_t map_capacity, int64_t *nt);
+
+/*
+ * Copies the squared distances of the lower-triangle tiles to a caller
+ * buffer for testing: D is n x n uint32 row-major (leading dimension ldd),
+ * entries (i, j) with j > i tile-wise are left untouched.  Needs a context
+ * created with keep_distances set through krr_set_keep_distances() before
+ * krr_build_kernel().  Host or device buffer.
+ */
+krr_status krr_set_keep_distances(krr_ctx *ctx, int32_t keep);
+krr_status krr_get_distances(krr_ctx *ctx, uint32_t *D, int64_t ldd);
+
+/*
+ * Copies the FP32 kernel matrix K (without lambda) for tile row i >= tile
+ * column j to a caller buffer: K is n x n FP32 row-major (leading dimension
+ * ldk); the strictly-upper tiles are left untouched.  Host or device buffer.
+ */
+krr_status krr_get_kernel(krr_ctx *ctx, float *K, int64_t ldk);
+
+/* Kernel classes timed by the optional profiler. */
+enum {
+    KRR_PROF_PACK = 0,     /* genotype packing and norms */
+    KRR_PROF_BUILD = 1,    /* distance GEMM + exp epilogue (Build) */
+    KRR_PROF_DIAG = 2,     /* diagonal-tile Cholesky + inverse */
+    KRR_PROF_TRSM = 3,     /* panel solve of a tile column */
+    KRR_PROF_CAST = 4,     /* adaptive-precision cast of a column */
+    KRR_PROF_UPDATE = 5,   /* trailing update */
+    KRR_PROF_SOLVE = 6,    /* forward + backward substitution */
+    KRR_PROF_RESIDUAL = 7, /* refinement residual */
+    KRR_PROF_PREDICT = 8,  /* predict (distance GEMM + exp + weights) */
+    KRR_PROF_CLASSES = 9
+};
+
+/*
+ * Measurement report: CUDA events recorded on the context's stream around
+ * every region of a class while profiling is on.  flops / bytes are the
+ * algorithmic operation counts and compulsory HBM bytes of the timed
+ * regions (definitions in the design doc of the repository), not counter values.
+ * launches counts the kernels this library launched (all contexts) since the
+ * last reset.
+ */
+typedef struct krr_profile {
+    int64_t launches;
+    int64_t count[KRR_PROF_CLASSES];
+    double ms[KRR_PROF_CLASSES];
+    double flops[KRR_PROF_CLASSES];
+    double bytes[KRR_PROF_CLASSES];
+} krr_profile;
+
+/* Turns event timing of the kernel classes on (1) or off (0). */
+krr_status krr_set_profiling(krr_ctx *ctx, int32_t on);
+
+/* Synchronises the stream and sums the timed regions into *out; reset = 1
+ * clears the records and the launch counter afterwards. */
+krr_status krr_get_profile(krr_ctx *ctx, krr_profile *out, int32_t reset);
+
+/* Waits for all work issued by the context. */
+krr_status krr_sync(krr_ctx *ctx);
+
+/* Message of the last failed call on ctx (or of the last failed krr_create
+ * when ctx is NULL).  Owned by the library. */
+const char *krr_last_error(const krr_ctx *ctx);
+
+/* Frees every buffer of the context.  ctx may be NULL. */
+void krr_destroy(krr_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRR_H */

@@ -1,0 +1,821 @@
+// C ABI of the KRR engine (include/krr.h) and the host-side orchestration of
+// the three phases of the paper's driver (Alg. 1): Build (Alg. 2), Associate
+// (Alg. 3: tile Cholesky + solves + refinement) and Predict (Alg. 4).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "krr_internal.h"
+
+using namespace krr;
+
+struct krr_ctx : public Ctx {};
+
+static thread_local std::string g_create_error;
+
+namespace krr {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace krr
+
+namespace {
+
+// Event-timed regions per kernel class (krr_get_profile).
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+    double flops, bytes;
+};
+struct ProfState {
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
+// Opens a timed region of class cls; returns its index or -1 when off.
+int prof_begin(Ctx *c, int cls) {
+    if (!c->prof_on || !c->prof) return -1;
+    ProfState *ps = (ProfState *)c->prof;
+    ProfRec r;
+    r.cls = cls;
+    r.a = ps->take();
+    r.b = ps->take();
+    r.flops = r.bytes = 0.0;
+    cudaEventRecord(r.a, c->stream);
+    ps->recs.push_back(r);
+    return (int)ps->recs.size() - 1;
+}
+
+void prof_end(Ctx *c, int idx, double flops, double bytes) {
+    if (idx < 0 || !c->prof) return;
+    ProfState *ps = (ProfState *)c->prof;
+    ProfRec &r = ps->recs[idx];
+    r.flops = flops;
+    r.bytes = bytes;
+    cudaEventRecord(r.b, c->stream);
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+krr_status dev_alloc(Ctx *c, T **p, size_t count, const char *what) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) return KRR_OK;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        c->last_error = std::string("cudaMalloc failed for ") + what + " (" +
+                        std::to_string(count * sizeof(T)) + " bytes): " + cudaGetErrorString(e);
+        return KRR_ENOMEM;
+    }
+    return KRR_OK;
+}
+
+template <typename T>
+void dev_free(T **p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+krr_status stage(Ctx *c, size_t bytes) {
+    if (bytes <= c->stage_cap) return KRR_OK;
+    void *p = nullptr;
+    if (c->stage) cudaFree(c->stage);
+    c->stage = nullptr;
+    c->stage_cap = 0;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->last_error = "cudaMalloc failed for the host-argument staging buffer";
+        return KRR_ENOMEM;
+    }
+    c->stage = p;
+    c->stage_cap = bytes;
+    return KRR_OK;
+}
+
+krr_status check_launch(Ctx *c, const char *where) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
+}
+
+// Copies an n x cols row-major caller matrix (host or device, leading
+// dimension ld) into a dense device matrix with rows_pad rows (zero padded).
+krr_status load_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, int64_t ld,
+                         int64_t rows_pad, float *dst) {
+    const float *dsrc = src;
+    if (!is_device_ptr(src)) {
+        KRR_TRY(stage(c, (size_t)n * ld * sizeof(float)));
+        KRR_CUDA_TRY(c, cudaMemcpyAsync(c->stage, src, (size_t)n * ld * sizeof(float),
+                                        cudaMemcpyHostToDevice, c->stream));
+        dsrc = (const float *)c->stage;
+    }
+    launch_copy_rows(dsrc, ld, dst, cols, n, cols, rows_pad, c->stream);
+    return check_launch(c, "copy rows");
+}
+
+// Copies the first n rows of a dense device matrix to a caller matrix.
+krr_status store_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, float *dst,
+                          int64_t ld) {
+    if (is_device_ptr(dst)) {
+        launch_copy_rows(src, cols, dst, ld, n, cols, n, c->stream);
+        return check_launch(c, "copy rows");
+    }
+    KRR_CUDA_TRY(c, cudaMemcpy2DAsync(dst, ld * sizeof(float), src, cols * sizeof(float),
+                                      cols * sizeof(float), n, cudaMemcpyDeviceToHost, c->stream));
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
+// Packs n x m int8 genotypes (host or device) into the context's padded
+// operand layout.
+krr_status pack(Ctx *c, const int8_t *g, int64_t n, int64_t m, int64_t ldg, int64_t rows_pad,
+                uint8_t *out8, float *outf, int32_t *norms) {
+    const int8_t *dg = g;
+    if (!is_device_ptr(g)) {
+        KRR_TRY(stage(c, (size_t)n * m));
+        KRR_CUDA_TRY(c, cudaMemcpy2DAsync(c->stage, m, g, ldg, m, n, cudaMemcpyHostToDevice,
+                                          c->stream));
+        dg = (const int8_t *)c->stage;
+        ldg = m;
+    }
+    launch_pack_genotypes(dg, n, m, ldg, rows_pad, c->m_pad, out8, outf, norms, c->stream);
+    return check_launch(c, "pack genotypes");
+}
+
+void free_factor(Ctx *c) {
+    tc_invalidate_factor_maps(c);
+    dev_free(&c->W);
+    dev_free(&c->Wd);
+    dev_free(&c->Linv);
+    dev_free(&c->Linv_hi);
+    dev_free(&c->Linv_lo);
+    dev_free(&c->diag64);
+    dev_free(&c->diag64_inv);
+    dev_free(&c->pool);
+    dev_free(&c->ltab);
+    dev_free(&c->colbuf);
+    dev_free(&c->pan_hi);
+    dev_free(&c->pan_lo);
+    dev_free(&c->pan_f8);
+    dev_free(&c->colnorm2);
+    dev_free(&c->colmax);
+    dev_free(&c->precmap);
+    c->pool_bytes = 0;
+    c->w_bytes = 0;
+    c->factored = false;
+}
+
+void free_build(Ctx *c) {
+    dev_free(&c->g8);
+    dev_free(&c->gf);
+    dev_free(&c->norms);
+    dev_free(&c->Kd);
+    dev_free(&c->Dd);
+    dev_free(&c->knorm2);
+    c->g_bytes = c->kd_bytes = c->dd_bytes = 0;
+    c->built = false;
+}
+
+bool mixed(const Ctx *c) { return c->opt.mode == KRR_MODE_MIXED; }
+
+}  // namespace
+
+extern "C" {
+
+void krr_default_options(krr_options *opt) {
+    if (!opt) return;
+    opt->tile = 1024;
+    opt->mode = KRR_MODE_MIXED;
+    opt->allow_fp8 = 1;
+    opt->eps = 1e-4;
+    opt->ir_tol = 1e-7;
+    opt->ir_max = 30;
+    opt->diag_fp64 = 0;
+    opt->wait_budget_ns = 2000000000LL;
+}
+
+krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return KRR_EINVAL;
+    }
+    *out = nullptr;
+    krr_options o;
+    krr_default_options(&o);
+    if (opt) o = *opt;
+    if (o.tile < 256 || o.tile % 256 != 0 || o.tile > 4096) {
+        g_create_error = "tile must be a multiple of 256 in [256, 4096]";
+        return KRR_EINVAL;
+    }
+    if (o.mode != KRR_MODE_MIXED && o.mode != KRR_MODE_FP32) {
+        g_create_error = "unknown mode";
+        return KRR_EINVAL;
+    }
+    if (!(o.eps > 0.0) || !(o.ir_tol > 0.0) || o.ir_max < 0 || o.ir_max > 1000) {
+        g_create_error = "eps and ir_tol must be positive, ir_max in [0, 1000]";
+        return KRR_EINVAL;
+    }
+    krr_ctx *c = new (std::nothrow) krr_ctx();
+    if (!c) {
+        g_create_error = "out of host memory";
+        return KRR_ENOMEM;
+    }
+    c->opt = o;
+    c->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "no usable CUDA device";
+        delete c;
+        return KRR_ECUDA;
+    }
+    if (cudaMalloc((void **)&c->derr, sizeof(DevErrors)) != cudaSuccess ||
+        cudaMallocHost((void **)&c->herr, sizeof(DevErrors)) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "allocation of the error record failed";
+        krr_destroy(c);
+        return KRR_ENOMEM;
+    }
+    if (mixed(c)) {
+        krr_status s = tc_init(c);
+        if (s != KRR_OK) {
+            g_create_error = c->last_error;
+            krr_destroy(c);
+            return s;
+        }
+    }
+    *out = c;
+    return KRR_OK;
+}
+
+void krr_destroy(krr_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_factor(c);
+    free_build(c);
+    dev_free(&c->derr);
+    if (c->herr) cudaFreeHost(c->herr);
+    if (c->hred) cudaFreeHost(c->hred);
+    dev_free(&c->red);
+    dev_free(&c->ybuf);
+    dev_free(&c->zbuf);
+    dev_free(&c->rbuf);
+    dev_free(&c->abuf);
+    dev_free(&c->dabuf);
+    dev_free(&c->pred_part);
+    dev_free(&c->pred_out);
+    dev_free(&c->t8);
+    dev_free(&c->tnorms);
+    if (c->stage) cudaFree(c->stage);
+    tc_free(c);
+    if (c->prof) {
+        ProfState *ps = (ProfState *)c->prof;
+        for (const ProfRec &r : ps->recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (cudaEvent_t e : ps->pool) cudaEventDestroy(e);
+        delete ps;
+    }
+    delete c;
+}
+
+const char *krr_last_error(const krr_ctx *c) {
+    if (!c) return g_create_error.c_str();
+    return c->last_error.c_str();
+}
+
+krr_status krr_sync(krr_ctx *c) {
+    if (!c) return KRR_EINVAL;
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
+krr_status krr_set_keep_distances(krr_ctx *c, int32_t keep) {
+    if (!c) return KRR_EINVAL;
+    c->keep_distances = keep ? 1 : 0;
+    return KRR_OK;
+}
+
+krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, int64_t ldg,
+                            double gamma) {
+    if (!c) return KRR_EINVAL;
+    if (!G || n < 1 || m < 1 || m > (int64_t(1) << 22) || ldg < m || !(gamma > 0.0) ||
+        !isfinite(gamma)) {
+        c->last_error = "krr_build_kernel: need G != NULL, n >= 1, 1 <= m <= 2^22, ldg >= m, "
+                        "0 < gamma < inf";
+        return KRR_EINVAL;
+    }
+    free_factor(c);
+    c->built = false;
+    const int64_t b = c->opt.tile;
+    const int64_t nt = (n + b - 1) / b;
+    const int64_t n_pad = nt * b;
+    const int64_t m_pad = (m + 127) / 128 * 128;
+    const size_t g_bytes = (size_t)n_pad * m_pad * (mixed(c) ? 1 : 4);
+    const int64_t ntri = nt * (nt + 1) / 2;
+    const size_t kd_bytes = (size_t)ntri * b * b * sizeof(float);
+    if (c->g_bytes != g_bytes || c->kd_bytes != kd_bytes || c->b != b || c->nt != nt) {
+        free_build(c);
+        if (mixed(c)) KRR_TRY(dev_alloc(c, &c->g8, g_bytes, "packed genotypes"));
+        else KRR_TRY(dev_alloc(c, &c->gf, g_bytes / 4, "FP32 genotypes"));
+        KRR_TRY(dev_alloc(c, &c->norms, (size_t)n_pad, "row norms"));
+        KRR_TRY(dev_alloc(c, &c->Kd, (size_t)ntri * b * b, "kernel tiles"));
+        // per-tile partial sums of K^2: one per 128 x 256 (tensor-core) or
+        // 128 x 128 (CUDA-core) block
+        const size_t per_tile = mixed(c) ? (size_t)(b / 128) * (b / 256) : (size_t)(b / 128) * (b / 128);
+        KRR_TRY(dev_alloc(c, &c->knorm2, (size_t)ntri * per_tile, "tile norms"));
+        c->g_bytes = g_bytes;
+        c->kd_bytes = kd_bytes;
+    }
+    const size_t dd_bytes = c->keep_distances ? (size_t)ntri * b * b * sizeof(uint32_t) : 0;
+    if (dd_bytes != c->dd_bytes) {
+        KRR_TRY(dev_alloc(c, &c->Dd, dd_bytes / sizeof(uint32_t), "distance tiles"));
+        c->dd_bytes = dd_bytes;
+    }
+    c->n = n;
+    c->m = m;
+    c->m_pad = m_pad;
+    c->b = b;
+    c->nt = nt;
+    c->n_pad = n_pad;
+    c->gamma = gamma;
+    const size_t red_count = 64 + (size_t)nt * (b / 64) + 16;
+    KRR_TRY(dev_alloc(c, &c->red, red_count, "reduction buffer"));
+    if (c->hred) cudaFreeHost(c->hred);
+    c->hred = nullptr;
+    if (cudaMallocHost((void **)&c->hred, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->last_error = "pinned allocation failed";
+        return KRR_ENOMEM;
+    }
+    int pr = prof_begin(c, KRR_PROF_PACK);
+    KRR_TRY(pack(c, G, n, m, ldg, n_pad, c->g8, c->gf, c->norms));
+    prof_end(c, pr, 0.0, (double)n * m + (double)g_bytes);
+    pr = prof_begin(c, KRR_PROF_BUILD);
+    if (mixed(c)) {
+        KRR_TRY(tc_build(c));
+    } else {
+        launch_build_simt(c);
+    }
+    // algorithmic work: 2 M multiply-adds per entry of the lower-triangle
+    // tiles; compulsory bytes: the K tiles written once (FP32)
+    prof_end(c, pr, 2.0 * (double)ntri * b * b * (double)m, (double)kd_bytes);
+    KRR_TRY(check_launch(c, "build"));
+    launch_kernel_sumsq(c, c->red + 2);  // red[2] = ||K||_F^2
+    KRR_TRY(check_launch(c, "kernel norm"));
+    c->built = true;
+    return KRR_OK;
+}
+
+krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
+    if (!c) return KRR_EINVAL;
+    if (!c->built) {
+        c->last_error = "krr_factor: no kernel built";
+        return KRR_ESTATE;
+    }
+    if (!isfinite(lambda)) {
+        c->last_error = "krr_factor: lambda must be finite";
+        return KRR_EINVAL;
+    }
+    c->factored = false;
+    c->lambda = lambda;
+    const int64_t b = c->b, nt = c->nt, bb = b * b;
+    const int64_t noff = nt * (nt - 1) / 2;
+    const bool mx = mixed(c);
+    cudaStream_t s = c->stream;
+    // buffers (kept across factorisations of the same shape)
+    const size_t w_bytes = (size_t)noff * bb * (mx ? 2 : 4);
+    if (!c->Wd || c->w_bytes != w_bytes) {
+        free_factor(c);
+        if (noff > 0) {
+            if (mx) {
+                KRR_TRY(dev_alloc(c, (__half **)&c->W, (size_t)noff * bb, "trailing tiles"));
+            } else {
+                KRR_TRY(dev_alloc(c, (float **)&c->W, (size_t)noff * bb, "trailing tiles"));
+            }
+        }
+        c->w_bytes = w_bytes;
+        KRR_TRY(dev_alloc(c, &c->Wd, (size_t)nt * bb, "diagonal tiles"));
+        KRR_TRY(dev_alloc(c, &c->Linv, (size_t)nt * bb, "diagonal inverses"));
+        KRR_TRY(dev_alloc(c, &c->diag64, (size_t)bb, "FP64 diagonal scratch"));
+        KRR_TRY(dev_alloc(c, &c->diag64_inv, (size_t)2 * bb, "FP64 inverse scratch"));
+        const size_t pool_bytes = (size_t)std::max<int64_t>(noff, 1) * bb * 4;
+        KRR_TRY(dev_alloc(c, &c->pool, pool_bytes, "factor pool"));
+        c->pool_bytes = pool_bytes;
+        KRR_TRY(dev_alloc(c, &c->ltab, (size_t)std::max<int64_t>(noff, 1), "tile table"));
+        KRR_TRY(dev_alloc(c, &c->precmap, (size_t)nt * nt, "precision map"));
+        if (mx) {
+            KRR_TRY(dev_alloc(c, &c->Linv_hi, (size_t)nt * bb, "inverse split"));
+            KRR_TRY(dev_alloc(c, &c->Linv_lo, (size_t)nt * bb, "inverse split"));
+            const size_t colt = (size_t)std::max<int64_t>(nt - 1, 1);
+            KRR_TRY(dev_alloc(c, &c->colbuf, colt * bb, "column buffer"));
+            KRR_TRY(dev_alloc(c, &c->pan_hi, colt * bb, "operand panel"));
+            KRR_TRY(dev_alloc(c, &c->pan_lo, colt * bb, "operand panel"));
+            KRR_TRY(dev_alloc(c, &c->pan_f8, colt * bb, "operand panel"));
+            KRR_TRY(dev_alloc(c, &c->colnorm2, colt * 16, "column norms"));
+            KRR_TRY(dev_alloc(c, &c->colmax, colt * 16, "column maxima"));
+        }
+    }
+    // reset the error record and the precision map
+    DevErrors e0;
+    memset(&e0, 0, sizeof(e0));
+    e0.bad_tile = -1;
+    e0.bad_column = -1;
+    e0.min_pivot = INFINITY;
+    *c->herr = e0;
+    KRR_CUDA_TRY(c, cudaMemcpyAsync(c->derr, c->herr, sizeof(DevErrors), cudaMemcpyHostToDevice, s));
+    {
+        std::vector<uint8_t> pm((size_t)nt * nt, 255);
+        for (int64_t i = 0; i < nt; ++i) {
+            pm[i * nt + i] = c->opt.diag_fp64 ? KRR_PREC_FP64 : KRR_PREC_FP32;
+            if (!mx)
+                for (int64_t j = 0; j < i; ++j) pm[i * nt + j] = KRR_PREC_FP32;
+        }
+        KRR_CUDA_TRY(c, cudaMemcpyAsync(c->precmap, pm.data(), pm.size(), cudaMemcpyHostToDevice, s));
+        if (!mx && noff > 0) {
+            std::vector<TileDesc> tab((size_t)noff);
+            for (int64_t t = 0; t < noff; ++t) {
+                tab[t].offset = t * bb * 4;
+                tab[t].scale = 1.f;
+                tab[t].prec = KRR_PREC_FP32;
+            }
+            KRR_CUDA_TRY(c, cudaMemcpyAsync(c->ltab, tab.data(), tab.size() * sizeof(TileDesc),
+                                            cudaMemcpyHostToDevice, s));
+        }
+        // the tables above live on the host stack: wait for the copies
+        KRR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    }
+    const double bd = (double)b;
+    for (int64_t k = 0; k < nt; ++k) {
+        int pr = prof_begin(c, KRR_PROF_DIAG);
+        KRR_TRY(diag_step(c, k));
+        prof_end(c, pr, 2.0 * bd * bd * bd / 3.0, 0.0);
+        KRR_TRY(check_launch(c, "diagonal step"));
+        if (k + 1 >= nt) break;
+        const double u = (double)(nt - k - 1);
+        // algorithmic work: triangular solve b^3 per panel tile; update 2 b^3
+        // per off-diagonal target and b^3 per diagonal target
+        const double trsm_flops = u * bd * bd * bd;
+        const double upd_flops = (u * (u - 1) / 2.0) * 2.0 * bd * bd * bd + u * bd * bd * bd;
+        if (mx) {
+            pr = prof_begin(c, KRR_PROF_TRSM);
+            KRR_TRY(tc_trsm(c, k));
+            prof_end(c, pr, trsm_flops, 0.0);
+            pr = prof_begin(c, KRR_PROF_CAST);
+            launch_column_cast(c, k);
+            prof_end(c, pr, 0.0, u * bd * bd * (4.0 + 2.0));
+            KRR_TRY(check_launch(c, "column cast"));
+            pr = prof_begin(c, KRR_PROF_UPDATE);
+            KRR_TRY(tc_update(c, k));
+            prof_end(c, pr, upd_flops, 0.0);
+        } else {
+            pr = prof_begin(c, KRR_PROF_TRSM);
+            launch_trsm_simt(c, k);
+            prof_end(c, pr, trsm_flops, 0.0);
+            KRR_TRY(check_launch(c, "trsm"));
+            pr = prof_begin(c, KRR_PROF_UPDATE);
+            launch_update_simt(c, k);
+            prof_end(c, pr, upd_flops, 0.0);
+            KRR_TRY(check_launch(c, "update"));
+        }
+    }
+    KRR_CUDA_TRY(c, cudaMemcpyAsync(c->herr, c->derr, sizeof(DevErrors), cudaMemcpyDeviceToHost, s));
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    const DevErrors &he = *c->herr;
+    if (info) {
+        info->nt = nt;
+        info->tiles_fp32 = mx ? he.fp32_tiles : noff;
+        info->tiles_fp16 = mx ? he.fp16_tiles : 0;
+        info->tiles_e4m3 = mx ? he.fp8_tiles : 0;
+        info->factor_bytes = mx ? he.pool_cursor : noff * bb * 4;
+        info->bad_tile = he.bad_tile;
+        info->bad_column = he.bad_column;
+        info->min_pivot = he.min_pivot;
+    }
+    if (he.code == KRR_ENOTPD) {
+        c->last_error = "krr_factor: matrix not positive definite (pivot <= 0 at column " +
+                        std::to_string(he.bad_column) + ")";
+        return KRR_ENOTPD;
+    }
+    if (he.code != 0) {
+        c->last_error = "krr_factor: device error " + std::to_string(he.code);
+        return (krr_status)he.code;
+    }
+    c->factored = true;
+    return KRR_OK;
+}
+
+krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *A, int64_t lda,
+                     krr_solve_info *info) {
+    if (!c) return KRR_EINVAL;
+    if (!c->factored) {
+        c->last_error = "krr_solve: no factorisation";
+        return KRR_ESTATE;
+    }
+    if (!Y || !A || p < 1 || ldy < p || lda < p) {
+        c->last_error = "krr_solve: need Y, A != NULL, p >= 1, ldy >= p, lda >= p";
+        return KRR_EINVAL;
+    }
+    cudaStream_t s = c->stream;
+    const int64_t cnt = c->n_pad * p;
+    if (c->vec_cap < cnt) {
+        KRR_TRY(dev_alloc(c, &c->ybuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->zbuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->abuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->dabuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->rbuf, (size_t)cnt, "residual"));
+        c->vec_cap = cnt;
+    }
+    KRR_TRY(load_rows_f32(c, Y, c->n, p, ldy, c->n_pad, c->ybuf));
+    KRR_CUDA_TRY(c, cudaMemcpyAsync(c->abuf, c->ybuf, cnt * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // compulsory bytes of one pair of sweeps: the stored factor read twice
+    // (diagonal inverses in FP32 plus the off-diagonal pool) and the vectors
+    const double pool_used = mixed(c) ? (double)c->herr->pool_cursor
+                                      : (double)c->nt * (c->nt - 1) / 2 * c->b * c->b * 4.0;
+    const double factor_bytes_all = pool_used + (double)c->nt * c->b * c->b * 4.0;
+    const double sweep_bytes = 2.0 * factor_bytes_all + 4.0 * (double)cnt * 4.0;
+    const double sweep_flops = 2.0 * 2.0 * (double)c->n_pad * c->n_pad * p;
+    int pr = prof_begin(c, KRR_PROF_SOLVE);
+    solve_inplace(c, c->abuf, c->zbuf, p);
+    prof_end(c, pr, sweep_flops, sweep_bytes);
+    KRR_TRY(check_launch(c, "solve"));
+    krr_solve_info si;
+    memset(&si, 0, sizeof(si));
+    krr_status st = KRR_OK;
+    const bool refine = mixed(c) && c->opt.ir_max > 0;
+    if (refine || info) {
+        double best = INFINITY;
+        int stall = 0;
+        for (int it = 0;; ++it) {
+            int rr = prof_begin(c, KRR_PROF_RESIDUAL);
+            launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
+            launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red, s);
+            // the lower-triangle K tiles are read once by the row pass and
+            // once by the column pass
+            prof_end(c, rr, 2.0 * (double)c->n_pad * c->n_pad * p, 2.0 * (double)c->kd_bytes);
+            KRR_TRY(check_launch(c, "residual"));
+            KRR_CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            KRR_CUDA_TRY(c, cudaStreamSynchronize(s));
+            const double ynorm = sqrt(c->hred[1]);
+            const double rel = ynorm > 0 ? sqrt(c->hred[0]) / ynorm : sqrt(c->hred[0]);
+            if (it < 32) si.history[it] = rel;
+            si.rel_residual = rel;
+            si.iterations = it;
+            if (rel <= c->opt.ir_tol) {
+                si.converged = 1;
+                break;
+            }
+            if (!refine) break;
+            if (it > 0 && !(rel <= si.history[0])) {  // diverging (or NaN)
+                st = KRR_ENOCONV;
+                break;
+            }
+            if (it >= c->opt.ir_max) {
+                st = KRR_ENOCONV;
+                break;
+            }
+            // stagnation: two successive steps that do not halve the residual
+            // mean the floor set by FP32 storage of K and A has been reached
+            if (rel > 0.5 * best) {
+                if (++stall >= 2) {
+                    si.converged = 2;
+                    break;
+                }
+            } else {
+                stall = 0;
+            }
+            best = std::min(best, rel);
+            launch_axpy_r(c->rbuf, c->dabuf, cnt, s);
+            int sr = prof_begin(c, KRR_PROF_SOLVE);
+            solve_inplace(c, c->dabuf, c->zbuf, p);
+            prof_end(c, sr, sweep_flops, sweep_bytes);
+            launch_add_inplace(c->abuf, c->dabuf, cnt, s);
+            KRR_TRY(check_launch(c, "refinement step"));
+        }
+    }
+    KRR_TRY(store_rows_f32(c, c->abuf, c->n, p, A, lda));
+    if (info) *info = si;
+    if (st == KRR_ENOCONV)
+        c->last_error = "krr_solve: refinement stopped at relative residual " + std::to_string(si.rel_residual);
+    return st;
+}
+
+krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt, const float *A,
+                       int64_t lda, int64_t p, float *Yt, int64_t ldyt) {
+    if (!c) return KRR_EINVAL;
+    if (!c->built) {
+        c->last_error = "krr_predict: no kernel built";
+        return KRR_ESTATE;
+    }
+    if (!T || !A || !Yt || n_test < 1 || ldt < c->m || p < 1 || p > 256 || lda < p || ldyt < p) {
+        c->last_error = "krr_predict: bad arguments (need 1 <= p <= 256, ldt >= m, lda, ldyt >= p)";
+        return KRR_EINVAL;
+    }
+    const bool mx = mixed(c);
+    const int64_t rows_pad = (n_test + 127) / 128 * 128;
+    const size_t tbytes = (size_t)rows_pad * c->m_pad * (mx ? 1 : 4);
+    if (c->t_cap < tbytes) {
+        KRR_TRY(dev_alloc(c, &c->t8, tbytes, "test genotypes"));
+        c->t_cap = tbytes;
+    }
+    if (c->tnorm_cap < (size_t)rows_pad) {
+        KRR_TRY(dev_alloc(c, &c->tnorms, (size_t)rows_pad, "test norms"));
+        c->tnorm_cap = rows_pad;
+    }
+    const int64_t cnt = c->n_pad * p;
+    if (c->vec_cap < cnt) {
+        KRR_TRY(dev_alloc(c, &c->ybuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->zbuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->abuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->dabuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->rbuf, (size_t)cnt, "residual"));
+        c->vec_cap = cnt;
+    }
+    const int64_t colblk = mx ? 256 : 128;
+    const int64_t nblk = c->n_pad / colblk;
+    const size_t part = (size_t)nblk * rows_pad * p;
+    if (c->pred_part_cap < part) {
+        KRR_TRY(dev_alloc(c, &c->pred_part, part, "predict partials"));
+        c->pred_part_cap = part;
+    }
+    if (c->pred_out_cap < (size_t)rows_pad * p) {
+        KRR_TRY(dev_alloc(c, &c->pred_out, (size_t)rows_pad * p, "predictions"));
+        c->pred_out_cap = (size_t)rows_pad * p;
+    }
+    KRR_TRY(pack(c, T, n_test, c->m, ldt, rows_pad, mx ? c->t8 : nullptr,
+                 mx ? nullptr : (float *)c->t8, c->tnorms));
+    float *aw = c->dabuf;  // padded copy of the weights
+    KRR_TRY(load_rows_f32(c, A, c->n, p, lda, c->n_pad, aw));
+    float *out = c->pred_out;
+    int pr = prof_begin(c, KRR_PROF_PREDICT);
+    if (mx) {
+        // the tensor-core epilogue holds at most 32 weight columns: chunk p
+        for (int64_t q0 = 0; q0 < p; q0 += 32) {
+            const int64_t pc = std::min<int64_t>(32, p - q0);
+            KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows_pad, aw + q0, p, pc, c->pred_part));
+            launch_predict_reduce(c->pred_part, nblk, rows_pad, n_test, pc, out + q0, p, c->stream);
+        }
+    } else {
+        launch_predict_simt(c, (const float *)c->t8, c->tnorms, n_test, rows_pad, aw, p,
+                            c->pred_part);
+        launch_predict_reduce(c->pred_part, nblk, rows_pad, n_test, p, out, p, c->stream);
+    }
+    prof_end(c, pr, 2.0 * (double)n_test * c->n * c->m + 2.0 * (double)n_test * c->n * p, 0.0);
+    KRR_TRY(check_launch(c, "predict"));
+    return store_rows_f32(c, out, n_test, p, Yt, ldyt);
+}
+
+krr_status krr_get_precision_map(krr_ctx *c, uint8_t *map, int64_t cap, int64_t *nt) {
+    if (!c) return KRR_EINVAL;
+    if (!c->factored) {
+        c->last_error = "krr_get_precision_map: no factorisation";
+        return KRR_ESTATE;
+    }
+    if (nt) *nt = c->nt;
+    if (!map) return KRR_OK;
+    if (cap < c->nt * c->nt) {
+        c->last_error = "krr_get_precision_map: map_capacity < nt * nt";
+        return KRR_EINVAL;
+    }
+    KRR_CUDA_TRY(c, cudaMemcpyAsync(map, c->precmap, (size_t)c->nt * c->nt,
+                                    is_device_ptr(map) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    c->stream));
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
+}  // extern "C"
+
+// Tile-to-dense copies for tests --------------------------------------------
+namespace {
+template <typename T>
+__global__ void tiles_to_dense_kernel(const T *tiles, int64_t b, int64_t n, T *dst, int64_t ld) {
+    const int64_t t = blockIdx.y;
+    int64_t ti, tj;
+    tri_decode(t, &ti, &tj);
+    const T *src = tiles + t * b * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < b * b;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = ti * b + e / b, q = tj * b + e % b;
+        if (r < n && q < n) dst[r * ld + q] = src[e];
+    }
+}
+
+template <typename T>
+krr_status tiles_to_dense(Ctx *c, const T *tiles, T *dst, int64_t ld) {
+    const int64_t ntri = c->nt * (c->nt + 1) / 2;
+    T *ddst = dst;
+    const bool dev = is_device_ptr(dst);
+    if (!dev) {
+        KRR_TRY(stage(c, (size_t)c->n * ld * sizeof(T)));
+        ddst = (T *)c->stage;
+        KRR_CUDA_TRY(c, cudaMemcpyAsync(ddst, dst, (size_t)c->n * ld * sizeof(T),
+                                        cudaMemcpyHostToDevice, c->stream));
+    }
+    count_launch(), tiles_to_dense_kernel<T><<<dim3(64, (unsigned)ntri), 256, 0, c->stream>>>(tiles, c->b, c->n, ddst, ld);
+    KRR_TRY(check_launch(c, "tiles to dense"));
+    if (!dev)
+        KRR_CUDA_TRY(c, cudaMemcpyAsync(dst, ddst, (size_t)c->n * ld * sizeof(T),
+                                        cudaMemcpyDeviceToHost, c->stream));
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+}  // namespace
+
+extern "C" krr_status krr_get_distances(krr_ctx *c, uint32_t *D, int64_t ldd) {
+    if (!c) return KRR_EINVAL;
+    if (!c->built || !c->Dd) {
+        c->last_error = "krr_get_distances: build with krr_set_keep_distances(ctx, 1) first";
+        return KRR_ESTATE;
+    }
+    if (!D || ldd < c->n) return KRR_EINVAL;
+    return tiles_to_dense<uint32_t>(c, c->Dd, D, ldd);
+}
+
+extern "C" krr_status krr_get_kernel(krr_ctx *c, float *K, int64_t ldk) {
+    if (!c) return KRR_EINVAL;
+    if (!c->built) {
+        c->last_error = "krr_get_kernel: no kernel built";
+        return KRR_ESTATE;
+    }
+    if (!K || ldk < c->n) return KRR_EINVAL;
+    return tiles_to_dense<float>(c, c->Kd, K, ldk);
+}
+
+extern "C" krr_status krr_set_profiling(krr_ctx *c, int32_t on) {
+    if (!c) return KRR_EINVAL;
+    if (on && !c->prof) {
+        c->prof = new (std::nothrow) ProfState();
+        if (!c->prof) return KRR_ENOMEM;
+    }
+    c->prof_on = on ? 1 : 0;
+    return KRR_OK;
+}
+
+extern "C" krr_status krr_get_profile(krr_ctx *c, krr_profile *out, int32_t reset) {
+    if (!c || !out) return KRR_EINVAL;
+    memset(out, 0, sizeof(*out));
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    out->launches = (int64_t)g_launches.load();
+    if (c->prof) {
+        ProfState *ps = (ProfState *)c->prof;
+        for (const ProfRec &r : ps->recs) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            out->count[r.cls] += 1;
+            out->ms[r.cls] += ms;
+            out->flops[r.cls] += r.flops;
+            out->bytes[r.cls] += r.bytes;
+        }
+        if (reset) {
+            for (const ProfRec &r : ps->recs) {
+                ps->pool.push_back(r.a);
+                ps->pool.push_back(r.b);
+            }
+            ps->recs.clear();
+        }
+    }
+    if (reset) g_launches.store(0);
+    return KRR_OK;
+}

@@ -1,0 +1,215 @@
+// Internal declarations of the KRR engine: context layout, tile indexing,
+// kernel launchers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/krr.h"
+
+namespace krr {
+
+// ---------------------------------------------------------------------------
+// Tile indexing.  K (and its factor) is kept as the lower triangle of an
+// NT x NT grid of b x b tiles, every tile row-major and contiguous.
+//   lower-triangle tile (i, j), i >= j :  tri_index = i (i + 1) / 2 + j
+//   strictly-lower tile (i, j), i > j  :  off_index = i (i - 1) / 2 + j
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int64_t tri_index(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
+__host__ __device__ inline int64_t off_index(int64_t i, int64_t j) { return i * (i - 1) / 2 + j; }
+
+// Inverse of the triangular numbering: t -> (i, j) with j <= i.
+__host__ __device__ inline void tri_decode(int64_t t, int64_t *i, int64_t *j) {
+    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while (r * (r + 1) / 2 > t) --r;
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    *i = r;
+    *j = t - r * (r + 1) / 2;
+}
+
+// Storage precision of an off-diagonal factor tile (values of the
+// KRR_PREC_* enum of krr.h).
+struct TileDesc {
+    int64_t offset;   // byte offset of the tile in the factor pool
+    float scale;      // stored value = scale * L (power of two; 1 for FP32)
+    int32_t prec;     // KRR_PREC_FP32 / KRR_PREC_FP16 / KRR_PREC_E4M3
+};
+
+// Device error record written by kernels that detect a failure.  Each field
+// is written with atomics so the first failure wins.
+struct DevErrors {
+    int32_t code;         // 0 = none, else a krr_status value
+    int32_t pad;
+    int64_t bad_tile;     // ENOTPD: diagonal tile index
+    int64_t bad_column;   // ENOTPD: global column
+    double bad_value;
+    int64_t fp8_tiles, fp16_tiles, fp32_tiles, pool_cursor;
+    double min_pivot;
+};
+
+struct Ctx {
+    // configuration
+    krr_options opt;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    std::string last_error;
+
+    // problem
+    int64_t n = 0, m = 0, m_pad = 0, b = 0, nt = 0, n_pad = 0;
+    double gamma = 0.0, lambda = 0.0;
+    bool built = false, factored = false;
+    int keep_distances = 0;
+
+    // build products
+    uint8_t *g8 = nullptr;     // E4M3 genotypes, n_pad x m_pad (mixed mode)
+    float *gf = nullptr;       // FP32 genotypes, n_pad x m_pad (fp32 mode)
+    int32_t *norms = nullptr;  // squared row norms, n_pad
+    float *Kd = nullptr;       // FP32 kernel tiles, lower triangle incl. diagonal
+    uint32_t *Dd = nullptr;    // exact squared distances (only with keep_distances)
+    double *knorm2 = nullptr;  // per lower-triangle tile sum of K^2
+    size_t g_bytes = 0, kd_bytes = 0, dd_bytes = 0;
+
+    // factor state
+    void *W = nullptr;         // strictly-lower trailing tiles: FP16 (mixed) / FP32 (fp32)
+    float *Wd = nullptr;       // diagonal working tiles, FP32, overwritten by L_kk
+    float *Linv = nullptr;     // inverse of every diagonal factor tile, FP32
+    __half *Linv_hi = nullptr, *Linv_lo = nullptr;  // FP16 split of Linv (mixed)
+    double *diag64 = nullptr;  // FP64 scratch diagonal tile (diag_fp64)
+    double *diag64_inv = nullptr;
+    uint8_t *pool = nullptr;   // off-diagonal factor tiles, each in its precision
+    size_t pool_bytes = 0;
+    TileDesc *ltab = nullptr;  // per strictly-lower tile: where/how L is stored
+    float *colbuf = nullptr;   // FP32 TRSM output of one tile column
+    __half *pan_hi = nullptr, *pan_lo = nullptr;  // FP16 operand copies of one column
+    uint8_t *pan_f8 = nullptr;                    // E4M3 operand copies of one column
+    double *colnorm2 = nullptr;  // per tile of the column: sum of L^2
+    float *colmax = nullptr;     // per tile of the column: max |L|
+    uint8_t *precmap = nullptr;  // device copy of the precision map (nt x nt)
+    DevErrors *derr = nullptr;
+    DevErrors *herr = nullptr;   // pinned host mirror
+    size_t w_bytes = 0;
+
+    // solve / predict scratch
+    float *ybuf = nullptr, *zbuf = nullptr;  // n_pad x p work vectors
+    double *rbuf = nullptr;                  // n_pad x p residual (FP64)
+    float *abuf = nullptr;                   // n_pad x p current solution
+    float *dabuf = nullptr;                  // n_pad x p correction
+    double *red = nullptr;                   // reductions (norms), small
+    double *hred = nullptr;                  // pinned host mirror of red
+    int64_t vec_cap = 0;                     // capacity in elements of the n_pad x p buffers
+    float *pred_part = nullptr;              // predict partial products
+    size_t pred_part_cap = 0;
+    float *pred_out = nullptr;               // reduced predictions, rows_pad x p
+    size_t pred_out_cap = 0;
+    uint8_t *t8 = nullptr;                   // packed test genotypes (E4M3 / FP32 bytes)
+    size_t t_cap = 0;
+    int32_t *tnorms = nullptr;
+    size_t tnorm_cap = 0;
+    void *stage = nullptr;                   // device staging for host arguments
+    size_t stage_cap = 0;
+
+    // tensor-core launch plumbing (opaque, owned by tc_gemm.cu)
+    void *tc = nullptr;
+
+    // profiler (opaque, owned by krr_api.cu)
+    void *prof = nullptr;
+    int prof_on = 0;
+};
+
+// Kernel launch counter of the whole library (reported by krr_get_profile).
+void count_launch();
+
+// Error helpers --------------------------------------------------------------
+#define KRR_CUDA_TRY(ctx, expr)                                                  \
+    do {                                                                         \
+        cudaError_t _e = (expr);                                                 \
+        if (_e != cudaSuccess) {                                                 \
+            (ctx)->last_error = std::string(#expr) + ": " + cudaGetErrorString(_e); \
+            return KRR_ECUDA;                                                    \
+        }                                                                        \
+    } while (0)
+
+#define KRR_TRY(expr)                  \
+    do {                               \
+        krr_status _s = (expr);        \
+        if (_s != KRR_OK) return _s;   \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// SIMT kernels (simt_kernels.cu)
+// ---------------------------------------------------------------------------
+// Pack int8 genotypes: E4M3 bytes (mixed) or FP32 (fp32) with zero padding to
+// n_pad x m_pad, plus exact squared row norms.
+void launch_pack_genotypes(const int8_t *g, int64_t n, int64_t m, int64_t ldg, int64_t n_pad,
+                           int64_t m_pad, uint8_t *out_e4m3, float *out_f32, int32_t *norms,
+                           cudaStream_t s);
+
+// Generic FP32/FP64 tiled GEMM on CUDA cores: C = alpha * op(A) op(B)^T + beta * Cin,
+// with A (M x K, row-major) and B either N x K row-major (b_trans = 0) or
+// K x N row-major (b_trans = 1).  'lower' skips 128 x 128 blocks strictly above
+// the diagonal of C.  Batched over `batch` problems with fixed strides.
+template <typename T>
+void launch_gemm_simt(int M, int N, int K, T alpha, const T *A, int64_t lda, int64_t strideA,
+                      const T *B, int64_t ldb, int64_t strideB, int b_trans, T beta,
+                      const T *Cin, int64_t ldcin, int64_t strideCin, T *C, int64_t ldc,
+                      int64_t strideC, int batch, int lower, cudaStream_t s);
+
+// FP32 Build on CUDA cores over lower-triangle tiles (fp32 mode).
+void launch_build_simt(Ctx *c);
+// FP32 trailing update of step k on CUDA cores (fp32 mode).
+void launch_update_simt(Ctx *c, int64_t k);
+// FP32 panel TRSM of column k on CUDA cores (fp32 mode): L_ik = W_ik Linv_kk^T.
+void launch_trsm_simt(Ctx *c, int64_t k);
+// FP32 predict partial products on CUDA cores (fp32 mode).  rows_pad is the
+// number of packed test rows (a multiple of 128); part is
+// (n_pad / 128) x rows_pad x p.
+void launch_predict_simt(Ctx *c, const float *tf, const int32_t *tn, int64_t n_test,
+                         int64_t rows_pad, const float *A, int64_t p, float *part);
+
+// Diagonal step: in-place Cholesky of Wd tile k and its inverse into Linv.
+krr_status diag_step(Ctx *c, int64_t k);
+
+// Casts the FP32 TRSM output of column k into the factor pool with the
+// precision chosen by the adaptive rule, plus the operand panels (mixed mode).
+// ||K||_F^2 is read from c->red[2] (written by the build).
+void launch_column_cast(Ctx *c, int64_t k);
+
+// Triangular solves with the stored factor: X <- (L L^T)^-1 X, n_pad x p
+// (row-major, leading dimension p); tmp is n_pad x p scratch.
+void solve_inplace(Ctx *c, float *x, float *tmp, int64_t p);
+
+// r = y - (K + lambda I) a (FP64 accumulation), norms into c->red.
+void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
+
+// Small helpers.
+void launch_fill_zero(void *p, size_t bytes, cudaStream_t s);
+void launch_reduce_norms(const double *r, const float *y, int64_t n, int64_t p, double *out,
+                         cudaStream_t s);
+void launch_axpy_r(const double *r, float *dst, int64_t count, cudaStream_t s);
+void launch_add_inplace(float *a, const float *da, int64_t count, cudaStream_t s);
+void launch_predict_reduce(const float *part, int64_t nblk, int64_t rows_pad, int64_t n_test,
+                           int64_t p, float *out, int64_t ldo, cudaStream_t s);
+void launch_copy_rows(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t rows,
+                      int64_t cols, int64_t rows_pad, cudaStream_t s);
+void launch_kernel_sumsq(Ctx *c, double *out);
+
+// ---------------------------------------------------------------------------
+// Tensor-core kernels (tc_gemm.cu)
+// ---------------------------------------------------------------------------
+krr_status tc_init(Ctx *c);
+void tc_free(Ctx *c);
+krr_status tc_build(Ctx *c);                 // distance GEMM + exp epilogue (E4M3)
+krr_status tc_trsm(Ctx *c, int64_t k);       // panel TRSM of column k (FP16 split)
+krr_status tc_update(Ctx *c, int64_t k);     // trailing update of step k
+// Predict partial products for weight columns A[:, 0:p] (p <= 32, leading
+// dimension lda): part is (n_pad / 256) x rows_pad x p.
+krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
+                      int64_t rows_pad, const float *A, int64_t lda, int64_t p, float *part);
+// Forget the cached factor tensor maps (the factor buffers were reallocated).
+void tc_invalidate_factor_maps(Ctx *c);
+
+}  // namespace krr

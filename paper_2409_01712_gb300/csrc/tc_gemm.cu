@@ -1,0 +1,816 @@
+// Tensor-core (tcgen05) kernels of the KRR engine for sm_103a.
+//
+// One persistent, warp-specialised kernel template computes 128 x 256 output
+// blocks of C = A B^T with both operands K-major in global memory:
+//   warp 0      TMA producer: 128-byte-swizzled A (128 rows) and B (256 rows)
+//               slabs of 128 bytes along K into a 4-stage shared-memory ring;
+//   warp 1      TMEM allocator and MMA issuer (one thread): tcgen05.mma
+//               M = 128, N = 256 into one of two TMEM accumulators;
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, fused per-op math,
+//               stores to global memory.
+// Every mbarrier wait is bounded by the context's wait budget
+// (%globaltimer); on expiry the kernel records KRR_ETIMEOUT, drains its own
+// copies and MMAs in flight, frees TMEM and returns.
+//
+// Ops (the paper's phases):
+//   OP_DIST    Build (Alg. 2, Gaussian kernel of Alg. 5) with the distance
+//              form of Sec. IV-B: S = G_I G_J^T on E4M3 operands (genotypes
+//              0/1/2 are exact), d = n_i + n_j - 2 S, K = exp(-gamma d).
+//   OP_PREDICT Predict (Alg. 4): the same distance tile for test x training
+//              rows, exponentiated and multiplied by the matching 256 rows of
+//              the weights; per-block partial products.
+//   OP_TRSM    Factorize (Alg. 3), panel solve of tile column k:
+//              L_ik = W_ik Linv_kk^T with FP16 hi/lo operand splits.
+//   OP_UPDATE  Factorize (Alg. 3), trailing update of step k:
+//              W_ij -= L_ik L_jk^T for k < j <= i, FP16 operands (hi/lo
+//              phases for tiles stored at FP32 accuracy), FP32 accumulation.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "krr_internal.h"
+
+namespace krr {
+
+namespace {
+
+constexpr int OP_DIST = 0, OP_PREDICT = 1, OP_TRSM = 2, OP_UPDATE = 3;
+constexpr int KIND_F16 = 0, KIND_F8 = 1;
+
+constexpr int BM = 128, BN = 256;       // output block
+constexpr int SLAB = 128;               // bytes of K per stage and row
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * SLAB;      // 16 KB
+constexpr int B_BYTES = BN * SLAB;      // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NUM_THREADS = 192;
+constexpr int TMEM_COLS = 512;          // two 256-column FP32 accumulators
+constexpr int PRED_MAX_P = 32;
+
+// Instruction descriptor (kind::f16 with F16 operands, kind::f8f6f4 with
+// E4M3 operands -- both formats encode as 0): D = F32, A and B K-major,
+// N = 256, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct TcParams {
+    // n: real training rows; n_pad: padded training rows; n_test / test_rows:
+    // real / padded test rows; p / ldaw: weight columns in this launch and the
+    // leading dimension of the weights.
+    int64_t n, n_pad, n_test, test_rows, b, nt, k, m_pad, items, p, ldaw;
+    float gamma, lambda;
+    const int32_t *norms_a, *norms_b;
+    float *Kd;
+    uint32_t *Dd;
+    double *knorm_part;
+    __half *W;
+    float *Wd;
+    const TileDesc *ltab;
+    float *colbuf;
+    const float *aw;
+    float *part;
+    uint64_t wait_ns;
+    DevErrors *err;
+};
+
+// One 128 x 256 output block: up to three operand phases, each nkb slabs.
+struct Work {
+    int nph, nkb;
+    int amap[3], bmap[3];
+    int arow[3], brow[3];
+    // epilogue coordinates
+    int64_t i, j, sm, sn;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok;
+}
+
+// Bounded wait; false when the budget ran out or another role aborted.
+__device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, uint64_t budget,
+                                         volatile int *abort_flag, DevErrors *err) {
+    if (mbar_try_wait(b, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(b, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > budget) {
+            *abort_flag = 1;
+            atomicCAS(&err->code, 0, (int)KRR_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                   // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    if (KIND == KIND_F16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Work decoding: item index -> operand phases and epilogue coordinates.
+// Every role calls this with the same arguments, so all agree on the number
+// of slabs of every block (zero for skipped blocks).
+// ---------------------------------------------------------------------------
+template <int OP>
+__device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w) {
+    const int64_t b = p.b;
+    const int64_t sub_cols = b / BN, sub_per_tile = (b / BM) * sub_cols;
+    if (OP == OP_DIST) {
+        const int64_t tile = t / sub_per_tile, sub = t % sub_per_tile;
+        tri_decode(tile, &w.i, &w.j);
+        w.sm = sub / sub_cols;
+        w.sn = sub % sub_cols;
+        w.nph = 1;
+        w.nkb = (int)(p.m_pad / SLAB);
+        w.amap[0] = 0;
+        w.bmap[0] = 2;
+        w.arow[0] = (int)(w.i * b + w.sm * BM);
+        w.brow[0] = (int)(w.j * b + w.sn * BN);
+    } else if (OP == OP_PREDICT) {
+        const int64_t ncb = p.n_pad / BN;
+        w.i = t / ncb;                 // 128-row block of test rows
+        w.j = t % ncb;                 // 256-column block of training rows
+        w.sm = w.sn = 0;
+        w.nph = 1;
+        w.nkb = (int)(p.m_pad / SLAB);
+        w.amap[0] = 0;
+        w.bmap[0] = 2;
+        w.arow[0] = (int)(w.i * BM);
+        w.brow[0] = (int)(w.j * BN);
+    } else if (OP == OP_TRSM) {
+        const int64_t k = p.k;
+        w.i = k + 1 + t / sub_per_tile;
+        w.j = k;
+        const int64_t sub = t % sub_per_tile;
+        w.sm = sub / sub_cols;
+        w.sn = sub % sub_cols;
+        // Linv_kk is lower triangular: output columns < (sn + 1) * 256 need
+        // K < (sn + 1) * 256 only.
+        w.nkb = (int)((w.sn + 1) * BN * 2 / SLAB);
+        const int arow = (k == 0) ? (int)((w.i - 1) * b + w.sm * BM)
+                                  : (int)(off_index(w.i, k) * b + w.sm * BM);
+        const int brow = (int)(k * b + w.sn * BN);
+        if (k == 0) {
+            // A = Kd column 0 split hi/lo; B = Linv hi/lo
+            w.nph = 3;
+            w.amap[0] = 0; w.bmap[0] = 2;
+            w.amap[1] = 0; w.bmap[1] = 3;
+            w.amap[2] = 1; w.bmap[2] = 2;
+        } else {
+            // A = FP16 trailing tile (exact in FP16); B = Linv hi/lo
+            w.nph = 2;
+            w.amap[0] = 0; w.bmap[0] = 2;
+            w.amap[1] = 0; w.bmap[1] = 3;
+        }
+        for (int q = 0; q < 3; ++q) {
+            w.arow[q] = arow;
+            w.brow[q] = brow;
+        }
+    } else {  // OP_UPDATE
+        const int64_t k = p.k;
+        const int64_t tile = t / sub_per_tile, sub = t % sub_per_tile;
+        int64_t ii, jj;
+        tri_decode(tile, &ii, &jj);
+        w.i = k + 1 + ii;
+        w.j = k + 1 + jj;
+        w.sm = sub / sub_cols;
+        w.sn = sub % sub_cols;
+        w.nkb = (int)(b * 2 / SLAB);
+        if (w.i == w.j && w.sn * BN >= (w.sm + 1) * BM) {
+            w.nph = 0;  // strictly above the diagonal of a diagonal tile
+            return;
+        }
+        const int pi = p.ltab[off_index(w.i, k)].prec;
+        const int pj = p.ltab[off_index(w.j, k)].prec;
+        const int arow = (int)((w.i - k - 1) * b + w.sm * BM);
+        const int brow = (int)((w.j - k - 1) * b + w.sn * BN);
+        int q = 0;
+        w.amap[q] = 0; w.bmap[q] = 2; ++q;
+        if (pj == KRR_PREC_FP32) { w.amap[q] = 0; w.bmap[q] = 3; ++q; }
+        if (pi == KRR_PREC_FP32) { w.amap[q] = 1; w.bmap[q] = 2; ++q; }
+        w.nph = q;
+        for (int e = 0; e < 3; ++e) {
+            w.arow[e] = arow;
+            w.brow[e] = brow;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Epilogues.  Thread r (0..127) owns accumulator row r = TMEM lane r.
+// ---------------------------------------------------------------------------
+template <int OP>
+__device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row,
+                                         int32_t *nb_s, float *aw_s, double *red_s) {
+    const int64_t b = p.b;
+    if (OP == OP_DIST) {
+        const int64_t gi = w.i * b + w.sm * BM + row;
+        const int32_t ni = p.norms_a[gi];
+        const int64_t tidx = tri_index(w.i, w.j);
+        float *krow = p.Kd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN;
+        uint32_t *drow = p.Dd ? p.Dd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN : nullptr;
+        double ss = 0.0;
+        for (int ch = 0; ch < BN / 16; ++ch) {
+            float v[16];
+            tmem_ld16(tacc + ch * 16, v);
+            float kv[16];
+            uint32_t dv[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int c = ch * 16 + e;
+                const int64_t gj = w.j * b + w.sn * BN + c;
+                const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
+                const bool real = gi < p.n && gj < p.n;
+                kv[e] = real ? expf(-p.gamma * (float)d) : (gi == gj ? 1.f : 0.f);
+                dv[e] = real ? (uint32_t)d : 0u;
+                ss += (double)kv[e] * (double)kv[e];
+            }
+            float4 *dst = reinterpret_cast<float4 *>(krow + ch * 16);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dst[e] = make_float4(kv[4 * e], kv[4 * e + 1], kv[4 * e + 2], kv[4 * e + 3]);
+            if (drow) {
+                uint4 *dd = reinterpret_cast<uint4 *>(drow + ch * 16);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dd[e] = make_uint4(dv[4 * e], dv[4 * e + 1], dv[4 * e + 2], dv[4 * e + 3]);
+            }
+        }
+        // deterministic per-block sum of K^2: warp sums, then the four warps in order
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if ((row & 31) == 0) red_s[row >> 5] = ss;
+        epi_bar();
+        if (row == 0) {
+            const int64_t sub_per_tile = (b / BM) * (b / BN);
+            p.knorm_part[tidx * sub_per_tile + w.sm * (b / BN) + w.sn] =
+                red_s[0] + red_s[1] + red_s[2] + red_s[3];
+        }
+    } else if (OP == OP_PREDICT) {
+        const int64_t gi = w.i * BM + row;  // test row
+        const int32_t ni = p.norms_a[gi];
+        float acc[PRED_MAX_P];
+#pragma unroll
+        for (int q = 0; q < PRED_MAX_P; ++q) acc[q] = 0.f;
+        const int pp = (int)p.p;
+        for (int ch = 0; ch < BN / 16; ++ch) {
+            float v[16];
+            tmem_ld16(tacc + ch * 16, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int c = ch * 16 + e;
+                const int64_t gj = w.j * BN + c;
+                const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
+                const float kv = (gi < p.n_test && gj < p.n) ? expf(-p.gamma * (float)d) : 0.f;
+                const float *ar = aw_s + c * PRED_MAX_P;
+#pragma unroll
+                for (int q = 0; q < PRED_MAX_P; ++q)
+                    if (q < pp) acc[q] = fmaf(kv, ar[q], acc[q]);
+            }
+        }
+        // partials are laid out [column block][padded test row][p]
+        float *dst = p.part + (w.j * p.test_rows + gi) * p.p;
+        for (int q = 0; q < pp; ++q) dst[q] = acc[q];
+    } else if (OP == OP_TRSM) {
+        float *orow = p.colbuf + (w.i - p.k - 1) * b * b + (w.sm * BM + row) * b + w.sn * BN;
+        for (int ch = 0; ch < BN / 16; ++ch) {
+            float v[16];
+            tmem_ld16(tacc + ch * 16, v);
+            float4 *dst = reinterpret_cast<float4 *>(orow + ch * 16);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        }
+    } else {  // OP_UPDATE
+        const int64_t k = p.k;
+        const float sc = 1.f / (p.ltab[off_index(w.i, k)].scale * p.ltab[off_index(w.j, k)].scale);
+        const int64_t lr = w.sm * BM + row;
+        const bool diag = (w.i == w.j);
+        const float *cin32 = nullptr;
+        float *out32 = nullptr;
+        __half *io16 = nullptr;
+        if (diag) {
+            out32 = p.Wd + w.i * b * b + lr * b + w.sn * BN;
+            cin32 = (k == 0) ? p.Kd + tri_index(w.i, w.i) * b * b + lr * b + w.sn * BN : out32;
+        } else {
+            io16 = p.W + off_index(w.i, w.j) * b * b + lr * b + w.sn * BN;
+            if (k == 0) cin32 = p.Kd + tri_index(w.i, w.j) * b * b + lr * b + w.sn * BN;
+        }
+        for (int ch = 0; ch < BN / 16; ++ch) {
+            float v[16];
+            tmem_ld16(tacc + ch * 16, v);
+            float cin[16];
+            if (cin32) {
+                const float4 *src = reinterpret_cast<const float4 *>(cin32 + ch * 16);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    float4 t4 = src[e];
+                    cin[4 * e] = t4.x; cin[4 * e + 1] = t4.y; cin[4 * e + 2] = t4.z; cin[4 * e + 3] = t4.w;
+                }
+            } else {
+                const uint4 *src = reinterpret_cast<const uint4 *>(io16 + ch * 16);
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    uint4 u = src[e];
+                    const __half2 *h2 = reinterpret_cast<const __half2 *>(&u);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float2 f = __half22float2(h2[q]);
+                        cin[8 * e + 2 * q] = f.x;
+                        cin[8 * e + 2 * q + 1] = f.y;
+                    }
+                }
+            }
+            float out[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                float c0 = cin[e];
+                if (k == 0 && diag && lr == w.sn * BN + ch * 16 + e) c0 += p.lambda;
+                out[e] = c0 - v[e] * sc;
+            }
+            if (diag) {
+                float4 *dst = reinterpret_cast<float4 *>(out32 + ch * 16);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) dst[e] = make_float4(out[4 * e], out[4 * e + 1], out[4 * e + 2], out[4 * e + 3]);
+            } else {
+                uint4 pk[2];
+                __half2 *h2 = reinterpret_cast<__half2 *>(pk);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) h2[q] = __floats2half2_rn(out[2 * q], out[2 * q + 1]);
+                uint4 *dst = reinterpret_cast<uint4 *>(io16 + ch * 16);
+                dst[0] = pk[0];
+                dst[1] = pk[1];
+            }
+        }
+    }
+}
+
+// Per-block epilogue inputs staged in shared memory by the epilogue warps.
+template <int OP>
+__device__ __forceinline__ void epilogue_stage(const TcParams &p, const Work &w, int row,
+                                               int32_t *nb_s, float *aw_s) {
+    if (OP == OP_DIST) {
+        for (int c = row; c < BN; c += 128) nb_s[c] = p.norms_b[w.j * p.b + w.sn * BN + c];
+    } else if (OP == OP_PREDICT) {
+        for (int c = row; c < BN; c += 128) nb_s[c] = p.norms_b[w.j * BN + c];
+        for (int e = row; e < BN * PRED_MAX_P; e += 128) {
+            const int c = e / PRED_MAX_P, q = e % PRED_MAX_P;
+            aw_s[e] = (q < p.p) ? p.aw[(w.j * BN + c) * p.ldaw + q] : 0.f;
+        }
+    }
+}
+
+template <int KIND, int OP>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+              const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
+              const TcParams p) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *stage_base = smem;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
+    uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES,
+             *tempty = bars + 2 * STAGES + 2, *drain = bars + 2 * STAGES + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    double *red_s = reinterpret_cast<double *>(tmem_slot + 2);
+    int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 4);
+    float *aw_s = reinterpret_cast<float *>(nb_s + BN);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA0)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA1)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB0)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB1)) : "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const uint64_t budget = p.wait_ns;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            const CUtensorMap *maps[4] = {&mA0, &mA1, &mB0, &mB1};
+            int s = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < p.items && ok; t += gridDim.x) {
+                Work w;
+                decode<OP>(p, t, w);
+                for (int q = 0; q < w.nph && ok; ++q) {
+                    for (int kb = 0; kb < w.nkb; ++kb) {
+                        if (!wait_bar(&empty[s], ph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
+                        uint8_t *sa = stage_base + s * STAGE_BYTES;
+                        uint8_t *sb = sa + A_BYTES;
+                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                        const int x = (KIND == KIND_F16) ? kb * (SLAB / 2) : kb * SLAB;
+                        tma_load_2d(sa, maps[w.amap[q]], x, w.arow[q], &full[s]);
+                        tma_load_2d(sb, maps[w.bmap[q]], x, w.brow[q], &full[s]);
+                        tma_load_2d(sb + A_BYTES, maps[w.bmap[q]], x, w.brow[q] + BM, &full[s]);
+                        ++issued;
+                        if (++s == STAGES) { s = 0; ph ^= 1; }
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the last loads issued to land
+                int n = issued < STAGES ? issued : STAGES;
+                int ss = s;
+                uint32_t pp = ph;
+                for (int e = 0; e < n; ++e) {
+                    if (--ss < 0) { ss = STAGES - 1; pp ^= 1; }
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < budget) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int s = 0;
+            uint32_t ph = 0;
+            int acc = 0;
+            uint32_t aph = 0;
+            bool ok = true;
+            bool any = false;
+            for (int64_t t = blockIdx.x; t < p.items && ok; t += gridDim.x) {
+                Work w;
+                decode<OP>(p, t, w);
+                const int total = w.nph * w.nkb;
+                if (total == 0) continue;
+                if (!wait_bar(&tempty[acc], aph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
+                tmem_fence_after();
+                const uint32_t tacc = tmem_base + (uint32_t)(acc * BN);
+                for (int it = 0; it < total; ++it) {
+                    if (!wait_bar(&full[s], ph, budget, abort_flag, p.err)) { ok = false; break; }
+                    tmem_fence_after();
+                    const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
+                    const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        mma<KIND>(tacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
+                                  (it > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    any = true;
+                    mma_commit(&empty[s]);
+                    if (++s == STAGES) { s = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1; }
+            }
+            if (!ok && any) {
+                mma_commit(drain);
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < budget) {}
+            }
+        }
+    } else {
+        // ---------------- epilogue warps ----------------
+        const int row = ((warp & 3) << 5) + lane;  // TMEM lane quarter of this warp
+        int acc = 0;
+        uint32_t aph = 0;
+        for (int64_t t = blockIdx.x; t < p.items; t += gridDim.x) {
+            Work w;
+            decode<OP>(p, t, w);
+            if (w.nph * w.nkb == 0) continue;
+            epi_bar();
+            epilogue_stage<OP>(p, w, threadIdx.x - 64, nb_s, aw_s);
+            epi_bar();
+            if (!wait_bar(&tfull[acc], aph, budget, abort_flag, p.err)) break;
+            tmem_fence_after();
+            const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * BN);
+            epilogue<OP>(p, w, tacc, row, nb_s, aw_s, red_s);
+            tmem_fence_before();
+            mbar_arrive(&tempty[acc]);
+            if (++acc == 2) { acc = 0; aph ^= 1; }
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Shared memory: ring + barriers/slots + norms + predict weights + alignment slack.
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 256 + BN * 4 + BN * PRED_MAX_P * 4 + 1024;
+
+__global__ void split_col0_kernel(const float *Kd, int64_t nt, int64_t b, __half *hi, __half *lo) {
+    const int64_t tile = 1 + blockIdx.y;  // tile row i >= 1 of column 0
+    const float *src = Kd + tri_index(tile, 0) * b * b;
+    __half *h = hi + (tile - 1) * b * b;
+    __half *l = lo + (tile - 1) * b * b;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < b * b;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const float v = src[e];
+        const __half x = __float2half_rn(v);
+        h[e] = x;
+        l[e] = __float2half_rn(v - __half2float(x));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps and launches.
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct TcState {
+    EncodeTiledFn encode = nullptr;
+    CUtensorMap g_map;                     // packed training genotypes
+    CUtensorMap w_map, hi_map, lo_map;     // trailing tiles, column panels
+    CUtensorMap linv_hi_map, linv_lo_map;  // diagonal inverse splits
+    bool factor_maps = false;
+};
+
+krr_status make_map(Ctx *c, CUtensorMap *map, const void *base, CUtensorMapDataType dt,
+                    int elem_bytes, int64_t rows, int64_t cols) {
+    TcState *st = (TcState *)c->tc;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(cols * elem_bytes)};
+    const cuuint32_t box[2] = {(cuuint32_t)(SLAB / elem_bytes), (cuuint32_t)BM};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = st->encode(map, dt, 2, const_cast<void *>(base), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->last_error = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
+}
+
+template <int KIND, int OP>
+krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
+                  const CUtensorMap &b1, TcParams &p) {
+    if (p.items <= 0) return KRR_OK;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_kernel<KIND, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)SMEM_BYTES);
+        if (e != cudaSuccess) {
+            c->last_error = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+        attr = true;
+    }
+    p.wait_ns = (uint64_t)c->opt.wait_budget_ns;
+    p.err = c->derr;
+    const int64_t grid = p.items < c->num_sms ? p.items : c->num_sms;
+    count_launch(), tc_kernel<KIND, OP><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, c->stream>>>(a0, a1, b0, b1, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->last_error = std::string("tensor-core launch: ") + cudaGetErrorString(e);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
+}
+
+TcParams base_params(Ctx *c) {
+    TcParams p;
+    memset(&p, 0, sizeof(p));
+    p.n = c->n;
+    p.b = c->b;
+    p.nt = c->nt;
+    p.m_pad = c->m_pad;
+    p.gamma = (float)c->gamma;
+    p.lambda = (float)c->lambda;
+    return p;
+}
+
+krr_status ensure_factor_maps(Ctx *c) {
+    TcState *st = (TcState *)c->tc;
+    if (st->factor_maps) return KRR_OK;
+    const int64_t b = c->b, nt = c->nt, noff = nt * (nt - 1) / 2;
+    const CUtensorMapDataType f16 = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    KRR_TRY(make_map(c, &st->w_map, c->W, f16, 2, noff * b, b));
+    KRR_TRY(make_map(c, &st->hi_map, c->pan_hi, f16, 2, (nt - 1) * b, b));
+    KRR_TRY(make_map(c, &st->lo_map, c->pan_lo, f16, 2, (nt - 1) * b, b));
+    KRR_TRY(make_map(c, &st->linv_hi_map, c->Linv_hi, f16, 2, nt * b, b));
+    KRR_TRY(make_map(c, &st->linv_lo_map, c->Linv_lo, f16, 2, nt * b, b));
+    st->factor_maps = true;
+    return KRR_OK;
+}
+
+}  // namespace
+
+krr_status tc_init(Ctx *c) {
+    TcState *st = new (std::nothrow) TcState();
+    if (!st) {
+        c->last_error = "out of host memory";
+        return KRR_ENOMEM;
+    }
+    c->tc = st;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        c->last_error = "cuTensorMapEncodeTiled is not available from the driver";
+        return KRR_ECUDA;
+    }
+    st->encode = (EncodeTiledFn)fn;
+    return KRR_OK;
+}
+
+void tc_free(Ctx *c) {
+    delete (TcState *)c->tc;
+    c->tc = nullptr;
+}
+
+void tc_invalidate_factor_maps(Ctx *c) {
+    if (c->tc) ((TcState *)c->tc)->factor_maps = false;
+}
+
+krr_status tc_build(Ctx *c) {
+    TcState *st = (TcState *)c->tc;
+    KRR_TRY(make_map(c, &st->g_map, c->g8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, c->n_pad, c->m_pad));
+    TcParams p = base_params(c);
+    p.norms_a = c->norms;
+    p.norms_b = c->norms;
+    p.Kd = c->Kd;
+    p.Dd = c->Dd;
+    p.knorm_part = c->knorm2;
+    const int64_t ntri = c->nt * (c->nt + 1) / 2;
+    p.items = ntri * (c->b / BM) * (c->b / BN);
+    return launch<KIND_F8, OP_DIST>(c, st->g_map, st->g_map, st->g_map, st->g_map, p);
+}
+
+krr_status tc_trsm(Ctx *c, int64_t k) {
+    TcState *st = (TcState *)c->tc;
+    KRR_TRY(ensure_factor_maps(c));
+    const int64_t b = c->b, nt = c->nt;
+    if (k == 0) {
+        count_launch(), split_col0_kernel<<<dim3(64, (unsigned)(nt - 1)), 256, 0, c->stream>>>(c->Kd, nt, b, c->pan_hi,
+                                                                               c->pan_lo);
+    }
+    TcParams p = base_params(c);
+    p.k = k;
+    p.colbuf = c->colbuf;
+    p.items = (nt - k - 1) * (b / BM) * (b / BN);
+    const CUtensorMap &a0 = (k == 0) ? st->hi_map : st->w_map;
+    return launch<KIND_F16, OP_TRSM>(c, a0, st->lo_map, st->linv_hi_map, st->linv_lo_map, p);
+}
+
+krr_status tc_update(Ctx *c, int64_t k) {
+    TcState *st = (TcState *)c->tc;
+    KRR_TRY(ensure_factor_maps(c));
+    const int64_t b = c->b, nt = c->nt;
+    const int64_t u = nt - k - 1;
+    TcParams p = base_params(c);
+    p.k = k;
+    p.Kd = c->Kd;
+    p.W = (__half *)c->W;
+    p.Wd = c->Wd;
+    p.ltab = c->ltab;
+    p.items = u * (u + 1) / 2 * (b / BM) * (b / BN);
+    return launch<KIND_F16, OP_UPDATE>(c, st->hi_map, st->lo_map, st->hi_map, st->lo_map, p);
+}
+
+krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
+                      int64_t rows_pad, const float *A, int64_t lda, int64_t p_cols, float *part) {
+    TcState *st = (TcState *)c->tc;
+    if (p_cols < 1 || p_cols > PRED_MAX_P) {
+        c->last_error = "tc_predict: at most 32 weight columns per launch";
+        return KRR_EINVAL;
+    }
+    CUtensorMap t_map;
+    KRR_TRY(make_map(c, &t_map, t8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, rows_pad, c->m_pad));
+    TcParams p = base_params(c);
+    p.n_pad = c->n_pad;
+    p.n_test = n_test;
+    p.test_rows = rows_pad;
+    p.norms_a = tn;
+    p.norms_b = c->norms;
+    p.aw = A;
+    p.ldaw = lda;
+    p.p = p_cols;
+    p.part = part;
+    p.items = (rows_pad / BM) * (c->n_pad / BN);
+    return launch<KIND_F8, OP_PREDICT>(c, t_map, t_map, st->g_map, st->g_map, p);
+}
+
+}  // namespace krr
