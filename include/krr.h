@@ -60,7 +60,9 @@ typedef struct krr_options {
     int64_t tile;            /* b: tile edge, a multiple of 256 (default 1024) */
     int32_t mode;            /* krr_mode (default KRR_MODE_MIXED) */
     int32_t allow_fp8;       /* 1: E4M3 allowed for factor tiles (default 1) */
-    double eps;              /* adaptive-precision threshold (default 1e-4) */
+    double eps;              /* adaptive-precision threshold: a factor tile L_ik may be stored
+                                at unit roundoff u when u max|L_ik| max|L_kk| <= eps * lambda
+                                (default 6e-4) */
     double ir_tol;           /* refinement stops at ||R||_F / ||Y||_F <= ir_tol (default 1e-7) */
     int32_t ir_max;          /* maximum refinement iterations (default 30; 0 = none) */
     int32_t diag_fp64;       /* 1: diagonal-tile Cholesky in FP64, 0: FP32 (default 0) */
@@ -138,11 +140,12 @@ krr_status krr_factor(krr_ctx *ctx, double lambda, krr_factor_info *info);
  * solved against one factorisation.
  *   Y : n x p FP32, leading dimension ldy >= p, host or device (read only).
  *   A : n x p FP32 output, leading dimension lda >= p, host or device.
- * Refinement stops when ||R||_F / ||Y||_F <= ir_tol or when two successive
- * steps fail to halve it (the floor set by FP32 storage of K and A).
- * Errors: KRR_ESTATE (no factor), KRR_EINVAL, KRR_ENOCONV (the residual grew
- * above that of the first solve, or ir_max iterations passed; A holds the last
- * iterate), KRR_ECUDA.
+ * Refinement stops when ||R||_F / ||Y||_F <= ir_tol, when two successive
+ * steps fail to halve it, or when a step makes it worse (that step is undone):
+ * the floor set by FP32 storage of K and A.  A holds the best iterate.
+ * Errors: KRR_ESTATE (no factor), KRR_EINVAL, KRR_ENOCONV (non-finite
+ * residual, or ir_max iterations without reaching the tolerance or the
+ * floor), KRR_ECUDA.
  */
 krr_status krr_solve(krr_ctx *ctx, const float *Y, int64_t p, int64_t ldy, float *A, int64_t lda,
                      krr_solve_info *info);
@@ -186,6 +189,15 @@ krr_status krr_get_distances(krr_ctx *ctx, uint32_t *D, int64_t ldd);
  * ldk); the strictly-upper tiles are left untouched.  Host or device buffer.
  */
 krr_status krr_get_kernel(krr_ctx *ctx, float *K, int64_t ldk);
+
+/*
+ * Copies the stored factor to a caller buffer for testing: L is n x n FP32
+ * row-major (leading dimension ldl), lower triangular; every tile is read in
+ * its storage precision and de-scaled, so L L^T shows the backward error of
+ * the mixed-precision factorisation.  Entries above the diagonal are 0 for a
+ * host buffer and left untouched for a device buffer.  Errors: KRR_ESTATE.
+ */
+krr_status krr_get_factor(krr_ctx *ctx, float *L, int64_t ldl);
 
 /* Kernel classes timed by the optional profiler. */
 enum {

@@ -223,7 +223,7 @@ void krr_default_options(krr_options *opt) {
     opt->tile = 1024;
     opt->mode = KRR_MODE_MIXED;
     opt->allow_fp8 = 1;
-    opt->eps = 1e-4;
+    opt->eps = 6e-4;
     opt->ir_tol = 1e-7;
     opt->ir_max = 30;
     opt->diag_fp64 = 0;
@@ -301,6 +301,7 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->dabuf);
     dev_free(&c->pred_part);
     dev_free(&c->pred_out);
+    dev_free(&c->colsum);
     dev_free(&c->t8);
     dev_free(&c->tnorms);
     if (c->stage) cudaFree(c->stage);
@@ -361,7 +362,7 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
         // per-tile partial sums of K^2: one per 128 x 256 (tensor-core) or
         // 128 x 128 (CUDA-core) block
         const size_t per_tile = mixed(c) ? (size_t)(b / 128) * (b / 256) : (size_t)(b / 128) * (b / 128);
-        KRR_TRY(dev_alloc(c, &c->knorm2, (size_t)ntri * per_tile, "tile norms"));
+        KRR_TRY(dev_alloc(c, &c->knorm2, (size_t)2 * ntri * per_tile, "tile norms"));
         c->g_bytes = g_bytes;
         c->kd_bytes = kd_bytes;
     }
@@ -377,7 +378,7 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
     c->nt = nt;
     c->n_pad = n_pad;
     c->gamma = gamma;
-    const size_t red_count = 64 + (size_t)nt * (b / 64) + 16;
+    const size_t red_count = RED_MINPIV + (size_t)nt * (b / 64) + (size_t)nt + 16;
     KRR_TRY(dev_alloc(c, &c->red, red_count, "reduction buffer"));
     if (c->hred) cudaFreeHost(c->hred);
     c->hred = nullptr;
@@ -399,7 +400,7 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
     // tiles; compulsory bytes: the K tiles written once (FP32)
     prof_end(c, pr, 2.0 * (double)ntri * b * b * (double)m, (double)kd_bytes);
     KRR_TRY(check_launch(c, "build"));
-    launch_kernel_sumsq(c, c->red + 2);  // red[2] = ||K||_F^2
+    launch_kernel_sumsq(c, c->red + RED_KNORM2);
     KRR_TRY(check_launch(c, "kernel norm"));
     c->built = true;
     return KRR_OK;
@@ -564,6 +565,10 @@ krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *
         KRR_TRY(dev_alloc(c, &c->rbuf, (size_t)cnt, "residual"));
         c->vec_cap = cnt;
     }
+    if (c->colsum_cap < p) {
+        KRR_TRY(dev_alloc(c, &c->colsum, (size_t)p, "column sums"));
+        c->colsum_cap = p;
+    }
     KRR_TRY(load_rows_f32(c, Y, c->n, p, ldy, c->n_pad, c->ybuf));
     KRR_CUDA_TRY(c, cudaMemcpyAsync(c->abuf, c->ybuf, cnt * sizeof(float), cudaMemcpyDeviceToDevice, s));
     // compulsory bytes of one pair of sweeps: the stored factor read twice
@@ -587,7 +592,7 @@ krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *
         for (int it = 0;; ++it) {
             int rr = prof_begin(c, KRR_PROF_RESIDUAL);
             launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
-            launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red, s);
+            launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
             // the lower-triangle K tiles are read once by the row pass and
             // once by the column pass
             prof_end(c, rr, 2.0 * (double)c->n_pad * c->n_pad * p, 2.0 * (double)c->kd_bytes);
@@ -599,21 +604,29 @@ krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *
             if (it < 32) si.history[it] = rel;
             si.rel_residual = rel;
             si.iterations = it;
+            if (it == 0) best = rel;
+            if (!(rel == rel) || rel > 1e300) {  // NaN or overflow
+                st = KRR_ENOCONV;
+                break;
+            }
+            if (it > 0 && rel > best) {
+                // the last correction made things worse: the floor set by FP32
+                // storage of K and A is reached -- undo it and keep the best
+                launch_add_scaled(c->abuf, c->dabuf, -1.0f, cnt, s);
+                si.rel_residual = best;
+                si.converged = best <= c->opt.ir_tol ? 1 : 2;
+                break;
+            }
             if (rel <= c->opt.ir_tol) {
                 si.converged = 1;
                 break;
             }
             if (!refine) break;
-            if (it > 0 && !(rel <= si.history[0])) {  // diverging (or NaN)
-                st = KRR_ENOCONV;
-                break;
-            }
             if (it >= c->opt.ir_max) {
                 st = KRR_ENOCONV;
                 break;
             }
             // stagnation: two successive steps that do not halve the residual
-            // mean the floor set by FP32 storage of K and A has been reached
             if (rel > 0.5 * best) {
                 if (++stall >= 2) {
                     si.converged = 2;
@@ -627,7 +640,7 @@ krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *
             int sr = prof_begin(c, KRR_PROF_SOLVE);
             solve_inplace(c, c->dabuf, c->zbuf, p);
             prof_end(c, sr, sweep_flops, sweep_bytes);
-            launch_add_inplace(c->abuf, c->dabuf, cnt, s);
+            launch_add_scaled(c->abuf, c->dabuf, 1.0f, cnt, s);
             KRR_TRY(check_launch(c, "refinement step"));
         }
     }
@@ -817,5 +830,27 @@ extern "C" krr_status krr_get_profile(krr_ctx *c, krr_profile *out, int32_t rese
         }
     }
     if (reset) g_launches.store(0);
+    return KRR_OK;
+}
+
+extern "C" krr_status krr_get_factor(krr_ctx *c, float *L, int64_t ldl) {
+    if (!c) return KRR_EINVAL;
+    if (!c->factored) {
+        c->last_error = "krr_get_factor: no factorisation";
+        return KRR_ESTATE;
+    }
+    if (!L || ldl < c->n) return KRR_EINVAL;
+    const bool dev = is_device_ptr(L);
+    float *dst = L;
+    const size_t bytes = (size_t)c->n * ldl * sizeof(float);
+    if (!dev) {
+        KRR_TRY(stage(c, bytes));
+        dst = (float *)c->stage;
+        KRR_CUDA_TRY(c, cudaMemsetAsync(dst, 0, bytes, c->stream));
+    }
+    launch_factor_to_dense(c, dst, ldl);
+    KRR_TRY(check_launch(c, "factor to dense"));
+    if (!dev) KRR_CUDA_TRY(c, cudaMemcpyAsync(L, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return KRR_OK;
 }

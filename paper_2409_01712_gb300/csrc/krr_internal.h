@@ -30,6 +30,13 @@ __host__ __device__ inline void tri_decode(int64_t t, int64_t *i, int64_t *j) {
     *j = t - r * (r + 1) / 2;
 }
 
+// Slots of the small FP64 reduction buffer Ctx::red.
+constexpr int RED_RNORM = 0;     // [0] ||R||_F^2, [1] ||Y||_F^2 of the last residual
+constexpr int RED_KNORM2 = 2;    // ||K||_F^2
+constexpr int RED_KSUM = 3;      // sum of the entries of K
+constexpr int RED_KSHIFT = 4;    // mean off-diagonal entry of K (residual shift)
+constexpr int RED_MINPIV = 64;   // nt * (b / 64) block minimum pivots, then nt max|L_kk| bounds
+
 // Storage precision of an off-diagonal factor tile (values of the
 // KRR_PREC_* enum of krr.h).
 struct TileDesc {
@@ -98,7 +105,9 @@ struct Ctx {
     double *rbuf = nullptr;                  // n_pad x p residual (FP64)
     float *abuf = nullptr;                   // n_pad x p current solution
     float *dabuf = nullptr;                  // n_pad x p correction
-    double *red = nullptr;                   // reductions (norms), small
+    double *red = nullptr;                   // reductions (norms), small; slots RED_*
+    double *colsum = nullptr;                // column sums of the current iterate (FP64)
+    int64_t colsum_cap = 0;
     double *hred = nullptr;                  // pinned host mirror of red
     int64_t vec_cap = 0;                     // capacity in elements of the n_pad x p buffers
     float *pred_part = nullptr;              // predict partial products
@@ -190,12 +199,15 @@ void launch_fill_zero(void *p, size_t bytes, cudaStream_t s);
 void launch_reduce_norms(const double *r, const float *y, int64_t n, int64_t p, double *out,
                          cudaStream_t s);
 void launch_axpy_r(const double *r, float *dst, int64_t count, cudaStream_t s);
-void launch_add_inplace(float *a, const float *da, int64_t count, cudaStream_t s);
+void launch_add_scaled(float *a, const float *da, float alpha, int64_t count, cudaStream_t s);
 void launch_predict_reduce(const float *part, int64_t nblk, int64_t rows_pad, int64_t n_test,
                            int64_t p, float *out, int64_t ldo, cudaStream_t s);
 void launch_copy_rows(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t rows,
                       int64_t cols, int64_t rows_pad, cudaStream_t s);
+// out[0] = ||K||_F^2, out[1] = sum of K, out[2] = mean off-diagonal entry.
 void launch_kernel_sumsq(Ctx *c, double *out);
+// Dense lower-triangular copy of the stored factor into dst (n x n, device).
+void launch_factor_to_dense(Ctx *c, float *dst, int64_t ld);
 
 // ---------------------------------------------------------------------------
 // Tensor-core kernels (tc_gemm.cu)

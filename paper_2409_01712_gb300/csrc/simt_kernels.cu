@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) build_simt_kernel(const float *gf, const 
                           acc);
     float *kt = Kd + tri_index(ti, tj) * b * b;
     uint32_t *dt = Dd ? Dd + tri_index(ti, tj) * b * b : nullptr;
-    double ss = 0.0;
+    double ss = 0.0, s1 = 0.0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int64_t lr = sm * SG_BM + sg_row(i), gi = ti * b + lr;
@@ -261,16 +261,27 @@ __global__ void __launch_bounds__(256) build_simt_kernel(const float *gf, const 
             kt[lr * b + lc] = kv;
             if (dt) dt[lr * b + lc] = (gi < n && gj < n) ? (uint32_t)d : 0u;
             ss += (double)kv * (double)kv;
+            s1 += (double)kv;
         }
     }
-    __shared__ double red[8];
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_down_sync(0xffffffffu, ss, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __shared__ double red[16];
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_down_sync(0xffffffffu, ss, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = ss;
+        red[8 + (threadIdx.x >> 5)] = s1;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double s = 0;
-        for (int w = 0; w < 8; ++w) s += red[w];
-        knorm_part[blockIdx.x] = s;
+        double a = 0, b1 = 0;
+        for (int w = 0; w < 8; ++w) {
+            a += red[w];
+            b1 += red[8 + w];
+        }
+        knorm_part[blockIdx.x] = a;
+        knorm_part[gridDim.x + blockIdx.x] = b1;
     }
 }
 
@@ -281,26 +292,45 @@ void launch_build_simt(Ctx *c) {
         c->gf, c->norms, c->m_pad, c->n, c->b, (float)c->gamma, c->Kd, c->Dd, c->knorm2);
 }
 
-// Deterministic sum of the per-CTA (or per-tile) K^2 partials into
-// out[0] = ||K||_F^2 with off-diagonal tiles counted twice.
+// Deterministic sums of the per-block partials: out[0] = ||K||_F^2 and
+// out[1] = sum of all entries of K (off-diagonal tiles counted twice), and
+// out[2] = the mean off-diagonal entry c used to shift the refinement
+// residual.  part holds ntri * per_tile sums of K^2 then as many sums of K.
 __global__ void kernel_sumsq_kernel(const double *part, int64_t ntri, int64_t per_tile,
-                                    double *out) {
-    __shared__ double red[32];
-    double s = 0.0;
+                                    int64_t n_pad, double *out) {
+    __shared__ double red[64];
+    double s = 0.0, s1 = 0.0;
+    const double *part1 = part + ntri * per_tile;
     for (int64_t t = threadIdx.x; t < ntri; t += blockDim.x) {
         int64_t i, j;
         tri_decode(t, &i, &j);
-        double ts = 0.0;
-        for (int64_t q = 0; q < per_tile; ++q) ts += part[t * per_tile + q];
+        double ts = 0.0, ts1 = 0.0;
+        for (int64_t q = 0; q < per_tile; ++q) {
+            ts += part[t * per_tile + q];
+            ts1 += part1[t * per_tile + q];
+        }
         s += (i == j) ? ts : 2.0 * ts;
+        s1 += (i == j) ? ts1 : 2.0 * ts1;
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = s;
+        red[32 + (threadIdx.x >> 5)] = s1;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        double tot = 0.0, tot1 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            tot += red[w];
+            tot1 += red[32 + w];
+        }
         out[0] = tot;
+        out[1] = tot1;
+        const double nn = (double)n_pad;
+        out[2] = nn > 1 ? (tot1 - nn) / (nn * nn - nn) : 0.0;
     }
 }
 
@@ -593,6 +623,27 @@ static void diag_factor_tile(Ctx *c, T *W, T *Winv, T *tmp, int64_t k, double *m
     }
 }
 
+// sqrt of the largest diagonal entry of W_kk: a bound on every |L_kk| entry
+// (|L_rc| <= sqrt(W_rr) for a Cholesky factor).
+__global__ void diag_max_kernel(const float *w, int64_t b, double *out) {
+    __shared__ float red[32];
+    float mx = 0.f;
+    for (int64_t r = threadIdx.x; r < b; r += blockDim.x) mx = fmaxf(mx, w[r * b + r]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = fmaxf(m, red[q]);
+        *out = sqrt((double)fmaxf(m, 0.f));
+    }
+}
+
+__global__ void f64_to_f32_kernel(const double *src, float *dst, int64_t count) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < count) dst[e] = (float)src[e];
+}
+
 __global__ void min_pivot_kernel(const double *mp, int n, DevErrors *err) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double m = err->min_pivot;
@@ -606,12 +657,15 @@ krr_status diag_step(Ctx *c, int64_t k) {
     float *wd = c->Wd + k * bb;
     float *linv = c->Linv + k * bb;
     const int nq = (int)(b / DNB);
-    double *minpiv = c->red + 64;  // nt * nq doubles reserved after the norm slots
+    double *minpiv = c->red + RED_MINPIV;
+    double *lkk = c->red + RED_MINPIV + c->nt * nq;
     unsigned g = cdiv(bb, 256);
     if (k == 0) count_launch(), copy_add_diag_kernel<<<g, 256, 0, s>>>(c->Kd, wd, bb, (float)c->lambda, b);
+    count_launch(), diag_max_kernel<<<1, 256, 0, s>>>(wd, b, lkk + k);
     if (c->opt.diag_fp64) {
         count_launch(), f32_to_f64_kernel<<<g, 256, 0, s>>>(wd, c->diag64, bb, 0.0, b);
         diag_factor_tile<double>(c, c->diag64, c->diag64_inv, c->diag64_inv + bb, k, minpiv);
+        count_launch(), f64_to_f32_kernel<<<g, 256, 0, s>>>(c->diag64, wd, bb);
         count_launch(), finish_inverse_kernel<<<g, 256, 0, s>>>(c->diag64_inv, linv,
                                                 c->Linv_hi ? c->Linv_hi + k * bb : nullptr,
                                                 c->Linv_lo ? c->Linv_lo + k * bb : nullptr, bb);
@@ -627,12 +681,14 @@ krr_status diag_step(Ctx *c, int64_t k) {
 
 // ----------------------------------------------------------------------------
 // Adaptive precision of one factor column (mixed mode).
-// For tile (i, k), i > k, with F = ||L_ik||_F and the kernel norm ||K||_F:
-// the tile may be stored at unit roundoff u_p when u_p F <= eps ||K||_F / NT
-// (Frobenius form of the tile-centric adaptive-precision rule the paper
-// cites); the lowest allowed of E4M3 (u = 2^-4), FP16 (u = 2^-11) is taken,
-// else FP32.  FP16/E4M3 tiles carry a power-of-two scale so the largest
-// entry sits near the top of the format's range.
+// Tile (i, k), i > k, is stored at unit roundoff u_p when
+//     u_p * max|L_ik| * max|L_kk| <= eps * lambda,
+// the lowest allowed of E4M3 (u = 2^-4) and FP16 (u = 2^-11), else FP32.
+// Rounding L_ik perturbs L L^T in block (i, k) by about u_p |L_ik| |L_kk|;
+// the refinement converges while that stays well below lambda, the smallest
+// possible eigenvalue of K + lambda I.  max|L_kk| is bounded by
+// sqrt(max_r W_kk[r, r]) from the diagonal step.  FP16/E4M3 tiles carry a
+// power-of-two scale so the largest entry sits near the top of the format.
 // ----------------------------------------------------------------------------
 __global__ void column_stats_kernel(const float *col, int64_t bb, int chunks, double *part_ss,
                                     float *part_max) {
@@ -673,23 +729,23 @@ __device__ inline float pow2_scale(float mx, float top) {
 }
 
 __global__ void column_decide_kernel(int64_t k, int64_t nt, int64_t bb, int chunks,
-                                     const double *part_ss, const float *part_max, double eps,
-                                     const double *knorm2_total, int allow_fp8, TileDesc *ltab,
+                                     const double *part_ss, const float *part_max, double thresh,
+                                     const double *lkk_max, int allow_fp8, TileDesc *ltab,
                                      uint8_t *precmap, DevErrors *err) {
     const int64_t tile = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tile >= nt - k - 1) return;
-    const double thresh = eps * sqrt(*knorm2_total) / (double)nt;
     double ss = 0;
     float mx = 0;
     for (int q = 0; q < chunks; ++q) {
         ss += part_ss[tile * chunks + q];
         mx = fmaxf(mx, part_max[tile * chunks + q]);
     }
-    const double f = sqrt(ss);
+    const double w = (double)mx * lkk_max[k];
     int prec;
-    if (allow_fp8 && 0.0625 * f <= thresh) prec = KRR_PREC_E4M3;
-    else if (0x1p-11 * f <= thresh) prec = KRR_PREC_FP16;
+    if (allow_fp8 && 0.0625 * w <= thresh) prec = KRR_PREC_E4M3;
+    else if (0x1p-11 * w <= thresh) prec = KRR_PREC_FP16;
     else prec = KRR_PREC_FP32;
+    (void)ss;
     const int64_t i = k + 1 + tile;
     TileDesc d;
     d.prec = prec;
@@ -745,8 +801,10 @@ void launch_column_cast(Ctx *c, int64_t k) {
     float *part_max = c->colmax;
     count_launch(), column_stats_kernel<<<dim3(chunks, (unsigned)u), 256, 0, c->stream>>>(c->colbuf, bb, chunks,
                                                                           part_ss, part_max);
+    const double thresh = c->opt.eps * c->lambda;
+    const double *lkk = c->red + RED_MINPIV + c->nt * (c->b / 64);
     count_launch(), column_decide_kernel<<<cdiv(u, 128), 128, 0, c->stream>>>(k, c->nt, bb, chunks, part_ss, part_max,
-                                                               c->opt.eps, c->red + 2, c->opt.allow_fp8,
+                                                               thresh, lkk, c->opt.allow_fp8,
                                                                c->ltab, c->precmap, c->derr);
     count_launch(), column_write_kernel<<<dim3(64, (unsigned)u), 256, 0, c->stream>>>(k, bb, c->colbuf, c->ltab,
                                                                       c->pool, c->pan_hi, c->pan_lo,
@@ -757,7 +815,7 @@ void launch_kernel_sumsq(Ctx *c, double *out) {
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     const int64_t per = (c->opt.mode == KRR_MODE_FP32) ? (c->b / SG_BM) * (c->b / SG_BM)
                                                        : (c->b / 128) * (c->b / 256);
-    count_launch(), kernel_sumsq_kernel<<<1, 1024, 0, c->stream>>>(c->knorm2, ntri, per, out);
+    count_launch(), kernel_sumsq_kernel<<<1, 1024, 0, c->stream>>>(c->knorm2, ntri, per, c->n_pad, out);
 }
 
 // ----------------------------------------------------------------------------
@@ -924,7 +982,9 @@ void solve_inplace(Ctx *c, float *x, float *tmp, int64_t p) {
 __global__ void __launch_bounds__(256) residual_n_kernel(int64_t nt, int64_t b, float lambda,
                                                          const float *Kd, const float *y,
                                                          const float *a, double *r, int64_t p,
-                                                         int q0, int pc) {
+                                                         int q0, int pc, const double *shift,
+                                                         const double *colsum) {
+    const float cs = (float)*shift;
     extern __shared__ float ash[];  // b x pc (block j of a)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t i = blockIdx.y;
@@ -944,7 +1004,7 @@ __global__ void __launch_bounds__(256) residual_n_kernel(int64_t nt, int64_t b, 
 #pragma unroll
             for (int q = 0; q < PC; ++q) acc[q] = 0.f;
             for (int64_t cidx = lane; cidx < b; cidx += 32) {
-                const float kv = kt[row * b + cidx];
+                const float kv = kt[row * b + cidx] - cs;
                 const float *ar = ash + cidx * pc;
 #pragma unroll
                 for (int q = 0; q < PC; ++q)
@@ -963,14 +1023,16 @@ __global__ void __launch_bounds__(256) residual_n_kernel(int64_t nt, int64_t b, 
         const int64_t row = i * b + rbase + warp + 8 * t;
         if (lane < pc) {
             const int64_t e = row * p + q0 + lane;
-            r[e] = (double)y[e] - (double)lambda * (double)a[e] - rowacc[t];
+            r[e] = (double)y[e] - (double)lambda * (double)a[e] - rowacc[t] -
+                   (double)cs * colsum[q0 + lane];
         }
     }
 }
 
 __global__ void __launch_bounds__(128) residual_t_kernel(int64_t nt, int64_t b, const float *Kd,
                                                          const float *a, double *r, int64_t p,
-                                                         int q0, int pc) {
+                                                         int q0, int pc, const double *shift) {
+    const float cs = (float)*shift;
     extern __shared__ float ash[];  // b x pc (block j of a)
     const int64_t i = blockIdx.y;
     const int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -987,7 +1049,7 @@ __global__ void __launch_bounds__(128) residual_t_kernel(int64_t nt, int64_t b, 
 #pragma unroll
         for (int q = 0; q < PC; ++q) acc[q] = 0.f;
         for (int64_t rr = 0; rr < b; ++rr) {
-            const float kv = kt[rr * b + cidx];
+            const float kv = kt[rr * b + cidx] - cs;
             const float *ar = ash + rr * pc;
 #pragma unroll
             for (int q = 0; q < PC; ++q)
@@ -999,6 +1061,25 @@ __global__ void __launch_bounds__(128) residual_t_kernel(int64_t nt, int64_t b, 
     for (int q = 0; q < pc; ++q) r[(i * b + cidx) * p + q0 + q] -= acc64[q];
 }
 
+// Column sums of a (n x p) in FP64, one block per column.
+__global__ void colsum_kernel(const float *a, int64_t n, int64_t p, double *out) {
+    __shared__ double red[32];
+    const int64_t q = blockIdx.x;
+    double s = 0.0;
+    for (int64_t r = threadIdx.x; r < n; r += blockDim.x) s += (double)a[r * p + q];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        out[q] = t;
+    }
+}
+
+// K A = (K - c 1 1^T) A + c 1 (1^T A): the shifted products are small, so
+// FP32 products and partial sums lose far less to cancellation; c 1^T A is
+// formed in FP64.  c = the mean off-diagonal entry of K (red[RED_KSHIFT]).
 void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
     const int64_t b = c->b, nt = c->nt;
     const int pcmax = (int)std::max<int64_t>(1, std::min<int64_t>(PC, 32768 / b));
@@ -1008,13 +1089,15 @@ void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t 
         cudaFuncSetAttribute(residual_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
+    const double *shift = c->red + RED_KSHIFT;
+    count_launch(), colsum_kernel<<<(unsigned)p, 512, 0, c->stream>>>(a, c->n_pad, p, c->colsum);
     for (int q0 = 0; q0 < p; q0 += pcmax) {
         const int pc = (int)std::min<int64_t>(pcmax, p - q0);
         const size_t sh = (size_t)b * pc * sizeof(float);
         count_launch(), residual_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)nt), 256, sh, c->stream>>>(
-            nt, b, (float)c->lambda, c->Kd, y, a, r, p, q0, pc);
+            nt, b, (float)c->lambda, c->Kd, y, a, r, p, q0, pc, shift, c->colsum);
         count_launch(), residual_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)nt), 128, sh, c->stream>>>(
-            nt, b, c->Kd, a, r, p, q0, pc);
+            nt, b, c->Kd, a, r, p, q0, pc, shift);
     }
 }
 
@@ -1053,12 +1136,12 @@ void launch_axpy_r(const double *r, float *dst, int64_t count, cudaStream_t s) {
     count_launch(), d2f_kernel<<<cdiv(count, 256), 256, 0, s>>>(r, dst, count);
 }
 
-__global__ void add_kernel(float *a, const float *da, int64_t count) {
+__global__ void add_kernel(float *a, const float *da, float alpha, int64_t count) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e < count) a[e] += da[e];
+    if (e < count) a[e] += alpha * da[e];
 }
-void launch_add_inplace(float *a, const float *da, int64_t count, cudaStream_t s) {
-    count_launch(), add_kernel<<<cdiv(count, 256), 256, 0, s>>>(a, da, count);
+void launch_add_scaled(float *a, const float *da, float alpha, int64_t count, cudaStream_t s) {
+    count_launch(), add_kernel<<<cdiv(count, 256), 256, 0, s>>>(a, da, alpha, count);
 }
 
 // dst (rows_pad x cols, dense) <- src rows (zero padding rows >= rows).
@@ -1076,5 +1159,41 @@ void launch_copy_rows(const float *src, int64_t lds, float *dst, int64_t ldd, in
 }
 
 void launch_fill_zero(void *p, size_t bytes, cudaStream_t s) { cudaMemsetAsync(p, 0, bytes, s); }
+
+// Dense lower-triangular copy of the stored factor (diagonal tiles from Wd,
+// off-diagonal tiles from the pool in their precision, de-scaled).
+__global__ void factor_to_dense_kernel(const float *Wd, const uint8_t *pool, const TileDesc *ltab,
+                                       int64_t b, int64_t n, float *dst, int64_t ld) {
+    const int64_t t = blockIdx.y;
+    int64_t ti, tj;
+    tri_decode(t, &ti, &tj);
+    const uint8_t *base;
+    int prec;
+    float inv_scale = 1.f;
+    if (ti == tj) {
+        base = reinterpret_cast<const uint8_t *>(Wd + ti * b * b);
+        prec = KRR_PREC_FP32;
+    } else {
+        const TileDesc d = ltab[off_index(ti, tj)];
+        base = pool + d.offset;
+        prec = d.prec;
+        if (prec != KRR_PREC_FP32) inv_scale = 1.f / d.scale;
+    }
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < b * b;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lr = e / b, lc = e % b;
+        const int64_t r = ti * b + lr, q = tj * b + lc;
+        if (r >= n || q >= n) continue;
+        float v = load_l(base, prec, e) * inv_scale;
+        if (ti == tj && lc > lr) v = 0.f;
+        dst[r * ld + q] = v;
+    }
+}
+
+void launch_factor_to_dense(Ctx *c, float *dst, int64_t ld) {
+    const int64_t ntri = c->nt * (c->nt + 1) / 2;
+    count_launch(), factor_to_dense_kernel<<<dim3(64, (unsigned)ntri), 256, 0, c->stream>>>(
+        c->Wd, c->pool, c->ltab, c->b, c->n, dst, ld);
+}
 
 }  // namespace krr

@@ -303,7 +303,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
         const int64_t tidx = tri_index(w.i, w.j);
         float *krow = p.Kd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN;
         uint32_t *drow = p.Dd ? p.Dd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN : nullptr;
-        double ss = 0.0;
+        double ss = 0.0, s1 = 0.0;
         for (int ch = 0; ch < BN / 16; ++ch) {
             float v[16];
             tmem_ld16(tacc + ch * 16, v);
@@ -318,6 +318,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                 kv[e] = real ? expf(-p.gamma * (float)d) : (gi == gj ? 1.f : 0.f);
                 dv[e] = real ? (uint32_t)d : 0u;
                 ss += (double)kv[e] * (double)kv[e];
+                s1 += (double)kv[e];
             }
             float4 *dst = reinterpret_cast<float4 *>(krow + ch * 16);
 #pragma unroll
@@ -328,14 +329,22 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                 for (int e = 0; e < 4; ++e) dd[e] = make_uint4(dv[4 * e], dv[4 * e + 1], dv[4 * e + 2], dv[4 * e + 3]);
             }
         }
-        // deterministic per-block sum of K^2: warp sums, then the four warps in order
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        if ((row & 31) == 0) red_s[row >> 5] = ss;
+        // deterministic per-block sums of K^2 and K: warp sums, then the four
+        // warps in order.  Layout: all K^2 partials, then all K partials.
+        for (int o = 16; o > 0; o >>= 1) {
+            ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if ((row & 31) == 0) {
+            red_s[row >> 5] = ss;
+            red_s[4 + (row >> 5)] = s1;
+        }
         epi_bar();
         if (row == 0) {
             const int64_t sub_per_tile = (b / BM) * (b / BN);
-            p.knorm_part[tidx * sub_per_tile + w.sm * (b / BN) + w.sn] =
-                red_s[0] + red_s[1] + red_s[2] + red_s[3];
+            const int64_t slot = tidx * sub_per_tile + w.sm * (b / BN) + w.sn;
+            p.knorm_part[slot] = red_s[0] + red_s[1] + red_s[2] + red_s[3];
+            p.knorm_part[p.items + slot] = red_s[4] + red_s[5] + red_s[6] + red_s[7];
         }
     } else if (OP == OP_PREDICT) {
         const int64_t gi = w.i * BM + row;  // test row
@@ -464,7 +473,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red_s = reinterpret_cast<double *>(tmem_slot + 2);
-    int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 4);
+    int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 8);
     float *aw_s = reinterpret_cast<float *>(nb_s + BN);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -152,3 +152,29 @@ def test_errors():
     with pytest.raises(KRRError) as e:
         KRR(tile=300)
     assert e.value.status == krrmod.EINVAL
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_factor_backward_error(mode):
+    """L L^T reconstructs K + lambda I: FP32 mode to FP32 rounding; mixed mode
+    within the adaptive-precision budget (spectral error well below lambda,
+    which keeps the refinement contracting)."""
+    prob = _problem(1536, 512, 1, 10, seed=21)
+    lam = 0.1
+    with KRR(tile=256, mode=mode) as model:
+        model.build_kernel(_to(prob["G"]), 1.0 / 512)
+        model.factor(lam)
+        k = model.kernel().astype(np.float64)
+        l = model.factor_matrix().astype(np.float64)
+        pmap = model.precision_map()
+    k = np.tril(k) + np.tril(k, -1).T
+    m = k + lam * np.eye(len(k))
+    e = l @ l.T - m
+    assert np.array_equal(l, np.tril(l))
+    if mode == "fp32":
+        assert np.linalg.norm(e) / np.linalg.norm(m) <= 1e-6
+    else:
+        assert np.linalg.norm(e, 2) <= 0.1 * lam
+        # the mean component sits in tile column 0: it needs FP32; the rest FP16
+        assert np.all(pmap[1:, 0] == 1), pmap
+        assert np.all(pmap[np.tril_indices(len(pmap), -1)][len(pmap) - 1:] >= 1)
