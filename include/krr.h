@@ -199,6 +199,28 @@ krr_status krr_get_kernel(krr_ctx *ctx, float *K, int64_t ldk);
  */
 krr_status krr_get_factor(krr_ctx *ctx, float *L, int64_t ldl);
 
+/*
+ * Predict without allocating.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory at call time --
+ * code recorded into a CUDA graph, processes whose device memory is owned up
+ * front by another allocator, or latency-critical callers that must not enter
+ * the driver's allocator.  It computes the same Yt = K_test A as
+ * krr_predict() with the same kernels, but every working buffer lives in one
+ * file-scope device array of fixed size (about 12.6 MB, present on every GPU
+ * that loads the library until the process exits), so it calls no
+ * cudaMalloc / cudaFree.
+ *   T, A, Yt : device pointers only (host pointers give KRR_EINVAL).
+ *   Limits   : 1 <= n_test <= 256, 1 <= p <= 8, padded N <= 131072, padded
+ *              M <= 16384, context in KRR_MODE_MIXED; otherwise KRR_EINVAL.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams or contexts) race on it.
+ * Errors: KRR_ESTATE (no kernel built), KRR_EINVAL, KRR_ECUDA.
+ */
+krr_status krr_predict_noalloc(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt,
+                               const float *A, int64_t lda, int64_t p, float *Yt, int64_t ldyt);
+
 /* Kernel classes timed by the optional profiler. */
 enum {
     KRR_PROF_PACK = 0,     /* genotype packing and norms */

@@ -31,7 +31,8 @@ PREC_NAMES = {0: "fp64", 1: "fp32", 2: "fp16", 3: "e4m3", 255: "-"}
 # Every symbol include/krr.h declares (checked by the CPU test suite).
 EXPORTED = ["krr_default_options", "krr_create", "krr_build_kernel", "krr_factor", "krr_solve",
             "krr_predict", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
-            "krr_get_kernel", "krr_get_factor", "krr_set_profiling", "krr_get_profile", "krr_sync", "krr_last_error",
+            "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_set_profiling",
+            "krr_get_profile", "krr_sync", "krr_last_error",
             "krr_destroy"]
 PROF_CLASSES = ["pack", "build", "diag", "trsm", "cast", "update", "solve", "residual", "predict"]
 
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH):
     lib.krr_get_distances.argtypes = [vp, vp, i64]
     lib.krr_get_kernel.argtypes = [vp, vp, i64]
     lib.krr_get_factor.argtypes = [vp, vp, i64]
+    lib.krr_predict_noalloc.argtypes = [vp, vp, i64, i64, vp, i64, i64, vp, i64]
     lib.krr_set_profiling.argtypes = [vp, i32]
     lib.krr_get_profile.argtypes = [vp, ctypes.POINTER(Profile), i32]
     lib.krr_sync.argtypes = [vp]
@@ -99,7 +101,8 @@ def load_library(path: str = LIB_PATH):
     lib.krr_destroy.restype = None
     for name in ("krr_create", "krr_build_kernel", "krr_factor", "krr_solve", "krr_predict",
                  "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
-                 "krr_get_kernel", "krr_get_factor", "krr_set_profiling", "krr_get_profile", "krr_sync"):
+                 "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_set_profiling",
+            "krr_get_profile", "krr_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
