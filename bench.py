@@ -35,11 +35,13 @@ CONFIGS = {
     "c1": (2048, 512, 1, 512, 256),
     "c2": (32768, 8192, 10, 4096, 1024),
     "c3": (131072, 16384, 20, 4096, 1024),
+    # small case for ncu captures (about 1.5 GB on the device, K tiles > L2)
+    "p1": (16384, 4096, 8, 1024, 1024),
 }
 LAMBDA = 0.1
 SEED = 2409017120
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "update_kernel_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "update_kernel_traffic.txt")
 TC_SRC = os.path.join(ROOT, "paper_2409_01712_gb300", "csrc", "tc_gemm.cu")
 
 
@@ -62,17 +64,22 @@ def peaks():
 
 
 def update_traffic():
-    """DRAM bytes per update launch from the committed ncu summary, if it was
-    taken on the current tensor-core source (else None)."""
+    """DRAM bytes per algorithmic flop of the trailing-update kernel from the
+    committed ncu summary (key = value lines), if it was taken on the current
+    tensor-core source; else None."""
     try:
+        rec = {}
         with open(TRAFFIC_FILE) as f:
-            rec = json.load(f)
+            for line in f:
+                if "=" in line and not line.lstrip().startswith("#"):
+                    k, v = line.split("=", 1)
+                    rec[k.strip()] = v.strip()
         with open(TC_SRC, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
         if rec.get("tc_gemm_sha256") != sha:
             return None
-        return rec.get("bytes_per_launch")
-    except (OSError, ValueError):
+        return float(rec["dram_bytes_per_flop"])
+    except (OSError, ValueError, KeyError):
         return None
 
 
@@ -256,7 +263,10 @@ def run_ours(args):
     if upd["count"] > 0 and upd["ms"] > 0:
         ach = upd["flops"] / (upd["ms"] / 1e3) / 1e12
         peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")))
-        traffic = update_traffic() if args.mode == "mixed" else None
+        bpf = update_traffic() if args.mode == "mixed" else None
+        # the capture is of a small case: scale its bytes per flop to the
+        # average launch here (operand and C traffic grow with the tiles)
+        traffic = bpf * upd["flops"] / upd["count"] if bpf else None
         roof = {"bound": "tensor", "kernel": "tc_kernel<F16, OP_UPDATE> (trailing update)",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "peak_source": f"{pk_kind}: bf16 dense sustained (FP16 dense runs at the same rate)",

@@ -206,7 +206,7 @@ krr_status krr_get_factor(krr_ctx *ctx, float *L, int64_t ldl);
  * front by another allocator, or latency-critical callers that must not enter
  * the driver's allocator.  It computes the same Yt = K_test A as
  * krr_predict() with the same kernels, but every working buffer lives in one
- * file-scope device array of fixed size (about 12.6 MB, present on every GPU
+ * file-scope device array of fixed size (about 16.8 MB, present on every GPU
  * that loads the library until the process exits), so it calls no
  * cudaMalloc / cudaFree.
  *   T, A, Yt : device pointers only (host pointers give KRR_EINVAL).
@@ -220,6 +220,28 @@ krr_status krr_get_factor(krr_ctx *ctx, float *L, int64_t ldl);
  */
 krr_status krr_predict_noalloc(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt,
                                const float *A, int64_t lda, int64_t p, float *Yt, int64_t ldyt);
+
+/*
+ * Gradient of the held-out loss with respect to the hyperparameters (the
+ * paper picks gamma and alpha by cross-validation, Sec. III; the gradient
+ * itself is not in the paper).  With M = K + lambda I, A = M^-1 Y (the
+ * caller's current solution), Yhat = K_test A and
+ *     loss = ||Yhat - Yt||_F^2 / (n_test p):
+ *   G_p = 2 (Yhat - Yt) / (n_test p);  B = K_test^T G_p;  Z = M^-1 B (the
+ *   stored factor with refinement);
+ *   d loss / d log lambda = -lambda <Z, A>;
+ *   d loss / d log gamma  = gamma ( sum_ij D_ij K_ij (Z A^T)_ij
+ *                                  - sum_tj D_tj K_tj (G_p A^T)_tj ),
+ * with D the exact squared distances, recomputed on the tensor cores.
+ *   T  : n_test x m int8 held-out genotypes (ldt >= m), host or device.
+ *   Yt : n_test x p FP32 held-out phenotypes (ldy >= p), host or device.
+ *   A  : n x p FP32 weights from krr_solve (lda >= p), host or device.
+ *   out: host double[3] = {loss, d loss / d log gamma, d loss / d log lambda}.
+ * Needs a factorisation in KRR_MODE_MIXED; 1 <= p <= 16.
+ * Errors: KRR_ESTATE, KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA.
+ */
+krr_status krr_grad_hyper(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt, const float *Yt,
+                          int64_t ldy, const float *A, int64_t lda, int64_t p, double *out);
 
 /* Kernel classes timed by the optional profiler. */
 enum {

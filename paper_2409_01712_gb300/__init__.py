@@ -5,6 +5,7 @@ include/krr.h); this package only marshals arguments (``KRR``) and draws
 seeded synthetic inputs (``inputs``).
 """
 from . import inputs  # noqa: F401
+from .autograd import held_out_loss  # noqa: F401
 from .krr import KRR, KRRError, load_library  # noqa: F401
 
-__all__ = ["KRR", "KRRError", "inputs", "load_library"]
+__all__ = ["KRR", "KRRError", "held_out_loss", "inputs", "load_library"]

@@ -183,6 +183,7 @@ void free_factor(Ctx *c) {
     dev_free(&c->W);
     dev_free(&c->Wd);
     dev_free(&c->Linv);
+    dev_free(&c->LinvT);
     dev_free(&c->Linv_hi);
     dev_free(&c->Linv_lo);
     dev_free(&c->diag64);
@@ -214,6 +215,116 @@ void free_build(Ctx *c) {
 
 bool mixed(const Ctx *c) { return c->opt.mode == KRR_MODE_MIXED; }
 
+}  // namespace
+
+namespace {
+// Allocates (or keeps) the n_pad x p work vectors of the solve.
+krr_status ensure_vectors(Ctx *c, int64_t p) {
+    const int64_t cnt = c->n_pad * p;
+    if (c->vec_cap < cnt) {
+        KRR_TRY(dev_alloc(c, &c->ybuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->zbuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->abuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->dabuf, (size_t)cnt, "solve vectors"));
+        KRR_TRY(dev_alloc(c, &c->rbuf, (size_t)cnt, "residual"));
+        c->vec_cap = cnt;
+    }
+    if (c->colsum_cap < p) {
+        KRR_TRY(dev_alloc(c, &c->colsum, (size_t)p, "column sums"));
+        c->colsum_cap = p;
+    }
+    const size_t rp = (size_t)c->nt * c->nt * c->b * (size_t)std::min<int64_t>(p, 32);
+    if (c->res_part_cap < rp) {
+        KRR_TRY(dev_alloc(c, &c->res_part, rp, "residual partials"));
+        c->res_part_cap = rp;
+    }
+    return KRR_OK;
+}
+
+// A = (K + lambda I)^-1 ybuf into abuf with the stored factor, then
+// refinement (mixed mode) or one residual for the report (info != NULL).
+krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
+    cudaStream_t s = c->stream;
+    const int64_t cnt = c->n_pad * p;
+    KRR_CUDA_TRY(c, cudaMemcpyAsync(c->abuf, c->ybuf, cnt * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // compulsory bytes of one pair of sweeps: the stored factor read twice
+    // (diagonal inverses in FP32 plus the off-diagonal pool) and the vectors
+    const double pool_used = mixed(c) ? (double)c->herr->pool_cursor
+                                      : (double)c->nt * (c->nt - 1) / 2 * c->b * c->b * 4.0;
+    const double factor_bytes_all = pool_used + (double)c->nt * c->b * c->b * 4.0;
+    const double sweep_bytes = 2.0 * factor_bytes_all + 4.0 * (double)cnt * 4.0;
+    const double sweep_flops = 2.0 * 2.0 * (double)c->n_pad * c->n_pad * p;
+    int pr = prof_begin(c, KRR_PROF_SOLVE);
+    solve_inplace(c, c->abuf, c->zbuf, p);
+    prof_end(c, pr, sweep_flops, sweep_bytes);
+    KRR_TRY(check_launch(c, "solve"));
+    krr_solve_info si;
+    memset(&si, 0, sizeof(si));
+    krr_status st = KRR_OK;
+    const bool refine = mixed(c) && c->opt.ir_max > 0;
+    if (refine || info) {
+        double best = INFINITY;
+        int stall = 0;
+        for (int it = 0;; ++it) {
+            int rr = prof_begin(c, KRR_PROF_RESIDUAL);
+            launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
+            launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
+            // the lower-triangle K tiles are read once by the row pass and
+            // once by the column pass
+            prof_end(c, rr, 2.0 * (double)c->n_pad * c->n_pad * p, 2.0 * (double)c->kd_bytes);
+            KRR_TRY(check_launch(c, "residual"));
+            KRR_CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            KRR_CUDA_TRY(c, cudaStreamSynchronize(s));
+            const double ynorm = sqrt(c->hred[1]);
+            const double rel = ynorm > 0 ? sqrt(c->hred[0]) / ynorm : sqrt(c->hred[0]);
+            if (it < 32) si.history[it] = rel;
+            si.rel_residual = rel;
+            si.iterations = it;
+            if (it == 0) best = rel;
+            if (!(rel == rel) || rel > 1e300) {  // NaN or overflow
+                st = KRR_ENOCONV;
+                break;
+            }
+            if (it > 0 && rel > best) {
+                // the last correction made things worse: the floor set by FP32
+                // storage of K and A is reached -- undo it and keep the best
+                launch_add_scaled(c->abuf, c->dabuf, -1.0f, cnt, s);
+                si.rel_residual = best;
+                si.converged = best <= c->opt.ir_tol ? 1 : 2;
+                break;
+            }
+            if (rel <= c->opt.ir_tol) {
+                si.converged = 1;
+                break;
+            }
+            if (!refine) break;
+            if (it >= c->opt.ir_max) {
+                st = KRR_ENOCONV;
+                break;
+            }
+            // stagnation: two successive steps that do not halve the residual
+            if (rel > 0.5 * best) {
+                if (++stall >= 2) {
+                    si.converged = 2;
+                    break;
+                }
+            } else {
+                stall = 0;
+            }
+            best = std::min(best, rel);
+            launch_axpy_r(c->rbuf, c->dabuf, cnt, s);
+            int sr = prof_begin(c, KRR_PROF_SOLVE);
+            solve_inplace(c, c->dabuf, c->zbuf, p);
+            prof_end(c, sr, sweep_flops, sweep_bytes);
+            launch_add_scaled(c->abuf, c->dabuf, 1.0f, cnt, s);
+            KRR_TRY(check_launch(c, "refinement step"));
+        }
+    }
+    if (info) *info = si;
+    if (st == KRR_ENOCONV)
+        c->last_error = "krr_solve: refinement stopped at relative residual " + std::to_string(si.rel_residual);
+    return st;
+}
 }  // namespace
 
 extern "C" {
@@ -302,6 +413,15 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->pred_part);
     dev_free(&c->pred_out);
     dev_free(&c->colsum);
+    dev_free(&c->res_part);
+    dev_free(&c->g_yt);
+    dev_free(&c->g_gp);
+    dev_free(&c->g_aw);
+    dev_free(&c->g_part);
+    dev_free(&c->g_sq);
+    dev_free(&c->g_tpart);
+    dev_free(&c->g_kpart);
+    dev_free(&c->g_scal);
     dev_free(&c->t8);
     dev_free(&c->tnorms);
     if (c->stage) cudaFree(c->stage);
@@ -436,6 +556,7 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
         c->w_bytes = w_bytes;
         KRR_TRY(dev_alloc(c, &c->Wd, (size_t)nt * bb, "diagonal tiles"));
         KRR_TRY(dev_alloc(c, &c->Linv, (size_t)nt * bb, "diagonal inverses"));
+        KRR_TRY(dev_alloc(c, &c->LinvT, (size_t)nt * bb, "transposed diagonal inverses"));
         KRR_TRY(dev_alloc(c, &c->diag64, (size_t)bb, "FP64 diagonal scratch"));
         KRR_TRY(dev_alloc(c, &c->diag64_inv, (size_t)2 * bb, "FP64 inverse scratch"));
         const size_t pool_bytes = (size_t)std::max<int64_t>(noff, 1) * bb * 4;
@@ -555,99 +676,11 @@ krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *
         c->last_error = "krr_solve: need Y, A != NULL, p >= 1, ldy >= p, lda >= p";
         return KRR_EINVAL;
     }
-    cudaStream_t s = c->stream;
-    const int64_t cnt = c->n_pad * p;
-    if (c->vec_cap < cnt) {
-        KRR_TRY(dev_alloc(c, &c->ybuf, (size_t)cnt, "solve vectors"));
-        KRR_TRY(dev_alloc(c, &c->zbuf, (size_t)cnt, "solve vectors"));
-        KRR_TRY(dev_alloc(c, &c->abuf, (size_t)cnt, "solve vectors"));
-        KRR_TRY(dev_alloc(c, &c->dabuf, (size_t)cnt, "solve vectors"));
-        KRR_TRY(dev_alloc(c, &c->rbuf, (size_t)cnt, "residual"));
-        c->vec_cap = cnt;
-    }
-    if (c->colsum_cap < p) {
-        KRR_TRY(dev_alloc(c, &c->colsum, (size_t)p, "column sums"));
-        c->colsum_cap = p;
-    }
+    KRR_TRY(ensure_vectors(c, p));
     KRR_TRY(load_rows_f32(c, Y, c->n, p, ldy, c->n_pad, c->ybuf));
-    KRR_CUDA_TRY(c, cudaMemcpyAsync(c->abuf, c->ybuf, cnt * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    // compulsory bytes of one pair of sweeps: the stored factor read twice
-    // (diagonal inverses in FP32 plus the off-diagonal pool) and the vectors
-    const double pool_used = mixed(c) ? (double)c->herr->pool_cursor
-                                      : (double)c->nt * (c->nt - 1) / 2 * c->b * c->b * 4.0;
-    const double factor_bytes_all = pool_used + (double)c->nt * c->b * c->b * 4.0;
-    const double sweep_bytes = 2.0 * factor_bytes_all + 4.0 * (double)cnt * 4.0;
-    const double sweep_flops = 2.0 * 2.0 * (double)c->n_pad * c->n_pad * p;
-    int pr = prof_begin(c, KRR_PROF_SOLVE);
-    solve_inplace(c, c->abuf, c->zbuf, p);
-    prof_end(c, pr, sweep_flops, sweep_bytes);
-    KRR_TRY(check_launch(c, "solve"));
-    krr_solve_info si;
-    memset(&si, 0, sizeof(si));
-    krr_status st = KRR_OK;
-    const bool refine = mixed(c) && c->opt.ir_max > 0;
-    if (refine || info) {
-        double best = INFINITY;
-        int stall = 0;
-        for (int it = 0;; ++it) {
-            int rr = prof_begin(c, KRR_PROF_RESIDUAL);
-            launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
-            launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
-            // the lower-triangle K tiles are read once by the row pass and
-            // once by the column pass
-            prof_end(c, rr, 2.0 * (double)c->n_pad * c->n_pad * p, 2.0 * (double)c->kd_bytes);
-            KRR_TRY(check_launch(c, "residual"));
-            KRR_CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-            KRR_CUDA_TRY(c, cudaStreamSynchronize(s));
-            const double ynorm = sqrt(c->hred[1]);
-            const double rel = ynorm > 0 ? sqrt(c->hred[0]) / ynorm : sqrt(c->hred[0]);
-            if (it < 32) si.history[it] = rel;
-            si.rel_residual = rel;
-            si.iterations = it;
-            if (it == 0) best = rel;
-            if (!(rel == rel) || rel > 1e300) {  // NaN or overflow
-                st = KRR_ENOCONV;
-                break;
-            }
-            if (it > 0 && rel > best) {
-                // the last correction made things worse: the floor set by FP32
-                // storage of K and A is reached -- undo it and keep the best
-                launch_add_scaled(c->abuf, c->dabuf, -1.0f, cnt, s);
-                si.rel_residual = best;
-                si.converged = best <= c->opt.ir_tol ? 1 : 2;
-                break;
-            }
-            if (rel <= c->opt.ir_tol) {
-                si.converged = 1;
-                break;
-            }
-            if (!refine) break;
-            if (it >= c->opt.ir_max) {
-                st = KRR_ENOCONV;
-                break;
-            }
-            // stagnation: two successive steps that do not halve the residual
-            if (rel > 0.5 * best) {
-                if (++stall >= 2) {
-                    si.converged = 2;
-                    break;
-                }
-            } else {
-                stall = 0;
-            }
-            best = std::min(best, rel);
-            launch_axpy_r(c->rbuf, c->dabuf, cnt, s);
-            int sr = prof_begin(c, KRR_PROF_SOLVE);
-            solve_inplace(c, c->dabuf, c->zbuf, p);
-            prof_end(c, sr, sweep_flops, sweep_bytes);
-            launch_add_scaled(c->abuf, c->dabuf, 1.0f, cnt, s);
-            KRR_TRY(check_launch(c, "refinement step"));
-        }
-    }
+    krr_status st = solve_device(c, p, info);
+    if (st != KRR_OK && st != KRR_ENOCONV) return st;
     KRR_TRY(store_rows_f32(c, c->abuf, c->n, p, A, lda));
-    if (info) *info = si;
-    if (st == KRR_ENOCONV)
-        c->last_error = "krr_solve: refinement stopped at relative residual " + std::to_string(si.rel_residual);
     return st;
 }
 
@@ -682,8 +715,7 @@ krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt,
         KRR_TRY(dev_alloc(c, &c->rbuf, (size_t)cnt, "residual"));
         c->vec_cap = cnt;
     }
-    const int64_t colblk = mx ? 256 : 128;
-    const int64_t nblk = c->n_pad / colblk;
+    const int64_t nblk = c->n_pad / 128;  // partial products per 128 training rows
     const size_t part = (size_t)nblk * rows_pad * p;
     if (c->pred_part_cap < part) {
         KRR_TRY(dev_alloc(c, &c->pred_part, part, "predict partials"));
@@ -852,5 +884,100 @@ extern "C" krr_status krr_get_factor(krr_ctx *c, float *L, int64_t ldl) {
     KRR_TRY(check_launch(c, "factor to dense"));
     if (!dev) KRR_CUDA_TRY(c, cudaMemcpyAsync(L, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
     KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return KRR_OK;
+}
+
+extern "C" krr_status krr_grad_hyper(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt,
+                                     const float *Yt, int64_t ldy, const float *A, int64_t lda,
+                                     int64_t p, double *out) {
+    if (!c) return KRR_EINVAL;
+    if (!c->factored) {
+        c->last_error = "krr_grad_hyper: no factorisation";
+        return KRR_ESTATE;
+    }
+    if (!mixed(c) || !c->tc) {
+        c->last_error = "krr_grad_hyper: needs a context in KRR_MODE_MIXED";
+        return KRR_EINVAL;
+    }
+    if (!T || !Yt || !A || !out || n_test < 1 || ldt < c->m || p < 1 || p > 16 || ldy < p || lda < p) {
+        c->last_error = "krr_grad_hyper: bad arguments (need 1 <= p <= 16, ldt >= m, ldy, lda >= p)";
+        return KRR_EINVAL;
+    }
+    cudaStream_t s = c->stream;
+    const int64_t rows = (n_test + 255) / 256 * 256;
+    const int64_t npad = c->n_pad;
+    // buffers
+    const size_t tbytes = (size_t)rows * c->m_pad;
+    if (c->t_cap < tbytes) {
+        KRR_TRY(dev_alloc(c, &c->t8, tbytes, "test genotypes"));
+        c->t_cap = tbytes;
+    }
+    if (c->tnorm_cap < (size_t)rows) {
+        KRR_TRY(dev_alloc(c, &c->tnorms, (size_t)rows, "test norms"));
+        c->tnorm_cap = rows;
+    }
+    KRR_TRY(ensure_vectors(c, p));
+    if (c->g_rows_cap < (size_t)rows * p) {
+        KRR_TRY(dev_alloc(c, &c->g_yt, (size_t)rows * p, "gradient buffers"));
+        KRR_TRY(dev_alloc(c, &c->g_gp, (size_t)rows * p, "gradient buffers"));
+        KRR_TRY(dev_alloc(c, &c->g_sq, (size_t)rows * p, "gradient buffers"));
+        KRR_TRY(dev_alloc(c, &c->pred_out, (size_t)rows * p, "predictions"));
+        c->pred_out_cap = (size_t)rows * p;
+        c->g_rows_cap = (size_t)rows * p;
+    }
+    if (c->g_aw_cap < (size_t)npad * p) {
+        KRR_TRY(dev_alloc(c, &c->g_aw, (size_t)npad * p, "gradient buffers"));
+        c->g_aw_cap = (size_t)npad * p;
+    }
+    const size_t part_pred = (size_t)(npad / 128) * rows * p;      // Yhat partials
+    const size_t part_t = (size_t)(2 * rows / 256) * npad * p;     // K_t^T G_p partials
+    const size_t part = std::max(part_pred, part_t);
+    if (c->g_part_cap < part) {
+        KRR_TRY(dev_alloc(c, &c->g_part, part, "gradient partials"));
+        c->g_part_cap = part;
+    }
+    const size_t it = (size_t)(rows / 128) * (npad / 256);
+    const size_t ik = (size_t)c->nt * (c->nt + 1) / 2 * (c->b / 128) * (c->b / 256);
+    if (c->g_tpart_cap < it) {
+        KRR_TRY(dev_alloc(c, &c->g_tpart, it, "gradient partials"));
+        c->g_tpart_cap = it;
+    }
+    if (c->g_kpart_cap < ik) {
+        KRR_TRY(dev_alloc(c, &c->g_kpart, ik, "gradient partials"));
+        c->g_kpart_cap = ik;
+    }
+    if (!c->g_scal) KRR_TRY(dev_alloc(c, &c->g_scal, (size_t)8, "gradient scalars"));
+
+    // 1. inputs: packed test genotypes, padded weights and held-out phenotypes
+    KRR_TRY(pack(c, T, n_test, c->m, ldt, rows, c->t8, nullptr, c->tnorms));
+    KRR_TRY(load_rows_f32(c, A, c->n, p, lda, npad, c->g_aw));
+    KRR_TRY(load_rows_f32(c, Yt, n_test, p, ldy, rows, c->g_yt));
+    // 2. Yhat = K_t A (Alg. 4)
+    KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows, c->g_aw, p, p, c->g_part));
+    launch_predict_reduce(c->g_part, npad / 128, rows, n_test, p, c->pred_out, p, s);
+    // 3. G_p = d loss / d Yhat and the loss
+    launch_grad_prep(c->pred_out, c->g_yt, n_test, p, rows, c->g_gp, c->g_sq, s);
+    launch_sum_f64(c->g_sq, rows * p, c->g_scal + 0, s);
+    // 4. B = K_t^T G_p into the solve's right-hand side, then Z = (K + lambda I)^-1 B
+    KRR_TRY(tc_predict_t(c, c->t8, c->tnorms, n_test, rows, c->g_gp, p, p, c->g_part));
+    launch_predict_reduce(c->g_part, 2 * rows / 256, npad, npad, p, c->ybuf, p, s);
+    KRR_TRY(check_launch(c, "gradient adjoint right-hand side"));
+    krr_solve_info si;
+    krr_status st = solve_device(c, p, &si);
+    if (st != KRR_OK && st != KRR_ENOCONV) return st;
+    // 5. <Z, A> and the two d K-weighted contractions
+    launch_dot_f32(c->abuf, c->g_aw, npad * p, c->g_scal + 1, s);
+    int64_t nit = 0, nik = 0;
+    KRR_TRY(tc_grad_terms(c, c->t8, c->tnorms, n_test, rows, c->g_aw, c->abuf, c->g_gp, p, p,
+                          c->g_tpart, c->g_kpart, &nit, &nik));
+    launch_sum_f64(c->g_tpart, nit, c->g_scal + 2, s);
+    launch_sum_f64(c->g_kpart, nik, c->g_scal + 3, s);
+    KRR_TRY(check_launch(c, "gradient sums"));
+    KRR_CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->g_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KRR_CUDA_TRY(c, cudaStreamSynchronize(s));
+    const double loss = c->hred[0] / (double)(n_test * p);
+    out[0] = loss;
+    out[1] = c->gamma * (c->hred[3] - c->hred[2]);
+    out[2] = -c->lambda * c->hred[1];
     return KRR_OK;
 }

@@ -23,7 +23,8 @@ __host__ __device__ inline int64_t off_index(int64_t i, int64_t j) { return i * 
 
 // Inverse of the triangular numbering: t -> (i, j) with j <= i.
 __host__ __device__ inline void tri_decode(int64_t t, int64_t *i, int64_t *j) {
-    int64_t r = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    // single-precision estimate, corrected exactly by the loops below
+    int64_t r = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
     while (r * (r + 1) / 2 > t) --r;
     while ((r + 1) * (r + 2) / 2 <= t) ++r;
     *i = r;
@@ -84,6 +85,7 @@ struct Ctx {
     void *W = nullptr;         // strictly-lower trailing tiles: FP16 (mixed) / FP32 (fp32)
     float *Wd = nullptr;       // diagonal working tiles, FP32, overwritten by L_kk
     float *Linv = nullptr;     // inverse of every diagonal factor tile, FP32
+    float *LinvT = nullptr;    // and its transpose (row-oriented backward sweep)
     __half *Linv_hi = nullptr, *Linv_lo = nullptr;  // FP16 split of Linv (mixed)
     double *diag64 = nullptr;  // FP64 scratch diagonal tile (diag_fp64)
     double *diag64_inv = nullptr;
@@ -107,6 +109,8 @@ struct Ctx {
     float *dabuf = nullptr;                  // n_pad x p correction
     double *red = nullptr;                   // reductions (norms), small; slots RED_*
     double *colsum = nullptr;                // column sums of the current iterate (FP64)
+    float *res_part = nullptr;               // residual partial slots, nt * nt * b * min(p, 32)
+    size_t res_part_cap = 0;
     int64_t colsum_cap = 0;
     double *hred = nullptr;                  // pinned host mirror of red
     int64_t vec_cap = 0;                     // capacity in elements of the n_pad x p buffers
@@ -114,6 +118,10 @@ struct Ctx {
     size_t pred_part_cap = 0;
     float *pred_out = nullptr;               // reduced predictions, rows_pad x p
     size_t pred_out_cap = 0;
+    // hyperparameter gradient buffers (krr_grad_hyper)
+    float *g_yt = nullptr, *g_gp = nullptr, *g_aw = nullptr, *g_part = nullptr;
+    double *g_sq = nullptr, *g_tpart = nullptr, *g_kpart = nullptr, *g_scal = nullptr;
+    size_t g_rows_cap = 0, g_aw_cap = 0, g_part_cap = 0, g_tpart_cap = 0, g_kpart_cap = 0;
     uint8_t *t8 = nullptr;                   // packed test genotypes (E4M3 / FP32 bytes)
     size_t t_cap = 0;
     int32_t *tnorms = nullptr;
@@ -209,6 +217,12 @@ void launch_kernel_sumsq(Ctx *c, double *out);
 // Dense lower-triangular copy of the stored factor into dst (n x n, device).
 void launch_factor_to_dense(Ctx *c, float *dst, int64_t ld);
 
+// Gradient helpers: G_p and squared errors, FP64 sums and dot products.
+void launch_grad_prep(const float *yhat, const float *yt, int64_t n_test, int64_t p, int64_t rows,
+                      float *gp, double *sq, cudaStream_t s);
+void launch_sum_f64(const double *x, int64_t n, double *out, cudaStream_t s);
+void launch_dot_f32(const float *a, const float *b, int64_t n, double *out, cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // Tensor-core kernels (tc_gemm.cu)
 // ---------------------------------------------------------------------------
@@ -218,9 +232,17 @@ krr_status tc_build(Ctx *c);                 // distance GEMM + exp epilogue (E4
 krr_status tc_trsm(Ctx *c, int64_t k);       // panel TRSM of column k (FP16 split)
 krr_status tc_update(Ctx *c, int64_t k);     // trailing update of step k
 // Predict partial products for weight columns A[:, 0:p] (p <= 32, leading
-// dimension lda): part is (n_pad / 256) x rows_pad x p.
+// dimension lda): part is (n_pad / 128) x rows_pad x p.
 krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
                       int64_t rows_pad, const float *A, int64_t lda, int64_t p, float *part);
+// B = K_test^T G_p (roles swapped): part is (2 * test_rows256 / 256) x n_pad x p.
+krr_status tc_predict_t(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
+                        int64_t test_rows256, const float *gp, int64_t ldgp, int64_t p, float *part);
+// d K-weighted gradient contractions, one partial per block (p <= 16).
+krr_status tc_grad_terms(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
+                         int64_t test_rows, const float *aw, const float *zw, const float *gp,
+                         int64_t ld, int64_t p, double *part_t, double *part_k, int64_t *items_t,
+                         int64_t *items_k);
 // Forget the cached factor tensor maps (the factor buffers were reallocated).
 void tc_invalidate_factor_maps(Ctx *c);
 

@@ -9,7 +9,7 @@
 // every working buffer carved out of one file-scope device array of fixed
 // size instead of context-owned allocations.
 //
-// The array (about 12.6 MB) exists on every GPU
+// The array (about 16.8 MB) exists on every GPU
 // that loads the library, from module load until process exit.  Host code
 // cannot use the array's name as a device address: its device address is
 // looked up with cudaGetSymbolAddress once per device, with that device
@@ -33,7 +33,7 @@ constexpr size_t NA_T8 = 0;                                                     
 constexpr size_t NA_TN = NA_T8 + align256(NA_MAX_TEST * NA_MAX_MPAD);           // test norms
 constexpr size_t NA_AW = NA_TN + align256(NA_MAX_TEST * 4);                     // padded weights
 constexpr size_t NA_PART = NA_AW + align256(NA_MAX_NPAD * NA_MAX_P * 4);        // partial products
-constexpr size_t NA_OUT = NA_PART + align256((NA_MAX_NPAD / 256) * NA_MAX_TEST * NA_MAX_P * 4);
+constexpr size_t NA_OUT = NA_PART + align256((NA_MAX_NPAD / 128) * NA_MAX_TEST * NA_MAX_P * 4);
 constexpr size_t NA_BYTES = NA_OUT + align256(NA_MAX_TEST * NA_MAX_P * 4);
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[NA_BYTES];
@@ -113,7 +113,7 @@ extern "C" krr_status krr_predict_noalloc(krr_ctx *ctx, const int8_t *T, int64_t
     krr::launch_pack_genotypes(T, n_test, c->m, ldt, rows_pad, c->m_pad, t8, nullptr, tn, c->stream);
     krr::launch_copy_rows(A, lda, aw, p, c->n, p, c->n_pad, c->stream);
     KRR_TRY(krr::tc_predict(c, t8, tn, n_test, rows_pad, aw, p, p, part));
-    krr::launch_predict_reduce(part, c->n_pad / 256, rows_pad, n_test, p, out, p, c->stream);
+    krr::launch_predict_reduce(part, c->n_pad / 128, rows_pad, n_test, p, out, p, c->stream);
     krr::launch_copy_rows(out, p, Yt, ldyt, n_test, p, n_test, c->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -503,13 +503,24 @@ template <typename T>
 __global__ void __launch_bounds__(256) potrf_block_kernel(T *W, T *Winv, int64_t b, int q,
                                                           int64_t tile_k, DevErrors *err,
                                                           double *minpiv) {
-    __shared__ T a[DNB][DNB + 1];
+    // dynamic shared memory: a[DNB][DNB + 1] (the block, then L_qq) and
+    // x[DNB][DNB + 1] (its inverse).  Thread (tx, ty) = (t % 64, t / 64)
+    // owns column tx and rows ty, ty + 4, ... of the rank-1 updates.
+    extern __shared__ __align__(16) unsigned char pb_smem[];
+    T (*a)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(pb_smem);
+    T (*x)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(pb_smem + sizeof(T) * DNB * (DNB + 1));
     __shared__ int bad;
+    const int tx = threadIdx.x & (DNB - 1), ty = threadIdx.x / DNB;
+    constexpr int RS = 256 / DNB;  // row stride of a thread
     T *blk = W + (int64_t)q * DNB * b + q * DNB;
-    for (int e = threadIdx.x; e < DNB * DNB; e += blockDim.x) a[e / DNB][e % DNB] = blk[(e / DNB) * b + e % DNB];
+    for (int r = ty; r < DNB; r += RS) {
+        a[r][tx] = blk[(int64_t)r * b + tx];
+        x[r][tx] = (r == tx) ? T(1) : T(0);
+    }
     if (threadIdx.x == 0) bad = -1;
     __syncthreads();
     double mp = 1e300;
+    // Cholesky, right-looking: pivot, scale the column, rank-1 update
     for (int c = 0; c < DNB; ++c) {
         if (threadIdx.x == 0) {
             T d = a[c][c];
@@ -518,36 +529,34 @@ __global__ void __launch_bounds__(256) potrf_block_kernel(T *W, T *Winv, int64_t
                 d = T(1);
             }
             a[c][c] = sqrt(d);
+            if ((double)a[c][c] < mp) mp = (double)a[c][c];
         }
         __syncthreads();
-        const T piv = a[c][c];
-        if (threadIdx.x == 0 && (double)piv < mp) mp = (double)piv;
-        for (int r = c + 1 + threadIdx.x; r < DNB; r += blockDim.x) a[r][c] /= piv;
+        if (ty == 0 && tx > c) a[tx][c] /= a[c][c];
         __syncthreads();
-        for (int e = threadIdx.x; e < (DNB - c - 1) * (DNB - c - 1); e += blockDim.x) {
-            int r = c + 1 + e / (DNB - c - 1), s = c + 1 + e % (DNB - c - 1);
-            if (s <= r) a[r][s] -= a[r][c] * a[s][c];
+        if (tx > c) {
+            const T lsc = a[tx][c];
+            for (int r = ty; r < DNB; r += RS)
+                if (r >= tx) a[r][tx] -= a[r][c] * lsc;
         }
         __syncthreads();
     }
-    // inverse by forward substitution: thread t < DNB owns column t of inv(L)
-    // and reads back only the entries it wrote itself.
+    // inverse, right-looking forward substitution on the identity:
+    // row c of X is final after the division; then rows r > c are updated
+    for (int c = 0; c < DNB; ++c) {
+        if (ty == 0 && tx <= c) x[c][tx] /= a[c][c];
+        __syncthreads();
+        if (tx <= c) {
+            const T xc = x[c][tx];
+            for (int r = ty; r < DNB; r += RS)
+                if (r > c) x[r][tx] -= a[r][c] * xc;
+        }
+        __syncthreads();
+    }
     T *iblk = Winv + (int64_t)q * DNB * b + q * DNB;
-    if (threadIdx.x < DNB) {
-        const int col = threadIdx.x;
-        for (int r = 0; r < DNB; ++r) {
-            T v = T(0);
-            if (r >= col) {
-                T s = (r == col) ? T(1) : T(0);
-                for (int kk = col; kk < r; ++kk) s -= a[r][kk] * iblk[(int64_t)kk * b + col];
-                v = s / a[r][r];
-            }
-            iblk[(int64_t)r * b + col] = v;
-        }
-    }
-    for (int e = threadIdx.x; e < DNB * DNB; e += blockDim.x) {
-        int r = e / DNB, s = e % DNB;
-        blk[r * b + s] = (s <= r) ? a[r][s] : T(0);
+    for (int r = ty; r < DNB; r += RS) {
+        blk[(int64_t)r * b + tx] = (tx <= r) ? a[r][tx] : T(0);
+        iblk[(int64_t)r * b + tx] = (tx <= r) ? x[r][tx] : T(0);
     }
     if (threadIdx.x == 0) {
         minpiv[q] = mp;
@@ -555,6 +564,82 @@ __global__ void __launch_bounds__(256) potrf_block_kernel(T *W, T *Winv, int64_t
             err->bad_tile = tile_k;
             err->bad_column = tile_k * b + (int64_t)q * DNB + bad;
         }
+    }
+}
+
+// Triangular inverse of the factored diagonal tile, one CTA per 64-column
+// block j: X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj for i = j + 1, ..., in
+// order (the diagonal blocks X_ii = inv(L_ii) come from potrf_block_kernel).
+// 64 x 64 block products in shared memory, 4 x 4 outputs per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) trtri_cols_kernel(const T *L, T *X, int64_t b) {
+    extern __shared__ __align__(16) unsigned char tr_smem[];
+    T (*As)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(tr_smem);
+    T (*Bs)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(tr_smem + sizeof(T) * DNB * (DNB + 1));
+    const int j = blockIdx.x, nq = (int)(b / DNB);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
+    const int lx = threadIdx.x & (DNB - 1), ly = threadIdx.x / DNB;  // loader mapping
+    for (int i = j + 1; i < nq; ++i) {
+        T acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+        for (int k = j; k < i; ++k) {
+            const T *lb = L + (int64_t)i * DNB * b + (int64_t)k * DNB;
+            const T *xb = X + (int64_t)k * DNB * b + (int64_t)j * DNB;
+            for (int r = ly; r < DNB; r += 256 / DNB) {
+                As[r][lx] = lb[(int64_t)r * b + lx];
+                Bs[r][lx] = xb[(int64_t)r * b + lx];
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < DNB; ++kk) {
+                T av[4], bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    av[u] = As[ty * 4 + u][kk];
+                    bv[u] = Bs[kk][tx * 4 + u];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
+            }
+            __syncthreads();
+        }
+        // X_ij = -X_ii * acc
+        const T *xii = X + (int64_t)i * DNB * b + (int64_t)i * DNB;
+        for (int r = ly; r < DNB; r += 256 / DNB) As[r][lx] = xii[(int64_t)r * b + lx];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Bs[ty * 4 + u][tx * 4 + v] = acc[u][v];
+        __syncthreads();
+        T out[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) out[u][v] = T(0);
+#pragma unroll 8
+        for (int kk = 0; kk < DNB; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                av[u] = As[ty * 4 + u][kk];
+                bv[u] = Bs[kk][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) out[u][v] -= av[u] * bv[v];
+        }
+        T *xij = X + (int64_t)i * DNB * b + (int64_t)j * DNB;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) xij[(int64_t)(ty * 4 + u) * b + tx * 4 + v] = out[u][v];
+        __syncthreads();  // X_ij is read by the next i (global memory, same block)
     }
 }
 
@@ -596,8 +681,14 @@ static void diag_factor_tile(Ctx *c, T *W, T *Winv, T *tmp, int64_t k, double *m
     const int nq = (int)(b / DNB);
     cudaStream_t s = c->stream;
     cudaMemsetAsync(Winv, 0, sizeof(T) * b * b, s);
+    const size_t pb_smem = 2 * sizeof(T) * DNB * (DNB + 1);
+    static bool pb_attr = false;
+    if (!pb_attr) {
+        cudaFuncSetAttribute(potrf_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb_smem);
+        pb_attr = true;
+    }
     for (int q = 0; q < nq; ++q) {
-        count_launch(), potrf_block_kernel<T><<<1, 256, 0, s>>>(W, Winv, b, q, k, c->derr, minpiv + k * nq);
+        count_launch(), potrf_block_kernel<T><<<1, 256, pb_smem, s>>>(W, Winv, b, q, k, c->derr, minpiv + k * nq);
         const int rest = (int)(b - (int64_t)(q + 1) * DNB);
         if (rest <= 0) break;
         T *panel = W + (int64_t)(q + 1) * DNB * b + q * DNB;
@@ -609,18 +700,14 @@ static void diag_factor_tile(Ctx *c, T *W, T *Winv, T *tmp, int64_t k, double *m
         launch_gemm_simt<T>(rest, rest, DNB, T(-1), panel, b, 0, panel, b, 0, 0, T(1), trail, b, 0,
                             trail, b, 0, 1, 1, s);
     }
-    // Triangular inverse by block diagonals: X_ij = -X_ii sum_{l=j}^{i-1} L_il X_lj.
-    for (int d = 1; d < nq; ++d) {
-        const int cnt = nq - d;
-        const int64_t diag_stride = (int64_t)DNB * b + DNB;
-        // tmp_j = L[i-block, j..i-1 blocks] * X[j..i-1 blocks, j-block]   (i = j + d)
-        launch_gemm_simt<T>(DNB, DNB, DNB * d, T(1), W + (int64_t)d * DNB * b, b, diag_stride, Winv,
-                            b, diag_stride, 1, T(0), nullptr, 0, 0, tmp, DNB, DNB * DNB, cnt, 0, s);
-        // X_ij = -X_ii tmp_j
-        launch_gemm_simt<T>(DNB, DNB, DNB, T(-1), Winv + (int64_t)d * DNB * b + d * DNB, b,
-                            diag_stride, tmp, DNB, DNB * DNB, 1, T(0), nullptr, 0, 0,
-                            Winv + (int64_t)d * DNB * b, b, diag_stride, cnt, 0, s);
+    // Triangular inverse: one CTA per 64-column block of X = L^-1.
+    static bool tr_attr = false;
+    if (!tr_attr) {
+        cudaFuncSetAttribute(trtri_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb_smem);
+        tr_attr = true;
     }
+    if (nq > 1) count_launch(), trtri_cols_kernel<T><<<(unsigned)(nq - 1), 256, pb_smem, s>>>(W, Winv, b);
+    (void)tmp;
 }
 
 // sqrt of the largest diagonal entry of W_kk: a bound on every |L_kk| entry
@@ -642,6 +729,15 @@ __global__ void diag_max_kernel(const float *w, int64_t b, double *out) {
 __global__ void f64_to_f32_kernel(const double *src, float *dst, int64_t count) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e < count) dst[e] = (float)src[e];
+}
+
+// dst = src^T for one b x b tile (32 x 32 shared-memory tiles).
+__global__ void transpose_kernel(const float *src, float *dst, int64_t b) {
+    __shared__ float t[32][33];
+    const int64_t bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) t[r][threadIdx.x] = src[(by + r) * b + bx + threadIdx.x];
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) dst[(bx + r) * b + by + threadIdx.x] = t[threadIdx.x][r];
 }
 
 __global__ void min_pivot_kernel(const double *mp, int n, DevErrors *err) {
@@ -675,6 +771,8 @@ krr_status diag_step(Ctx *c, int64_t k) {
             count_launch(), finish_inverse_kernel<<<g, 256, 0, s>>>(nullptr, linv, c->Linv_hi + k * bb,
                                                     c->Linv_lo + k * bb, bb);
     }
+    count_launch(), transpose_kernel<<<dim3((unsigned)(b / 32), (unsigned)(b / 32)), dim3(32, 8), 0, s>>>(
+        linv, c->LinvT + k * bb, b);
     count_launch(), min_pivot_kernel<<<1, 1, 0, s>>>(minpiv + k * nq, nq, c->derr);
     return KRR_OK;
 }
@@ -759,35 +857,47 @@ __global__ void column_decide_kernel(int64_t k, int64_t nt, int64_t bb, int chun
               1ull);
 }
 
+// Four consecutive elements per thread: vector loads and stores.
 __global__ void column_write_kernel(int64_t k, int64_t bb, const float *col, const TileDesc *ltab,
                                     uint8_t *pool, __half *pan_hi, __half *pan_lo,
                                     uint8_t *pan_f8) {
     const int64_t tile = blockIdx.y;
     const int64_t i = k + 1 + tile;
     const TileDesc d = ltab[off_index(i, k)];
-    const float *src = col + tile * bb;
-    __half *hi = pan_hi + tile * bb;
-    __half *lo = pan_lo + tile * bb;
-    uint8_t *f8 = pan_f8 + tile * bb;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < bb;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const float v = src[e];
-        const float sv = v * d.scale;
+    const float4 *src = reinterpret_cast<const float4 *>(col + tile * bb);
+    __half2 *hi = reinterpret_cast<__half2 *>(pan_hi + tile * bb);
+    __half2 *lo = reinterpret_cast<__half2 *>(pan_lo + tile * bb);
+    for (int64_t e4 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e4 < bb / 4;
+         e4 += (int64_t)gridDim.x * blockDim.x) {
+        const float4 v = src[e4];
+        const float sv[4] = {v.x * d.scale, v.y * d.scale, v.z * d.scale, v.w * d.scale};
         if (d.prec == KRR_PREC_E4M3) {
-            __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(sv, __NV_SATFINITE, __NV_E4M3);
-            f8[e] = q;
-            pool[d.offset + e] = q;
-            __half_raw hr = __nv_cvt_fp8_to_halfraw(q, __NV_E4M3);
-            hi[e] = __half(hr);
+            uint32_t packed = 0;
+            __half h[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const __nv_fp8_storage_t qv = __nv_cvt_float_to_fp8(sv[t], __NV_SATFINITE, __NV_E4M3);
+                packed |= (uint32_t)qv << (8 * t);
+                h[t] = __half(__nv_cvt_fp8_to_halfraw(qv, __NV_E4M3));
+            }
+            reinterpret_cast<uint32_t *>(pan_f8 + tile * bb)[e4] = packed;
+            reinterpret_cast<uint32_t *>(pool + d.offset)[e4] = packed;
+            hi[2 * e4] = __halves2half2(h[0], h[1]);
+            hi[2 * e4 + 1] = __halves2half2(h[2], h[3]);
         } else if (d.prec == KRR_PREC_FP16) {
-            __half h = __float2half_rn(sv);
-            hi[e] = h;
-            reinterpret_cast<__half *>(pool + d.offset)[e] = h;
+            // the trailing update reads FP16 tiles from the pool itself
+            const __half2 a = __floats2half2_rn(sv[0], sv[1]), b2 = __floats2half2_rn(sv[2], sv[3]);
+            __half2 *pp = reinterpret_cast<__half2 *>(pool + d.offset);
+            pp[2 * e4] = a;
+            pp[2 * e4 + 1] = b2;
         } else {
-            reinterpret_cast<float *>(pool + d.offset)[e] = v;
-            __half h = __float2half_rn(sv);
-            hi[e] = h;
-            lo[e] = __float2half_rn(sv - __half2float(h));
+            reinterpret_cast<float4 *>(pool + d.offset)[e4] = v;
+            const __half2 a = __floats2half2_rn(sv[0], sv[1]), b2 = __floats2half2_rn(sv[2], sv[3]);
+            hi[2 * e4] = a;
+            hi[2 * e4 + 1] = b2;
+            const float2 fa = __half22float2(a), fb = __half22float2(b2);
+            lo[2 * e4] = __floats2half2_rn(sv[0] - fa.x, sv[1] - fa.y);
+            lo[2 * e4 + 1] = __floats2half2_rn(sv[2] - fb.x, sv[3] - fb.y);
         }
     }
 }
@@ -819,11 +929,20 @@ void launch_kernel_sumsq(Ctx *c, double *out) {
 }
 
 // ----------------------------------------------------------------------------
-// Triangular solves with the stored factor, p right-hand sides (columns
-// processed in chunks of at most PC).  Forward: for k = 0..NT-1,
-// Z_k = Linv_kk Y_k, then Y_i -= L_ik Z_k for i > k.  Backward: for
-// k = NT-1..0, A_k = Linv_kk^T Z_k, then Z_j -= L_kj^T A_k for j < k.
-// Every output element has one owner (no atomics): results are deterministic.
+// Tile matrix-vector products on CUDA cores (HBM-bound), p right-hand sides
+// processed in column chunks of at most PC.
+//
+//   gemv_n:  out[r][q] (op)= sum_c M[r][c] x[c][q]   (row-oriented)
+//            each lane covers 4 consecutive columns per 128-column step with
+//            one 16/8/4-byte load (FP32/FP16/E4M3); x is staged transposed in
+//            shared memory so the lanes' float4 reads are conflict-free; one
+//            warp per row at a time, warp-shuffle reduction.
+//   gemv_t:  out[c][q] (op)= sum_r M[r][c] x[r][q]   (column-oriented)
+//            a CTA covers 128 columns; its 8 warps split the rows; lanes cover
+//            4 columns; per-warp partials are summed in a fixed order in
+//            shared memory.
+// M is a b x b row-major tile in its storage precision: value = stored *
+// inv_scale - shift.  Every output element has one owner (no atomics).
 // ----------------------------------------------------------------------------
 constexpr int PC = 32;
 
@@ -834,231 +953,339 @@ __device__ __forceinline__ float load_l(const uint8_t *base, int prec, int64_t e
     return __half2float(__half(h));
 }
 
-// Forward kernel: out rows (-)= M x_k, one warp per row, lanes over c.
-// mode 0: M = Linv_kk (FP32, lower: c <= r); out = block k of `out`, stored.
-// mode 1: M = L_ik for every i > k (grid.y); out = block i of `out`,
-//         subtracted.  x_k is block k of `in`; `in` and the written blocks of
-//         `out` never overlap.
-__global__ void __launch_bounds__(256) solve_fwd_kernel(int mode, int64_t k, int64_t b,
-                                                        const float *Linv, const uint8_t *pool,
-                                                        const TileDesc *ltab, const float *in,
-                                                        float *out, int64_t ldx, int q0, int pc) {
-    extern __shared__ float zs[];  // b x pc
-    const float *zsrc = in + k * b * ldx;
-    for (int64_t e = threadIdx.x; e < b * pc; e += blockDim.x) zs[e] = zsrc[(e / pc) * ldx + q0 + e % pc];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t tile = (mode == 0) ? k : (k + 1 + blockIdx.y);
-    const int64_t rbase = blockIdx.x * 64;
-    const uint8_t *base;
-    int prec;
-    float inv_scale;
-    if (mode == 0) {
-        base = reinterpret_cast<const uint8_t *>(Linv + k * b * b);
-        prec = KRR_PREC_FP32;
-        inv_scale = 1.f;
-    } else {
-        const TileDesc d = ltab[off_index(tile, k)];
-        base = pool + d.offset;
-        prec = d.prec;
-        inv_scale = (prec == KRR_PREC_FP32) ? 1.f : 1.f / d.scale;
+template <int PREC>
+__device__ __forceinline__ float4 load4(const uint8_t *base, int64_t e) {
+    if (PREC == KRR_PREC_FP32) return *reinterpret_cast<const float4 *>(base + e * 4);
+    if (PREC == KRR_PREC_FP16) {
+        uint2 u = *reinterpret_cast<const uint2 *>(base + e * 2);
+        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
+        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
     }
-    float *dst_blk = out + tile * b * ldx;
-    for (int64_t r = rbase + warp; r < rbase + 64; r += 8) {
+    uint32_t u = *reinterpret_cast<const uint32_t *>(base + e);
+    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
+    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
+    float2 a = __half22float2(__half2(lo));
+    float2 b = __half22float2(__half2(hi));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Where a gemv launch reads its tiles and writes its outputs.
+enum GemvJob {
+    JOB_DIAG = 0,      // one FP32 tile (Linv_kk or its transpose), out block k, store
+    JOB_FWD = 1,       // factor tiles L_ik, i > k (grid.y = i - k - 1), out block i, subtract
+    JOB_BWD = 2,       // factor tiles L_kj, j < k (grid.y = j), out block j, subtract
+    JOB_RES_N = 3,     // K tiles (i, j), j <= i (grid.y = tri index): partial slot (i, j), store
+    JOB_RES_T = 4      // K tiles (i, j), i > j (grid.y = off index): partial slot (j, i), store
+};
+
+struct GemvArgs {
+    int job;
+    int64_t k, b, nt;
+    const float *diag;       // JOB_DIAG tile
+    const uint8_t *pool;
+    const TileDesc *ltab;
+    const float *Kd;
+    float shift_dummy;
+    const double *shift;     // residual shift (device), JOB_RES_*
+    const float *x;          // input vectors, n_pad x ldx
+    int64_t ldx;
+    float *out;              // output vectors (n_pad x ldx) or partial slots (nt*nt x b x pc)
+    int q0, pc;
+};
+
+__device__ __forceinline__ void gemv_locate(const GemvArgs &g, int64_t y, const uint8_t *&base, int &prec,
+                                            float &inv_scale, float &shift, int64_t &in_blk,
+                                            float *&out, int64_t &ldo) {
+    shift = 0.f;
+    inv_scale = 1.f;
+    prec = KRR_PREC_FP32;
+    ldo = g.ldx;
+    if (g.job == JOB_DIAG) {
+        base = reinterpret_cast<const uint8_t *>(g.diag);
+        in_blk = g.k;
+        out = g.out + g.k * g.b * g.ldx;
+    } else if (g.job == JOB_FWD || g.job == JOB_BWD) {
+        const int64_t i = (g.job == JOB_FWD) ? g.k + 1 + y : g.k;
+        const int64_t j = (g.job == JOB_FWD) ? g.k : y;
+        const TileDesc d = g.ltab[off_index(i, j)];
+        base = g.pool + d.offset;
+        prec = d.prec;
+        if (prec != KRR_PREC_FP32) inv_scale = 1.f / d.scale;
+        in_blk = g.k;
+        out = g.out + ((g.job == JOB_FWD) ? i : j) * g.b * g.ldx;
+    } else {
+        int64_t i, j;  // y is the lower-triangle index of tile (i, j)
+        tri_decode(y, &i, &j);
+        base = reinterpret_cast<const uint8_t *>(g.Kd + tri_index(i, j) * g.b * g.b);
+        shift = (float)*g.shift;
+        in_blk = (g.job == JOB_RES_N) ? j : i;
+        const int64_t slot = (g.job == JOB_RES_N) ? (i * g.nt + j) : (j * g.nt + i);
+        out = g.out + slot * g.b * g.pc;
+        ldo = g.pc;
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ void gemv_n_rows(const uint8_t *base, float inv_scale, float shift, int64_t b,
+                                            int64_t r0, int64_t r1, const float *zt, int pc,
+                                            float *out, int64_t ldo, int q0, bool subtract) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t r = r0 + warp; r < r1; r += nw) {
         float acc[PC];
 #pragma unroll
         for (int q = 0; q < PC; ++q) acc[q] = 0.f;
-        const int64_t cend = (mode == 0) ? r + 1 : b;
-        for (int64_t cidx = lane; cidx < cend; cidx += 32) {
-            const float l = load_l(base, prec, r * b + cidx);
-            const float *zr = zs + cidx * pc;
+        const int64_t rowe = r * b;
+        for (int64_t c0 = 0; c0 < b; c0 += 512) {
+            float4 v[4];
 #pragma unroll
-            for (int q = 0; q < PC; ++q)
-                if (q < pc) acc[q] = fmaf(l, zr[q], acc[q]);
+            for (int u = 0; u < 4; ++u) {
+                const int64_t c = c0 + u * 128 + lane * 4;
+                v[u] = (c < b) ? load4<PREC>(base, rowe + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v[u].x -= shift; v[u].y -= shift; v[u].z -= shift; v[u].w -= shift;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t c = c0 + u * 128 + lane * 4;
+                if (c >= b) break;
+#pragma unroll
+                for (int q = 0; q < PC; ++q) {
+                    if (q < pc) {
+                        const float4 z = *reinterpret_cast<const float4 *>(zt + q * b + c);
+                        acc[q] = fmaf(v[u].x, z.x, fmaf(v[u].y, z.y, fmaf(v[u].z, z.z, fmaf(v[u].w, z.w, acc[q]))));
+                    }
+                }
+            }
         }
         float mine = 0.f;
 #pragma unroll
         for (int q = 0; q < PC; ++q) {
-            if (q >= pc) break;
-            float v = acc[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == q) mine = v;
+            if (q < pc) {
+                float t = acc[q];
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+                if (lane == q) mine = t;
+            }
         }
         if (lane < pc) {
-            float *dst = dst_blk + r * ldx + q0 + lane;
-            if (mode == 0) *dst = mine * inv_scale;
-            else *dst -= mine * inv_scale;
+            float *dst = out + r * ldo + q0 + lane;
+            const float v = mine * inv_scale;
+            if (subtract) *dst -= v;
+            else *dst = v;
         }
     }
 }
 
-// Backward kernel: out cols (-)= M^T x_k, one thread per column c.
-// mode 0: M = Linv_kk (lower: r >= c); out = block k of `out`, stored.
-// mode 1: M = L_kj for every j < k (grid.y); out = block j of `out`,
-//         subtracted.  x_k is block k of `in`.
-__global__ void __launch_bounds__(128) solve_bwd_kernel(int mode, int64_t k, int64_t b,
-                                                        const float *Linv, const uint8_t *pool,
-                                                        const TileDesc *ltab, const float *in,
-                                                        float *out, int64_t ldx, int q0, int pc) {
-    extern __shared__ float as[];  // b x pc
-    const float *asrc = in + k * b * ldx;
-    for (int64_t e = threadIdx.x; e < b * pc; e += blockDim.x) as[e] = asrc[(e / pc) * ldx + q0 + e % pc];
-    __syncthreads();
-    const int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t j = (mode == 0) ? k : blockIdx.y;
+// grid: (b / rows_per_cta, tasks); dynamic smem: pc * b floats (x block, transposed)
+__global__ void __launch_bounds__(256) gemv_n_kernel(GemvArgs g, int rows_per_cta) {
+    extern __shared__ float zt[];
     const uint8_t *base;
     int prec;
-    float inv_scale;
-    if (mode == 0) {
-        base = reinterpret_cast<const uint8_t *>(Linv + k * b * b);
-        prec = KRR_PREC_FP32;
-        inv_scale = 1.f;
-    } else {
-        const TileDesc d = ltab[off_index(k, j)];
-        base = pool + d.offset;
-        prec = d.prec;
-        inv_scale = (prec == KRR_PREC_FP32) ? 1.f : 1.f / d.scale;
+    float inv_scale, shift;
+    int64_t in_blk, ldo;
+    float *out;
+    gemv_locate(g, blockIdx.y, base, prec, inv_scale, shift, in_blk, out, ldo);
+    const float *xin = g.x + in_blk * g.b * g.ldx + g.q0;
+    {
+        // stage x_k transposed (zt[q][c]) without integer division
+        const int bi = (int)g.b, ldx = (int)g.ldx, pc = g.pc;
+        for (int c = threadIdx.x; c < bi; c += blockDim.x) {
+            const float *src = xin + (int64_t)c * ldx;
+            for (int q = 0; q < pc; ++q) zt[q * bi + c] = src[q];
+        }
     }
-    float acc[PC];
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta, r1 = r0 + rows_per_cta;
+    const bool sub = (g.job == JOB_FWD || g.job == JOB_BWD);
+    const int q0o = (g.job >= JOB_RES_N) ? 0 : g.q0;
+    if (prec == KRR_PREC_FP32) gemv_n_rows<KRR_PREC_FP32>(base, inv_scale, shift, g.b, r0, r1, zt, g.pc, out, ldo, q0o, sub);
+    else if (prec == KRR_PREC_FP16) gemv_n_rows<KRR_PREC_FP16>(base, inv_scale, shift, g.b, r0, r1, zt, g.pc, out, ldo, q0o, sub);
+    else gemv_n_rows<KRR_PREC_E4M3>(base, inv_scale, shift, g.b, r0, r1, zt, g.pc, out, ldo, q0o, sub);
+}
+
+template <int PREC>
+__device__ __forceinline__ void gemv_t_cols(const uint8_t *base, float inv_scale, float shift, int64_t b,
+                                            int64_t c0, const float *at, int pcp, int pc, float *red,
+                                            float *out, int64_t ldo, int q0, bool subtract) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t rows_per_warp = b / 8;
+    const int64_t ra = warp * rows_per_warp, rb = ra + rows_per_warp;
+    const int64_t col = c0 + lane * 4;
+    float acc[4][PC];
 #pragma unroll
-    for (int q = 0; q < PC; ++q) acc[q] = 0.f;
-    const int64_t rstart = (mode == 0) ? cidx : 0;
-    for (int64_t r = rstart; r < b; ++r) {
-        const float l = load_l(base, prec, r * b + cidx);
-        const float *ar = as + r * pc;
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int q = 0; q < PC; ++q) acc[e][q] = 0.f;
+    for (int64_t r = ra; r < rb; r += 4) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            v[u] = load4<PREC>(base, (r + u) * b + col);
+            v[u].x -= shift; v[u].y -= shift; v[u].z -= shift; v[u].w -= shift;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float *ar = at + (r + u) * pcp;
+#pragma unroll
+            for (int q4 = 0; q4 < PC / 4; ++q4) {
+                if (q4 * 4 < pc) {
+                    const float4 a = *reinterpret_cast<const float4 *>(ar + q4 * 4);
+                    const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const int q = q4 * 4 + t;
+                        acc[0][q] = fmaf(v[u].x, av[t], acc[0][q]);
+                        acc[1][q] = fmaf(v[u].y, av[t], acc[1][q]);
+                        acc[2][q] = fmaf(v[u].z, av[t], acc[2][q]);
+                        acc[3][q] = fmaf(v[u].w, av[t], acc[3][q]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();  // at[] is no longer read: red[] may alias it
+    // red layout: [warp][128 columns][pc]
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
 #pragma unroll
         for (int q = 0; q < PC; ++q)
-            if (q < pc) acc[q] = fmaf(l, ar[q], acc[q]);
-    }
-    float *dst = out + (j * b + cidx) * ldx + q0;
+            if (q < pc) red[(warp * 128 + lane * 4 + e) * pc + q] = acc[e][q];
+    __syncthreads();
+    for (int t = threadIdx.x; t < 128 * pc; t += blockDim.x) {
+        const int cc = t / pc, q = t % pc;
+        float s = 0.f;
 #pragma unroll
-    for (int q = 0; q < PC; ++q) {
-        if (q >= pc) break;
-        if (mode == 0) dst[q] = acc[q] * inv_scale;
-        else dst[q] -= acc[q] * inv_scale;
+        for (int w = 0; w < 8; ++w) s += red[(w * 128 + cc) * pc + q];
+        float *dst = out + (c0 + cc) * ldo + q0 + q;
+        const float v = s * inv_scale;
+        if (subtract) *dst -= v;
+        else *dst = v;
     }
+}
+
+// grid: (b / 128, tasks), 256 threads; dynamic smem: max(b * pcp, 8 * 128 * pc) floats
+__global__ void __launch_bounds__(256) gemv_t_kernel(GemvArgs g) {
+    extern __shared__ float at[];
+    const uint8_t *base;
+    int prec;
+    float inv_scale, shift;
+    int64_t in_blk, ldo;
+    float *out;
+    int64_t y = blockIdx.y;
+    if (g.job == JOB_RES_T) {
+        // grid.y runs over the strictly-lower tiles: off_index(i, j) =
+        // tri_index(i - 1, j), so decode with the triangle of size nt - 1
+        int64_t i, j;
+        tri_decode(y, &i, &j);
+        y = tri_index(i + 1, j);
+    }
+    gemv_locate(g, y, base, prec, inv_scale, shift, in_blk, out, ldo);
+    const int pcp = (g.pc + 3) & ~3;
+    const float *xin = g.x + in_blk * g.b * g.ldx + g.q0;
+    {
+        // stage x_k row-major with padded width pcp, without integer division
+        const int bi = (int)g.b, ldx = (int)g.ldx, pc = g.pc;
+        for (int r = threadIdx.x; r < bi; r += blockDim.x) {
+            const float *src = xin + (int64_t)r * ldx;
+            float *dst = at + r * pcp;
+            for (int q = 0; q < pcp; ++q) dst[q] = (q < pc) ? src[q] : 0.f;
+        }
+    }
+    __syncthreads();
+    const int64_t c0 = (int64_t)blockIdx.x * 128;
+    const bool sub = (g.job == JOB_FWD || g.job == JOB_BWD);
+    const int q0o = (g.job >= JOB_RES_N) ? 0 : g.q0;
+    if (prec == KRR_PREC_FP32) gemv_t_cols<KRR_PREC_FP32>(base, inv_scale, shift, g.b, c0, at, pcp, g.pc, at, out, ldo, q0o, sub);
+    else if (prec == KRR_PREC_FP16) gemv_t_cols<KRR_PREC_FP16>(base, inv_scale, shift, g.b, c0, at, pcp, g.pc, at, out, ldo, q0o, sub);
+    else gemv_t_cols<KRR_PREC_E4M3>(base, inv_scale, shift, g.b, c0, at, pcp, g.pc, at, out, ldo, q0o, sub);
+}
+
+static size_t gemv_n_smem(int64_t b, int pc) { return (size_t)b * pc * sizeof(float); }
+static size_t gemv_t_smem(int64_t b, int pc) {
+    const size_t a = (size_t)b * ((pc + 3) & ~3), r = (size_t)8 * 128 * pc;
+    return (a > r ? a : r) * sizeof(float);
+}
+
+static void gemv_attrs() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(gemv_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(gemv_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    done = true;
+}
+
+static GemvArgs gemv_args(Ctx *c, int job, int64_t k, const float *x, int64_t ldx, float *out, int q0,
+                          int pc) {
+    GemvArgs g;
+    memset(&g, 0, sizeof(g));
+    g.job = job;
+    g.k = k;
+    g.b = c->b;
+    g.nt = c->nt;
+    g.pool = c->pool;
+    g.ltab = c->ltab;
+    g.Kd = c->Kd;
+    g.shift = c->red + RED_KSHIFT;
+    g.x = x;
+    g.ldx = ldx;
+    g.out = out;
+    g.q0 = q0;
+    g.pc = pc;
+    return g;
 }
 
 // x (n_pad x p) <- (L L^T)^-1 x.  tmp is n_pad x p scratch.  Forward:
 // tmp_k = Linv_kk x_k, then x_i -= L_ik tmp_k (i > k); tmp ends as Z.
-// Backward: x_k = Linv_kk^T tmp_k, then tmp_j -= L_kj^T x_k (j < k).
+// Backward: x_k = Linv_kk^T tmp_k (through the stored transpose), then
+// tmp_j -= L_kj^T x_k (j < k).
 void solve_inplace(Ctx *c, float *x, float *tmp, int64_t p) {
-    const int64_t b = c->b, nt = c->nt;
+    const int64_t b = c->b, nt = c->nt, bb = b * b;
     cudaStream_t s = c->stream;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(solve_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(solve_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
-    const int pcmax = (int)std::max<int64_t>(1, std::min<int64_t>(PC, 32768 / b));
-    for (int q0 = 0; q0 < p; q0 += pcmax) {
-        const int pc = (int)std::min<int64_t>(pcmax, p - q0);
-        const size_t sh = (size_t)b * pc * sizeof(float);
+    gemv_attrs();
+    for (int q0 = 0; q0 < p; q0 += PC) {
+        const int pc = (int)std::min<int64_t>(PC, p - q0);
+        const size_t shn = gemv_n_smem(b, pc), sht = gemv_t_smem(b, pc);
         for (int64_t k = 0; k < nt; ++k) {
-            count_launch(), solve_fwd_kernel<<<dim3((unsigned)(b / 64), 1), 256, sh, s>>>(0, k, b, c->Linv, c->pool,
-                                                                           c->ltab, x, tmp, p, q0, pc);
-            if (k + 1 < nt)
-                count_launch(), solve_fwd_kernel<<<dim3((unsigned)(b / 64), (unsigned)(nt - k - 1)), 256, sh, s>>>(
-                    1, k, b, c->Linv, c->pool, c->ltab, tmp, x, p, q0, pc);
+            GemvArgs g = gemv_args(c, JOB_DIAG, k, x, p, tmp, q0, pc);
+            g.diag = c->Linv + k * bb;
+            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 16), 1), 256, shn, s>>>(g, 16);
+            if (k + 1 < nt) {
+                GemvArgs f = gemv_args(c, JOB_FWD, k, tmp, p, x, q0, pc);
+                count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)(nt - k - 1)), 256, shn, s>>>(f, 64);
+            }
         }
         for (int64_t k = nt - 1; k >= 0; --k) {
-            count_launch(), solve_bwd_kernel<<<dim3((unsigned)(b / 128), 1), 128, sh, s>>>(0, k, b, c->Linv, c->pool,
-                                                                            c->ltab, tmp, x, p, q0, pc);
-            if (k > 0)
-                count_launch(), solve_bwd_kernel<<<dim3((unsigned)(b / 128), (unsigned)k), 128, sh, s>>>(
-                    1, k, b, c->Linv, c->pool, c->ltab, x, tmp, p, q0, pc);
+            GemvArgs g = gemv_args(c, JOB_DIAG, k, tmp, p, x, q0, pc);
+            g.diag = c->LinvT + k * bb;
+            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 16), 1), 256, shn, s>>>(g, 16);
+            if (k > 0) {
+                GemvArgs f = gemv_args(c, JOB_BWD, k, x, p, tmp, q0, pc);
+                count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)k), 256, sht, s>>>(f);
+            }
         }
     }
 }
 
 // ----------------------------------------------------------------------------
-// Residual r = y - lambda a - K a with K read from the FP32 lower-triangle
-// tiles (symmetric use).  Products in FP32, partial sums per tile row in
-// FP32, tiles accumulated in FP64.  Two passes so that every output element
-// has one owner: the N pass covers tiles (i, j <= i) row-wise, the T pass
-// covers tiles (j > i, i) column-wise.
+// Refinement residual r = y - lambda a - K a, K from the FP32 lower-triangle
+// tiles (symmetric use), computed as (K - c 1 1^T) a + c 1 (1^T a): the
+// shifted entries are small, so FP32 products and per-tile FP32 sums lose far
+// less to cancellation; c 1^T a is formed in FP64 (c = the mean off-diagonal
+// entry of K).  Every tile pair (i, j) writes its own partial slot:
+// slot (i, j <= i) = (K_ij - c) a_j from the row pass and slot (j, i > j) =
+// (K_ij - c)^T a_i from the column pass; the slots of a row block are then
+// summed in FP64 in a fixed order.
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) residual_n_kernel(int64_t nt, int64_t b, float lambda,
-                                                         const float *Kd, const float *y,
-                                                         const float *a, double *r, int64_t p,
-                                                         int q0, int pc, const double *shift,
-                                                         const double *colsum) {
-    const float cs = (float)*shift;
-    extern __shared__ float ash[];  // b x pc (block j of a)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t i = blockIdx.y;
-    const int64_t rbase = blockIdx.x * 64;
-    // each warp owns 8 rows: rbase + warp + 8 * t
-    double rowacc[8];
-    for (int t = 0; t < 8; ++t) rowacc[t] = 0.0;
-    for (int64_t j = 0; j <= i; ++j) {
-        __syncthreads();
-        for (int64_t e = threadIdx.x; e < b * pc; e += blockDim.x)
-            ash[e] = a[(j * b + e / pc) * p + q0 + e % pc];
-        __syncthreads();
-        const float *kt = Kd + tri_index(i, j) * b * b;
-        for (int t = 0; t < 8; ++t) {
-            const int64_t row = rbase + warp + 8 * t;
-            float acc[PC];
-#pragma unroll
-            for (int q = 0; q < PC; ++q) acc[q] = 0.f;
-            for (int64_t cidx = lane; cidx < b; cidx += 32) {
-                const float kv = kt[row * b + cidx] - cs;
-                const float *ar = ash + cidx * pc;
-#pragma unroll
-                for (int q = 0; q < PC; ++q)
-                    if (q < pc) acc[q] = fmaf(kv, ar[q], acc[q]);
-            }
-#pragma unroll
-            for (int q = 0; q < PC; ++q) {
-                if (q >= pc) break;
-                float v = acc[q];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == q) rowacc[t] += (double)v;
-            }
-        }
-    }
-    for (int t = 0; t < 8; ++t) {
-        const int64_t row = i * b + rbase + warp + 8 * t;
-        if (lane < pc) {
-            const int64_t e = row * p + q0 + lane;
-            r[e] = (double)y[e] - (double)lambda * (double)a[e] - rowacc[t] -
-                   (double)cs * colsum[q0 + lane];
-        }
-    }
-}
-
-__global__ void __launch_bounds__(128) residual_t_kernel(int64_t nt, int64_t b, const float *Kd,
-                                                         const float *a, double *r, int64_t p,
-                                                         int q0, int pc, const double *shift) {
-    const float cs = (float)*shift;
-    extern __shared__ float ash[];  // b x pc (block j of a)
-    const int64_t i = blockIdx.y;
-    const int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double acc64[PC];
-#pragma unroll
-    for (int q = 0; q < PC; ++q) acc64[q] = 0.0;
-    for (int64_t j = i + 1; j < nt; ++j) {
-        __syncthreads();
-        for (int64_t e = threadIdx.x; e < b * pc; e += blockDim.x)
-            ash[e] = a[(j * b + e / pc) * p + q0 + e % pc];
-        __syncthreads();
-        const float *kt = Kd + tri_index(j, i) * b * b;
-        float acc[PC];
-#pragma unroll
-        for (int q = 0; q < PC; ++q) acc[q] = 0.f;
-        for (int64_t rr = 0; rr < b; ++rr) {
-            const float kv = kt[rr * b + cidx] - cs;
-            const float *ar = ash + rr * pc;
-#pragma unroll
-            for (int q = 0; q < PC; ++q)
-                if (q < pc) acc[q] = fmaf(kv, ar[q], acc[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < PC; ++q) acc64[q] += (double)acc[q];
-    }
-    for (int q = 0; q < pc; ++q) r[(i * b + cidx) * p + q0 + q] -= acc64[q];
+// grid: (b / 8, nt), block (pc, 8): one thread per (row, column) of a row block.
+__global__ void residual_reduce_kernel(const float *part, int64_t nt, int64_t b, int pc, int q0,
+                                       int64_t p, float lambda, const float *y, const float *a,
+                                       const double *shift, const double *colsum, double *r) {
+    const int64_t i = blockIdx.y, lr = (int64_t)blockIdx.x * 8 + threadIdx.y;
+    const int q = threadIdx.x;
+    const int64_t row = i * b + lr;
+    double s = 0.0;
+    for (int64_t j = 0; j < nt; ++j) s += (double)part[((i * nt + j) * b + lr) * pc + q];
+    const int64_t idx = row * p + q0 + q;
+    r[idx] = (double)y[idx] - (double)lambda * (double)a[idx] - s - (*shift) * colsum[q0 + q];
 }
 
 // Column sums of a (n x p) in FP64, one block per column.
@@ -1077,27 +1304,21 @@ __global__ void colsum_kernel(const float *a, int64_t n, int64_t p, double *out)
     }
 }
 
-// K A = (K - c 1 1^T) A + c 1 (1^T A): the shifted products are small, so
-// FP32 products and partial sums lose far less to cancellation; c 1^T A is
-// formed in FP64.  c = the mean off-diagonal entry of K (red[RED_KSHIFT]).
 void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
     const int64_t b = c->b, nt = c->nt;
-    const int pcmax = (int)std::max<int64_t>(1, std::min<int64_t>(PC, 32768 / b));
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(residual_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(residual_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
-    const double *shift = c->red + RED_KSHIFT;
+    gemv_attrs();
     count_launch(), colsum_kernel<<<(unsigned)p, 512, 0, c->stream>>>(a, c->n_pad, p, c->colsum);
-    for (int q0 = 0; q0 < p; q0 += pcmax) {
-        const int pc = (int)std::min<int64_t>(pcmax, p - q0);
-        const size_t sh = (size_t)b * pc * sizeof(float);
-        count_launch(), residual_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)nt), 256, sh, c->stream>>>(
-            nt, b, (float)c->lambda, c->Kd, y, a, r, p, q0, pc, shift, c->colsum);
-        count_launch(), residual_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)nt), 128, sh, c->stream>>>(
-            nt, b, c->Kd, a, r, p, q0, pc, shift);
+    const int64_t ntri = nt * (nt + 1) / 2, noff = nt * (nt - 1) / 2;
+    for (int q0 = 0; q0 < p; q0 += PC) {
+        const int pc = (int)std::min<int64_t>(PC, p - q0);
+        GemvArgs gn = gemv_args(c, JOB_RES_N, 0, a, p, c->res_part, q0, pc);
+        count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)ntri), 256, gemv_n_smem(b, pc), c->stream>>>(gn, 64);
+        if (noff > 0) {
+            GemvArgs gt = gemv_args(c, JOB_RES_T, 0, a, p, c->res_part, q0, pc);
+            count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)noff), 256, gemv_t_smem(b, pc), c->stream>>>(gt);
+        }
+        count_launch(), residual_reduce_kernel<<<dim3((unsigned)(b / 8), (unsigned)nt), dim3(pc, 8), 0, c->stream>>>(
+            c->res_part, nt, b, pc, q0, p, (float)c->lambda, y, a, c->red + RED_KSHIFT, c->colsum, r);
     }
 }
 
@@ -1196,4 +1417,65 @@ void launch_factor_to_dense(Ctx *c, float *dst, int64_t ld) {
         c->Wd, c->pool, c->ltab, c->b, c->n, dst, ld);
 }
 
+}  // namespace krr
+
+namespace krr {
+// ---------------------------------------------------------------------------
+// Helpers of the hyperparameter gradient (deterministic single-block sums).
+// ---------------------------------------------------------------------------
+// gp[r][q] = 2 (yhat - yt) / (n_test p) for r < n_test, 0 for padding rows;
+// sq[r * p + q] = (yhat - yt)^2 (r < n_test).
+__global__ void grad_prep_kernel(const float *yhat, const float *yt, int64_t n_test, int64_t p,
+                                 int64_t rows, float *gp, double *sq) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= rows * p) return;
+    const int64_t r = e / p;
+    if (r < n_test) {
+        const double d = (double)yhat[e] - (double)yt[e];
+        gp[e] = (float)(2.0 * d / (double)(n_test * p));
+        sq[e] = d * d;
+    } else {
+        gp[e] = 0.f;
+        sq[e] = 0.0;
+    }
+}
+
+__global__ void sum_f64_kernel(const double *x, int64_t n, double *out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += x[e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *out = t;
+    }
+}
+
+__global__ void dot_f32_kernel(const float *a, const float *b, int64_t n, double *out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) s += (double)a[e] * (double)b[e];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        *out = t;
+    }
+}
+
+void launch_grad_prep(const float *yhat, const float *yt, int64_t n_test, int64_t p, int64_t rows,
+                      float *gp, double *sq, cudaStream_t s) {
+    count_launch(), grad_prep_kernel<<<cdiv(rows * p, 256), 256, 0, s>>>(yhat, yt, n_test, p, rows, gp, sq);
+}
+void launch_sum_f64(const double *x, int64_t n, double *out, cudaStream_t s) {
+    count_launch(), sum_f64_kernel<<<1, 1024, 0, s>>>(x, n, out);
+}
+void launch_dot_f32(const float *a, const float *b, int64_t n, double *out, cudaStream_t s) {
+    count_launch(), dot_f32_kernel<<<1, 1024, 0, s>>>(a, b, n, out);
+}
 }  // namespace krr

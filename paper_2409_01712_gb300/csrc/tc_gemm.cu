@@ -21,6 +21,11 @@
 //              the weights; per-block partial products.
 //   OP_TRSM    Factorize (Alg. 3), panel solve of tile column k:
 //              L_ik = W_ik Linv_kk^T with FP16 hi/lo operand splits.
+//   OP_GRADT   Gradient of the held-out loss (not in the paper): the test x
+//              training distance tile again, contracted as
+//              sum_j d_tj K_tj <G_p,t, A_j> per block.
+//   OP_GRADK   Same over the lower-triangle training tiles:
+//              sum_ij d_ij K_ij <Z_i, A_j> (both triangles through symmetry).
 //   OP_UPDATE  Factorize (Alg. 3), trailing update of step k:
 //              W_ij -= L_ik L_jk^T for k < j <= i, FP16 operands (hi/lo
 //              phases for tiles stored at FP32 accuracy), FP32 accumulation.
@@ -36,7 +41,8 @@ namespace krr {
 
 namespace {
 
-constexpr int OP_DIST = 0, OP_PREDICT = 1, OP_TRSM = 2, OP_UPDATE = 3;
+constexpr int OP_DIST = 0, OP_PREDICT = 1, OP_TRSM = 2, OP_UPDATE = 3, OP_GRADT = 4, OP_GRADK = 5;
+constexpr int GRAD_MAX_P = 16;
 constexpr int KIND_F16 = 0, KIND_F8 = 1;
 
 constexpr int BM = 128, BN = 256;       // output block
@@ -45,7 +51,8 @@ constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * SLAB;      // 16 KB
 constexpr int B_BYTES = BN * SLAB;      // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int NUM_THREADS = 192;
+constexpr int NUM_THREADS = 320;        // 2 control warps + 8 epilogue warps
+constexpr int EPI_THREADS = 256;
 constexpr int TMEM_COLS = 512;          // two 256-column FP32 accumulators
 constexpr int PRED_MAX_P = 32;
 
@@ -71,6 +78,9 @@ struct TcParams {
     float *colbuf;
     const float *aw;
     float *part;
+    const float *zw;   // OP_GRADK: Z = (K + lambda I)^-1 K_t^T G_p, n_pad x ldaw
+    const float *gp;   // OP_GRADT: G_p, padded test rows x ldaw
+    double *gpart;     // OP_GRADT / OP_GRADK: one partial sum per block
     uint64_t wait_ns;
     DevErrors *err;
 };
@@ -82,6 +92,7 @@ struct Work {
     int arow[3], brow[3];
     // epilogue coordinates
     int64_t i, j, sm, sn;
+    int64_t t;  // item index
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -198,7 +209,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
 }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // ---------------------------------------------------------------------------
 // Work decoding: item index -> operand phases and epilogue coordinates.
@@ -206,10 +221,11 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 // of slabs of every block (zero for skipped blocks).
 // ---------------------------------------------------------------------------
 template <int OP>
-__device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w) {
+__device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, const TileDesc *col_desc) {
     const int64_t b = p.b;
     const int64_t sub_cols = b / BN, sub_per_tile = (b / BM) * sub_cols;
-    if (OP == OP_DIST) {
+    w.t = t;
+    if (OP == OP_DIST || OP == OP_GRADK) {
         const int64_t tile = t / sub_per_tile, sub = t % sub_per_tile;
         tri_decode(tile, &w.i, &w.j);
         w.sm = sub / sub_cols;
@@ -220,7 +236,7 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w) {
         w.bmap[0] = 2;
         w.arow[0] = (int)(w.i * b + w.sm * BM);
         w.brow[0] = (int)(w.j * b + w.sn * BN);
-    } else if (OP == OP_PREDICT) {
+    } else if (OP == OP_PREDICT || OP == OP_GRADT) {
         const int64_t ncb = p.n_pad / BN;
         w.i = t / ncb;                 // 128-row block of test rows
         w.j = t % ncb;                 // 256-column block of training rows
@@ -274,29 +290,62 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w) {
             w.nph = 0;  // strictly above the diagonal of a diagonal tile
             return;
         }
-        const int pi = p.ltab[off_index(w.i, k)].prec;
-        const int pj = p.ltab[off_index(w.j, k)].prec;
-        const int arow = (int)((w.i - k - 1) * b + w.sm * BM);
-        const int brow = (int)((w.j - k - 1) * b + w.sn * BN);
+        // operand maps: 0 = factor pool viewed as FP16 rows of b, 1 = FP16 (hi)
+        // panel of the column, 2 = FP16 lo panel.  FP16 tiles are read from the
+        // pool directly; FP32 tiles use the hi/lo split, E4M3 tiles their FP16
+        // shadow in the hi panel.
+        const TileDesc di = col_desc[w.i - k - 1];
+        const TileDesc dj = col_desc[w.j - k - 1];
+        const int ahi_map = (di.prec == KRR_PREC_FP16) ? 0 : 1;
+        const int bhi_map = (dj.prec == KRR_PREC_FP16) ? 0 : 1;
+        const int ahi_row = (int)((di.prec == KRR_PREC_FP16 ? di.offset / (2 * b) : (w.i - k - 1) * b) + w.sm * BM);
+        const int bhi_row = (int)((dj.prec == KRR_PREC_FP16 ? dj.offset / (2 * b) : (w.j - k - 1) * b) + w.sn * BN);
+        const int alo_row = (int)((w.i - k - 1) * b + w.sm * BM);
+        const int blo_row = (int)((w.j - k - 1) * b + w.sn * BN);
         int q = 0;
-        w.amap[q] = 0; w.bmap[q] = 2; ++q;
-        if (pj == KRR_PREC_FP32) { w.amap[q] = 0; w.bmap[q] = 3; ++q; }
-        if (pi == KRR_PREC_FP32) { w.amap[q] = 1; w.bmap[q] = 2; ++q; }
+        w.amap[q] = ahi_map; w.arow[q] = ahi_row; w.bmap[q] = bhi_map; w.brow[q] = bhi_row; ++q;
+        if (dj.prec == KRR_PREC_FP32) { w.amap[q] = ahi_map; w.arow[q] = ahi_row; w.bmap[q] = 2; w.brow[q] = blo_row; ++q; }
+        if (di.prec == KRR_PREC_FP32) { w.amap[q] = 2; w.arow[q] = alo_row; w.bmap[q] = bhi_map; w.brow[q] = bhi_row; ++q; }
         w.nph = q;
-        for (int e = 0; e < 3; ++e) {
-            w.arow[e] = arow;
-            w.brow[e] = brow;
-        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Epilogues.  Thread r (0..127) owns accumulator row r = TMEM lane r.
+// Epilogues.  Eight warps: warp w (2..9) reads TMEM lane quarter w % 4, so
+// thread `row` owns accumulator row `row`; `half` = (w - 2) / 4 selects
+// columns [half * 128, half * 128 + 128) of the 256-column block.
 // ---------------------------------------------------------------------------
+constexpr int CH_PER_HALF = BN / 16 / 2;
+
+// Issues L2 prefetches for the trailing-update input row segment of this
+// thread, before it waits for the accumulator.
 template <int OP>
-__device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row,
-                                         int32_t *nb_s, float *aw_s, double *red_s) {
+__device__ __forceinline__ void epilogue_prefetch(const TcParams &p, const Work &w, int row, int half) {
+    if (OP != OP_UPDATE) return;
+    const int64_t b = p.b, k = p.k;
+    const int64_t lr = w.sm * BM + row, c0 = w.sn * BN + half * 128;
+    const char *ptr;
+    int bytes;
+    if (w.i == w.j) {
+        ptr = reinterpret_cast<const char *>((k == 0 ? p.Kd + tri_index(w.i, w.i) * b * b : p.Wd + w.i * b * b) +
+                                             lr * b + c0);
+        bytes = 512;
+    } else if (k == 0) {
+        ptr = reinterpret_cast<const char *>(p.Kd + tri_index(w.i, w.j) * b * b + lr * b + c0);
+        bytes = 512;
+    } else {
+        ptr = reinterpret_cast<const char *>(p.W + off_index(w.i, w.j) * b * b + lr * b + c0);
+        bytes = 256;
+    }
+    for (int o = 0; o < bytes; o += 128) prefetch_l2(ptr + o);
+}
+
+template <int OP>
+__device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row, int half,
+                                         int32_t *nb_s, float *aw_s, double *red_s,
+                                         const TileDesc *col_desc) {
     const int64_t b = p.b;
+    const int ch0 = half * CH_PER_HALF;
     if (OP == OP_DIST) {
         const int64_t gi = w.i * b + w.sm * BM + row;
         const int32_t ni = p.norms_a[gi];
@@ -304,7 +353,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
         float *krow = p.Kd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN;
         uint32_t *drow = p.Dd ? p.Dd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN : nullptr;
         double ss = 0.0, s1 = 0.0;
-        for (int ch = 0; ch < BN / 16; ++ch) {
+        for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
             float v[16];
             tmem_ld16(tacc + ch * 16, v);
             float kv[16];
@@ -329,22 +378,28 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                 for (int e = 0; e < 4; ++e) dd[e] = make_uint4(dv[4 * e], dv[4 * e + 1], dv[4 * e + 2], dv[4 * e + 3]);
             }
         }
-        // deterministic per-block sums of K^2 and K: warp sums, then the four
+        // deterministic per-block sums of K^2 and K: warp sums, then the eight
         // warps in order.  Layout: all K^2 partials, then all K partials.
         for (int o = 16; o > 0; o >>= 1) {
             ss += __shfl_xor_sync(0xffffffffu, ss, o);
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
         }
-        if ((row & 31) == 0) {
-            red_s[row >> 5] = ss;
-            red_s[4 + (row >> 5)] = s1;
+        const int ew = (threadIdx.x >> 5) - 2;
+        if ((threadIdx.x & 31) == 0) {
+            red_s[ew] = ss;
+            red_s[8 + ew] = s1;
         }
         epi_bar();
-        if (row == 0) {
+        if (threadIdx.x == 64) {
             const int64_t sub_per_tile = (b / BM) * (b / BN);
             const int64_t slot = tidx * sub_per_tile + w.sm * (b / BN) + w.sn;
-            p.knorm_part[slot] = red_s[0] + red_s[1] + red_s[2] + red_s[3];
-            p.knorm_part[p.items + slot] = red_s[4] + red_s[5] + red_s[6] + red_s[7];
+            double a0 = 0.0, a1 = 0.0;
+            for (int q = 0; q < 8; ++q) {
+                a0 += red_s[q];
+                a1 += red_s[8 + q];
+            }
+            p.knorm_part[slot] = a0;
+            p.knorm_part[p.items + slot] = a1;
         }
     } else if (OP == OP_PREDICT) {
         const int64_t gi = w.i * BM + row;  // test row
@@ -353,7 +408,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
 #pragma unroll
         for (int q = 0; q < PRED_MAX_P; ++q) acc[q] = 0.f;
         const int pp = (int)p.p;
-        for (int ch = 0; ch < BN / 16; ++ch) {
+        for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
             float v[16];
             tmem_ld16(tacc + ch * 16, v);
 #pragma unroll
@@ -368,12 +423,57 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                     if (q < pp) acc[q] = fmaf(kv, ar[q], acc[q]);
             }
         }
-        // partials are laid out [column block][padded test row][p]
-        float *dst = p.part + (w.j * p.test_rows + gi) * p.p;
+        // partials: [128-column block][padded test row][p]
+        float *dst = p.part + ((2 * w.j + half) * p.test_rows + gi) * p.p;
         for (int q = 0; q < pp; ++q) dst[q] = acc[q];
+    } else if (OP == OP_GRADT || OP == OP_GRADK) {
+        // d K-weighted contractions for the hyperparameter gradient
+        const bool kterm = (OP == OP_GRADK);
+        const int64_t gi = kterm ? w.i * b + w.sm * BM + row : w.i * BM + row;
+        const int64_t a_real = kterm ? p.n : p.n_test;
+        const int32_t ni = p.norms_a[gi];
+        const int pp = (int)p.p;
+        float accA[GRAD_MAX_P], accZ[GRAD_MAX_P];
+#pragma unroll
+        for (int q = 0; q < GRAD_MAX_P; ++q) accA[q] = accZ[q] = 0.f;
+        for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
+            float v[16];
+            tmem_ld16(tacc + ch * 16, v);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int c = ch * 16 + e;
+                const int64_t gj = kterm ? w.j * b + w.sn * BN + c : w.j * BN + c;
+                const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
+                const float sv = (gi < a_real && gj < p.n) ? (float)d * expf(-p.gamma * (float)d) : 0.f;
+                const float *ar = aw_s + c * PRED_MAX_P;
+#pragma unroll
+                for (int q = 0; q < GRAD_MAX_P; ++q) {
+                    if (q < pp) {
+                        accA[q] = fmaf(sv, ar[q], accA[q]);
+                        if (kterm) accZ[q] = fmaf(sv, ar[GRAD_MAX_P + q], accZ[q]);
+                    }
+                }
+            }
+        }
+        double val = 0.0;
+        if (gi < a_real) {
+            const float *own = kterm ? p.zw : p.gp;  // Z_i or G_p,t
+            for (int q = 0; q < pp; ++q) val += (double)own[gi * p.ldaw + q] * (double)accA[q];
+            if (kterm && w.i != w.j)  // mirror entry (j, i) of an off-diagonal tile
+                for (int q = 0; q < pp; ++q) val += (double)p.aw[gi * p.ldaw + q] * (double)accZ[q];
+        }
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+        const int ew = (threadIdx.x >> 5) - 2;
+        if ((threadIdx.x & 31) == 0) red_s[ew] = val;
+        epi_bar();
+        if (threadIdx.x == 64) {
+            double a0 = 0.0;
+            for (int q = 0; q < 8; ++q) a0 += red_s[q];
+            p.gpart[w.t] = a0;
+        }
     } else if (OP == OP_TRSM) {
         float *orow = p.colbuf + (w.i - p.k - 1) * b * b + (w.sm * BM + row) * b + w.sn * BN;
-        for (int ch = 0; ch < BN / 16; ++ch) {
+        for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
             float v[16];
             tmem_ld16(tacc + ch * 16, v);
             float4 *dst = reinterpret_cast<float4 *>(orow + ch * 16);
@@ -382,7 +482,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
         }
     } else {  // OP_UPDATE
         const int64_t k = p.k;
-        const float sc = 1.f / (p.ltab[off_index(w.i, k)].scale * p.ltab[off_index(w.j, k)].scale);
+        const float sc = 1.f / (col_desc[w.i - k - 1].scale * col_desc[w.j - k - 1].scale);
         const int64_t lr = w.sm * BM + row;
         const bool diag = (w.i == w.j);
         const float *cin32 = nullptr;
@@ -395,7 +495,9 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
             io16 = p.W + off_index(w.i, w.j) * b * b + lr * b + w.sn * BN;
             if (k == 0) cin32 = p.Kd + tri_index(w.i, w.j) * b * b + lr * b + w.sn * BN;
         }
-        for (int ch = 0; ch < BN / 16; ++ch) {
+#pragma unroll
+        for (int cc = 0; cc < CH_PER_HALF; ++cc) {
+            const int ch = ch0 + cc;
             float v[16];
             tmem_ld16(tacc + ch * 16, v);
             float cin[16];
@@ -449,10 +551,24 @@ template <int OP>
 __device__ __forceinline__ void epilogue_stage(const TcParams &p, const Work &w, int row,
                                                int32_t *nb_s, float *aw_s) {
     if (OP == OP_DIST) {
-        for (int c = row; c < BN; c += 128) nb_s[c] = p.norms_b[w.j * p.b + w.sn * BN + c];
-    } else if (OP == OP_PREDICT) {
-        for (int c = row; c < BN; c += 128) nb_s[c] = p.norms_b[w.j * BN + c];
-        for (int e = row; e < BN * PRED_MAX_P; e += 128) {
+        for (int c = row; c < BN; c += EPI_THREADS) nb_s[c] = p.norms_b[w.j * p.b + w.sn * BN + c];
+    } else if (OP == OP_GRADK) {
+        // columns j of the block: norms, A_j in slots [0, 16), Z_j in [16, 32)
+        const int64_t j0 = w.j * p.b + w.sn * BN;
+        for (int c = row; c < BN; c += EPI_THREADS) nb_s[c] = p.norms_b[j0 + c];
+        for (int e = row; e < BN * PRED_MAX_P; e += EPI_THREADS) {
+            const int c = e / PRED_MAX_P, q = e % PRED_MAX_P;
+            float v = 0.f;
+            if (q < GRAD_MAX_P) {
+                if (q < p.p) v = p.aw[(j0 + c) * p.ldaw + q];
+            } else if (q - GRAD_MAX_P < p.p) {
+                v = p.zw[(j0 + c) * p.ldaw + (q - GRAD_MAX_P)];
+            }
+            aw_s[e] = v;
+        }
+    } else if (OP == OP_PREDICT || OP == OP_GRADT) {
+        for (int c = row; c < BN; c += EPI_THREADS) nb_s[c] = p.norms_b[w.j * BN + c];
+        for (int e = row; e < BN * PRED_MAX_P; e += EPI_THREADS) {
             const int c = e / PRED_MAX_P, q = e % PRED_MAX_P;
             aw_s[e] = (q < p.p) ? p.aw[(w.j * BN + c) * p.ldaw + q] : 0.f;
         }
@@ -473,8 +589,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red_s = reinterpret_cast<double *>(tmem_slot + 2);
-    int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 8);
+    int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 16);
     float *aw_s = reinterpret_cast<float *>(nb_s + BN);
+    // trailing update: descriptors of factor column k, staged once (aw_s is
+    // unused by that op; 32 KB hold 2048 descriptors)
+    TileDesc *col_desc = reinterpret_cast<TileDesc *>(aw_s);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -484,7 +603,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 128);
+            mbar_init(&tempty[a], EPI_THREADS);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -504,6 +623,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB0)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB1)) : "memory");
     }
+    if (OP == OP_UPDATE) {
+        const int64_t ncol = p.nt - p.k - 1;
+        for (int64_t e = threadIdx.x; e < ncol; e += blockDim.x) col_desc[e] = p.ltab[off_index(p.k + 1 + e, p.k)];
+    }
     tmem_fence_before();
     __syncthreads();
     tmem_fence_after();
@@ -520,7 +643,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int64_t t = blockIdx.x; t < p.items && ok; t += gridDim.x) {
                 Work w;
-                decode<OP>(p, t, w);
+                decode<OP>(p, t, w, col_desc);
                 for (int q = 0; q < w.nph && ok; ++q) {
                     for (int kb = 0; kb < w.nkb; ++kb) {
                         if (!wait_bar(&empty[s], ph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
@@ -559,7 +682,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool any = false;
             for (int64_t t = blockIdx.x; t < p.items && ok; t += gridDim.x) {
                 Work w;
-                decode<OP>(p, t, w);
+                decode<OP>(p, t, w, col_desc);
                 const int total = w.nph * w.nkb;
                 if (total == 0) continue;
                 if (!wait_bar(&tempty[acc], aph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
@@ -592,19 +715,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     } else {
         // ---------------- epilogue warps ----------------
         const int row = ((warp & 3) << 5) + lane;  // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;          // column half of the block
         int acc = 0;
         uint32_t aph = 0;
         for (int64_t t = blockIdx.x; t < p.items; t += gridDim.x) {
             Work w;
-            decode<OP>(p, t, w);
+            decode<OP>(p, t, w, col_desc);
             if (w.nph * w.nkb == 0) continue;
             epi_bar();
             epilogue_stage<OP>(p, w, threadIdx.x - 64, nb_s, aw_s);
+            epilogue_prefetch<OP>(p, w, row, half);
             epi_bar();
             if (!wait_bar(&tfull[acc], aph, budget, abort_flag, p.err)) break;
             tmem_fence_after();
             const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * BN);
-            epilogue<OP>(p, w, tacc, row, nb_s, aw_s, red_s);
+            epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc);
             tmem_fence_before();
             mbar_arrive(&tempty[acc]);
             if (++acc == 2) { acc = 0; aph ^= 1; }
@@ -650,6 +775,7 @@ struct TcState {
     EncodeTiledFn encode = nullptr;
     CUtensorMap g_map;                     // packed training genotypes
     CUtensorMap w_map, hi_map, lo_map;     // trailing tiles, column panels
+    CUtensorMap pool_map;                  // factor pool viewed as FP16 rows of b
     CUtensorMap linv_hi_map, linv_lo_map;  // diagonal inverse splits
     bool factor_maps = false;
 };
@@ -717,6 +843,7 @@ krr_status ensure_factor_maps(Ctx *c) {
     KRR_TRY(make_map(c, &st->w_map, c->W, f16, 2, noff * b, b));
     KRR_TRY(make_map(c, &st->hi_map, c->pan_hi, f16, 2, (nt - 1) * b, b));
     KRR_TRY(make_map(c, &st->lo_map, c->pan_lo, f16, 2, (nt - 1) * b, b));
+    KRR_TRY(make_map(c, &st->pool_map, c->pool, f16, 2, (int64_t)(c->pool_bytes / (2 * b)), b));
     KRR_TRY(make_map(c, &st->linv_hi_map, c->Linv_hi, f16, 2, nt * b, b));
     KRR_TRY(make_map(c, &st->linv_lo_map, c->Linv_lo, f16, 2, nt * b, b));
     st->factor_maps = true;
@@ -796,7 +923,77 @@ krr_status tc_update(Ctx *c, int64_t k) {
     p.Wd = c->Wd;
     p.ltab = c->ltab;
     p.items = u * (u + 1) / 2 * (b / BM) * (b / BN);
-    return launch<KIND_F16, OP_UPDATE>(c, st->hi_map, st->lo_map, st->hi_map, st->lo_map, p);
+    return launch<KIND_F16, OP_UPDATE>(c, st->pool_map, st->hi_map, st->lo_map, st->lo_map, p);
+}
+
+// B = K_test^T G_p: the predict kernel with the roles of the two genotype
+// sets swapped (A = training rows, B = test rows padded to 256).  part is
+// (2 * test_rows256 / 256) x n_pad x p.
+krr_status tc_predict_t(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
+                        int64_t test_rows256, const float *gp, int64_t ldgp, int64_t p_cols, float *part) {
+    TcState *st = (TcState *)c->tc;
+    if (p_cols < 1 || p_cols > PRED_MAX_P || test_rows256 % BN != 0) {
+        c->last_error = "tc_predict_t: bad shape";
+        return KRR_EINVAL;
+    }
+    CUtensorMap t_map;
+    KRR_TRY(make_map(c, &t_map, t8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, test_rows256, c->m_pad));
+    TcParams p = base_params(c);
+    p.n = n_test;           // real rows of the B operand (test)
+    p.n_pad = test_rows256;  // padded rows of the B operand
+    p.n_test = c->n;        // real rows of the A operand (training)
+    p.test_rows = c->n_pad;  // padded rows of the A operand (partial stride)
+    p.norms_a = c->norms;
+    p.norms_b = tn;
+    p.aw = gp;
+    p.ldaw = ldgp;
+    p.p = p_cols;
+    p.part = part;
+    p.items = (c->n_pad / BM) * (test_rows256 / BN);
+    return launch<KIND_F8, OP_PREDICT>(c, st->g_map, st->g_map, t_map, t_map, p);
+}
+
+// The two d K-weighted contractions of the hyperparameter gradient: one
+// partial per block into part_t (test x training blocks) and part_k
+// (lower-triangle training blocks).  aw = A (n_pad x ld), zw = Z, gp = G_p
+// (test_rows x ld), p_cols <= 16.
+krr_status tc_grad_terms(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
+                         int64_t test_rows, const float *aw, const float *zw, const float *gp,
+                         int64_t ld, int64_t p_cols, double *part_t, double *part_k,
+                         int64_t *items_t, int64_t *items_k) {
+    TcState *st = (TcState *)c->tc;
+    if (p_cols < 1 || p_cols > GRAD_MAX_P) {
+        c->last_error = "tc_grad_terms: at most 16 columns per launch";
+        return KRR_EINVAL;
+    }
+    CUtensorMap t_map;
+    KRR_TRY(make_map(c, &t_map, t8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, test_rows, c->m_pad));
+    TcParams p = base_params(c);
+    p.n_pad = c->n_pad;
+    p.n_test = n_test;
+    p.test_rows = test_rows;
+    p.norms_a = tn;
+    p.norms_b = c->norms;
+    p.aw = aw;
+    p.zw = zw;
+    p.gp = gp;
+    p.ldaw = ld;
+    p.p = p_cols;
+    p.gpart = part_t;
+    p.items = (test_rows / BM) * (c->n_pad / BN);
+    *items_t = p.items;
+    KRR_TRY((launch<KIND_F8, OP_GRADT>(c, t_map, t_map, st->g_map, st->g_map, p)));
+    TcParams q = base_params(c);
+    q.norms_a = c->norms;
+    q.norms_b = c->norms;
+    q.aw = aw;
+    q.zw = zw;
+    q.ldaw = ld;
+    q.p = p_cols;
+    q.gpart = part_k;
+    q.items = c->nt * (c->nt + 1) / 2 * (c->b / BM) * (c->b / BN);
+    *items_k = q.items;
+    return launch<KIND_F8, OP_GRADK>(c, st->g_map, st->g_map, st->g_map, st->g_map, q);
 }
 
 krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,

@@ -31,7 +31,7 @@ PREC_NAMES = {0: "fp64", 1: "fp32", 2: "fp16", 3: "e4m3", 255: "-"}
 # Every symbol include/krr.h declares (checked by the CPU test suite).
 EXPORTED = ["krr_default_options", "krr_create", "krr_build_kernel", "krr_factor", "krr_solve",
             "krr_predict", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
-            "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_set_profiling",
+            "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_sync", "krr_last_error",
             "krr_destroy"]
 PROF_CLASSES = ["pack", "build", "diag", "trsm", "cast", "update", "solve", "residual", "predict"]
@@ -92,6 +92,7 @@ def load_library(path: str = LIB_PATH):
     lib.krr_get_kernel.argtypes = [vp, vp, i64]
     lib.krr_get_factor.argtypes = [vp, vp, i64]
     lib.krr_predict_noalloc.argtypes = [vp, vp, i64, i64, vp, i64, i64, vp, i64]
+    lib.krr_grad_hyper.argtypes = [vp, vp, i64, i64, vp, i64, vp, i64, i64, ctypes.POINTER(dbl)]
     lib.krr_set_profiling.argtypes = [vp, i32]
     lib.krr_get_profile.argtypes = [vp, ctypes.POINTER(Profile), i32]
     lib.krr_sync.argtypes = [vp]
@@ -101,7 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.krr_destroy.restype = None
     for name in ("krr_create", "krr_build_kernel", "krr_factor", "krr_solve", "krr_predict",
                  "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
-                 "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_set_profiling",
+                 "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_sync"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -224,6 +225,15 @@ class KRR:
                                           ctypes.c_void_p(_ptr(a)), _ld(a), p, ctypes.c_void_p(_ptr(yt)),
                                           _ld(yt)))
         return yt
+
+    # -- hyperparameter gradient (adjoint reusing the factor) ----------------
+    def grad_hyper(self, t, yt, a):
+        """(loss, d loss/d log gamma, d loss/d log lambda) of the held-out MSE."""
+        out = (ctypes.c_double * 3)()
+        self._check(self._lib.krr_grad_hyper(self._ctx, ctypes.c_void_p(_ptr(t)), t.shape[0], _ld(t),
+                                             ctypes.c_void_p(_ptr(yt)), _ld(yt), ctypes.c_void_p(_ptr(a)),
+                                             _ld(a), a.shape[1], out))
+        return out[0], out[1], out[2]
 
     # -- inspection -----------------------------------------------------------
     def precision_map(self) -> np.ndarray:

@@ -178,3 +178,19 @@ def test_factor_backward_error(mode):
         # the mean component sits in tile column 0: it needs FP32; the rest FP16
         assert np.all(pmap[1:, 0] == 1), pmap
         assert np.all(pmap[np.tril_indices(len(pmap), -1)][len(pmap) - 1:] >= 1)
+
+
+def test_fp64_diagonal_option():
+    """The FP64 diagonal-tile Cholesky option gives the same answers."""
+    prob = _problem(1100, 300, 2, 150, seed=51)
+    gamma, lam = 1.0 / 300, 0.1
+    _, a_ref, yt_ref = oracle.krr(gamma, lam, prob["G"], prob["Y"].astype(np.float64), prob["T"])
+    with KRR(tile=256, mode="mixed", diag_fp64=True) as model:
+        model.build_kernel(_to(prob["G"]), gamma)
+        model.factor(lam)
+        a, info = model.solve(_to(prob["Y"]))
+        yt = model.predict(_to(prob["T"]), a)
+        pmap = model.precision_map()
+    assert np.all(np.diag(pmap) == 0)  # diagonal tiles report FP64
+    err = np.linalg.norm(yt.cpu().numpy() - yt_ref) / np.linalg.norm(yt_ref)
+    assert err <= 1e-4, (err, info)
