@@ -243,6 +243,52 @@ krr_status krr_predict_noalloc(krr_ctx *ctx, const int8_t *T, int64_t n_test, in
 krr_status krr_grad_hyper(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt, const float *Yt,
                           int64_t ldy, const float *A, int64_t lda, int64_t p, double *out);
 
+/*
+ * Batched problems: many (cohort, cross-validation fold, lambda) problems of
+ * uneven size -- the paper picks gamma and alpha by cross-validation (Sec.
+ * III), i.e. by solving many such problems.  krr_batch_create() gives every
+ * problem its own context and stream, picks each problem's tile edge with an
+ * autotuner (timed trial runs of the smallest, median and largest problem
+ * with tile edges 256 / 512 / 1024) when autotune != 0, runs every pipeline
+ * once to allocate, and captures Build -> Factor -> Solve (with
+ * options->ir_max refinement steps, no host decisions) -> Predict of all
+ * problems into one CUDA graph with a fork/join over the problem streams.
+ * krr_batch_run() launches that graph once and reports per-problem status,
+ * tile and final relative residual.  The graph is captured on a stream of
+ * the batch's own and launched on `stream` (which may be the legacy default
+ * stream).  All pointers are device pointers and are read at every run
+ * (update the data in place between runs).  krr_batch_last_error(NULL) gives
+ * the message of the calling thread's last failed krr_batch_create().
+ * Errors: KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA, and the first per-problem error.
+ */
+typedef struct krr_batch_problem {
+    const int8_t *G;    /* n x m training genotypes, leading dimension ldg */
+    int64_t n, ldg;
+    double gamma, lambda;
+    const float *Y;     /* n x p phenotypes, leading dimension ldy */
+    int64_t ldy;
+    float *A;           /* n x p weights (output), leading dimension lda */
+    int64_t lda;
+    const int8_t *T;    /* n_test x m held-out genotypes (ldt), or NULL */
+    int64_t n_test, ldt;
+    float *Yt;          /* n_test x p predictions (output), leading dimension ldyt */
+    int64_t ldyt;
+} krr_batch_problem;
+
+typedef struct krr_batch_result {
+    int32_t status;         /* KRR_OK or the problem's device-side error */
+    int32_t tile;           /* tile edge the autotuner picked */
+    double rel_residual;    /* final ||Y - (K + lambda I) A||_F / ||Y||_F */
+} krr_batch_result;
+
+typedef struct krr_batch krr_batch;
+
+krr_status krr_batch_create(krr_batch **out, const krr_options *opt, void *stream, int64_t m, int64_t p,
+                            const krr_batch_problem *problems, int32_t count, int32_t autotune);
+krr_status krr_batch_run(krr_batch *bt, krr_batch_result *results);
+const char *krr_batch_last_error(const krr_batch *bt);
+void krr_batch_destroy(krr_batch *bt);
+
 /* Kernel classes timed by the optional profiler. */
 enum {
     KRR_PROF_PACK = 0,     /* genotype packing and norms */

@@ -6,6 +6,6 @@ seeded synthetic inputs (``inputs``).
 """
 from . import inputs  # noqa: F401
 from .autograd import held_out_loss  # noqa: F401
-from .krr import KRR, KRRError, load_library  # noqa: F401
+from .krr import KRR, KRRBatch, KRRError, load_library  # noqa: F401
 
-__all__ = ["KRR", "KRRError", "held_out_loss", "inputs", "load_library"]
+__all__ = ["KRR", "KRRBatch", "KRRError", "held_out_loss", "inputs", "load_library"]

@@ -261,6 +261,22 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
     krr_solve_info si;
     memset(&si, 0, sizeof(si));
     krr_status st = KRR_OK;
+    if (c->graph_mode) {
+        // fixed number of refinement steps without host decisions; the final
+        // relative residual is left in red[RED_RNORM..+1] for the caller
+        const int iters = mixed(c) ? c->opt.ir_max : 0;
+        for (int it = 0; it < iters; ++it) {
+            launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
+            launch_axpy_r(c->rbuf, c->dabuf, cnt, s);
+            solve_inplace(c, c->dabuf, c->zbuf, p);
+            launch_add_scaled(c->abuf, c->dabuf, 1.0f, cnt, s);
+        }
+        launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
+        launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
+        KRR_TRY(check_launch(c, "refinement (graph mode)"));
+        if (info) *info = si;
+        return KRR_OK;
+    }
     const bool refine = mixed(c) && c->opt.ir_max > 0;
     if (refine || info) {
         double best = INFINITY;
@@ -464,10 +480,11 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
                         "0 < gamma < inf";
         return KRR_EINVAL;
     }
-    free_factor(c);
     c->built = false;
+    c->factored = false;
     const int64_t b = c->opt.tile;
     const int64_t nt = (n + b - 1) / b;
+    if (nt != c->nt || b != c->b) free_factor(c);  // factor buffers depend on the tile grid
     const int64_t n_pad = nt * b;
     const int64_t m_pad = (m + 127) / 128 * 128;
     const size_t g_bytes = (size_t)n_pad * m_pad * (mixed(c) ? 1 : 4);
@@ -499,11 +516,13 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
     c->n_pad = n_pad;
     c->gamma = gamma;
     const size_t red_count = RED_MINPIV + (size_t)nt * (b / 64) + (size_t)nt + 16;
-    KRR_TRY(dev_alloc(c, &c->red, red_count, "reduction buffer"));
-    if (c->hred) cudaFreeHost(c->hred);
-    c->hred = nullptr;
-    if (cudaMallocHost((void **)&c->hred, 64 * sizeof(double)) != cudaSuccess) {
+    if (c->red_cap < red_count) {
+        KRR_TRY(dev_alloc(c, &c->red, red_count, "reduction buffer"));
+        c->red_cap = red_count;
+    }
+    if (!c->hred && cudaMallocHost((void **)&c->hred, 64 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
+        c->hred = nullptr;
         c->last_error = "pinned allocation failed";
         return KRR_ENOMEM;
     }
@@ -576,35 +595,10 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
             KRR_TRY(dev_alloc(c, &c->colmax, colt * 16, "column maxima"));
         }
     }
-    // reset the error record and the precision map
-    DevErrors e0;
-    memset(&e0, 0, sizeof(e0));
-    e0.bad_tile = -1;
-    e0.bad_column = -1;
-    e0.min_pivot = INFINITY;
-    *c->herr = e0;
-    KRR_CUDA_TRY(c, cudaMemcpyAsync(c->derr, c->herr, sizeof(DevErrors), cudaMemcpyHostToDevice, s));
-    {
-        std::vector<uint8_t> pm((size_t)nt * nt, 255);
-        for (int64_t i = 0; i < nt; ++i) {
-            pm[i * nt + i] = c->opt.diag_fp64 ? KRR_PREC_FP64 : KRR_PREC_FP32;
-            if (!mx)
-                for (int64_t j = 0; j < i; ++j) pm[i * nt + j] = KRR_PREC_FP32;
-        }
-        KRR_CUDA_TRY(c, cudaMemcpyAsync(c->precmap, pm.data(), pm.size(), cudaMemcpyHostToDevice, s));
-        if (!mx && noff > 0) {
-            std::vector<TileDesc> tab((size_t)noff);
-            for (int64_t t = 0; t < noff; ++t) {
-                tab[t].offset = t * bb * 4;
-                tab[t].scale = 1.f;
-                tab[t].prec = KRR_PREC_FP32;
-            }
-            KRR_CUDA_TRY(c, cudaMemcpyAsync(c->ltab, tab.data(), tab.size() * sizeof(TileDesc),
-                                            cudaMemcpyHostToDevice, s));
-        }
-        // the tables above live on the host stack: wait for the copies
-        KRR_CUDA_TRY(c, cudaStreamSynchronize(s));
-    }
+    // reset the error record, the precision map and (fp32 mode) the tile
+    // table on the device: no host data, so the sequence can be captured
+    launch_factor_init(c);
+    KRR_TRY(check_launch(c, "factor init"));
     const double bd = (double)b;
     for (int64_t k = 0; k < nt; ++k) {
         int pr = prof_begin(c, KRR_PROF_DIAG);
@@ -638,6 +632,11 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
             prof_end(c, pr, upd_flops, 0.0);
             KRR_TRY(check_launch(c, "update"));
         }
+    }
+    if (c->graph_mode) {  // results are read after the captured sequence ran
+        c->factored = true;
+        if (info) memset(info, 0, sizeof(*info));
+        return KRR_OK;
     }
     KRR_CUDA_TRY(c, cudaMemcpyAsync(c->herr, c->derr, sizeof(DevErrors), cudaMemcpyDeviceToHost, s));
     KRR_CUDA_TRY(c, cudaStreamSynchronize(s));

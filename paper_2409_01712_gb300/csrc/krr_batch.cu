@@ -1,0 +1,243 @@
+// Batched KRR: many (cohort, fold, lambda) problems of uneven size -- the
+// paper picks gamma and alpha by cross-validation (Sec. III), which means
+// solving many such problems.  Every problem gets its own context and
+// stream; the whole set (Build, Factor, Solve, Predict of every problem) is
+// captured once into one CUDA graph with a fork/join over the problem
+// streams, so independent problems overlap on the GPU and a run is a single
+// graph launch.  An autotuner picks the tile edge per problem size from
+// timed trial runs.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "krr_internal.h"
+
+struct krr_batch {
+    krr_options opt;
+    cudaStream_t main = nullptr;     // caller's stream: trials and graph launches
+    cudaStream_t capture = nullptr;  // own stream the graph is captured on (the
+                                     // caller's may be the legacy default stream,
+                                     // which cannot be captured)
+    int64_t m = 0, p = 0;
+    std::vector<krr_batch_problem> probs;
+    std::vector<krr_ctx *> ctx;
+    std::vector<cudaStream_t> streams;
+    std::vector<int32_t> tiles;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_batch_create_error;
+
+krr_status issue(krr_ctx *c, const krr_batch_problem &pr, int64_t m, int64_t p) {
+    KRR_TRY(krr_build_kernel(c, pr.G, pr.n, m, pr.ldg, pr.gamma));
+    KRR_TRY(krr_factor(c, pr.lambda, nullptr));
+    krr_status st = krr_solve(c, pr.Y, p, pr.ldy, pr.A, pr.lda, nullptr);
+    if (st != KRR_OK) return st;
+    if (pr.T && pr.n_test > 0) KRR_TRY(krr_predict(c, pr.T, pr.n_test, pr.ldt, pr.A, pr.lda, p, pr.Yt, pr.ldyt));
+    return KRR_OK;
+}
+
+// Wall time (ms) of one eager pipeline of problem pr with tile b.
+krr_status trial_ms(const krr_options &base, cudaStream_t s, const krr_batch_problem &pr, int64_t m, int64_t p,
+                    int64_t b, double *ms) {
+    krr_options o = base;
+    o.tile = b;
+    krr_ctx *c = nullptr;
+    KRR_TRY(krr_create(&c, &o, s));
+    reinterpret_cast<krr::Ctx *>(c)->graph_mode = 1;
+    krr_status st = issue(c, pr, m, p);  // warm-up (allocations)
+    if (st == KRR_OK) {
+        cudaStreamSynchronize(s);
+        const auto t0 = std::chrono::steady_clock::now();
+        st = issue(c, pr, m, p);
+        cudaStreamSynchronize(s);
+        *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    krr_destroy(c);
+    return st;
+}
+
+}  // namespace
+
+extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, void *stream, int64_t m,
+                                       int64_t p, const krr_batch_problem *problems, int32_t count,
+                                       int32_t autotune) {
+    if (!out || !problems || count < 1 || m < 1 || p < 1) return KRR_EINVAL;
+    *out = nullptr;
+    krr_batch *bt = new (std::nothrow) krr_batch();
+    if (!bt) return KRR_ENOMEM;
+    krr_default_options(&bt->opt);
+    if (opt) bt->opt = *opt;
+    bt->main = (cudaStream_t)stream;
+    bt->m = m;
+    bt->p = p;
+    bt->probs.assign(problems, problems + count);
+    g_batch_create_error.clear();
+    auto fail = [&](krr_status st, const std::string &msg) {
+        g_batch_create_error = msg;
+        krr_batch_destroy(bt);
+        return st;
+    };
+    for (int32_t i = 0; i < count; ++i) {
+        const krr_batch_problem &pr = problems[i];
+        if (!pr.G || !pr.Y || !pr.A || pr.n < 1 || pr.ldg < m || pr.ldy < p || pr.lda < p)
+            return fail(KRR_EINVAL, "krr_batch_create: bad problem " + std::to_string(i));
+    }
+    // ---- autotune the tile edge: time the smallest, median and largest
+    // problems with every candidate; each problem takes the candidate that was
+    // fastest on the measured problem nearest to it in log N.
+    bt->tiles.assign(count, (int32_t)bt->opt.tile);
+    if (autotune) {
+        std::vector<int32_t> order(count);
+        for (int32_t i = 0; i < count; ++i) order[i] = i;
+        std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b2) { return problems[a].n < problems[b2].n; });
+        const int32_t probes[3] = {order[0], order[count / 2], order[count - 1]};
+        const int64_t cand[3] = {256, 512, 1024};
+        int64_t best_b[3];
+        for (int q = 0; q < 3; ++q) {
+            double best = INFINITY;
+            best_b[q] = bt->opt.tile;
+            for (int64_t b : cand) {
+                if (b > 2 * ((problems[probes[q]].n + 255) / 256 * 256) && b != 256) continue;
+                double ms = 0.0;
+                krr_status st = trial_ms(bt->opt, bt->main, problems[probes[q]], m, p, b, &ms);
+                if (st != KRR_OK) return fail(st, "krr_batch_create: autotune trial failed");
+                if (ms < best) {
+                    best = ms;
+                    best_b[q] = b;
+                }
+            }
+        }
+        for (int32_t i = 0; i < count; ++i) {
+            int qbest = 0;
+            double dist = INFINITY;
+            for (int q = 0; q < 3; ++q) {
+                const double d = fabs(log((double)problems[i].n) - log((double)problems[probes[q]].n));
+                if (d < dist) {
+                    dist = d;
+                    qbest = q;
+                }
+            }
+            bt->tiles[i] = (int32_t)best_b[qbest];
+        }
+    }
+    // ---- one context and stream per problem, warm-up run (allocations)
+    bt->ctx.assign(count, nullptr);
+    bt->streams.assign(count, nullptr);
+    bt->join.assign(count, nullptr);
+    if (cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&bt->capture, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(KRR_ECUDA, "event / stream creation failed");
+    for (int32_t i = 0; i < count; ++i) {
+        if (cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&bt->join[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(KRR_ECUDA, "stream creation failed");
+        krr_options o = bt->opt;
+        o.tile = bt->tiles[i];
+        krr_status st = krr_create(&bt->ctx[i], &o, bt->streams[i]);
+        if (st != KRR_OK) return fail(st, std::string("krr_batch_create: ") + krr_last_error(nullptr));
+        reinterpret_cast<krr::Ctx *>(bt->ctx[i])->graph_mode = 1;
+        st = issue(bt->ctx[i], problems[i], m, p);
+        if (st != KRR_OK)
+            return fail(st, std::string("krr_batch_create: warm-up of problem ") + std::to_string(i) + ": " +
+                                krr_last_error(bt->ctx[i]));
+    }
+    {
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return fail(KRR_ECUDA, std::string("warm-up failed: ") + cudaGetErrorString(e));
+    }
+    // ---- capture every problem's pipeline into one graph (fork / join)
+    {
+        const cudaError_t e = cudaStreamBeginCapture(bt->capture, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess)
+            return fail(KRR_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    }
+    cudaEventRecord(bt->fork, bt->capture);
+    krr_status cst = KRR_OK;
+    std::string cmsg;
+    for (int32_t i = 0; i < count && cst == KRR_OK; ++i) {
+        cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
+        cst = issue(bt->ctx[i], problems[i], m, p);
+        if (cst != KRR_OK) cmsg = "problem " + std::to_string(i) + ": " + krr_last_error(bt->ctx[i]);
+        cudaEventRecord(bt->join[i], bt->streams[i]);
+        cudaStreamWaitEvent(bt->capture, bt->join[i], 0);
+    }
+    const cudaError_t ce = cudaStreamEndCapture(bt->capture, &bt->graph);
+    if (cst != KRR_OK || ce != cudaSuccess || !bt->graph) {
+        cudaGetLastError();
+        return fail(cst != KRR_OK ? cst : KRR_ECUDA,
+                    "graph capture failed: " + (cst != KRR_OK ? cmsg : std::string(cudaGetErrorString(ce))));
+    }
+    {
+        const cudaError_t e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KRR_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+    }
+    *out = bt;
+    return KRR_OK;
+}
+
+extern "C" krr_status krr_batch_run(krr_batch *bt, krr_batch_result *results) {
+    if (!bt || !bt->exec) return KRR_EINVAL;
+    if (cudaGraphLaunch(bt->exec, bt->main) != cudaSuccess ||
+        cudaStreamSynchronize(bt->main) != cudaSuccess) {
+        cudaGetLastError();
+        bt->last_error = "graph launch failed";
+        return KRR_ECUDA;
+    }
+    krr_status worst = KRR_OK;
+    for (size_t i = 0; i < bt->ctx.size(); ++i) {
+        krr::Ctx *c = reinterpret_cast<krr::Ctx *>(bt->ctx[i]);
+        krr::DevErrors e;
+        double rn[2] = {0.0, 0.0};
+        if (cudaMemcpy(&e, c->derr, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(rn, c->red + krr::RED_RNORM, sizeof(rn), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            bt->last_error = "result readback failed";
+            return KRR_ECUDA;
+        }
+        const krr_status st = e.code ? (krr_status)e.code : KRR_OK;
+        if (st != KRR_OK && worst == KRR_OK) {
+            worst = st;
+            bt->last_error = "problem " + std::to_string(i) + " failed with status " + std::to_string(e.code);
+        }
+        if (results) {
+            results[i].status = st;
+            results[i].tile = bt->tiles[i];
+            results[i].rel_residual = rn[1] > 0 ? sqrt(rn[0] / rn[1]) : sqrt(rn[0]);
+        }
+    }
+    return worst;
+}
+
+extern "C" const char *krr_batch_last_error(const krr_batch *bt) {
+    return bt ? bt->last_error.c_str() : g_batch_create_error.c_str();
+}
+
+extern "C" void krr_batch_destroy(krr_batch *bt) {
+    if (!bt) return;
+    if (bt->exec) cudaStreamSynchronize(bt->main);
+    if (bt->capture) cudaStreamDestroy(bt->capture);
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    for (krr_ctx *c : bt->ctx) krr_destroy(c);
+    for (cudaStream_t s : bt->streams)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : bt->join)
+        if (e) cudaEventDestroy(e);
+    if (bt->fork) cudaEventDestroy(bt->fork);
+    delete bt;
+}

@@ -135,6 +135,11 @@ struct Ctx {
     // profiler (opaque, owned by krr_api.cu)
     void *prof = nullptr;
     int prof_on = 0;
+
+    // graph mode: no host synchronisation or readback inside build / factor /
+    // solve / predict, fixed refinement count (used by the batch runner)
+    int graph_mode = 0;
+    size_t red_cap = 0;
 };
 
 // Kernel launch counter of the whole library (reported by krr_get_profile).
@@ -201,6 +206,10 @@ void solve_inplace(Ctx *c, float *x, float *tmp, int64_t p);
 
 // r = y - (K + lambda I) a (FP64 accumulation), norms into c->red.
 void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
+
+// Resets the device error record and the precision map, and (fp32 mode)
+// fills the tile table: every factor tile FP32 at a fixed slot.
+void launch_factor_init(Ctx *c);
 
 // Small helpers.
 void launch_fill_zero(void *p, size_t bytes, cudaStream_t s);

@@ -499,19 +499,21 @@ void launch_predict_reduce(const float *part, int64_t nblk, int64_t rows_pad, in
 // ----------------------------------------------------------------------------
 constexpr int DNB = 64;
 
+constexpr int PB_THREADS = 1024;
+
 template <typename T>
-__global__ void __launch_bounds__(256) potrf_block_kernel(T *W, T *Winv, int64_t b, int q,
+__global__ void __launch_bounds__(PB_THREADS) potrf_block_kernel(T *W, T *Winv, int64_t b, int q,
                                                           int64_t tile_k, DevErrors *err,
                                                           double *minpiv) {
     // dynamic shared memory: a[DNB][DNB + 1] (the block, then L_qq) and
     // x[DNB][DNB + 1] (its inverse).  Thread (tx, ty) = (t % 64, t / 64)
-    // owns column tx and rows ty, ty + 4, ... of the rank-1 updates.
+    // owns column tx and rows ty, ty + 16, ... of the rank-1 updates.
     extern __shared__ __align__(16) unsigned char pb_smem[];
     T (*a)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(pb_smem);
     T (*x)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(pb_smem + sizeof(T) * DNB * (DNB + 1));
     __shared__ int bad;
     const int tx = threadIdx.x & (DNB - 1), ty = threadIdx.x / DNB;
-    constexpr int RS = 256 / DNB;  // row stride of a thread
+    constexpr int RS = PB_THREADS / DNB;  // row stride of a thread
     T *blk = W + (int64_t)q * DNB * b + q * DNB;
     for (int r = ty; r < DNB; r += RS) {
         a[r][tx] = blk[(int64_t)r * b + tx];
@@ -536,6 +538,7 @@ __global__ void __launch_bounds__(256) potrf_block_kernel(T *W, T *Winv, int64_t
         __syncthreads();
         if (tx > c) {
             const T lsc = a[tx][c];
+#pragma unroll
             for (int r = ty; r < DNB; r += RS)
                 if (r >= tx) a[r][tx] -= a[r][c] * lsc;
         }
@@ -548,6 +551,7 @@ __global__ void __launch_bounds__(256) potrf_block_kernel(T *W, T *Winv, int64_t
         __syncthreads();
         if (tx <= c) {
             const T xc = x[c][tx];
+#pragma unroll
             for (int r = ty; r < DNB; r += RS)
                 if (r > c) x[r][tx] -= a[r][c] * xc;
         }
@@ -564,82 +568,6 @@ __global__ void __launch_bounds__(256) potrf_block_kernel(T *W, T *Winv, int64_t
             err->bad_tile = tile_k;
             err->bad_column = tile_k * b + (int64_t)q * DNB + bad;
         }
-    }
-}
-
-// Triangular inverse of the factored diagonal tile, one CTA per 64-column
-// block j: X_ij = -X_ii sum_{k=j}^{i-1} L_ik X_kj for i = j + 1, ..., in
-// order (the diagonal blocks X_ii = inv(L_ii) come from potrf_block_kernel).
-// 64 x 64 block products in shared memory, 4 x 4 outputs per thread.
-template <typename T>
-__global__ void __launch_bounds__(256) trtri_cols_kernel(const T *L, T *X, int64_t b) {
-    extern __shared__ __align__(16) unsigned char tr_smem[];
-    T (*As)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(tr_smem);
-    T (*Bs)[DNB + 1] = reinterpret_cast<T (*)[DNB + 1]>(tr_smem + sizeof(T) * DNB * (DNB + 1));
-    const int j = blockIdx.x, nq = (int)(b / DNB);
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 4 x 4 outputs each
-    const int lx = threadIdx.x & (DNB - 1), ly = threadIdx.x / DNB;  // loader mapping
-    for (int i = j + 1; i < nq; ++i) {
-        T acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
-        for (int k = j; k < i; ++k) {
-            const T *lb = L + (int64_t)i * DNB * b + (int64_t)k * DNB;
-            const T *xb = X + (int64_t)k * DNB * b + (int64_t)j * DNB;
-            for (int r = ly; r < DNB; r += 256 / DNB) {
-                As[r][lx] = lb[(int64_t)r * b + lx];
-                Bs[r][lx] = xb[(int64_t)r * b + lx];
-            }
-            __syncthreads();
-#pragma unroll 8
-            for (int kk = 0; kk < DNB; ++kk) {
-                T av[4], bv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    av[u] = As[ty * 4 + u][kk];
-                    bv[u] = Bs[kk][tx * 4 + u];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] += av[u] * bv[v];
-            }
-            __syncthreads();
-        }
-        // X_ij = -X_ii * acc
-        const T *xii = X + (int64_t)i * DNB * b + (int64_t)i * DNB;
-        for (int r = ly; r < DNB; r += 256 / DNB) As[r][lx] = xii[(int64_t)r * b + lx];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) Bs[ty * 4 + u][tx * 4 + v] = acc[u][v];
-        __syncthreads();
-        T out[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) out[u][v] = T(0);
-#pragma unroll 8
-        for (int kk = 0; kk < DNB; ++kk) {
-            T av[4], bv[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                av[u] = As[ty * 4 + u][kk];
-                bv[u] = Bs[kk][tx * 4 + u];
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) out[u][v] -= av[u] * bv[v];
-        }
-        T *xij = X + (int64_t)i * DNB * b + (int64_t)j * DNB;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) xij[(int64_t)(ty * 4 + u) * b + tx * 4 + v] = out[u][v];
-        __syncthreads();  // X_ij is read by the next i (global memory, same block)
     }
 }
 
@@ -688,7 +616,7 @@ static void diag_factor_tile(Ctx *c, T *W, T *Winv, T *tmp, int64_t k, double *m
         pb_attr = true;
     }
     for (int q = 0; q < nq; ++q) {
-        count_launch(), potrf_block_kernel<T><<<1, 256, pb_smem, s>>>(W, Winv, b, q, k, c->derr, minpiv + k * nq);
+        count_launch(), potrf_block_kernel<T><<<1, PB_THREADS, pb_smem, s>>>(W, Winv, b, q, k, c->derr, minpiv + k * nq);
         const int rest = (int)(b - (int64_t)(q + 1) * DNB);
         if (rest <= 0) break;
         T *panel = W + (int64_t)(q + 1) * DNB * b + q * DNB;
@@ -700,14 +628,19 @@ static void diag_factor_tile(Ctx *c, T *W, T *Winv, T *tmp, int64_t k, double *m
         launch_gemm_simt<T>(rest, rest, DNB, T(-1), panel, b, 0, panel, b, 0, 0, T(1), trail, b, 0,
                             trail, b, 0, 1, 1, s);
     }
-    // Triangular inverse: one CTA per 64-column block of X = L^-1.
-    static bool tr_attr = false;
-    if (!tr_attr) {
-        cudaFuncSetAttribute(trtri_cols_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb_smem);
-        tr_attr = true;
+    // Triangular inverse by recursive doubling: with the 64-blocks X_qq already
+    // inverted, for s = 64, 128, ..., b / 2 and every pair of diagonal
+    // s-blocks, X_21 = -X_22 (L_21 X_11) (two batched GEMMs per level).
+    for (int64_t sz = DNB; sz < b; sz *= 2) {
+        const int pairs = (int)(b / (2 * sz));
+        const int64_t pstride = 2 * sz * b + 2 * sz;
+        // tmp_p = L_21 X_11
+        launch_gemm_simt<T>((int)sz, (int)sz, (int)sz, T(1), W + sz * b, b, pstride, Winv, b, pstride, 1, T(0),
+                            nullptr, 0, 0, tmp, sz, sz * sz, pairs, 0, s);
+        // X_21 = -X_22 tmp_p
+        launch_gemm_simt<T>((int)sz, (int)sz, (int)sz, T(-1), Winv + sz * b + sz, b, pstride, tmp, sz, sz * sz, 1,
+                            T(0), nullptr, 0, 0, Winv + sz * b, b, pstride, pairs, 0, s);
     }
-    if (nq > 1) count_launch(), trtri_cols_kernel<T><<<(unsigned)(nq - 1), 256, pb_smem, s>>>(W, Winv, b);
-    (void)tmp;
 }
 
 // sqrt of the largest diagonal entry of W_kk: a bound on every |L_kk| entry
@@ -1026,89 +959,124 @@ __device__ __forceinline__ void gemv_locate(const GemvArgs &g, int64_t y, const 
     }
 }
 
-template <int PREC>
-__device__ __forceinline__ void gemv_n_rows(const uint8_t *base, float inv_scale, float shift, int64_t b,
-                                            int64_t r0, int64_t r1, const float *zt, int pc,
-                                            float *out, int64_t ldo, int q0, bool subtract) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int64_t r = r0 + warp; r < r1; r += nw) {
-        float acc[PC];
+// Row-oriented product for RPL rows per lane: CTA = 8 warps x 32 lanes; warp
+// w covers columns [w * b / 8, (w + 1) * b / 8), lane l rows r0 + l + 32 u
+// (u < RPL).  A warp load touches 32 rows (many lines in flight); x rows
+// come from shared memory as broadcasts; the 8 column-slice partials of a
+// row are summed in a fixed order in shared memory.
+template <int PREC, int RPL>
+__device__ __forceinline__ void gemv_n_block(const uint8_t *base, float inv_scale, float shift, int64_t b,
+                                             int64_t r0, const float *xs, int pcp, int pc, float *red,
+                                             float *out, int64_t ldo, int q0, bool subtract) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cw = b / 8, c0 = warp * cw;
+    float acc[RPL][PC];
 #pragma unroll
-        for (int q = 0; q < PC; ++q) acc[q] = 0.f;
-        const int64_t rowe = r * b;
-        for (int64_t c0 = 0; c0 < b; c0 += 512) {
-            float4 v[4];
+    for (int u = 0; u < RPL; ++u)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t c = c0 + u * 128 + lane * 4;
-                v[u] = (c < b) ? load4<PREC>(base, rowe + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-                v[u].x -= shift; v[u].y -= shift; v[u].z -= shift; v[u].w -= shift;
+        for (int q = 0; q < PC; ++q) acc[u][q] = 0.f;
+    int64_t re[RPL];
+#pragma unroll
+    for (int u = 0; u < RPL; ++u) re[u] = (r0 + lane + 32 * u) * b;
+    for (int64_t c = c0; c < c0 + cw; c += 8) {
+        float4 v[RPL][2];
+#pragma unroll
+        for (int u = 0; u < RPL; ++u)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                v[u][h] = load4<PREC>(base, re[u] + c + 4 * h);
+                v[u][h].x -= shift; v[u][h].y -= shift; v[u][h].z -= shift; v[u][h].w -= shift;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t c = c0 + u * 128 + lane * 4;
-                if (c >= b) break;
+        for (int h = 0; h < 2; ++h) {
 #pragma unroll
-                for (int q = 0; q < PC; ++q) {
-                    if (q < pc) {
-                        const float4 z = *reinterpret_cast<const float4 *>(zt + q * b + c);
-                        acc[q] = fmaf(v[u].x, z.x, fmaf(v[u].y, z.y, fmaf(v[u].z, z.z, fmaf(v[u].w, z.w, acc[q]))));
+            for (int e = 0; e < 4; ++e) {
+                const float *xr = xs + (c + 4 * h + e) * pcp;
+#pragma unroll
+                for (int q4 = 0; q4 < PC / 4; ++q4) {
+                    if (q4 * 4 < pc) {
+                        const float4 z = *reinterpret_cast<const float4 *>(xr + q4 * 4);
+#pragma unroll
+                        for (int u = 0; u < RPL; ++u) {
+                            const float vv = (e == 0) ? v[u][h].x : (e == 1) ? v[u][h].y : (e == 2) ? v[u][h].z : v[u][h].w;
+                            acc[u][q4 * 4 + 0] = fmaf(vv, z.x, acc[u][q4 * 4 + 0]);
+                            acc[u][q4 * 4 + 1] = fmaf(vv, z.y, acc[u][q4 * 4 + 1]);
+                            acc[u][q4 * 4 + 2] = fmaf(vv, z.z, acc[u][q4 * 4 + 2]);
+                            acc[u][q4 * 4 + 3] = fmaf(vv, z.w, acc[u][q4 * 4 + 3]);
+                        }
                     }
                 }
             }
         }
-        float mine = 0.f;
+    }
+    // red layout: [warp][32 * RPL rows][pc]; it overlays the x block, so
+    // every warp must be done reading x first
+    constexpr int R = 32 * RPL;
+    __syncthreads();
 #pragma unroll
-        for (int q = 0; q < PC; ++q) {
-            if (q < pc) {
-                float t = acc[q];
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                if (lane == q) mine = t;
-            }
-        }
-        if (lane < pc) {
-            float *dst = out + r * ldo + q0 + lane;
-            const float v = mine * inv_scale;
-            if (subtract) *dst -= v;
-            else *dst = v;
-        }
+    for (int u = 0; u < RPL; ++u)
+#pragma unroll
+        for (int q = 0; q < PC; ++q)
+            if (q < pc) red[(warp * R + lane + 32 * u) * pc + q] = acc[u][q];
+    __syncthreads();
+    for (int t = threadIdx.x; t < R * pc; t += blockDim.x) {
+        const int rr = t / pc, q = t % pc;
+        float sum = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) sum += red[(w * R + rr) * pc + q];
+        float *dst = out + (r0 + rr) * ldo + q0 + q;
+        const float val = sum * inv_scale;
+        if (subtract) *dst -= val;
+        else *dst = val;
     }
 }
 
-// grid: (b / rows_per_cta, tasks); dynamic smem: pc * b floats (x block, transposed)
-__global__ void __launch_bounds__(256) gemv_n_kernel(GemvArgs g, int rows_per_cta) {
-    extern __shared__ float zt[];
+// grid: (b / (32 * rows_per_lane), tasks), 256 threads; dynamic smem:
+// max(b * pcp, 8 * 32 * rows_per_lane * pc) floats (x block, then the
+// column-slice partials in the same space).
+__global__ void __launch_bounds__(256) gemv_n_kernel(GemvArgs g, int rows_per_lane) {
+    extern __shared__ float xs[];
     const uint8_t *base;
     int prec;
     float inv_scale, shift;
     int64_t in_blk, ldo;
     float *out;
     gemv_locate(g, blockIdx.y, base, prec, inv_scale, shift, in_blk, out, ldo);
+    const int pcp = (g.pc + 3) & ~3;
     const float *xin = g.x + in_blk * g.b * g.ldx + g.q0;
     {
-        // stage x_k transposed (zt[q][c]) without integer division
+        // stage x_k row-major with padded width pcp, no integer division
         const int bi = (int)g.b, ldx = (int)g.ldx, pc = g.pc;
-        for (int c = threadIdx.x; c < bi; c += blockDim.x) {
-            const float *src = xin + (int64_t)c * ldx;
-            for (int q = 0; q < pc; ++q) zt[q * bi + c] = src[q];
+        for (int r = threadIdx.x; r < bi; r += blockDim.x) {
+            const float *src = xin + (int64_t)r * ldx;
+            float *dst = xs + r * pcp;
+            for (int q = 0; q < pcp; ++q) dst[q] = (q < pc) ? src[q] : 0.f;
         }
     }
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta, r1 = r0 + rows_per_cta;
+    float *red = xs;
+    const int64_t r0 = (int64_t)blockIdx.x * 32 * rows_per_lane;
     const bool sub = (g.job == JOB_FWD || g.job == JOB_BWD);
     const int q0o = (g.job >= JOB_RES_N) ? 0 : g.q0;
-    if (prec == KRR_PREC_FP32) gemv_n_rows<KRR_PREC_FP32>(base, inv_scale, shift, g.b, r0, r1, zt, g.pc, out, ldo, q0o, sub);
-    else if (prec == KRR_PREC_FP16) gemv_n_rows<KRR_PREC_FP16>(base, inv_scale, shift, g.b, r0, r1, zt, g.pc, out, ldo, q0o, sub);
-    else gemv_n_rows<KRR_PREC_E4M3>(base, inv_scale, shift, g.b, r0, r1, zt, g.pc, out, ldo, q0o, sub);
+    if (rows_per_lane == 2) {
+        if (prec == KRR_PREC_FP32) gemv_n_block<KRR_PREC_FP32, 2>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
+        else if (prec == KRR_PREC_FP16) gemv_n_block<KRR_PREC_FP16, 2>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
+        else gemv_n_block<KRR_PREC_E4M3, 2>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
+    } else {
+        if (prec == KRR_PREC_FP32) gemv_n_block<KRR_PREC_FP32, 1>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
+        else if (prec == KRR_PREC_FP16) gemv_n_block<KRR_PREC_FP16, 1>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
+        else gemv_n_block<KRR_PREC_E4M3, 1>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
+    }
 }
 
 template <int PREC>
 __device__ __forceinline__ void gemv_t_cols(const uint8_t *base, float inv_scale, float shift, int64_t b,
-                                            int64_t c0, const float *at, int pcp, int pc, float *red,
-                                            float *out, int64_t ldo, int q0, bool subtract) {
+                                            int64_t c0, int64_t ra0, int64_t rows, const float *at, int pcp,
+                                            int pc, float *red, float *out, int64_t ldo, int q0, int mode) {
+    // mode 0: out = v, 1: out -= v (out rows are the tile's columns)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t rows_per_warp = b / 8;
-    const int64_t ra = warp * rows_per_warp, rb = ra + rows_per_warp;
+    const int64_t rows_per_warp = rows / 8;
+    const int64_t ra = ra0 + warp * rows_per_warp, rb = ra + rows_per_warp;
     const int64_t col = c0 + lane * 4;
     float acc[4][PC];
 #pragma unroll
@@ -1124,7 +1092,7 @@ __device__ __forceinline__ void gemv_t_cols(const uint8_t *base, float inv_scale
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const float *ar = at + (r + u) * pcp;
+            const float *ar = at + (r + u - ra0) * pcp;
 #pragma unroll
             for (int q4 = 0; q4 < PC / 4; ++q4) {
                 if (q4 * 4 < pc) {
@@ -1157,13 +1125,16 @@ __device__ __forceinline__ void gemv_t_cols(const uint8_t *base, float inv_scale
         for (int w = 0; w < 8; ++w) s += red[(w * 128 + cc) * pc + q];
         float *dst = out + (c0 + cc) * ldo + q0 + q;
         const float v = s * inv_scale;
-        if (subtract) *dst -= v;
+        if (mode == 1) *dst -= v;
         else *dst = v;
     }
 }
 
-// grid: (b / 128, tasks), 256 threads; dynamic smem: max(b * pcp, 8 * 128 * pc) floats
-__global__ void __launch_bounds__(256) gemv_t_kernel(GemvArgs g) {
+// grid: (b / 128, tasks, row chunks), 256 threads; dynamic smem:
+// max((b / chunks) * pcp, 8 * 128 * pc) floats.  With more than one row chunk
+// (JOB_BWD only) each CTA writes its partial to part[(task * chunks + z)][b][pc]
+// and gemv_t_reduce_kernel subtracts the chunk sums in a fixed order.
+__global__ void __launch_bounds__(256) gemv_t_kernel(GemvArgs g, float *part) {
     extern __shared__ float at[];
     const uint8_t *base;
     int prec;
@@ -1179,29 +1150,50 @@ __global__ void __launch_bounds__(256) gemv_t_kernel(GemvArgs g) {
         y = tri_index(i + 1, j);
     }
     gemv_locate(g, y, base, prec, inv_scale, shift, in_blk, out, ldo);
+    const int chunks = gridDim.z, z = blockIdx.z;
+    const int64_t rows = g.b / chunks, ra0 = (int64_t)z * rows;
     const int pcp = (g.pc + 3) & ~3;
     const float *xin = g.x + in_blk * g.b * g.ldx + g.q0;
     {
-        // stage x_k row-major with padded width pcp, without integer division
-        const int bi = (int)g.b, ldx = (int)g.ldx, pc = g.pc;
-        for (int r = threadIdx.x; r < bi; r += blockDim.x) {
-            const float *src = xin + (int64_t)r * ldx;
+        // stage rows [ra0, ra0 + rows) of x_k with padded width pcp, no integer division
+        const int ri = (int)rows, ldx = (int)g.ldx, pc = g.pc;
+        for (int r = threadIdx.x; r < ri; r += blockDim.x) {
+            const float *src = xin + (ra0 + r) * ldx;
             float *dst = at + r * pcp;
             for (int q = 0; q < pcp; ++q) dst[q] = (q < pc) ? src[q] : 0.f;
         }
     }
     __syncthreads();
     const int64_t c0 = (int64_t)blockIdx.x * 128;
-    const bool sub = (g.job == JOB_FWD || g.job == JOB_BWD);
-    const int q0o = (g.job >= JOB_RES_N) ? 0 : g.q0;
-    if (prec == KRR_PREC_FP32) gemv_t_cols<KRR_PREC_FP32>(base, inv_scale, shift, g.b, c0, at, pcp, g.pc, at, out, ldo, q0o, sub);
-    else if (prec == KRR_PREC_FP16) gemv_t_cols<KRR_PREC_FP16>(base, inv_scale, shift, g.b, c0, at, pcp, g.pc, at, out, ldo, q0o, sub);
-    else gemv_t_cols<KRR_PREC_E4M3>(base, inv_scale, shift, g.b, c0, at, pcp, g.pc, at, out, ldo, q0o, sub);
+    int mode = (g.job == JOB_FWD || g.job == JOB_BWD) ? 1 : 0;
+    int q0o = (g.job >= JOB_RES_N) ? 0 : g.q0;
+    if (chunks > 1) {  // partial slot of this chunk
+        out = part + ((int64_t)blockIdx.y * chunks + z) * g.b * g.pc;
+        ldo = g.pc;
+        q0o = 0;
+        mode = 0;
+    }
+    if (prec == KRR_PREC_FP32) gemv_t_cols<KRR_PREC_FP32>(base, inv_scale, shift, g.b, c0, ra0, rows, at, pcp, g.pc, at, out, ldo, q0o, mode);
+    else if (prec == KRR_PREC_FP16) gemv_t_cols<KRR_PREC_FP16>(base, inv_scale, shift, g.b, c0, ra0, rows, at, pcp, g.pc, at, out, ldo, q0o, mode);
+    else gemv_t_cols<KRR_PREC_E4M3>(base, inv_scale, shift, g.b, c0, ra0, rows, at, pcp, g.pc, at, out, ldo, q0o, mode);
 }
 
-static size_t gemv_n_smem(int64_t b, int pc) { return (size_t)b * pc * sizeof(float); }
-static size_t gemv_t_smem(int64_t b, int pc) {
-    const size_t a = (size_t)b * ((pc + 3) & ~3), r = (size_t)8 * 128 * pc;
+// out block j (JOB_BWD task j) -= sum over chunks of the partials, fixed order.
+// grid: (b / 8, tasks), block (pc, 8).
+__global__ void gemv_t_reduce_kernel(const float *part, int chunks, int64_t b, int pc, float *x,
+                                     int64_t ldx, int q0) {
+    const int64_t j = blockIdx.y, c = (int64_t)blockIdx.x * 8 + threadIdx.y;
+    const int q = threadIdx.x;
+    float s = 0.f;
+    for (int z = 0; z < chunks; ++z) s += part[((j * chunks + z) * b + c) * pc + q];
+    x[(j * b + c) * ldx + q0 + q] -= s;
+}
+
+static size_t gemv_n_smem(int64_t b, int pc, int rows_per_lane) {
+    return std::max((size_t)b * ((pc + 3) & ~3), (size_t)8 * 32 * rows_per_lane * pc) * sizeof(float);
+}
+static size_t gemv_t_smem(int64_t rows, int pc) {
+    const size_t a = (size_t)rows * ((pc + 3) & ~3), r = (size_t)8 * 128 * pc;
     return (a > r ? a : r) * sizeof(float);
 }
 
@@ -1243,23 +1235,29 @@ void solve_inplace(Ctx *c, float *x, float *tmp, int64_t p) {
     gemv_attrs();
     for (int q0 = 0; q0 < p; q0 += PC) {
         const int pc = (int)std::min<int64_t>(PC, p - q0);
-        const size_t shn = gemv_n_smem(b, pc), sht = gemv_t_smem(b, pc);
+        const size_t shn1 = gemv_n_smem(b, pc, 1), shn2 = gemv_n_smem(b, pc, 2);
         for (int64_t k = 0; k < nt; ++k) {
             GemvArgs g = gemv_args(c, JOB_DIAG, k, x, p, tmp, q0, pc);
             g.diag = c->Linv + k * bb;
-            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 16), 1), 256, shn, s>>>(g, 16);
+            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 32), 1), 256, shn1, s>>>(g, 1);
             if (k + 1 < nt) {
                 GemvArgs f = gemv_args(c, JOB_FWD, k, tmp, p, x, q0, pc);
-                count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)(nt - k - 1)), 256, shn, s>>>(f, 64);
+                count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)(nt - k - 1)), 256, shn2, s>>>(f, 2);
             }
         }
         for (int64_t k = nt - 1; k >= 0; --k) {
             GemvArgs g = gemv_args(c, JOB_DIAG, k, tmp, p, x, q0, pc);
             g.diag = c->LinvT + k * bb;
-            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 16), 1), 256, shn, s>>>(g, 16);
+            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 32), 1), 256, shn1, s>>>(g, 1);
             if (k > 0) {
+                // few tiles in early steps: split the rows of each tile in chunks
+                const int chunks = (k < 32) ? 4 : 1;
                 GemvArgs f = gemv_args(c, JOB_BWD, k, x, p, tmp, q0, pc);
-                count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)k), 256, sht, s>>>(f);
+                count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)k, (unsigned)chunks), 256,
+                                                 gemv_t_smem(b / chunks, pc), s>>>(f, c->res_part);
+                if (chunks > 1)
+                    count_launch(), gemv_t_reduce_kernel<<<dim3((unsigned)(b / 8), (unsigned)k), dim3(pc, 8), 0, s>>>(
+                        c->res_part, chunks, b, pc, tmp, p, q0);
             }
         }
     }
@@ -1312,10 +1310,10 @@ void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t 
     for (int q0 = 0; q0 < p; q0 += PC) {
         const int pc = (int)std::min<int64_t>(PC, p - q0);
         GemvArgs gn = gemv_args(c, JOB_RES_N, 0, a, p, c->res_part, q0, pc);
-        count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)ntri), 256, gemv_n_smem(b, pc), c->stream>>>(gn, 64);
+        count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)ntri), 256, gemv_n_smem(b, pc, 2), c->stream>>>(gn, 2);
         if (noff > 0) {
             GemvArgs gt = gemv_args(c, JOB_RES_T, 0, a, p, c->res_part, q0, pc);
-            count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)noff), 256, gemv_t_smem(b, pc), c->stream>>>(gt);
+            count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)noff, 1), 256, gemv_t_smem(b, pc), c->stream>>>(gt, nullptr);
         }
         count_launch(), residual_reduce_kernel<<<dim3((unsigned)(b / 8), (unsigned)nt), dim3(pc, 8), 0, c->stream>>>(
             c->res_part, nt, b, pc, q0, p, (float)c->lambda, y, a, c->red + RED_KSHIFT, c->colsum, r);
@@ -1477,5 +1475,40 @@ void launch_sum_f64(const double *x, int64_t n, double *out, cudaStream_t s) {
 }
 void launch_dot_f32(const float *a, const float *b, int64_t n, double *out, cudaStream_t s) {
     count_launch(), dot_f32_kernel<<<1, 1024, 0, s>>>(a, b, n, out);
+}
+}  // namespace krr
+
+namespace krr {
+__global__ void factor_init_kernel(DevErrors *err, uint8_t *precmap, TileDesc *ltab, int64_t nt,
+                                   int64_t bb, int diag_code, int fp32_mode) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e == 0) {
+        err->code = 0;
+        err->pad = 0;
+        err->bad_tile = -1;
+        err->bad_column = -1;
+        err->bad_value = 0.0;
+        err->fp8_tiles = err->fp16_tiles = err->fp32_tiles = err->pool_cursor = 0;
+        err->min_pivot = INFINITY;
+    }
+    if (e < nt * nt) {
+        const int64_t i = e / nt, j = e % nt;
+        precmap[e] = (i == j) ? (uint8_t)diag_code : ((j < i && fp32_mode) ? (uint8_t)KRR_PREC_FP32 : (uint8_t)255);
+    }
+    if (fp32_mode && e < nt * (nt - 1) / 2) {
+        TileDesc d;
+        d.offset = e * bb * 4;
+        d.scale = 1.f;
+        d.prec = KRR_PREC_FP32;
+        ltab[e] = d;
+    }
+}
+
+void launch_factor_init(Ctx *c) {
+    const int64_t nt = c->nt;
+    const int64_t count = nt * nt > 1 ? nt * nt : 1;
+    count_launch(), factor_init_kernel<<<cdiv(count, 256), 256, 0, c->stream>>>(
+        c->derr, c->precmap, c->ltab, nt, c->b * c->b, c->opt.diag_fp64 ? KRR_PREC_FP64 : KRR_PREC_FP32,
+        c->opt.mode == KRR_MODE_FP32 ? 1 : 0);
 }
 }  // namespace krr

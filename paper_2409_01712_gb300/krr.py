@@ -33,7 +33,7 @@ EXPORTED = ["krr_default_options", "krr_create", "krr_build_kernel", "krr_factor
             "krr_predict", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
             "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_sync", "krr_last_error",
-            "krr_destroy"]
+            "krr_destroy", "krr_batch_create", "krr_batch_run", "krr_batch_last_error", "krr_batch_destroy"]
 PROF_CLASSES = ["pack", "build", "diag", "trsm", "cast", "update", "solve", "residual", "predict"]
 
 
@@ -58,6 +58,18 @@ class SolveInfo(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("count", ctypes.c_int64 * 9), ("ms", ctypes.c_double * 9),
                 ("flops", ctypes.c_double * 9), ("bytes", ctypes.c_double * 9)]
+
+
+class BatchProblem(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_void_p), ("n", ctypes.c_int64), ("ldg", ctypes.c_int64),
+                ("gamma", ctypes.c_double), ("lam", ctypes.c_double), ("Y", ctypes.c_void_p),
+                ("ldy", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("T", ctypes.c_void_p), ("n_test", ctypes.c_int64), ("ldt", ctypes.c_int64),
+                ("Yt", ctypes.c_void_p), ("ldyt", ctypes.c_int64)]
+
+
+class BatchResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("tile", ctypes.c_int32), ("rel_residual", ctypes.c_double)]
 
 
 class KRRError(RuntimeError):
@@ -95,6 +107,15 @@ def load_library(path: str = LIB_PATH):
     lib.krr_grad_hyper.argtypes = [vp, vp, i64, i64, vp, i64, vp, i64, i64, ctypes.POINTER(dbl)]
     lib.krr_set_profiling.argtypes = [vp, i32]
     lib.krr_get_profile.argtypes = [vp, ctypes.POINTER(Profile), i32]
+    lib.krr_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Options), vp, i64, i64,
+                                     ctypes.POINTER(BatchProblem), i32, i32]
+    lib.krr_batch_create.restype = ctypes.c_int
+    lib.krr_batch_run.argtypes = [vp, ctypes.POINTER(BatchResult)]
+    lib.krr_batch_run.restype = ctypes.c_int
+    lib.krr_batch_last_error.argtypes = [vp]
+    lib.krr_batch_last_error.restype = ctypes.c_char_p
+    lib.krr_batch_destroy.argtypes = [vp]
+    lib.krr_batch_destroy.restype = None
     lib.krr_sync.argtypes = [vp]
     lib.krr_last_error.argtypes = [vp]
     lib.krr_last_error.restype = ctypes.c_char_p
@@ -276,3 +297,68 @@ class KRR:
 
     def sync(self):
         self._check(self._lib.krr_sync(self._ctx))
+
+
+class KRRBatch:
+    """Many KRR problems (cohorts x folds x lambdas) captured into one CUDA graph.
+
+    problems: list of dicts with device tensors G (n x m int8), Y (n x p),
+    optional T (n_t x m int8), and floats gamma, lam.  Outputs A and Yt are
+    allocated here and refreshed by every run().
+    """
+
+    def __init__(self, problems, ir_iters: int = 3, autotune: bool = True, tile: int = 1024, stream=None):
+        lib = load_library()
+        self._lib = lib
+        o = default_options()
+        o.tile = tile
+        o.ir_max = ir_iters
+        if stream is None and torch is not None and torch.cuda.is_available():
+            stream = torch.cuda.current_stream().cuda_stream
+        m = problems[0]["G"].shape[1]
+        p = problems[0]["Y"].shape[1]
+        self.A, self.Yt = [], []
+        arr = (BatchProblem * len(problems))()
+        for i, pr in enumerate(problems):
+            g, y = pr["G"], pr["Y"]
+            a = torch.empty((g.shape[0], p), dtype=torch.float32, device=g.device)
+            self.A.append(a)
+            t = pr.get("T")
+            yt = torch.empty((t.shape[0], p), dtype=torch.float32, device=g.device) if t is not None else None
+            self.Yt.append(yt)
+            arr[i] = BatchProblem(g.data_ptr(), g.shape[0], _ld(g), pr["gamma"], pr["lam"], y.data_ptr(), _ld(y),
+                                  a.data_ptr(), _ld(a), t.data_ptr() if t is not None else None,
+                                  t.shape[0] if t is not None else 0, _ld(t) if t is not None else m,
+                                  yt.data_ptr() if yt is not None else None, p)
+        self._problems = problems  # keep the inputs alive: the graph reads them at every run
+        self._arr = arr
+        self._bt = ctypes.c_void_p()
+        st = lib.krr_batch_create(ctypes.byref(self._bt), ctypes.byref(o), ctypes.c_void_p(stream or 0), m, p,
+                                  arr, len(problems), int(autotune))
+        if st != OK:
+            raise KRRError(st, "krr_batch_create failed: " + lib.krr_batch_last_error(None).decode())
+        self.count = len(problems)
+
+    def run(self):
+        res = (BatchResult * self.count)()
+        st = self._lib.krr_batch_run(self._bt, res)
+        if st != OK:
+            raise KRRError(st, self._lib.krr_batch_last_error(self._bt).decode())
+        return [{"status": r.status, "tile": r.tile, "rel_residual": r.rel_residual} for r in res]
+
+    def close(self):
+        if self._bt:
+            self._lib.krr_batch_destroy(self._bt)
+            self._bt = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,38 @@
+"""Batched problems under one captured CUDA graph (cross-validation style:
+cohorts x lambdas of uneven size) against the CPU oracle, and run-to-run
+identity of the graph replays.  Y_test tolerance 1e-4 (as the other parity
+tests)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_01712_gb300 import KRRBatch, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+def test_batch_matches_oracle_and_replays():
+    m, p = 300, 2
+    sizes = [(700, 0.1), (700, 1.0), (1300, 0.1), (1300, 0.01), (300, 0.1)]
+    problems, refs = [], []
+    for idx, (n, lam) in enumerate(sizes):
+        prob = inputs.problem(n, m, p, 120, seed=900 + n)  # same n -> same cohort data
+        g, y, t = prob["G"].numpy(), prob["Y"].numpy(), prob["T"].numpy()
+        _, a_ref, yt_ref = oracle.krr(1.0 / m, lam, g, y.astype(np.float64), t)
+        refs.append((a_ref, yt_ref))
+        problems.append({"G": prob["G"].to(DEV), "Y": prob["Y"].to(DEV), "T": prob["T"].to(DEV),
+                         "gamma": 1.0 / m, "lam": lam})
+    with KRRBatch(problems, ir_iters=3, autotune=True) as bt:
+        res = bt.run()
+        first = [yt.clone() for yt in bt.Yt]
+        res2 = bt.run()
+        for i, (a_ref, yt_ref) in enumerate(refs):
+            assert res[i]["status"] == 0
+            assert res[i]["tile"] in (256, 512, 1024)
+            yt = bt.Yt[i].cpu().numpy().astype(np.float64)
+            err = np.linalg.norm(yt - yt_ref) / np.linalg.norm(yt_ref)
+            assert err <= 1e-4, (i, err, res[i])
+            assert torch.equal(bt.Yt[i], first[i])  # deterministic replay
+            assert res2[i]["rel_residual"] == res[i]["rel_residual"]
