@@ -255,7 +255,7 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
     const double sweep_bytes = 2.0 * factor_bytes_all + 4.0 * (double)cnt * 4.0;
     const double sweep_flops = 2.0 * 2.0 * (double)c->n_pad * c->n_pad * p;
     int pr = prof_begin(c, KRR_PROF_SOLVE);
-    solve_inplace(c, c->abuf, c->zbuf, p);
+    KRR_TRY(solve_inplace(c, c->abuf, c->zbuf, p));
     prof_end(c, pr, sweep_flops, sweep_bytes);
     KRR_TRY(check_launch(c, "solve"));
     krr_solve_info si;
@@ -266,12 +266,12 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
         // relative residual is left in red[RED_RNORM..+1] for the caller
         const int iters = mixed(c) ? c->opt.ir_max : 0;
         for (int it = 0; it < iters; ++it) {
-            launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
+            KRR_TRY(launch_residual(c, c->ybuf, c->abuf, c->rbuf, p));
             launch_axpy_r(c->rbuf, c->dabuf, cnt, s);
-            solve_inplace(c, c->dabuf, c->zbuf, p);
+            KRR_TRY(solve_inplace(c, c->dabuf, c->zbuf, p));
             launch_add_scaled(c->abuf, c->dabuf, 1.0f, cnt, s);
         }
-        launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
+        KRR_TRY(launch_residual(c, c->ybuf, c->abuf, c->rbuf, p));
         launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
         KRR_TRY(check_launch(c, "refinement (graph mode)"));
         if (info) *info = si;
@@ -283,7 +283,7 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
         int stall = 0;
         for (int it = 0;; ++it) {
             int rr = prof_begin(c, KRR_PROF_RESIDUAL);
-            launch_residual(c, c->ybuf, c->abuf, c->rbuf, p);
+            KRR_TRY(launch_residual(c, c->ybuf, c->abuf, c->rbuf, p));
             launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
             // the lower-triangle K tiles are read once by the row pass and
             // once by the column pass
@@ -330,7 +330,7 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
             best = std::min(best, rel);
             launch_axpy_r(c->rbuf, c->dabuf, cnt, s);
             int sr = prof_begin(c, KRR_PROF_SOLVE);
-            solve_inplace(c, c->dabuf, c->zbuf, p);
+            KRR_TRY(solve_inplace(c, c->dabuf, c->zbuf, p));
             prof_end(c, sr, sweep_flops, sweep_bytes);
             launch_add_scaled(c->abuf, c->dabuf, 1.0f, cnt, s);
             KRR_TRY(check_launch(c, "refinement step"));
@@ -430,6 +430,8 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->pred_out);
     dev_free(&c->colsum);
     dev_free(&c->res_part);
+    dev_free(&c->sw_flags);
+    dev_free(&c->sw_acc);
     dev_free(&c->g_yt);
     dev_free(&c->g_gp);
     dev_free(&c->g_aw);

@@ -116,6 +116,10 @@ struct Ctx {
     int64_t vec_cap = 0;                     // capacity in elements of the n_pad x p buffers
     float *pred_part = nullptr;              // predict partial products
     size_t pred_part_cap = 0;
+    int *sw_flags = nullptr;                 // sweep item counter, abort flag, block counters
+    int64_t sw_flags_cap = 0;
+    float *sw_acc = nullptr;                 // sweep partial vectors, n_pad x p
+    int64_t sw_acc_cap = 0;
     float *pred_out = nullptr;               // reduced predictions, rows_pad x p
     size_t pred_out_cap = 0;
     // hyperparameter gradient buffers (krr_grad_hyper)
@@ -202,10 +206,16 @@ void launch_column_cast(Ctx *c, int64_t k);
 
 // Triangular solves with the stored factor: X <- (L L^T)^-1 X, n_pad x p
 // (row-major, leading dimension p); tmp is n_pad x p scratch.
-void solve_inplace(Ctx *c, float *x, float *tmp, int64_t p);
+krr_status solve_inplace(Ctx *c, float *x, float *tmp, int64_t p);
+
+// Persistent dataflow sweeps (sweep.cu): the two substitutions of a solve,
+// and the residual r = y - (K + lambda I) a given the column sums of a in
+// c->colsum.
+krr_status sweep_solve(Ctx *c, float *x, float *tmp, int64_t p);
+krr_status sweep_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
 
 // r = y - (K + lambda I) a (FP64 accumulation), norms into c->red.
-void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
+krr_status launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
 
 // Resets the device error record and the precision map, and (fp32 mode)
 // fills the tile table: every factor tile FP32 at a fixed slot.

@@ -1225,43 +1225,8 @@ static GemvArgs gemv_args(Ctx *c, int job, int64_t k, const float *x, int64_t ld
     return g;
 }
 
-// x (n_pad x p) <- (L L^T)^-1 x.  tmp is n_pad x p scratch.  Forward:
-// tmp_k = Linv_kk x_k, then x_i -= L_ik tmp_k (i > k); tmp ends as Z.
-// Backward: x_k = Linv_kk^T tmp_k (through the stored transpose), then
-// tmp_j -= L_kj^T x_k (j < k).
-void solve_inplace(Ctx *c, float *x, float *tmp, int64_t p) {
-    const int64_t b = c->b, nt = c->nt, bb = b * b;
-    cudaStream_t s = c->stream;
-    gemv_attrs();
-    for (int q0 = 0; q0 < p; q0 += PC) {
-        const int pc = (int)std::min<int64_t>(PC, p - q0);
-        const size_t shn1 = gemv_n_smem(b, pc, 1), shn2 = gemv_n_smem(b, pc, 2);
-        for (int64_t k = 0; k < nt; ++k) {
-            GemvArgs g = gemv_args(c, JOB_DIAG, k, x, p, tmp, q0, pc);
-            g.diag = c->Linv + k * bb;
-            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 32), 1), 256, shn1, s>>>(g, 1);
-            if (k + 1 < nt) {
-                GemvArgs f = gemv_args(c, JOB_FWD, k, tmp, p, x, q0, pc);
-                count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)(nt - k - 1)), 256, shn2, s>>>(f, 2);
-            }
-        }
-        for (int64_t k = nt - 1; k >= 0; --k) {
-            GemvArgs g = gemv_args(c, JOB_DIAG, k, tmp, p, x, q0, pc);
-            g.diag = c->LinvT + k * bb;
-            count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 32), 1), 256, shn1, s>>>(g, 1);
-            if (k > 0) {
-                // few tiles in early steps: split the rows of each tile in chunks
-                const int chunks = (k < 32) ? 4 : 1;
-                GemvArgs f = gemv_args(c, JOB_BWD, k, x, p, tmp, q0, pc);
-                count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)k, (unsigned)chunks), 256,
-                                                 gemv_t_smem(b / chunks, pc), s>>>(f, c->res_part);
-                if (chunks > 1)
-                    count_launch(), gemv_t_reduce_kernel<<<dim3((unsigned)(b / 8), (unsigned)k), dim3(pc, 8), 0, s>>>(
-                        c->res_part, chunks, b, pc, tmp, p, q0);
-            }
-        }
-    }
-}
+// x (n_pad x p) <- (L L^T)^-1 x.  tmp is n_pad x p scratch (ends as Z).
+krr_status solve_inplace(Ctx *c, float *x, float *tmp, int64_t p) { return sweep_solve(c, x, tmp, p); }
 
 // ----------------------------------------------------------------------------
 // Refinement residual r = y - lambda a - K a, K from the FP32 lower-triangle
@@ -1302,22 +1267,9 @@ __global__ void colsum_kernel(const float *a, int64_t n, int64_t p, double *out)
     }
 }
 
-void launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
-    const int64_t b = c->b, nt = c->nt;
-    gemv_attrs();
+krr_status launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
     count_launch(), colsum_kernel<<<(unsigned)p, 512, 0, c->stream>>>(a, c->n_pad, p, c->colsum);
-    const int64_t ntri = nt * (nt + 1) / 2, noff = nt * (nt - 1) / 2;
-    for (int q0 = 0; q0 < p; q0 += PC) {
-        const int pc = (int)std::min<int64_t>(PC, p - q0);
-        GemvArgs gn = gemv_args(c, JOB_RES_N, 0, a, p, c->res_part, q0, pc);
-        count_launch(), gemv_n_kernel<<<dim3((unsigned)(b / 64), (unsigned)ntri), 256, gemv_n_smem(b, pc, 2), c->stream>>>(gn, 2);
-        if (noff > 0) {
-            GemvArgs gt = gemv_args(c, JOB_RES_T, 0, a, p, c->res_part, q0, pc);
-            count_launch(), gemv_t_kernel<<<dim3((unsigned)(b / 128), (unsigned)noff, 1), 256, gemv_t_smem(b, pc), c->stream>>>(gt, nullptr);
-        }
-        count_launch(), residual_reduce_kernel<<<dim3((unsigned)(b / 8), (unsigned)nt), dim3(pc, 8), 0, c->stream>>>(
-            c->res_part, nt, b, pc, q0, p, (float)c->lambda, y, a, c->red + RED_KSHIFT, c->colsum, r);
-    }
+    return sweep_residual(c, y, a, r, p);
 }
 
 // ||r||_F^2 and ||y||_F^2 into out[0], out[1] (deterministic single block).

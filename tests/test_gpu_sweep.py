@@ -1,0 +1,48 @@
+"""The substitution sweeps and the refinement residual (persistent dataflow
+kernel) against FP64 references on the same stored factor.
+
+With ir_max = 0 a solve is one forward and one backward sweep, so the
+returned A must equal (L L^T)^-1 Y for the factor L the library stored (read
+back densely), up to FP32 rounding: relative error <= 2e-5 here (FP32
+products, FP32 accumulation over N = 1300 terms, L well conditioned).  The
+reported relative residual must match ||Y - (K + lambda I) A|| / ||Y||
+recomputed in FP64 from the oracle's K to 1e-3 of its value (the device
+forms it from FP32 K tiles with FP64 row sums).
+
+Cases: ragged N over several tiles; more than 32 right-hand sides (two
+column chunks per sweep) with a leading dimension that is not a multiple of
+4 (4-byte vector copies); a narrow kernel (gamma = 8 / M, off-diagonal K
+around 4e-3) with an error bound loose enough for E4M3 factor tiles.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_01712_gb300 import KRR, inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
+
+
+@pytest.mark.parametrize("p,eps,tile,gmul", [(37, None, 256, 1.0), (40, None, 512, 1.0), (5, 0.05, 256, 8.0)])
+def test_sweep_solve_and_residual_match_fp64(p, eps, tile, gmul):
+    n, m, lam = 1300, 300, 0.1
+    gamma = gmul / m
+    prob = inputs.problem(n, m, p, 1, seed=4242 + p)
+    g, y = prob["G"], prob["Y"].numpy().astype(np.float64)
+    with KRR(tile=tile, mode="mixed", eps=eps, ir_max=0) as model:
+        model.build_kernel(g.to(DEV), gamma)
+        finfo = model.factor(lam)
+        a, sinfo = model.solve(torch.from_numpy(prob["Y"].numpy()).to(DEV), raise_on_noconv=False)
+        l_stored = model.factor_matrix().astype(np.float64)
+    if eps is not None:
+        assert finfo["tiles_e4m3"] > 0, finfo
+    a = a.cpu().numpy().astype(np.float64)
+    a_ref = oracle.backward_subst(l_stored, oracle.forward_subst(l_stored, y))
+    err = np.linalg.norm(a - a_ref) / np.linalg.norm(a_ref)
+    assert err <= 2e-5, err
+    k = oracle.build_kernel(gamma, g.numpy())
+    r = y - k @ a - lam * a
+    rel = np.linalg.norm(r) / np.linalg.norm(y)
+    assert abs(sinfo["rel_residual"] - rel) <= 1e-3 * rel + 1e-9, (sinfo["rel_residual"], rel)
