@@ -431,7 +431,6 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->colsum);
     dev_free(&c->res_part);
     dev_free(&c->sw_flags);
-    dev_free(&c->sw_acc);
     dev_free(&c->g_yt);
     dev_free(&c->g_gp);
     dev_free(&c->g_aw);

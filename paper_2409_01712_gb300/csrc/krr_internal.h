@@ -116,10 +116,8 @@ struct Ctx {
     int64_t vec_cap = 0;                     // capacity in elements of the n_pad x p buffers
     float *pred_part = nullptr;              // predict partial products
     size_t pred_part_cap = 0;
-    int *sw_flags = nullptr;                 // sweep item counter, abort flag, block counters
+    int *sw_flags = nullptr;                 // sweep item counter, abort flag, progress counters
     int64_t sw_flags_cap = 0;
-    float *sw_acc = nullptr;                 // sweep partial vectors, n_pad x p
-    int64_t sw_acc_cap = 0;
     float *pred_out = nullptr;               // reduced predictions, rows_pad x p
     size_t pred_out_cap = 0;
     // hyperparameter gradient buffers (krr_grad_hyper)

@@ -2,34 +2,36 @@
 // forward substitution L z = y, backward substitution L^T x = z) and for the
 // refinement residual r = y - (K + lambda I) a.
 //
-// Work is cut into items that each own 128 output rows ("slab" s of row
-// block i) and read every tile that contributes to them:
-//   forward   ACC(i, s)    acc_i = y_i - sum_{j<i} L_ij z_j     (row slabs of L_ij)
-//             DIAG(i, s)   z_i   = Linv_ii acc_i                 (row slab of Linv_ii)
-//   backward  ACC(j, s)    acc_j = z_j - sum_{i>j} L_ij^T x_i   (column slabs of L_ij)
-//             DIAG(j, s)   x_j   = Linv_jj^T acc_j               (row slab of Linv_jj^T)
-//   residual  RES(i, s)    r_i = y_i - lambda a_i - sum_j K_ij a_j, K symmetric:
-//             row slabs of the stored tiles (i, j <= i), column slabs of (j > i, i)
-// Items are claimed in an order that respects the dependencies (all items of
-// block i before block i + 1 forward, the reverse backward), from a device
-// counter, by whichever CTA is free.  Readiness is published per block with
-// counters: done[i] counts finished ACC slabs of block i, ready[i] finished
-// DIAG slabs.  A CTA only waits for items that were claimed before its own,
-// by CTAs that are running, so the sweep always progresses; every wait is
-// still bounded (%globaltimer) and ends the kernel with KRR_ETIMEOUT.
+// Work items (one 128-row slab s of a row block each):
+//   forward   DIAG(j, s)     z_j[s] = Linv_jj[s, :] y_j            (y_j fully updated)
+//             LINK(i, j, s)  y_i[s] -= L_ij[s, :] z_j, i > j       (row slab of L_ij)
+//   backward  DIAG(j, s)     x_j[s] = Linv_jj^T[s, :] z_j
+//             LINK(t, j, s)  z_t[s] -= L_jt[:, s]^T x_j, t < j     (column slab of L_jt)
+//   residual  RES(i, s)      r_i[s] = y_i - lambda a_i - sum_j K_ij a_j; K is symmetric,
+//                            so row slabs of the stored tiles (i, j <= i) and
+//                            column slabs of (j > i, i)
+// The right-hand side is updated in place.  Items are claimed from a device
+// counter in dependency order: the forward sweep lists, for j = 0, 1, ...,
+// the DIAG items of block j and then every LINK item that reads z_j (the
+// backward sweep the same for j = nt - 1, ...).  Counters publish progress:
+// ready[j] (DIAG slabs of block j done), done[i] (slabs of block i whose last
+// LINK is done), seq[i][s] (LINKs applied to slab (i, s)); the LINKs of one
+// slab apply their updates in a fixed order, so results are deterministic.
+// A CTA only waits on items claimed before its own by running CTAs, so the
+// sweep always progresses; every wait is still bounded (%globaltimer) and
+// ends the kernel with KRR_ETIMEOUT.
 //
-// CTA layout: warp 0 produces, warps 1..8 consume.
-//   producer  claims items, streams the tile data of each contribution as
-//             16 KB chunks into a shared-memory ring with TMA (128-byte
-//             swizzle), and copies the matching rows of the input vectors
-//             (cp.async) once their producer item has published them;
-//   consumers 256 threads, FP32 FMAs from shared memory.  A row chunk (128
-//             rows x 128 bytes) gives each thread 2 rows and a quarter of the
-//             columns; a column chunk (128 columns x 128 bytes per row) gives
-//             each thread 2 columns and a quarter of the rows.  Partial sums
-//             of the four quarters are added in a fixed order (deterministic).
-// The residual folds every tile's FP32 partial into FP64 before the next tile,
-// as the row sums of one tile are where cancellation happens.
+// CTA: warp 0 produces, warps 1..8 consume.
+//   producer  claims items; streams each tile slab as 16 KB chunks by TMA
+//             (128-byte swizzle) into a shared-memory ring, and copies the
+//             matching vector rows (cp.async) once they are published;
+//   consumers FP32 FMAs from shared memory, 4 accumulated rows (row chunk)
+//             or 4 columns (column chunk) per thread; 8 lanes share each row
+//             or column and are summed by warp shuffles, so every output has
+//             one owner thread and no shared-memory reduction is needed.
+// The residual folds each tile's FP32 partial sums into FP64 (owner threads,
+// shared memory) before the next tile: cancellation happens within a tile's
+// row sums.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -50,16 +52,16 @@ constexpr int SW_THREADS = 32 + SW_CONSUMERS;
 constexpr int SW_SLAB = 128;        // output rows of an item
 constexpr int SW_CHUNK = 16384;     // tile bytes per stage
 constexpr int SW_HDR = 64;          // stage header bytes
-constexpr int SW_PCMAX = 32;        // right-hand sides per launch
+constexpr int SW_PCMAX = 24;        // right-hand sides per launch
 
 enum SweepJob { SW_FWD = 0, SW_BWD = 1, SW_RES = 2 };
-enum ChunkKind { CK_ROW = 0, CK_COL = 1, CK_NONE = 2, CK_END = 3 };
-enum ChunkFlags { F_FIRST = 1, F_LAST_CONTRIB = 2, F_LAST_ITEM = 4 };
-enum EndOp { E_ACC = 0, E_DIAG = 1, E_RES = 2 };
+enum ChunkKind { CK_ROW = 0, CK_COL = 1, CK_END = 3 };
+enum ChunkFlags { F_FIRST = 1, F_LAST_CONTRIB = 2, F_LAST_ITEM = 4, F_SWITCH = 8, F_LAST_LINK = 16 };
+enum EndOp { E_LINK = 0, E_DIAG = 1, E_RES = 2 };
 
 struct StageHdr {
     int32_t kind, prec, flags, endop;
-    int32_t blk, slab;
+    int32_t blk, slab, seq;   // output block and slab; LINK: updates applied before this one
     float inv_scale, shift;
 };
 
@@ -70,8 +72,7 @@ struct SweepParams {
     int64_t ldx;
     int stages;
     int64_t stage_bytes;
-    const float *rhs;         // FWD: y; BWD: z; RES: y
-    float *acc;               // FWD / BWD: partial results (n_pad x ldx)
+    float *rhs;               // FWD: y, BWD: z (updated in place); RES: y
     float *out;               // FWD: z; BWD: x
     const float *xv;          // RES: a
     double *r;                // RES: residual (n_pad x ldx)
@@ -79,7 +80,7 @@ struct SweepParams {
     const double *colsum;     // RES: 1^T a per column
     float lambda;
     const TileDesc *ltab;
-    int *flags;               // [0] item counter, [1] abort, [2 + i] done[i], [2 + nt + i] ready[i]
+    int *flags;               // [0] item counter, [1] abort, then done[nt], ready[nt], seq[nt * S]
     uint64_t wait_ns;
     DevErrors *err;
 };
@@ -87,6 +88,10 @@ struct SweepParams {
 __host__ __device__ constexpr int esize_of(int prec) {
     return prec == KRR_PREC_FP32 ? 4 : (prec == KRR_PREC_FP16 ? 2 : 1);
 }
+
+__device__ __forceinline__ int *done_ctr(const SweepParams &p) { return p.flags + 2; }
+__device__ __forceinline__ int *ready_ctr(const SweepParams &p) { return p.flags + 2 + p.nt; }
+__device__ __forceinline__ int *seq_ctr(const SweepParams &p) { return p.flags + 2 + 2 * p.nt; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -135,15 +140,19 @@ __device__ __forceinline__ void record_timeout(const SweepParams &p) {
 }
 
 // Bounded wait on a CTA barrier; false on expiry or when the sweep aborted.
+// The abort flag (global memory) and the clock are read every 32 polls only,
+// so a completed phase is seen within one try_wait.
 __device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, const SweepParams &p) {
     if (mbar_try_wait(b, parity)) return true;
     const uint64_t t0 = globaltimer();
-    while (true) {
+    for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(b, parity)) return true;
-        if (*(volatile int *)&p.flags[1]) return false;
-        if (globaltimer() - t0 > p.wait_ns) {
-            record_timeout(p);
-            return false;
+        if ((it & 31) == 0) {
+            if (*(volatile int *)&p.flags[1]) return false;
+            if (globaltimer() - t0 > p.wait_ns) {
+                record_timeout(p);
+                return false;
+            }
         }
     }
 }
@@ -152,13 +161,14 @@ __device__ __forceinline__ bool wait_bar(uint64_t *b, uint32_t parity, const Swe
 __device__ __forceinline__ bool wait_count(const int *ctr, int target, const SweepParams &p) {
     if (ld_acquire(ctr) >= target) return true;
     const uint64_t t0 = globaltimer();
-    while (true) {
-        __nanosleep(64);
+    for (uint32_t it = 1;; ++it) {
         if (ld_acquire(ctr) >= target) return true;
-        if (*(volatile int *)&p.flags[1]) return false;
-        if (globaltimer() - t0 > p.wait_ns) {
-            record_timeout(p);
-            return false;
+        if ((it & 15) == 0) {
+            if (*(volatile int *)&p.flags[1]) return false;
+            if (globaltimer() - t0 > p.wait_ns) {
+                record_timeout(p);
+                return false;
+            }
         }
     }
 }
@@ -181,60 +191,85 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *b) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
 }
 
-// One contribution of an item: a tile streamed as chunks plus the vector
-// block it multiplies.
-struct Contrib {
-    int kind;          // CK_ROW / CK_COL
-    int prec;
-    int map;           // tensor map index 0..3
-    int64_t trow;      // first row of the tile in its tensor map
-    float inv_scale, shift;
-    int64_t xblk;      // vector block
-    const float *xsrc; // vector base (n_pad x ldx)
-    const int *dep;    // counter to wait for before reading the vector (or null)
-};
-
-struct ItemInfo {
+// ---------------------------------------------------------------------------
+// Item decoding.
+// ---------------------------------------------------------------------------
+struct Item {
     int endop;
-    int64_t blk, slab;
-    int ncontrib;      // contributions
+    int64_t blk, slab;   // output block and slab
+    int64_t src;         // FWD/BWD: block of the vector read (LINK: j; DIAG: blk)
+    int64_t seqv;        // LINK: number of updates applied to (blk, slab) before this one
+    bool last_link;
+    int ncontrib;
 };
 
-// Decodes item t: the end operation and output location.
-__device__ __forceinline__ void item_info(const SweepParams &p, int64_t t, ItemInfo &it) {
+// Sweeps: column c (0..nt-1) of the item list holds S DIAG items and then
+// S * (nt - 1 - c) LINK items; it starts at S * (c * nt - c (c - 1) / 2).
+__device__ __forceinline__ int64_t col_start(int64_t S, int64_t nt, int64_t c) {
+    return S * (c * nt - c * (c - 1) / 2);
+}
+
+__device__ __forceinline__ void decode_item(const SweepParams &p, int64_t t, Item &it) {
+    const int64_t S = p.S, nt = p.nt;
     if (p.job == SW_RES) {
         it.endop = E_RES;
-        it.blk = t / p.S;
-        it.slab = t % p.S;
-        it.ncontrib = (int)p.nt;
+        it.blk = t / S;
+        it.slab = t % S;
+        it.src = 0;
+        it.seqv = 0;
+        it.last_link = false;
+        it.ncontrib = (int)nt;
         return;
     }
-    const int64_t q = t / (2 * p.S), r = t % (2 * p.S);
-    it.blk = (p.job == SW_FWD) ? q : p.nt - 1 - q;
-    if (r < p.S) {
-        it.endop = E_ACC;
-        it.slab = r;
-        it.ncontrib = (int)((p.job == SW_FWD) ? it.blk : p.nt - 1 - it.blk);
-    } else {
+    int64_t lo = 0, hi = nt - 1;  // largest c with col_start(c) <= t
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (col_start(S, nt, mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t c = lo, r = t - col_start(S, nt, c);
+    const bool fwd = (p.job == SW_FWD);
+    const int64_t j = fwd ? c : nt - 1 - c;  // block whose vector this column publishes / reads
+    it.src = j;
+    it.ncontrib = 1;
+    if (r < S) {
         it.endop = E_DIAG;
-        it.slab = r - p.S;
-        it.ncontrib = 1;
+        it.blk = j;
+        it.slab = r;
+        it.seqv = 0;
+        it.last_link = false;
+    } else {
+        const int64_t m = (r - S) / S;   // m-th block updated from block j
+        it.endop = E_LINK;
+        it.slab = (r - S) % S;
+        it.blk = fwd ? j + 1 + m : j - 1 - m;
+        it.seqv = fwd ? j : nt - 1 - j;
+        it.last_link = fwd ? (j == it.blk - 1) : (j == it.blk + 1);
     }
 }
 
-// Contribution e (0-based, in processing order) of an item.
-__device__ __forceinline__ void contrib_info(const SweepParams &p, const ItemInfo &it, int e, Contrib &c) {
+// One contribution: a tile slab streamed as chunks and the vector block it
+// multiplies.
+struct Contrib {
+    int kind, prec, map;
+    int64_t trow;        // first row of the tile in its tensor map
+    float inv_scale, shift;
+    const float *xsrc;   // vector rows of the contribution (block start)
+    const int *dep;      // counter that must reach dep_target before reading them
+    int dep_target;
+};
+
+__device__ __forceinline__ void contrib_info(const SweepParams &p, const Item &it, int e, Contrib &c) {
     const int64_t b = p.b, nt = p.nt;
-    c.shift = 0.f;
     c.inv_scale = 1.f;
-    const int *done = p.flags + 2, *ready = p.flags + 2 + nt;
+    c.shift = 0.f;
+    c.dep = nullptr;
+    c.dep_target = 0;
     if (p.job == SW_RES) {
         const int64_t i = it.blk, j = e;
         c.prec = KRR_PREC_FP32;
         c.shift = (float)*p.shift;
-        c.xblk = j;
-        c.xsrc = p.xv;
-        c.dep = nullptr;
+        c.xsrc = p.xv + j * b * p.ldx + p.q0;
         if (j <= i) {
             c.kind = CK_ROW;
             c.map = 0;
@@ -246,173 +281,192 @@ __device__ __forceinline__ void contrib_info(const SweepParams &p, const ItemInf
         }
         return;
     }
+    const bool fwd = (p.job == SW_FWD);
     if (it.endop == E_DIAG) {
         c.kind = CK_ROW;
         c.prec = KRR_PREC_FP32;
         c.map = 3;
         c.trow = it.blk * b;
-        c.xblk = it.blk;
-        c.xsrc = p.acc;
-        c.dep = done + it.blk;
+        c.xsrc = p.rhs + it.blk * b * p.ldx + p.q0;
+        const bool first = fwd ? (it.blk == 0) : (it.blk == nt - 1);
+        c.dep = done_ctr(p) + it.blk;
+        c.dep_target = first ? 0 : (int)p.S;
         return;
     }
-    int64_t i, j, vb;
-    if (p.job == SW_FWD) {
-        i = it.blk;
-        j = e;
-        vb = j;
-        c.kind = CK_ROW;
-    } else {
-        j = it.blk;
-        i = nt - 1 - e;
-        vb = i;
-        c.kind = CK_COL;
-    }
-    const TileDesc d = p.ltab[off_index(i, j)];
+    // LINK: forward reads row slab `slab` of L_{blk, src}; backward column
+    // slab `slab` of L_{src, blk}
+    const int64_t ti = fwd ? it.blk : it.src, tj = fwd ? it.src : it.blk;
+    const TileDesc d = p.ltab[off_index(ti, tj)];
+    c.kind = fwd ? CK_ROW : CK_COL;
     c.prec = d.prec;
     c.map = (d.prec == KRR_PREC_FP16) ? 0 : (d.prec == KRR_PREC_FP32 ? 1 : 2);
     c.trow = d.offset / (b * esize_of(d.prec));
     if (d.prec != KRR_PREC_FP32) c.inv_scale = 1.f / d.scale;
-    c.xblk = vb;
-    c.xsrc = p.out;
-    c.dep = ready + vb;
+    c.xsrc = p.out + it.src * b * p.ldx + p.q0;
+    c.dep = ready_ctr(p) + it.src;
+    c.dep_target = (int)p.S;
+}
+
+// Vector rows in a stage: row r at r * pcp + (r >> vs) * 4 floats, vs =
+// log2(values per 16-byte unit of the tile precision).  The skew of 16 bytes
+// per group of (1 << vs) rows puts the rows that the 8 lanes of a row-chunk
+// read at once (one per 16-byte unit) in different banks.
+__host__ __device__ __forceinline__ int xrow_off(int r, int vs, int pcp) { return r * pcp + ((r >> vs) << 2); }
+__host__ __device__ constexpr int vshift_of(int prec) {
+    return prec == KRR_PREC_FP32 ? 2 : (prec == KRR_PREC_FP16 ? 3 : 4);
 }
 
 // ---------------------------------------------------------------------------
-// Consumer math.  The tile chunk is 128-byte swizzled: byte `x` of row `r`
-// (128-byte rows) sits at r * 128 + ((x / 16) ^ (r % 8)) * 16 + x % 16.
+// Consumer math.  A chunk is 128-byte swizzled: byte x of 128-byte row r sits
+// at r * 128 + ((x / 16) ^ (r % 8)) * 16 + x % 16.  Thread = (warp w, lane l).
+//   row chunk (128 rows x 128 B): rows 4w + (l / 8) + 32u (u < 4), 16-byte
+//       unit l % 8 of each; x row = column of the value.
+//   column chunk (128 columns x 128 / esize rows, esize boxes of 128 / esize
+//       columns): columns 16w + 4 (l % 4) + u (u < 4), rows l / 4 + 8k.
+// acc[u][q] belongs to output row u of the thread's mapping.
 // ---------------------------------------------------------------------------
 template <int PREC>
-__device__ __forceinline__ void unpack16(const uint4 &u, float *v) {
-    if (PREC == KRR_PREC_FP32) {
-        v[0] = __uint_as_float(u.x); v[1] = __uint_as_float(u.y);
-        v[2] = __uint_as_float(u.z); v[3] = __uint_as_float(u.w);
-    } else if (PREC == KRR_PREC_FP16) {
-        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
-            v[2 * k] = f.x;
-            v[2 * k + 1] = f.y;
-        }
-    } else {
-        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] & 0xffffu), __NV_E4M3);
-            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> 16), __NV_E4M3);
-            const float2 a = __half22float2(__half2(lo)), c = __half22float2(__half2(hi));
-            v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = c.x; v[4 * k + 3] = c.y;
-        }
-    }
-}
+__device__ __forceinline__ void to_f32x4(uint32_t w0, uint32_t w1, float *v);
 
-// Row chunk: 128 rows x (128 / esize) columns.  Thread ct: rows ra = ct % 64
-// and ra + 64, columns of quarter ct / 64 (32 bytes of every row).
-template <int PREC, int NQ>
-__device__ __forceinline__ void row_chunk(const uint8_t *tile, const float *xs, int pcp, float inv_scale,
-                                          float shift, int ct, float (&acc)[2][4 * NQ]) {
-    constexpr int ES = esize_of(PREC), VPU = 16 / ES;  // values per 16-byte unit
-    const int qq = ct >> 6, ra = ct & 63, rb = ra + 64;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int unit = 2 * qq + h;
-        const uint4 ua = *reinterpret_cast<const uint4 *>(tile + ra * 128 + ((unit ^ (ra & 7)) << 4));
-        const uint4 ub = *reinterpret_cast<const uint4 *>(tile + rb * 128 + ((unit ^ (rb & 7)) << 4));
-        float va[VPU], vb[VPU];
-        unpack16<PREC>(ua, va);
-        unpack16<PREC>(ub, vb);
-#pragma unroll
-        for (int e = 0; e < VPU; ++e) {
-            const float a = fmaf(va[e], inv_scale, -shift), c = fmaf(vb[e], inv_scale, -shift);
-            const float *xr = xs + (unit * VPU + e) * pcp;
-#pragma unroll
-            for (int q4 = 0; q4 < NQ; ++q4) {
-                const float4 z = *reinterpret_cast<const float4 *>(xr + 4 * q4);
-                acc[0][4 * q4 + 0] = fmaf(a, z.x, acc[0][4 * q4 + 0]);
-                acc[0][4 * q4 + 1] = fmaf(a, z.y, acc[0][4 * q4 + 1]);
-                acc[0][4 * q4 + 2] = fmaf(a, z.z, acc[0][4 * q4 + 2]);
-                acc[0][4 * q4 + 3] = fmaf(a, z.w, acc[0][4 * q4 + 3]);
-                acc[1][4 * q4 + 0] = fmaf(c, z.x, acc[1][4 * q4 + 0]);
-                acc[1][4 * q4 + 1] = fmaf(c, z.y, acc[1][4 * q4 + 1]);
-                acc[1][4 * q4 + 2] = fmaf(c, z.z, acc[1][4 * q4 + 2]);
-                acc[1][4 * q4 + 3] = fmaf(c, z.w, acc[1][4 * q4 + 3]);
-            }
-        }
-    }
-}
-
-// Column chunk: 128 columns x (128 / esize) rows, stored as esize boxes of
-// (128 / esize) columns.  Thread ct: columns 2 (ct % 64) and 2 (ct % 64) + 1,
-// rows of quarter ct / 64.
-template <int PREC, int NQ>
-__device__ __forceinline__ void col_chunk(const uint8_t *tile, const float *xs, int pcp, float inv_scale,
-                                          float shift, int ct, float (&acc)[2][4 * NQ]) {
-    constexpr int ES = esize_of(PREC), RR = 128 / ES, RQ = RR / 4;
-    const int qq = ct >> 6, c0 = 2 * (ct & 63);
-    const int box = c0 / RR, within = (c0 % RR) * ES, unit = within >> 4, boff = within & 15;
-    const uint8_t *bbase = tile + box * (RR * 128) + boff;
-#pragma unroll 4
-    for (int rr = 0; rr < RQ; ++rr) {
-        const int r = qq * RQ + rr;
-        const uint8_t *pe = bbase + r * 128 + ((unit ^ (r & 7)) << 4);
-        float v0, v1;
-        if (PREC == KRR_PREC_FP32) {
-            const float2 f = *reinterpret_cast<const float2 *>(pe);
-            v0 = f.x;
-            v1 = f.y;
-        } else if (PREC == KRR_PREC_FP16) {
-            const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(pe));
-            v0 = f.x;
-            v1 = f.y;
-        } else {
-            const uint16_t w = *reinterpret_cast<const uint16_t *>(pe);
-            const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)w, __NV_E4M3);
-            const float2 f = __half22float2(__half2(h));
-            v0 = f.x;
-            v1 = f.y;
-        }
-        v0 = fmaf(v0, inv_scale, -shift);
-        v1 = fmaf(v1, inv_scale, -shift);
-        const float *xr = xs + r * pcp;
-#pragma unroll
-        for (int q4 = 0; q4 < NQ; ++q4) {
-            const float4 z = *reinterpret_cast<const float4 *>(xr + 4 * q4);
-            acc[0][4 * q4 + 0] = fmaf(v0, z.x, acc[0][4 * q4 + 0]);
-            acc[0][4 * q4 + 1] = fmaf(v0, z.y, acc[0][4 * q4 + 1]);
-            acc[0][4 * q4 + 2] = fmaf(v0, z.z, acc[0][4 * q4 + 2]);
-            acc[0][4 * q4 + 3] = fmaf(v0, z.w, acc[0][4 * q4 + 3]);
-            acc[1][4 * q4 + 0] = fmaf(v1, z.x, acc[1][4 * q4 + 0]);
-            acc[1][4 * q4 + 1] = fmaf(v1, z.y, acc[1][4 * q4 + 1]);
-            acc[1][4 * q4 + 2] = fmaf(v1, z.z, acc[1][4 * q4 + 2]);
-            acc[1][4 * q4 + 3] = fmaf(v1, z.w, acc[1][4 * q4 + 3]);
-        }
-    }
-}
-
-// Writes the thread's partials into red[quarter][row][q] (rows of the item).
 template <int NQ>
-__device__ __forceinline__ void spill_partials(int kind, int ct, int pc, int pcp, const float (&acc)[2][4 * NQ],
-                                               float *red) {
-    const int qq = ct >> 6;
-    int r0, r1;
-    if (kind == CK_ROW) {
-        r0 = ct & 63;
-        r1 = r0 + 64;
-    } else {
-        r0 = 2 * (ct & 63);
-        r1 = r0 + 1;
-    }
-    float *d0 = red + (qq * SW_SLAB + r0) * pcp, *d1 = red + (qq * SW_SLAB + r1) * pcp;
+__device__ __forceinline__ void fma4(float (&acc)[4][4 * NQ], const float (&v)[4], const float *xr) {
 #pragma unroll
-    for (int q = 0; q < 4 * NQ; ++q) {
-        if (q < pc) {
-            d0[q] = acc[0][q];
-            d1[q] = acc[1][q];
+    for (int q4 = 0; q4 < NQ; ++q4) {
+        const float4 z = *reinterpret_cast<const float4 *>(xr + 4 * q4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            acc[u][4 * q4 + 0] = fmaf(v[u], z.x, acc[u][4 * q4 + 0]);
+            acc[u][4 * q4 + 1] = fmaf(v[u], z.y, acc[u][4 * q4 + 1]);
+            acc[u][4 * q4 + 2] = fmaf(v[u], z.z, acc[u][4 * q4 + 2]);
+            acc[u][4 * q4 + 3] = fmaf(v[u], z.w, acc[u][4 * q4 + 3]);
         }
     }
 }
 
+// Values e of the 16-byte unit u of 4 rows: FP32 4, FP16 8, E4M3 16 per unit.
+template <int PREC, int NQ>
+__device__ __forceinline__ void row_chunk(const uint8_t *tile, const float *xs, int pcp, float sc, float sh,
+                                          int w, int l, float (&acc)[4][4 * NQ]) {
+    const int part = l & 7, r0 = 4 * w + (l >> 3);
+    uint4 raw[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = r0 + 32 * u;
+        raw[u] = *reinterpret_cast<const uint4 *>(tile + r * 128 + ((part ^ (r & 7)) << 4));
+    }
+    if (PREC == KRR_PREC_FP32) {
+        const float *x0 = xs + part * (4 * pcp + 4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t bits = e == 0 ? raw[u].x : e == 1 ? raw[u].y : e == 2 ? raw[u].z : raw[u].w;
+                v[u] = fmaf(__uint_as_float(bits), sc, -sh);
+            }
+            fma4<NQ>(acc, v, x0 + e * pcp);
+        }
+    } else if (PREC == KRR_PREC_FP16) {
+        const float *x0 = xs + part * (8 * pcp + 4);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float v0[4], v1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t bits = h == 0 ? raw[u].x : h == 1 ? raw[u].y : h == 2 ? raw[u].z : raw[u].w;
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&bits));
+                v0[u] = fmaf(f.x, sc, -sh);
+                v1[u] = fmaf(f.y, sc, -sh);
+            }
+            fma4<NQ>(acc, v0, x0 + (2 * h) * pcp);
+            fma4<NQ>(acc, v1, x0 + (2 * h + 1) * pcp);
+        }
+    } else {
+        const float *x0 = xs + part * (16 * pcp + 4);
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            float v[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t bits = h == 0 ? raw[u].x : h == 1 ? raw[u].y : h == 2 ? raw[u].z : raw[u].w;
+                const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(bits & 0xffffu), __NV_E4M3);
+                const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(bits >> 16), __NV_E4M3);
+                const float2 a = __half22float2(__half2(lo)), c = __half22float2(__half2(hi));
+                v[0][u] = fmaf(a.x, sc, -sh);
+                v[1][u] = fmaf(a.y, sc, -sh);
+                v[2][u] = fmaf(c.x, sc, -sh);
+                v[3][u] = fmaf(c.y, sc, -sh);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) fma4<NQ>(acc, v[e], x0 + (4 * h + e) * pcp);
+        }
+    }
+}
+
+template <int PREC, int NQ>
+__device__ __forceinline__ void col_chunk(const uint8_t *tile, const float *xs, int pcp, float sc, float sh,
+                                          int w, int l, float (&acc)[4][4 * NQ]) {
+    constexpr int ES = esize_of(PREC), RR = 128 / ES;   // rows of the chunk = columns per box
+    constexpr int VS = (PREC == KRR_PREC_FP32) ? 2 : (PREC == KRR_PREC_FP16 ? 3 : 4);
+    const int c0 = 16 * w + 4 * (l & 3), rp = l >> 2;
+    const int box = c0 / RR, within = (c0 % RR) * ES, unit = within >> 4, boff = within & 15;
+    const uint8_t *bb = tile + box * (RR * 128) + boff;
+#pragma unroll 4
+    for (int k = 0; k < RR / 8; ++k) {
+        const int r = rp + 8 * k;
+        const uint8_t *pe = bb + r * 128 + ((unit ^ (r & 7)) << 4);
+        float v[4];
+        if (PREC == KRR_PREC_FP32) {
+            const float4 f = *reinterpret_cast<const float4 *>(pe);
+            v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+        } else if (PREC == KRR_PREC_FP16) {
+            const uint2 u2 = *reinterpret_cast<const uint2 *>(pe);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u2.x));
+            const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&u2.y));
+            v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
+        } else {
+            const uint32_t bits = *reinterpret_cast<const uint32_t *>(pe);
+            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(bits & 0xffffu), __NV_E4M3);
+            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(bits >> 16), __NV_E4M3);
+            const float2 a = __half22float2(__half2(lo)), c = __half22float2(__half2(hi));
+            v[0] = a.x; v[1] = a.y; v[2] = c.x; v[3] = c.y;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = fmaf(v[u], sc, -sh);
+        fma4<NQ>(acc, v, xs + xrow_off(r, VS, pcp));
+    }
+}
+
+// Sums the 8 lanes that share each output (row chunk: lanes l % 8; column
+// chunk: lanes l / 4) into the owner lane (l % 8 == 0, resp. l < 4).
+template <int NQ>
+__device__ __forceinline__ void reduce_lanes(int kind, float (&acc)[4][4 * NQ]) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4 * NQ; ++q) {
+            float v = acc[u][q];
+            if (kind == CK_ROW) {
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+            } else {
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 8);
+                v += __shfl_xor_sync(0xffffffffu, v, 16);
+            }
+            acc[u][q] = v;
+        }
+}
+
+__device__ __forceinline__ bool is_owner(int kind, int l) { return kind == CK_ROW ? (l & 7) == 0 : l < 4; }
+// Output row (0..127 within the slab) of acc[u] for the owner thread.
+__device__ __forceinline__ int owner_row(int kind, int w, int l, int u) {
+    return kind == CK_ROW ? 4 * w + (l >> 3) + 32 * u : 16 * w + 4 * (l & 3) + u;
+}
+
+// One CTA per SM.  9 warps put 3 warps on one SM sub-partition, whose 16K
+// registers then cap a thread at 168.
 template <int NQ>
 __global__ void __launch_bounds__(SW_THREADS, 1)
     sweep_kernel(const __grid_constant__ CUtensorMap m0, const __grid_constant__ CUtensorMap m1,
@@ -422,11 +476,10 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sw_smem_raw) + 1023) & ~uintptr_t(1023));
     const int NS = p.stages;
     const int64_t SB = p.stage_bytes;
-    // layout: stages x [chunk 16 KB | header 64 B | vector rows], red, acc64, barriers
-    float *red = reinterpret_cast<float *>(smem + NS * SB);
-    double *acc64 = reinterpret_cast<double *>(red + 4 * SW_SLAB * p.pcp);
+    // layout: stages x [chunk 16 KB | header | vector rows], FP64 row sums, barriers
+    double *acc64 = reinterpret_cast<double *>(smem + NS * SB);
     uint64_t *bars = reinterpret_cast<uint64_t *>(acc64 + SW_SLAB * p.pcp);
-    uint64_t *full = bars, *empty = bars + NS;
+    uint64_t *full = bars, *empty = bars + NS, *cbar = bars + 2 * NS;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -434,7 +487,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
             mbar_init(&full[s], 1 + 32);
             mbar_init(&empty[s], SW_CONSUMERS / 32);
         }
-        mbar_init(&bars[2 * NS], SW_CONSUMERS);  // consumer-group barrier
+        mbar_init(cbar, SW_CONSUMERS);  // consumer-group barrier
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0 && lane == 0) {
@@ -452,9 +505,15 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
         uint32_t ph = 0;
         int issued = 0;
         bool ok = true;
-        // emits one stage: optional TMA chunk + vector rows; returns false on abort
-        auto next_stage = [&](StageHdr h, const CUtensorMap *map, int nbox, int bx_step, int x0, int y0,
-                              int box_bytes, const float *xrows, int xr, const int *dep) -> bool {
+        // vector-row copies: a row is `per_row` pieces of 16 (x16) or 4 bytes;
+        // lanes take fixed (row offset, piece) pairs
+        const int per_row = p.x16 ? p.pc / 4 : p.pc;
+        const int rows_per_pass = 32 / per_row;
+        const int lane_row = lane / per_row, lane_q = (lane % per_row) * (p.x16 ? 4 : 1);
+        // emits one stage (TMA chunk + vector rows); false on abort
+        auto next_stage = [&](const StageHdr &h, const CUtensorMap *map, int nbox, int bx_step, int x0, int y0,
+                              int box_bytes, const float *xrows, int xr, const int *dep, int dep_target) -> bool {
+            const int vs = vshift_of(h.prec);
             // every lane waits (acquire); the vote keeps the warp's decision uniform
             if (!__all_sync(0xffffffffu, wait_bar(&empty[s], ph ^ 1, p))) return false;
             uint8_t *st = smem + s * SB;
@@ -469,28 +528,23 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
                 }
             }
             bool dep_ok = true;
-            if (xrows && dep) {
+            if (dep) {
                 int okl = 1;
-                if (lane == 0) okl = wait_count(dep, (int)p.S, p) ? 1 : 0;
-                okl = __shfl_sync(0xffffffffu, okl, 0);
-                dep_ok = okl != 0;
+                if (lane == 0) okl = wait_count(dep, dep_target, p) ? 1 : 0;
+                dep_ok = __shfl_sync(0xffffffffu, okl, 0) != 0;
                 if (dep_ok) (void)ld_acquire(dep);  // every lane acquires before its copies
             }
-            if (xrows && dep_ok) {
-                float *xs = reinterpret_cast<float *>(st + SW_CHUNK + SW_HDR);
-                const int pc = p.pc, pcp = p.pcp;
+            if (xrows && dep_ok && lane_row < rows_per_pass) {
+                // lane (lane_row, lane_q) copies piece lane_q of rows lane_row, + rows_per_pass, ...
+                float *xs = reinterpret_cast<float *>(st + SW_CHUNK + SW_HDR) + lane_q;
+                const float *src = xrows + (int64_t)lane_row * p.ldx + lane_q;
+                const int64_t sstep = (int64_t)rows_per_pass * p.ldx;
                 if (p.x16) {
-                    const int per_row = pc / 4, total = xr * per_row;
-                    for (int e = lane; e < total; e += 32) {
-                        const int r = e / per_row, q = (e % per_row) * 4;
-                        cp_async16(xs + r * pcp + q, xrows + (int64_t)r * p.ldx + q);
-                    }
+                    for (int r = lane_row; r < xr; r += rows_per_pass, src += sstep)
+                        cp_async16(xs + xrow_off(r, vs, p.pcp), src);
                 } else {
-                    const int total = xr * pc;
-                    for (int e = lane; e < total; e += 32) {
-                        const int r = e / pc, q = e % pc;
-                        cp_async4(xs + r * pcp + q, xrows + (int64_t)r * p.ldx + q);
-                    }
+                    for (int r = lane_row; r < xr; r += rows_per_pass, src += sstep)
+                        cp_async4(xs + xrow_off(r, vs, p.pcp), src);
                 }
             }
             cp_async_arrive(&full[s]);
@@ -503,21 +557,14 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
             if (lane == 0) t = atomicAdd(&p.flags[0], 1);
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= p.items) break;
-            ItemInfo it;
-            item_info(p, t, it);
+            Item it;
+            decode_item(p, t, it);
             StageHdr h;
             h.endop = it.endop;
             h.blk = (int)it.blk;
             h.slab = (int)it.slab;
-            if (it.ncontrib == 0) {
-                h.kind = CK_NONE;
-                h.prec = KRR_PREC_FP32;
-                h.flags = F_FIRST | F_LAST_CONTRIB | F_LAST_ITEM;
-                h.inv_scale = 1.f;
-                h.shift = 0.f;
-                ok = next_stage(h, nullptr, 0, 0, 0, 0, 0, nullptr, 0, nullptr);
-                continue;
-            }
+            h.seq = (int)it.seqv;
+            int prev_kind = -1;
             for (int e = 0; e < it.ncontrib && ok; ++e) {
                 Contrib c;
                 contrib_info(p, it, e, c);
@@ -528,20 +575,23 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
                 h.prec = c.prec;
                 h.inv_scale = c.inv_scale;
                 h.shift = c.shift;
+                const int sw = (prev_kind >= 0 && prev_kind != c.kind) ? F_SWITCH : 0;
+                prev_kind = c.kind;
                 for (int k = 0; k < nchunk && ok; ++k) {
-                    h.flags = ((e == 0 && k == 0) ? F_FIRST : 0) | (k == nchunk - 1 ? F_LAST_CONTRIB : 0) |
-                              ((e == it.ncontrib - 1 && k == nchunk - 1) ? F_LAST_ITEM : 0);
+                    h.flags = ((e == 0 && k == 0) ? F_FIRST : 0) | (k == nchunk - 1 ? sw | F_LAST_CONTRIB : 0) |
+                              ((e == it.ncontrib - 1 && k == nchunk - 1) ? F_LAST_ITEM : 0) |
+                              (it.last_link ? F_LAST_LINK : 0);
                     const int64_t xr0 = (int64_t)k * span;   // vector rows of this chunk within the block
-                    const float *xrows = c.xsrc + (c.xblk * p.b + xr0) * p.ldx + p.q0;
+                    const float *xrows = c.xsrc + xr0 * p.ldx;
                     const int *dep = (k == 0) ? c.dep : nullptr;
                     if (c.kind == CK_ROW) {
                         // rows [slab * 128, +128) of the tile, columns [xr0, xr0 + span)
                         ok = next_stage(h, maps[c.map], 1, 0, (int)xr0, (int)(c.trow + it.slab * SW_SLAB),
-                                        SW_CHUNK, xrows, span, dep);
+                                        SW_CHUNK, xrows, span, dep, c.dep_target);
                     } else {
                         // columns [slab * 128, +128) as ES boxes of span columns, rows [xr0, xr0 + span)
                         ok = next_stage(h, maps[c.map], ES, span, (int)(it.slab * SW_SLAB), (int)(c.trow + xr0),
-                                        SW_CHUNK / ES, xrows, span, dep);
+                                        SW_CHUNK / ES, xrows, span, dep, c.dep_target);
                     }
                 }
             }
@@ -550,7 +600,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
             StageHdr h;
             memset(&h, 0, sizeof(h));
             h.kind = CK_END;
-            ok = next_stage(h, nullptr, 0, 0, 0, 0, 0, nullptr, 0, nullptr);
+            ok = next_stage(h, nullptr, 0, 0, 0, 0, 0, nullptr, 0, nullptr, 0);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         if (!ok && lane == 0) {
@@ -566,11 +616,10 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
         }
     } else {
         // ------------------------------ consumers ------------------------------
-        // Consumer-group synchronisation uses an mbarrier with bounded waits
-        // (not bar.sync), so a consumer that gives up cannot strand the others.
-        const int ct = threadIdx.x - 32;
+        // Group synchronisation uses an mbarrier with bounded waits (not
+        // bar.sync), so a consumer that gives up cannot strand the others.
+        const int w = warp - 1, ct = threadIdx.x - 32;
         const int pc = p.pc, pcp = p.pcp;
-        uint64_t *cbar = bars + 2 * NS;
         uint32_t cph = 0;
         auto csync = [&]() -> bool {
             mbar_arrive(cbar);
@@ -578,8 +627,11 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
             cph ^= 1;
             return r;
         };
-        float acc[2][4 * NQ];
-        bool zero_next = true;
+        float acc[4][4 * NQ];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 4 * NQ; ++q) acc[u][q] = 0.f;
         int s = 0;
         uint32_t ph = 0;
         while (true) {
@@ -587,74 +639,97 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
             const uint8_t *st = smem + s * SB;
             const StageHdr h = *reinterpret_cast<const StageHdr *>(st + SW_CHUNK);
             if (h.kind == CK_END) break;
-            if ((h.flags & F_FIRST) && h.endop == E_RES)
+            if ((h.flags & F_FIRST) && h.endop == E_RES) {
+                // the previous item's last readers of acc64 passed a csync
                 for (int e = ct; e < SW_SLAB * pcp; e += SW_CONSUMERS) acc64[e] = 0.0;
-            if (zero_next) {
-#pragma unroll
-                for (int u = 0; u < 2; ++u)
-#pragma unroll
-                    for (int q = 0; q < 4 * NQ; ++q) acc[u][q] = 0.f;
-                zero_next = false;
+                if (!csync()) break;
             }
-            if (h.kind != CK_NONE) {
-                const float *xs = reinterpret_cast<const float *>(st + SW_CHUNK + SW_HDR);
-                if (h.kind == CK_ROW) {
-                    if (h.prec == KRR_PREC_FP16) row_chunk<KRR_PREC_FP16, NQ>(st, xs, pcp, h.inv_scale, h.shift, ct, acc);
-                    else if (h.prec == KRR_PREC_FP32) row_chunk<KRR_PREC_FP32, NQ>(st, xs, pcp, h.inv_scale, h.shift, ct, acc);
-                    else row_chunk<KRR_PREC_E4M3, NQ>(st, xs, pcp, h.inv_scale, h.shift, ct, acc);
-                } else {
-                    if (h.prec == KRR_PREC_FP16) col_chunk<KRR_PREC_FP16, NQ>(st, xs, pcp, h.inv_scale, h.shift, ct, acc);
-                    else if (h.prec == KRR_PREC_FP32) col_chunk<KRR_PREC_FP32, NQ>(st, xs, pcp, h.inv_scale, h.shift, ct, acc);
-                    else col_chunk<KRR_PREC_E4M3, NQ>(st, xs, pcp, h.inv_scale, h.shift, ct, acc);
-                }
+            const float *xs = reinterpret_cast<const float *>(st + SW_CHUNK + SW_HDR);
+            if (h.kind == CK_ROW) {
+                if (h.prec == KRR_PREC_FP16) row_chunk<KRR_PREC_FP16, NQ>(st, xs, pcp, h.inv_scale, h.shift, w, lane, acc);
+                else if (h.prec == KRR_PREC_FP32) row_chunk<KRR_PREC_FP32, NQ>(st, xs, pcp, h.inv_scale, h.shift, w, lane, acc);
+                else row_chunk<KRR_PREC_E4M3, NQ>(st, xs, pcp, h.inv_scale, h.shift, w, lane, acc);
+            } else {
+                if (h.prec == KRR_PREC_FP16) col_chunk<KRR_PREC_FP16, NQ>(st, xs, pcp, h.inv_scale, h.shift, w, lane, acc);
+                else if (h.prec == KRR_PREC_FP32) col_chunk<KRR_PREC_FP32, NQ>(st, xs, pcp, h.inv_scale, h.shift, w, lane, acc);
+                else col_chunk<KRR_PREC_E4M3, NQ>(st, xs, pcp, h.inv_scale, h.shift, w, lane, acc);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);  // the stage is free again
             if (++s == NS) { s = 0; ph ^= 1; }
-            const bool item_end = (h.flags & F_LAST_ITEM) != 0;
-            if (h.endop == E_RES && (h.flags & F_LAST_CONTRIB)) {
-                // fold this tile's FP32 partials into the FP64 row sums
-                spill_partials<NQ>(h.kind, ct, pc, pcp, acc, red);
-                if (!csync()) break;
-                for (int e = ct; e < SW_SLAB * pc; e += SW_CONSUMERS) {
-                    const int row = e / pc, q = e % pc;
-                    const float *rr = red + row * pcp + q;
-                    const float sum = ((rr[0] + rr[SW_SLAB * pcp]) + rr[2 * SW_SLAB * pcp]) + rr[3 * SW_SLAB * pcp];
-                    acc64[row * pcp + q] += (double)sum;
-                }
-                if (!csync()) break;
-                zero_next = true;
-            }
-            if (!item_end) continue;
-            const bool have = (h.kind != CK_NONE);
-            if (h.endop != E_RES && have) {
-                spill_partials<NQ>(h.kind, ct, pc, pcp, acc, red);
-                if (!csync()) break;
-            }
+            if (!(h.flags & F_LAST_CONTRIB)) continue;
+            reduce_lanes<NQ>(h.kind, acc);
+            const bool own = is_owner(h.kind, lane);
             const int64_t row0 = (int64_t)h.blk * p.b + (int64_t)h.slab * SW_SLAB;
-            for (int e = ct; e < SW_SLAB * pc; e += SW_CONSUMERS) {
-                const int row = e / pc, q = e % pc;
-                const int64_t gi = (row0 + row) * p.ldx + p.q0 + q;
-                if (h.endop == E_RES) {
-                    p.r[gi] = ((double)p.rhs[gi] - (double)p.lambda * (double)p.xv[gi]) - acc64[row * pcp + q] -
-                              (*p.shift) * p.colsum[p.q0 + q];
-                    continue;
+            bool ok = true;
+            if (h.endop == E_RES) {
+                // the owners of a row change when the tiles switch from row to
+                // column slabs: order the earlier owners' FP64 updates first
+                if ((h.flags & F_SWITCH) && !csync()) break;
+                if (own) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        double *a64 = acc64 + owner_row(h.kind, w, lane, u) * pcp;
+#pragma unroll
+                        for (int q = 0; q < 4 * NQ; ++q)
+                            if (q < pc) a64[q] += (double)acc[u][q];
+                    }
+                    if (h.flags & F_LAST_ITEM) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int row = owner_row(h.kind, w, lane, u);
+                            const int64_t gi = (row0 + row) * p.ldx + p.q0;
+                            for (int q = 0; q < pc; ++q)
+                                p.r[gi + q] = ((double)p.rhs[gi + q] - (double)p.lambda * (double)p.xv[gi + q]) -
+                                              acc64[row * pcp + q] - (*p.shift) * p.colsum[p.q0 + q];
+                        }
+                    }
                 }
-                float sum = 0.f;
-                if (have) {
-                    const float *rr = red + row * pcp + q;
-                    sum = ((rr[0] + rr[SW_SLAB * pcp]) + rr[2 * SW_SLAB * pcp]) + rr[3 * SW_SLAB * pcp];
+                if ((h.flags & F_LAST_ITEM) && !csync()) break;  // acc64 is free for the next item
+            } else if (h.endop == E_DIAG) {
+                if (own) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t gi = (row0 + owner_row(h.kind, w, lane, u)) * p.ldx + p.q0;
+#pragma unroll
+                        for (int q = 0; q < 4 * NQ; ++q)
+                            if (q < pc) __stcg(p.out + gi + q, acc[u][q]);
+                    }
                 }
-                if (h.endop == E_ACC) __stcg(p.acc + gi, __ldcg(p.rhs + gi) - sum);
-                else __stcg(p.out + gi, sum);
+                ok = csync();
+                if (ok && ct == 0) {
+                    __threadfence();
+                    atomicAdd(ready_ctr(p) + h.blk, 1);
+                }
+            } else {  // E_LINK: y_blk[slab] -= sum, after the earlier updates of this slab
+                int *sq = seq_ctr(p) + (int64_t)h.blk * p.S + h.slab;
+                int okw = 1;
+                if (lane == 0) okw = wait_count(sq, h.seq, p) ? 1 : 0;
+                ok = __shfl_sync(0xffffffffu, okw, 0) != 0;
+                if (ok) {
+                    (void)ld_acquire(sq);
+                    if (own) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int64_t gi = (row0 + owner_row(h.kind, w, lane, u)) * p.ldx + p.q0;
+#pragma unroll
+                            for (int q = 0; q < 4 * NQ; ++q)
+                                if (q < pc) __stcg(p.rhs + gi + q, __ldcg(p.rhs + gi + q) - acc[u][q]);
+                        }
+                    }
+                }
+                ok = csync() && ok;
+                if (ok && ct == 0) {
+                    __threadfence();
+                    atomicAdd(sq, 1);
+                    if (h.flags & F_LAST_LINK) atomicAdd(done_ctr(p) + h.blk, 1);
+                }
             }
-            if (!csync()) break;  // outputs written; red / acc64 free again
-            if (ct == 0 && h.endop != E_RES) {
-                __threadfence();
-                int *ctr = (h.endop == E_ACC) ? p.flags + 2 + h.blk : p.flags + 2 + p.nt + h.blk;
-                atomicAdd(ctr, 1);
-            }
-            zero_next = true;
+            if (!ok) break;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int q = 0; q < 4 * NQ; ++q) acc[u][q] = 0.f;
         }
     }
 }
@@ -704,18 +779,17 @@ krr_status map_rows(Ctx *c, CUtensorMap *m, const void *base, int prec, int64_t 
 
 constexpr size_t smem_limit() { return 227 * 1024; }
 
-// Dynamic shared memory of a launch: stages, partials, FP64 row sums,
-// barriers, alignment slack.
+// Dynamic shared memory: stages, FP64 row sums, barriers, alignment slack.
 size_t smem_bytes(int stages, int64_t stage_bytes, int pcp) {
-    return (size_t)stages * stage_bytes + (size_t)4 * SW_SLAB * pcp * 4 + (size_t)SW_SLAB * pcp * 8 +
-           (size_t)(2 * stages + 1) * 8 + 1024;
+    return (size_t)stages * stage_bytes + (size_t)SW_SLAB * pcp * 8 + (size_t)(2 * stages + 1) * 8 + 1024;
 }
 
 template <int NQ>
 krr_status launch_nq(Ctx *c, const CUtensorMap (&m)[4], const SweepParams &p, size_t smem) {
     static bool attr = false;
     if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(sweep_kernel<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit());
+        const cudaError_t e =
+            cudaFuncSetAttribute(sweep_kernel<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit());
         if (e != cudaSuccess) {
             c->last_error = std::string("cudaFuncSetAttribute (sweep): ") + cudaGetErrorString(e);
             return KRR_ECUDA;
@@ -732,9 +806,10 @@ krr_status launch_nq(Ctx *c, const CUtensorMap (&m)[4], const SweepParams &p, si
     return KRR_OK;
 }
 
+int64_t flag_count(const Ctx *c) { return 2 + 2 * c->nt + c->nt * (c->b / SW_SLAB); }
 
-krr_status ensure_sweep_buffers(Ctx *c, int64_t p) {
-    const int64_t nflags = 2 + 2 * c->nt;
+krr_status ensure_sweep_buffers(Ctx *c) {
+    const int64_t nflags = flag_count(c);
     if (c->sw_flags_cap < nflags) {
         if (c->sw_flags) cudaFree(c->sw_flags);
         c->sw_flags = nullptr;
@@ -746,28 +821,16 @@ krr_status ensure_sweep_buffers(Ctx *c, int64_t p) {
         }
         c->sw_flags_cap = nflags;
     }
-    const int64_t cnt = c->n_pad * p;
-    if (c->sw_acc_cap < cnt) {
-        if (c->sw_acc) cudaFree(c->sw_acc);
-        c->sw_acc = nullptr;
-        c->sw_acc_cap = 0;
-        if (cudaMalloc((void **)&c->sw_acc, cnt * sizeof(float)) != cudaSuccess) {
-            cudaGetLastError();
-            c->last_error = "cudaMalloc failed for the sweep partial vectors";
-            return KRR_ENOMEM;
-        }
-        c->sw_acc_cap = cnt;
-    }
     return KRR_OK;
 }
 
-krr_status run_job(Ctx *c, int job, const float *rhs, float *out, const float *xv, double *r, int64_t p) {
+krr_status run_job(Ctx *c, int job, float *rhs, float *out, const float *xv, double *r, int64_t p) {
     const int64_t b = c->b, nt = c->nt;
     if (b % SW_SLAB != 0) {
         c->last_error = "sweep: the tile edge must be a multiple of 128";
         return KRR_EINVAL;
     }
-    KRR_TRY(ensure_sweep_buffers(c, p));
+    KRR_TRY(ensure_sweep_buffers(c));
     CUtensorMap m[4];
     if (job == SW_RES) {
         const int64_t rows = nt * (nt + 1) / 2 * b;
@@ -790,7 +853,7 @@ krr_status run_job(Ctx *c, int job, const float *rhs, float *out, const float *x
         sp.b = b;
         sp.nt = nt;
         sp.S = b / SW_SLAB;
-        sp.items = (job == SW_RES) ? nt * sp.S : 2 * nt * sp.S;
+        sp.items = (job == SW_RES) ? nt * sp.S : sp.S * nt * (nt + 1) / 2;
         sp.pc = (int)std::min<int64_t>(SW_PCMAX, p - q0);
         sp.pcp = (sp.pc + 3) & ~3;
         sp.q0 = (int)q0;
@@ -798,12 +861,11 @@ krr_status run_job(Ctx *c, int job, const float *rhs, float *out, const float *x
         sp.x16 = (p % 4 == 0 && sp.pc % 4 == 0) ? 1 : 0;
         // vector rows per stage: 32 (FP32 tiles) up to 128 (E4M3 tiles)
         const int64_t xrows = (job == SW_RES) ? 32 : 128;
-        sp.stage_bytes = (SW_CHUNK + SW_HDR + xrows * sp.pcp * 4 + 1023) / 1024 * 1024;
-        int stages = 6;
+        sp.stage_bytes = (SW_CHUNK + SW_HDR + xrows * sp.pcp * 4 + 128 + 1023) / 1024 * 1024;
+        int stages = 8;
         while (stages > 2 && smem_bytes(stages, sp.stage_bytes, sp.pcp) > smem_limit()) --stages;
         sp.stages = stages;
         sp.rhs = rhs;
-        sp.acc = c->sw_acc;
         sp.out = out;
         sp.xv = xv;
         sp.r = r;
@@ -814,7 +876,7 @@ krr_status run_job(Ctx *c, int job, const float *rhs, float *out, const float *x
         sp.flags = c->sw_flags;
         sp.wait_ns = (uint64_t)c->opt.wait_budget_ns;
         sp.err = c->derr;
-        KRR_CUDA_TRY(c, cudaMemsetAsync(c->sw_flags, 0, (size_t)(2 + 2 * nt) * sizeof(int), c->stream));
+        KRR_CUDA_TRY(c, cudaMemsetAsync(c->sw_flags, 0, (size_t)flag_count(c) * sizeof(int), c->stream));
         const size_t smem = smem_bytes(stages, sp.stage_bytes, sp.pcp);
         krr_status st;
         switch (sp.pcp / 4) {
@@ -823,9 +885,7 @@ krr_status run_job(Ctx *c, int job, const float *rhs, float *out, const float *x
             case 3: st = launch_nq<3>(c, m, sp, smem); break;
             case 4: st = launch_nq<4>(c, m, sp, smem); break;
             case 5: st = launch_nq<5>(c, m, sp, smem); break;
-            case 6: st = launch_nq<6>(c, m, sp, smem); break;
-            case 7: st = launch_nq<7>(c, m, sp, smem); break;
-            default: st = launch_nq<8>(c, m, sp, smem); break;
+            default: st = launch_nq<6>(c, m, sp, smem); break;
         }
         KRR_TRY(st);
     }
@@ -834,8 +894,9 @@ krr_status run_job(Ctx *c, int job, const float *rhs, float *out, const float *x
 
 }  // namespace
 
-// x (n_pad x p) <- (L L^T)^-1 x with the stored factor: forward sweep into
-// tmp (z), backward sweep back into x.
+// x (n_pad x p) <- (L L^T)^-1 x with the stored factor: the forward sweep
+// updates x in place and writes z to tmp, the backward sweep updates tmp in
+// place and writes the solution to x.
 krr_status sweep_solve(Ctx *c, float *x, float *tmp, int64_t p) {
     KRR_TRY(run_job(c, SW_FWD, x, tmp, nullptr, nullptr, p));
     return run_job(c, SW_BWD, tmp, x, nullptr, nullptr, p);
@@ -844,7 +905,7 @@ krr_status sweep_solve(Ctx *c, float *x, float *tmp, int64_t p) {
 // r = y - lambda a - (K - c 1 1^T) a - c 1 (1^T a); the column sums 1^T a
 // must be in c->colsum.
 krr_status sweep_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
-    return run_job(c, SW_RES, y, nullptr, a, r, p);
+    return run_job(c, SW_RES, const_cast<float *>(y), nullptr, a, r, p);
 }
 
 }  // namespace krr

@@ -62,6 +62,19 @@ constexpr int PRED_MAX_P = 32;
 constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
+// Pair mode (PAIR = 2): two CTAs of a cluster run one tcgen05.mma with
+// cta_group::2 over a 256 x 256 block, M = 256: each CTA stages its own 128 A
+// rows and one 128-row half of B, and keeps its 128 output rows in its TMEM.
+// A stage is 32 KB instead of 48 KB, so the ring holds 6 stages.
+template <int PAIR>
+struct PairCfg {
+    static constexpr int stages = (PAIR == 2) ? 6 : STAGES;
+    static constexpr int stage_bytes = (PAIR == 2) ? 2 * A_BYTES : STAGE_BYTES;
+    static constexpr uint32_t idesc = (PAIR == 2)
+        ? (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24)
+        : IDESC;
+};
+
 struct TcParams {
     // n: real training rows; n_pad: padded training rows; n_test / test_rows:
     // real / padded test rows; p / ldaw: weight columns in this launch and the
@@ -156,6 +169,38 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Pair mode: the box lands in this CTA's shared memory and completes on the
+// barrier `bar_cluster` (a shared::cluster address, possibly in the peer CTA).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, int x, int y,
+                                                 uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+
+// shared::cluster address of the same shared-memory location in CTA `rank`.
+__device__ __forceinline__ uint32_t map_to_rank(const void *p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
@@ -166,9 +211,15 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
     return d;
 }
 
-template <int KIND>
+template <int KIND, int PAIR = 1>
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
-    if (KIND == KIND_F16) {
+    if (PAIR == 2) {
+        static_assert(PAIR != 2 || KIND == KIND_F16, "pair mode is FP16 only");
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(PairCfg<2>::idesc), "r"(acc));
+    } else if (KIND == KIND_F16) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
@@ -185,6 +236,16 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
+        : "memory");
+}
+
+// Pair mode: arrives on the barrier at the same offset in both CTAs of the
+// pair once the pair MMAs issued so far have completed.
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)0x3)
         : "memory");
 }
 
@@ -308,6 +369,17 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
         if (di.prec == KRR_PREC_FP32) { w.amap[q] = 2; w.arow[q] = alo_row; w.bmap[q] = bhi_map; w.brow[q] = bhi_row; ++q; }
         w.nph = q;
     }
+}
+
+// Cluster pairs (two CTAs along M share the B operand): pair unit u covers
+// the 256 x 256 region of 128 x 256 blocks (2 pm, sn) and (2 pm + 1, sn) of
+// one tile; CTA `rank` of the pair takes block 2 pm + rank.  Both CTAs of a
+// pair decode the same tile, phases and B rows.
+__device__ __forceinline__ int64_t pair_item(const TcParams &p, int64_t u, uint32_t rank) {
+    const int64_t sub_cols = p.b / BN, sub_per_tile = (p.b / BM) * sub_cols, pairs_per_tile = sub_per_tile / 2;
+    const int64_t tile = u / pairs_per_tile, pu = u % pairs_per_tile;
+    const int64_t sn = pu % sub_cols, pm = pu / sub_cols;
+    return tile * sub_per_tile + (2 * pm + rank) * sub_cols + sn;
 }
 
 // ---------------------------------------------------------------------------
@@ -575,18 +647,25 @@ __device__ __forceinline__ void epilogue_stage(const TcParams &p, const Work &w,
     }
 }
 
-template <int KIND, int OP>
+// PAIR = 2: clusters of two CTAs, one cta_group::2 MMA per 256 x 256 region
+// (rank 0 issues it).  Each CTA loads its own 128 A rows and B rows
+// [rank * 128, +128) into its own ring; both loads complete on rank 0's
+// `full` barrier, rank 0's commits free the stage in both CTAs and mark the
+// accumulator full in both, and both CTAs' epilogues release the accumulator
+// on rank 0's `tempty` barrier.
+template <int KIND, int OP, int PAIR>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
               const TcParams p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    constexpr int NST = PairCfg<PAIR>::stages, SBYTES = PairCfg<PAIR>::stage_bytes;
     uint8_t *stage_base = smem;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-    uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES,
-             *tempty = bars + 2 * STAGES + 2, *drain = bars + 2 * STAGES + 4;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 5);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NST * SBYTES);
+    uint64_t *full = bars, *empty = bars + NST, *tfull = bars + 2 * NST,
+             *tempty = bars + 2 * NST + 2, *drain = bars + 2 * NST + 4;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NST + 5);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red_s = reinterpret_cast<double *>(tmem_slot + 2);
     int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 16);
@@ -596,14 +675,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     TileDesc *col_desc = reinterpret_cast<TileDesc *>(aw_s);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = (PAIR == 2) ? cluster_rank() : 0u;
+    // work units: blocks (PAIR = 1) or pairs of blocks (PAIR = 2)
+    const int64_t nunits = p.items / PAIR;
+    const int64_t ustart = blockIdx.x / PAIR, ustep = gridDim.x / PAIR;
+    auto unit_item = [&](int64_t u) -> int64_t { return (PAIR == 2) ? pair_item(p, u, rank) : u; };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], EPI_THREADS);
+            mbar_init(&tempty[a], PAIR * (EPI_THREADS / 32));  // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -611,11 +695,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (PAIR == 2) {  // both CTAs of the pair allocate together
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     if (warp == 0 && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA0)) : "memory");
@@ -629,6 +721,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
     tmem_fence_before();
     __syncthreads();
+    if (PAIR == 2) cluster_sync();  // both CTAs' barriers and TMEM are ready before any pair traffic
     tmem_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const uint64_t budget = p.wait_ns;
@@ -641,38 +734,47 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t ph = 0;
             int issued = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < p.items && ok; t += gridDim.x) {
+            for (int64_t u = ustart; u < nunits && ok; u += ustep) {
                 Work w;
-                decode<OP>(p, t, w, col_desc);
+                decode<OP>(p, unit_item(u), w, col_desc);
                 for (int q = 0; q < w.nph && ok; ++q) {
                     for (int kb = 0; kb < w.nkb; ++kb) {
                         if (!wait_bar(&empty[s], ph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
-                        uint8_t *sa = stage_base + s * STAGE_BYTES;
+                        uint8_t *sa = stage_base + s * SBYTES;
                         uint8_t *sb = sa + A_BYTES;
-                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                         const int x = (KIND == KIND_F16) ? kb * (SLAB / 2) : kb * SLAB;
-                        tma_load_2d(sa, maps[w.amap[q]], x, w.arow[q], &full[s]);
-                        tma_load_2d(sb, maps[w.bmap[q]], x, w.brow[q], &full[s]);
-                        tma_load_2d(sb + A_BYTES, maps[w.bmap[q]], x, w.brow[q] + BM, &full[s]);
+                        if (PAIR == 2) {
+                            // rank 0 expects both CTAs' bytes; B rows [rank * 128, +128)
+                            const uint32_t fbar = map_to_rank(&full[s], 0);
+                            if (rank == 0) mbar_arrive_expect_tx(&full[s], 2 * SBYTES);
+                            tma_load_2d_pair(sa, maps[w.amap[q]], x, w.arow[q], fbar);
+                            tma_load_2d_pair(sb, maps[w.bmap[q]], x, w.brow[q] + (int)rank * BM, fbar);
+                        } else {
+                            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                            tma_load_2d(sa, maps[w.amap[q]], x, w.arow[q], &full[s]);
+                            tma_load_2d(sb, maps[w.bmap[q]], x, w.brow[q], &full[s]);
+                            tma_load_2d(sb + A_BYTES, maps[w.bmap[q]], x, w.brow[q] + BM, &full[s]);
+                        }
                         ++issued;
-                        if (++s == STAGES) { s = 0; ph ^= 1; }
+                        if (++s == NST) { s = 0; ph ^= 1; }
                     }
                 }
             }
-            if (!ok) {
+            if (!ok && (PAIR == 1 || rank == 0)) {
                 // drain: wait (bounded) for the last loads issued to land
-                int n = issued < STAGES ? issued : STAGES;
+                // (in pair mode they complete on rank 0's barriers)
+                int n = issued < NST ? issued : NST;
                 int ss = s;
                 uint32_t pp = ph;
                 for (int e = 0; e < n; ++e) {
-                    if (--ss < 0) { ss = STAGES - 1; pp ^= 1; }
+                    if (--ss < 0) { ss = NST - 1; pp ^= 1; }
                     const uint64_t t0 = globaltimer();
                     while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < budget) {}
                 }
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && (PAIR == 1 || rank == 0)) {
             // ---------------- MMA issuer ----------------
             int s = 0;
             uint32_t ph = 0;
@@ -680,9 +782,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t aph = 0;
             bool ok = true;
             bool any = false;
-            for (int64_t t = blockIdx.x; t < p.items && ok; t += gridDim.x) {
+            for (int64_t u = ustart; u < nunits && ok; u += ustep) {
                 Work w;
-                decode<OP>(p, t, w, col_desc);
+                decode<OP>(p, unit_item(u), w, col_desc);
                 const int total = w.nph * w.nkb;
                 if (total == 0) continue;
                 if (!wait_bar(&tempty[acc], aph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
@@ -691,23 +793,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 for (int it = 0; it < total; ++it) {
                     if (!wait_bar(&full[s], ph, budget, abort_flag, p.err)) { ok = false; break; }
                     tmem_fence_after();
-                    const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
+                    const uint32_t sa = smem_u32(stage_base + s * SBYTES);
                     const uint32_t sb = sa + A_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
-                        mma<KIND>(tacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
-                                  (it > 0 || kk > 0) ? 1u : 0u);
+                        mma<KIND, PAIR>(tacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
+                                        (it > 0 || kk > 0) ? 1u : 0u);
                     }
                     any = true;
-                    mma_commit(&empty[s]);
-                    if (++s == STAGES) { s = 0; ph ^= 1; }
+                    if (PAIR == 2) mma_commit_pair(&empty[s]);  // frees the stage in both CTAs
+                    else mma_commit(&empty[s]);
+                    if (++s == NST) { s = 0; ph ^= 1; }
                 }
                 if (!ok) break;
-                mma_commit(&tfull[acc]);
+                if (PAIR == 2) mma_commit_pair(&tfull[acc]);
+                else mma_commit(&tfull[acc]);
                 if (++acc == 2) { acc = 0; aph ^= 1; }
             }
             if (!ok && any) {
-                mma_commit(drain);
+                if (PAIR == 2) mma_commit_pair(drain);
+                else mma_commit(drain);
                 const uint64_t t0 = globaltimer();
                 while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < budget) {}
             }
@@ -718,9 +823,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int half = (warp - 2) >> 2;          // column half of the block
         int acc = 0;
         uint32_t aph = 0;
-        for (int64_t t = blockIdx.x; t < p.items; t += gridDim.x) {
+        for (int64_t u = ustart; u < nunits; u += ustep) {
             Work w;
-            decode<OP>(p, t, w, col_desc);
+            decode<OP>(p, unit_item(u), w, col_desc);
             if (w.nph * w.nkb == 0) continue;
             epi_bar();
             epilogue_stage<OP>(p, w, threadIdx.x - 64, nb_s, aw_s);
@@ -731,23 +836,37 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * BN);
             epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc);
             tmem_fence_before();
-            mbar_arrive(&tempty[acc]);
+            __syncwarp();
+            if (lane == 0) {
+                if (PAIR == 2) mbar_arrive_cluster(map_to_rank(&tempty[acc], 0));
+                else mbar_arrive(&tempty[acc]);
+            }
             if (++acc == 2) { acc = 0; aph ^= 1; }
         }
     }
     tmem_fence_before();
     __syncthreads();
+    // no CTA leaves while its peer may still multicast into it or arrive on
+    // its barriers
+    if (PAIR == 2) cluster_sync();
     tmem_fence_after();
     if (warp == 1) {
         __syncwarp();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"(TMEM_COLS)
-                     : "memory");
+        if (PAIR == 2)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                         : "memory");
     }
 }
 
 // Shared memory: ring + barriers/slots + norms + predict weights + alignment slack.
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 256 + BN * 4 + BN * PRED_MAX_P * 4 + 1024;
+template <int PAIR>
+constexpr size_t smem_bytes_of() {
+    return (size_t)PairCfg<PAIR>::stages * PairCfg<PAIR>::stage_bytes + 256 + BN * 4 + BN * PRED_MAX_P * 4 + 1024;
+}
 
 __global__ void split_col0_kernel(const float *Kd, int64_t nt, int64_t b, __half *hi, __half *lo) {
     const int64_t tile = 1 + blockIdx.y;  // tile row i >= 1 of column 0
@@ -797,14 +916,15 @@ krr_status make_map(Ctx *c, CUtensorMap *map, const void *base, CUtensorMapDataT
     return KRR_OK;
 }
 
-template <int KIND, int OP>
+template <int KIND, int OP, int PAIR = 1>
 krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                   const CUtensorMap &b1, TcParams &p) {
     if (p.items <= 0) return KRR_OK;
     static bool attr = false;
+    static int max_clusters = 0;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(tc_kernel<KIND, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)SMEM_BYTES);
+        cudaError_t e = cudaFuncSetAttribute(tc_kernel<KIND, OP, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes_of<PAIR>());
         if (e != cudaSuccess) {
             c->last_error = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
             return KRR_ECUDA;
@@ -813,8 +933,44 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
     }
     p.wait_ns = (uint64_t)c->opt.wait_budget_ns;
     p.err = c->derr;
-    const int64_t grid = p.items < c->num_sms ? p.items : c->num_sms;
-    count_launch(), tc_kernel<KIND, OP><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, c->stream>>>(a0, a1, b0, b1, p);
+    if (PAIR == 1) {
+        const int64_t grid = p.items < c->num_sms ? p.items : c->num_sms;
+        count_launch(), tc_kernel<KIND, OP, 1><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, c->stream>>>(a0, a1, b0, b1, p);
+    } else {
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = PAIR;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(NUM_THREADS);
+        cfg.dynamicSmemBytes = smem_bytes_of<PAIR>();
+        cfg.stream = c->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (max_clusters == 0) {
+            // clusters that fit at once (SMs of a cluster share a GPC); the
+            // kernel is persistent, so the grid never exceeds them
+            cfg.gridDim = dim3((unsigned)(c->num_sms / PAIR * PAIR));
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, tc_kernel<KIND, OP, PAIR>, &cfg) != cudaSuccess || n < 1) {
+                cudaGetLastError();
+                n = 1;
+            }
+            max_clusters = n;
+        }
+        const int64_t units = p.items / PAIR;
+        const int64_t clusters = units < max_clusters ? units : max_clusters;
+        cfg.gridDim = dim3((unsigned)(clusters * PAIR));
+        count_launch();
+        cudaError_t e = cudaLaunchKernelEx(&cfg, tc_kernel<KIND, OP, PAIR>, a0, a1, b0, b1, p);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->last_error = std::string("tensor-core cluster launch: ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         c->last_error = std::string("tensor-core launch: ") + cudaGetErrorString(e);
@@ -923,7 +1079,7 @@ krr_status tc_update(Ctx *c, int64_t k) {
     p.Wd = c->Wd;
     p.ltab = c->ltab;
     p.items = u * (u + 1) / 2 * (b / BM) * (b / BN);
-    return launch<KIND_F16, OP_UPDATE>(c, st->pool_map, st->hi_map, st->lo_map, st->lo_map, p);
+    return launch<KIND_F16, OP_UPDATE, 2>(c, st->pool_map, st->hi_map, st->lo_map, st->lo_map, p);
 }
 
 // B = K_test^T G_p: the predict kernel with the roles of the two genotype
