@@ -1,0 +1,480 @@
+// Diagonal step of the tile Cholesky (Alg. 3, the POTRF of tile (k, k)) and
+// the triangular inverse of the factor, as one persistent dataflow kernel over
+// 64 x 64 blocks of the b x b tile (FP32).
+//
+// Items, claimed from a device counter in an order that respects their
+// dependencies:
+//   factor, for q = 0 .. NB-1 (NB = b / 64):
+//     P(q)        L_qq = chol(A_qq) and X_qq = inv(L_qq) in shared memory
+//     T(i, q)     L_iq = A_iq X_qq^T                     (i > q)
+//     U(i, j, q)  A_ij -= L_iq L_jq^T                    (q < j <= i)
+//   inverse X = L^-1 by recursive doubling, for s = 64, 128, ..., b / 2 and
+//   every pair of diagonal s-blocks:
+//     step 1      T_p = L_21 X_11                        (one 64 x 64 output block per item)
+//     step 2      X_21 = -X_22 T_p
+//   finish        X^T (for the backward substitution) and the FP16 hi/lo
+//                 split of X (operands of the tensor-core panel solve), per
+//                 64-row block.
+// Progress counters: upd[i][j] (updates applied to block (i, j)), pdone[q],
+// tdone[i][q], the number of finished factor items, and finished items per
+// inverse step.  An item only waits for items claimed before it by running
+// CTAs, so the kernel always progresses; every wait is bounded
+// (%globaltimer) and ends the kernel with KRR_ETIMEOUT.  Blocks written by
+// other CTAs are read through L2 (ld.global.cg).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "krr_internal.h"
+
+namespace krr {
+
+namespace {
+
+constexpr int DB = 64;          // block edge
+constexpr int DT = 256;         // threads per CTA
+constexpr int DMAX_NB = 64;     // blocks per tile edge supported (b <= 4096)
+
+struct DiagParams {
+    float *W;          // tile, overwritten by L (lower part)
+    float *X;          // inverse (zeroed before the launch)
+    float *XT;         // transpose of the inverse
+    __half *hi, *lo;   // FP16 split of the inverse (or null)
+    float *tmp;        // b * b / 2 floats: products of the inverse step
+    int64_t b;
+    int NB, levels;
+    int64_t tile_k;
+    int64_t n_factor;  // number of factor items
+    int64_t items;
+    int *ctr;          // counters (layout in ctr_* below)
+    double *minpiv;    // NB minimum pivots of this tile
+    DevErrors *err;
+    uint64_t wait_ns;
+};
+
+// counter layout: [0] item counter, [1] abort, [2] finished factor items,
+// [3 .. 3 + 2 * levels) finished items per inverse step, then pdone[NB],
+// tdone[NB * NB], upd[NB * NB]
+__device__ __forceinline__ int *ctr_fdone(const DiagParams &p) { return p.ctr + 2; }
+__device__ __forceinline__ int *ctr_phase(const DiagParams &p, int ph) { return p.ctr + 3 + ph; }
+__device__ __forceinline__ int *ctr_pdone(const DiagParams &p) { return p.ctr + 3 + 2 * p.levels; }
+__device__ __forceinline__ int *ctr_tdone(const DiagParams &p) { return ctr_pdone(p) + p.NB; }
+__device__ __forceinline__ int *ctr_upd(const DiagParams &p) { return ctr_tdone(p) + p.NB * p.NB; }
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded wait (one thread) until *c >= target; false on expiry / abort.
+__device__ bool wait_ge(const int *c, int target, const DiagParams &p) {
+    if (ld_acquire(c) >= target) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (ld_acquire(c) >= target) return true;
+        if ((it & 15) == 0) {
+            if (*(volatile int *)&p.ctr[1]) return false;
+            if (globaltimer() - t0 > p.wait_ns) {
+                atomicExch(&p.ctr[1], 1);
+                atomicCAS(&p.err->code, 0, (int)KRR_ETIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Publishes the CTA's finished writes and increments a counter.
+__device__ __forceinline__ void signal(int *c) {
+    __threadfence();
+    atomicAdd(c, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Item list.
+// ---------------------------------------------------------------------------
+enum DiagKind { K_P = 0, K_T = 1, K_U = 2, K_I1 = 3, K_I2 = 4, K_FIN = 5 };
+
+struct DItem {
+    int kind;
+    int q, i, j;     // factor blocks
+    int level, pair, a, c;  // inverse output block (a, c) of pair `pair` at `level`
+    int phase;       // inverse step index 2 * level + (0 | 1)
+};
+
+__host__ __device__ inline int64_t factor_items_for(int NB) {
+    int64_t n = 0;
+    for (int q = 0; q < NB; ++q) {
+        const int64_t m = NB - q - 1;
+        n += 1 + m + m * (m + 1) / 2;
+    }
+    return n;
+}
+
+// Items of inverse step (level l, step s): pairs * (sz / 64)^2.
+__host__ __device__ inline int64_t inv_step_items(int NB, int l) {
+    const int64_t nb = (int64_t)1 << l;   // sz / 64
+    const int64_t pairs = NB / (2 * nb);
+    return pairs * nb * nb;
+}
+
+__device__ void decode_item(const DiagParams &p, int64_t t, DItem &it) {
+    const int NB = p.NB;
+    if (t < p.n_factor) {
+        // walk the q groups: 1 P, then rows i = q+1.. with T(i, q) and U(i, j, q)
+        int64_t r = t;
+        for (int q = 0; q < NB; ++q) {
+            const int64_t m = NB - q - 1, g = 1 + m + m * (m + 1) / 2;
+            if (r >= g) {
+                r -= g;
+                continue;
+            }
+            it.q = q;
+            if (r == 0) {
+                it.kind = K_P;
+                return;
+            }
+            --r;
+            for (int i = q + 1; i < NB; ++i) {
+                const int64_t row = 1 + (i - q);  // T + U(i, q+1..i)
+                if (r < row) {
+                    it.i = i;
+                    if (r == 0) {
+                        it.kind = K_T;
+                    } else {
+                        it.kind = K_U;
+                        it.j = q + (int)r;
+                    }
+                    return;
+                }
+                r -= row;
+            }
+        }
+    }
+    int64_t r = t - p.n_factor;
+    for (int l = 0; l < p.levels; ++l) {
+        const int64_t per = inv_step_items(NB, l);
+        for (int s = 0; s < 2; ++s) {
+            if (r < per) {
+                const int64_t nb = (int64_t)1 << l;
+                it.kind = s == 0 ? K_I1 : K_I2;
+                it.level = l;
+                it.phase = 2 * l + s;
+                it.pair = (int)(r / (nb * nb));
+                it.a = (int)((r % (nb * nb)) / nb);
+                it.c = (int)(r % nb);
+                return;
+            }
+            r -= per;
+        }
+    }
+    it.kind = K_FIN;
+    it.i = (int)r;  // 64-row block of the inverse
+}
+
+// ---------------------------------------------------------------------------
+// 64 x 64 block product on 256 threads: C = alpha * sum_k A_k op(B_k) + beta * C.
+// Thread (tx, ty) = (t % 16, t / 16) owns rows ty + 16 u and columns tx + 16 v.
+// ---------------------------------------------------------------------------
+struct BlkSmem {
+    float a[DB][DB + 1];
+    float b[DB][DB + 1];
+};
+
+__device__ __forceinline__ void load_blk(float (*dst)[DB + 1], const float *src, int64_t ld, bool trans) {
+    // 64 x 64 floats, 16 per thread as 4 float4 loads through L2
+    for (int e = threadIdx.x; e < DB * DB / 4; e += DT) {
+        const int r = e / (DB / 4), c4 = (e % (DB / 4)) * 4;
+        const float4 v = __ldcg(reinterpret_cast<const float4 *>(src + r * ld + c4));
+        if (trans) {
+            dst[c4 + 0][r] = v.x; dst[c4 + 1][r] = v.y; dst[c4 + 2][r] = v.z; dst[c4 + 3][r] = v.w;
+        } else {
+            dst[r][c4 + 0] = v.x; dst[r][c4 + 1] = v.y; dst[r][c4 + 2] = v.z; dst[r][c4 + 3] = v.w;
+        }
+    }
+}
+
+// acc += A_blk (64 x 64) * Bs (64 x 64, [k][n] layout)
+__device__ __forceinline__ void mac_blk(const BlkSmem &s, float (&acc)[4][4]) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll 8
+    for (int k = 0; k < DB; ++k) {
+        float av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) av[u] = s.a[ty + 16 * u][k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) bv[v] = s.b[k][tx + 16 * v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+    }
+}
+
+// C (ld) = alpha * acc + beta * C
+__device__ __forceinline__ void store_blk(float *C, int64_t ld, const float (&acc)[4][4], float alpha, float beta) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            float *cp = C + (int64_t)(ty + 16 * u) * ld + tx + 16 * v;
+            const float old = (beta != 0.f) ? __ldcg(cp) : 0.f;
+            __stcg(cp, alpha * acc[u][v] + beta * old);
+        }
+}
+
+// ---------------------------------------------------------------------------
+// P(q): Cholesky and inverse of the 64 x 64 diagonal block in shared memory
+// (right-looking, one column per step).  A pivot that is not positive is
+// recorded (first one wins) and replaced by 1 so the rest stays finite.
+// ---------------------------------------------------------------------------
+__device__ void potrf_inv_block(const DiagParams &p, int q, BlkSmem &s) {
+    float (*a)[DB + 1] = s.a;
+    float (*x)[DB + 1] = s.b;
+    const int64_t b = p.b;
+    float *blk = p.W + (int64_t)q * DB * b + q * DB;
+    __shared__ int bad;
+    __shared__ float mpiv;
+    const int tx = threadIdx.x & (DB - 1), ty = threadIdx.x / DB;  // 4 row groups
+    constexpr int RS = DT / DB;
+    for (int r = ty; r < DB; r += RS) {
+        a[r][tx] = __ldcg(blk + (int64_t)r * b + tx);
+        x[r][tx] = (r == tx) ? 1.f : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        bad = -1;
+        mpiv = 3.0e38f;
+    }
+    __syncthreads();
+    for (int c = 0; c < DB; ++c) {
+        if (threadIdx.x == 0) {
+            float d = a[c][c];
+            if (!(d > 0.f)) {
+                if (bad < 0) bad = c;
+                d = 1.f;
+            }
+            a[c][c] = sqrtf(d);
+            mpiv = fminf(mpiv, a[c][c]);
+        }
+        __syncthreads();
+        if (ty == 0 && tx > c) a[tx][c] /= a[c][c];
+        __syncthreads();
+        if (tx > c) {
+            const float lsc = a[tx][c];
+            for (int r = ty; r < DB; r += RS)
+                if (r >= tx) a[r][tx] -= a[r][c] * lsc;
+        }
+        __syncthreads();
+    }
+    // inverse: row c of X is final after the division; then rows r > c
+    for (int c = 0; c < DB; ++c) {
+        if (ty == 0 && tx <= c) x[c][tx] /= a[c][c];
+        __syncthreads();
+        if (tx <= c) {
+            const float xc = x[c][tx];
+            for (int r = ty; r < DB; r += RS)
+                if (r > c) x[r][tx] -= a[r][c] * xc;
+        }
+        __syncthreads();
+    }
+    float *iblk = p.X + (int64_t)q * DB * b + q * DB;
+    for (int r = ty; r < DB; r += RS) {
+        __stcg(blk + (int64_t)r * b + tx, (tx <= r) ? a[r][tx] : 0.f);
+        __stcg(iblk + (int64_t)r * b + tx, (tx <= r) ? x[r][tx] : 0.f);
+    }
+    if (threadIdx.x == 0) {
+        p.minpiv[q] = (double)mpiv;
+        if (bad >= 0 && atomicCAS(&p.err->code, 0, (int)KRR_ENOTPD) == 0) {
+            p.err->bad_tile = p.tile_k;
+            p.err->bad_column = p.tile_k * b + (int64_t)q * DB + bad;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
+    __shared__ BlkSmem s;
+    __shared__ int64_t item_s;
+    __shared__ int ok_s;
+    const int64_t b = p.b;
+    const int NB = p.NB;
+    while (true) {
+        if (threadIdx.x == 0) item_s = atomicAdd(&p.ctr[0], 1);
+        __syncthreads();
+        const int64_t t = item_s;
+        if (t >= p.items) break;
+        DItem it;
+        decode_item(p, t, it);
+        // ---- wait for the inputs (one thread), then all threads proceed
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            int *upd = ctr_upd(p), *tdone = ctr_tdone(p), *pdone = ctr_pdone(p);
+            if (it.kind == K_P) {
+                ok = wait_ge(upd + it.q * NB + it.q, it.q, p);
+            } else if (it.kind == K_T) {
+                ok = wait_ge(pdone + it.q, 1, p) && wait_ge(upd + it.i * NB + it.q, it.q, p);
+            } else if (it.kind == K_U) {
+                ok = wait_ge(tdone + it.i * NB + it.q, 1, p) && wait_ge(tdone + it.j * NB + it.q, 1, p) &&
+                     wait_ge(upd + it.i * NB + it.j, it.q, p);
+            } else if (it.kind == K_I1 || it.kind == K_I2) {
+                ok = (it.phase == 0) ? wait_ge(ctr_fdone(p), (int)p.n_factor, p)
+                                     : wait_ge(ctr_phase(p, it.phase - 1),
+                                               (int)inv_step_items(NB, (it.phase - 1) / 2), p);
+            } else {
+                ok = (p.levels == 0) ? wait_ge(ctr_fdone(p), (int)p.n_factor, p)
+                                     : wait_ge(ctr_phase(p, 2 * p.levels - 1),
+                                               (int)inv_step_items(NB, p.levels - 1), p);
+            }
+            ok_s = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (!ok_s) break;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        if (it.kind == K_P) {
+            potrf_inv_block(p, it.q, s);
+        } else if (it.kind == K_T) {
+            // L_iq = A_iq X_qq^T, in place
+            float *c = p.W + (int64_t)it.i * DB * b + it.q * DB;
+            load_blk(s.a, c, b, false);
+            load_blk(s.b, p.X + (int64_t)it.q * DB * b + it.q * DB, b, true);
+            __syncthreads();
+            mac_blk(s, acc);
+            __syncthreads();
+            store_blk(c, b, acc, 1.f, 0.f);
+        } else if (it.kind == K_U) {
+            // A_ij -= L_iq L_jq^T
+            load_blk(s.a, p.W + (int64_t)it.i * DB * b + it.q * DB, b, false);
+            load_blk(s.b, p.W + (int64_t)it.j * DB * b + it.q * DB, b, true);
+            __syncthreads();
+            mac_blk(s, acc);
+            __syncthreads();
+            store_blk(p.W + (int64_t)it.i * DB * b + it.j * DB, b, acc, -1.f, 1.f);
+        } else if (it.kind == K_I1 || it.kind == K_I2) {
+            const int64_t nb = (int64_t)1 << it.level, sz = nb * DB, base = 2 * it.pair * sz;
+            float *tp = p.tmp + (int64_t)it.pair * sz * sz;
+            if (it.kind == K_I1) {
+                // T_p[a][c] = sum_{k >= c} L21[a][k] X11[k][c]
+                for (int64_t kk = it.c; kk < nb; ++kk) {
+                    load_blk(s.a, p.W + (base + sz + it.a * DB) * b + base + kk * DB, b, false);
+                    load_blk(s.b, p.X + (base + kk * DB) * b + base + it.c * DB, b, false);
+                    __syncthreads();
+                    mac_blk(s, acc);
+                    __syncthreads();
+                }
+                store_blk(tp + (int64_t)it.a * DB * sz + it.c * DB, sz, acc, 1.f, 0.f);
+            } else {
+                // X21[a][c] = -sum_{k <= a} X22[a][k] T_p[k][c]
+                for (int64_t kk = 0; kk <= it.a; ++kk) {
+                    load_blk(s.a, p.X + (base + sz + it.a * DB) * b + base + sz + kk * DB, b, false);
+                    load_blk(s.b, tp + kk * DB * sz + it.c * DB, sz, false);
+                    __syncthreads();
+                    mac_blk(s, acc);
+                    __syncthreads();
+                }
+                store_blk(p.X + (base + sz + it.a * DB) * b + base + it.c * DB, b, acc, -1.f, 0.f);
+            }
+        } else {
+            // 64-row block r of X: transpose into X^T and the FP16 split
+            const int r = it.i;
+            for (int cb = 0; cb < NB; ++cb) {
+                const float *src = p.X + (int64_t)r * DB * b + cb * DB;
+                load_blk(s.a, src, b, false);
+                __syncthreads();
+                for (int e = threadIdx.x; e < DB * DB; e += DT) {
+                    const int rr = e / DB, cc = e % DB;
+                    // X^T block (cb, r): element (cc, rr) = X (rr, cc)
+                    __stcg(p.XT + ((int64_t)cb * DB + rr) * b + r * DB + cc, s.a[cc][rr]);
+                    if (p.hi) {
+                        const float v = s.a[rr][cc];
+                        const __half h = __float2half_rn(v);
+                        const int64_t o = ((int64_t)r * DB + rr) * b + cb * DB + cc;
+                        p.hi[o] = h;
+                        p.lo[o] = __float2half_rn(v - __half2float(h));
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        // ---- publish
+        if (threadIdx.x == 0) {
+            if (it.kind == K_P) {
+                signal(ctr_pdone(p) + it.q);
+            } else if (it.kind == K_T) {
+                signal(ctr_tdone(p) + it.i * NB + it.q);
+            } else if (it.kind == K_U) {
+                signal(ctr_upd(p) + it.i * NB + it.j);
+            } else if (it.kind == K_I1 || it.kind == K_I2) {
+                signal(ctr_phase(p, it.phase));
+            }
+            if (it.kind <= K_U) atomicAdd(ctr_fdone(p), 1);  // ordered after the signal's fence
+        }
+    }
+}
+
+}  // namespace
+
+int64_t diag_counter_count(int64_t b) {
+    const int64_t NB = b / DB;
+    int levels = 0;
+    while (((int64_t)DB << levels) < b) ++levels;
+    return 3 + 2 * levels + NB + 2 * NB * NB;
+}
+
+// Factor + inverse of diagonal tile k in FP32 (W in place, Linv, LinvT and
+// the FP16 split of Linv when present).  The counters `ctr` hold
+// diag_counter_count(b) ints.
+krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT, __half *hi, __half *lo,
+                                float *tmp, int *ctr, double *minpiv) {
+    const int64_t b = c->b;
+    if (b % DB != 0 || b / DB > DMAX_NB) {
+        c->last_error = "diagonal step: tile edge must be a multiple of 64 and at most 4096";
+        return KRR_EINVAL;
+    }
+    DiagParams p;
+    memset(&p, 0, sizeof(p));
+    p.W = W;
+    p.X = X;
+    p.XT = XT;
+    p.hi = hi;
+    p.lo = lo;
+    p.tmp = tmp;
+    p.b = b;
+    p.NB = (int)(b / DB);
+    int levels = 0;
+    while (((int64_t)DB << levels) < b) ++levels;
+    p.levels = levels;
+    p.tile_k = k;
+    p.n_factor = factor_items_for(p.NB);
+    int64_t inv = 0;
+    for (int l = 0; l < levels; ++l) inv += 2 * inv_step_items(p.NB, l);
+    p.items = p.n_factor + inv + p.NB;
+    p.ctr = ctr;
+    p.minpiv = minpiv;
+    p.err = c->derr;
+    p.wait_ns = (uint64_t)c->opt.wait_budget_ns;
+    cudaStream_t s = c->stream;
+    KRR_CUDA_TRY(c, cudaMemsetAsync(ctr, 0, (size_t)diag_counter_count(b) * sizeof(int), s));
+    KRR_CUDA_TRY(c, cudaMemsetAsync(X, 0, (size_t)b * b * sizeof(float), s));
+    const int64_t grid = std::min<int64_t>(c->num_sms, std::max<int64_t>(p.NB * (p.NB + 1) / 2, 1));
+    count_launch(), diag_kernel<<<(unsigned)grid, DT, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->last_error = std::string("diagonal step launch: ") + cudaGetErrorString(e);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
+}
+
+}  // namespace krr

@@ -188,6 +188,7 @@ void free_factor(Ctx *c) {
     dev_free(&c->Linv_lo);
     dev_free(&c->diag64);
     dev_free(&c->diag64_inv);
+    dev_free(&c->diag_ctr);
     dev_free(&c->pool);
     dev_free(&c->ltab);
     dev_free(&c->colbuf);
@@ -579,6 +580,7 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
         KRR_TRY(dev_alloc(c, &c->LinvT, (size_t)nt * bb, "transposed diagonal inverses"));
         KRR_TRY(dev_alloc(c, &c->diag64, (size_t)bb, "FP64 diagonal scratch"));
         KRR_TRY(dev_alloc(c, &c->diag64_inv, (size_t)2 * bb, "FP64 inverse scratch"));
+        KRR_TRY(dev_alloc(c, &c->diag_ctr, (size_t)diag_counter_count(b), "diagonal-step counters"));
         const size_t pool_bytes = (size_t)std::max<int64_t>(noff, 1) * bb * 4;
         KRR_TRY(dev_alloc(c, &c->pool, pool_bytes, "factor pool"));
         c->pool_bytes = pool_bytes;

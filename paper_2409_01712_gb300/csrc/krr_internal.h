@@ -87,7 +87,8 @@ struct Ctx {
     float *Linv = nullptr;     // inverse of every diagonal factor tile, FP32
     float *LinvT = nullptr;    // and its transpose (row-oriented backward sweep)
     __half *Linv_hi = nullptr, *Linv_lo = nullptr;  // FP16 split of Linv (mixed)
-    double *diag64 = nullptr;  // FP64 scratch diagonal tile (diag_fp64)
+    double *diag64 = nullptr;  // FP64 scratch diagonal tile (diag_fp64); FP32 scratch otherwise
+    int *diag_ctr = nullptr;   // progress counters of the diagonal-step kernel
     double *diag64_inv = nullptr;
     uint8_t *pool = nullptr;   // off-diagonal factor tiles, each in its precision
     size_t pool_bytes = 0;
@@ -193,6 +194,13 @@ void launch_trsm_simt(Ctx *c, int64_t k);
 // (n_pad / 128) x rows_pad x p.
 void launch_predict_simt(Ctx *c, const float *tf, const int32_t *tn, int64_t n_test,
                          int64_t rows_pad, const float *A, int64_t p, float *part);
+
+// Diagonal-step dataflow kernel (diag.cu): FP32 factor of tile W, inverse X,
+// its transpose XT and FP16 split hi/lo (optional); ctr holds
+// diag_counter_count(b) ints, minpiv b / 64 doubles.
+int64_t diag_counter_count(int64_t b);
+krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT, __half *hi, __half *lo,
+                                float *tmp, int *ctr, double *minpiv);
 
 // Diagonal step: in-place Cholesky of Wd tile k and its inverse into Linv.
 krr_status diag_step(Ctx *c, int64_t k);

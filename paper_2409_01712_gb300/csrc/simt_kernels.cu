@@ -698,14 +698,14 @@ krr_status diag_step(Ctx *c, int64_t k) {
         count_launch(), finish_inverse_kernel<<<g, 256, 0, s>>>(c->diag64_inv, linv,
                                                 c->Linv_hi ? c->Linv_hi + k * bb : nullptr,
                                                 c->Linv_lo ? c->Linv_lo + k * bb : nullptr, bb);
+        count_launch(), transpose_kernel<<<dim3((unsigned)(b / 32), (unsigned)(b / 32)), dim3(32, 8), 0, s>>>(
+            linv, c->LinvT + k * bb, b);
     } else {
-        diag_factor_tile<float>(c, wd, linv, (float *)c->diag64, k, minpiv);
-        if (c->Linv_hi)
-            count_launch(), finish_inverse_kernel<<<g, 256, 0, s>>>(nullptr, linv, c->Linv_hi + k * bb,
-                                                    c->Linv_lo + k * bb, bb);
+        // one dataflow launch: factor, inverse, transpose and FP16 split
+        KRR_TRY(launch_diag_dataflow(c, k, wd, linv, c->LinvT + k * bb, c->Linv_hi ? c->Linv_hi + k * bb : nullptr,
+                                     c->Linv_lo ? c->Linv_lo + k * bb : nullptr, (float *)c->diag64, c->diag_ctr,
+                                     minpiv + k * nq));
     }
-    count_launch(), transpose_kernel<<<dim3((unsigned)(b / 32), (unsigned)(b / 32)), dim3(32, 8), 0, s>>>(
-        linv, c->LinvT + k * bb, b);
     count_launch(), min_pivot_kernel<<<1, 1, 0, s>>>(minpiv + k * nq, nq, c->derr);
     return KRR_OK;
 }

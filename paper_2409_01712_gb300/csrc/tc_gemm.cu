@@ -65,10 +65,13 @@ constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >
 // Pair mode (PAIR = 2): two CTAs of a cluster run one tcgen05.mma with
 // cta_group::2 over a 256 x 256 block, M = 256: each CTA stages its own 128 A
 // rows and one 128-row half of B, and keeps its 128 output rows in its TMEM.
-// A stage is 32 KB instead of 48 KB, so the ring holds 6 stages.
+// A stage is 32 KB instead of 48 KB.
 template <int PAIR>
 struct PairCfg {
-    static constexpr int stages = (PAIR == 2) ? 6 : STAGES;
+    static constexpr int stages = (PAIR == 2) ? 4 : STAGES;
+    // pair mode (trailing update): the FP16 target block (128 x 256) is staged
+    // in shared memory by TMA, updated there and stored back by TMA
+    static constexpr int cbuf_bytes = (PAIR == 2) ? BM * BN * 2 : 0;
     static constexpr int stage_bytes = (PAIR == 2) ? 2 * A_BYTES : STAGE_BYTES;
     static constexpr uint32_t idesc = (PAIR == 2)
         ? (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24)
@@ -179,6 +182,16 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
         : "memory");
 }
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // shared::cluster address of the same shared-memory location in CTA `rank`.
 __device__ __forceinline__ uint32_t map_to_rank(const void *p, uint32_t rank) {
@@ -415,7 +428,7 @@ __device__ __forceinline__ void epilogue_prefetch(const TcParams &p, const Work 
 template <int OP>
 __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row, int half,
                                          int32_t *nb_s, float *aw_s, double *red_s,
-                                         const TileDesc *col_desc) {
+                                         const TileDesc *col_desc, uint8_t *cbuf = nullptr) {
     const int64_t b = p.b;
     const int ch0 = half * CH_PER_HALF;
     if (OP == OP_DIST) {
@@ -555,6 +568,32 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
     } else {  // OP_UPDATE
         const int64_t k = p.k;
         const float sc = 1.f / (col_desc[w.i - k - 1].scale * col_desc[w.j - k - 1].scale);
+        if (cbuf) {
+            // FP16 target staged in shared memory as 4 boxes of 64 columns x
+            // 128 rows, 128-byte swizzled: update in place
+#pragma unroll
+            for (int cc = 0; cc < CH_PER_HALF; ++cc) {
+                float v[16];
+                tmem_ld16(tacc + (ch0 + cc) * 16, v);
+                const int col = half * 128 + cc * 16, u0 = (col & 63) >> 3;
+                uint8_t *rp = cbuf + (col >> 6) * (BM * 128) + row * 128;
+                uint4 *q0 = reinterpret_cast<uint4 *>(rp + ((u0 ^ (row & 7)) << 4));
+                uint4 *q1 = reinterpret_cast<uint4 *>(rp + (((u0 + 1) ^ (row & 7)) << 4));
+                uint4 u[2] = {*q0, *q1};
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    __half2 *h2 = reinterpret_cast<__half2 *>(&u[e]);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        const float2 f = __half22float2(h2[qq]);
+                        h2[qq] = __floats2half2_rn(f.x - v[8 * e + 2 * qq] * sc, f.y - v[8 * e + 2 * qq + 1] * sc);
+                    }
+                }
+                *q0 = u[0];
+                *q1 = u[1];
+            }
+            return;
+        }
         const int64_t lr = w.sm * BM + row;
         const bool diag = (w.i == w.j);
         const float *cin32 = nullptr;
@@ -662,10 +701,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int NST = PairCfg<PAIR>::stages, SBYTES = PairCfg<PAIR>::stage_bytes;
     uint8_t *stage_base = smem;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NST * SBYTES);
+    uint8_t *cbuf = smem + NST * SBYTES;  // pair mode: staged target block
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NST * SBYTES + PairCfg<PAIR>::cbuf_bytes);
     uint64_t *full = bars, *empty = bars + NST, *tfull = bars + 2 * NST,
-             *tempty = bars + 2 * NST + 2, *drain = bars + 2 * NST + 4;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NST + 5);
+             *tempty = bars + 2 * NST + 2, *drain = bars + 2 * NST + 4, *cfull = bars + 2 * NST + 5;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NST + 6);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red_s = reinterpret_cast<double *>(tmem_slot + 2);
     int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 16);
@@ -690,6 +730,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mbar_init(&tempty[a], PAIR * (EPI_THREADS / 32));  // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
+        mbar_init(cfull, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -822,19 +863,36 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int row = ((warp & 3) << 5) + lane;  // TMEM lane quarter of this warp
         const int half = (warp - 2) >> 2;          // column half of the block
         int acc = 0;
-        uint32_t aph = 0;
+        uint32_t aph = 0, cph = 0;
+        bool cload_pending = false;  // thread 64: a staging load was issued and not waited for
         for (int64_t u = ustart; u < nunits; u += ustep) {
             Work w;
             decode<OP>(p, unit_item(u), w, col_desc);
             if (w.nph * w.nkb == 0) continue;
+            // pair mode, FP16 target: stage it by TMA while the MMAs run (the
+            // previous block's store must have read the buffer first)
+            const bool cstage = (PAIR == 2 && OP == OP_UPDATE) && p.k > 0 && w.i != w.j;
+            if (cstage && threadIdx.x == 64) {
+                bulk_wait_read();
+                mbar_arrive_expect_tx(cfull, (uint32_t)PairCfg<PAIR>::cbuf_bytes);
+                const int y = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
+                for (int bx = 0; bx < BN / 64; ++bx)
+                    tma_load_2d(cbuf + bx * (BM * 128), &mB1, (int)(w.sn * BN + bx * 64), y, cfull);
+                cload_pending = true;
+            }
             epi_bar();
             epilogue_stage<OP>(p, w, threadIdx.x - 64, nb_s, aw_s);
-            epilogue_prefetch<OP>(p, w, row, half);
+            if (!cstage) epilogue_prefetch<OP>(p, w, row, half);
             epi_bar();
             if (!wait_bar(&tfull[acc], aph, budget, abort_flag, p.err)) break;
+            if (cstage) {
+                if (!wait_bar(cfull, cph, budget, abort_flag, p.err)) break;
+                cph ^= 1;
+                cload_pending = false;
+            }
             tmem_fence_after();
             const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * BN);
-            epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc);
+            epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc, cstage ? cbuf : nullptr);
             tmem_fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -842,6 +900,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 else mbar_arrive(&tempty[acc]);
             }
             if (++acc == 2) { acc = 0; aph ^= 1; }
+            if (cstage) {
+                // generic-proxy writes become visible to the TMA store
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                epi_bar();
+                if (threadIdx.x == 64) {
+                    const int y = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
+                    for (int bx = 0; bx < BN / 64; ++bx)
+                        tma_store_2d(&mB1, (int)(w.sn * BN + bx * 64), y, cbuf + bx * (BM * 128));
+                    bulk_commit();
+                }
+            }
+        }
+        if (PAIR == 2 && threadIdx.x == 64) {
+            bulk_wait_all();  // stores finished before the CTA leaves
+            if (cload_pending) {  // aborted with a staging load in flight
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(cfull, cph) && globaltimer() - t0 < budget) {}
+            }
         }
     }
     tmem_fence_before();
@@ -865,7 +941,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 256 + BN * 4 + BN * PRED_MAX_P * 4 + 1024;
 template <int PAIR>
 constexpr size_t smem_bytes_of() {
-    return (size_t)PairCfg<PAIR>::stages * PairCfg<PAIR>::stage_bytes + 256 + BN * 4 + BN * PRED_MAX_P * 4 + 1024;
+    return (size_t)PairCfg<PAIR>::stages * PairCfg<PAIR>::stage_bytes + PairCfg<PAIR>::cbuf_bytes + 256 + BN * 4 +
+           BN * PRED_MAX_P * 4 + 1024;
 }
 
 __global__ void split_col0_kernel(const float *Kd, int64_t nt, int64_t b, __half *hi, __half *lo) {
@@ -1079,7 +1156,8 @@ krr_status tc_update(Ctx *c, int64_t k) {
     p.Wd = c->Wd;
     p.ltab = c->ltab;
     p.items = u * (u + 1) / 2 * (b / BM) * (b / BN);
-    return launch<KIND_F16, OP_UPDATE, 2>(c, st->pool_map, st->hi_map, st->lo_map, st->lo_map, p);
+    // mB1 = the FP16 trailing tiles: staged target blocks (TMA load and store)
+    return launch<KIND_F16, OP_UPDATE, 2>(c, st->pool_map, st->hi_map, st->lo_map, st->w_map, p);
 }
 
 // B = K_test^T G_p: the predict kernel with the roles of the two genotype
