@@ -298,7 +298,7 @@ def run_ours(args):
             "factor": {k: fi[k] for k in ("tiles_fp32", "tiles_fp16", "tiles_e4m3", "factor_bytes",
                                           "min_pivot")},
             "solve": {"iterations": si["iterations"], "rel_residual": si["rel_residual"],
-                      "converged": si["converged"]}}
+                      "converged": si["converged"], "history": si["history"]}}
     if roof:
         line["roofline"] = roof
 

@@ -84,8 +84,8 @@ typedef struct krr_factor_info {
 typedef struct krr_solve_info {
     int32_t iterations;      /* refinement iterations taken */
     int32_t converged;       /* 1: ||R||_F / ||Y||_F <= ir_tol; 2: refinement stopped at the
-                                attainable floor (two successive steps that did not halve the
-                                residual); 0: no refinement or not converged */
+                                attainable floor (a step that did not halve the residual);
+                                0: no refinement or not converged */
     double rel_residual;     /* final ||Y - (K + lambda I) A||_F / ||Y||_F */
     double history[32];      /* relative residual after the first solve and each iteration */
 } krr_solve_info;
@@ -140,9 +140,9 @@ krr_status krr_factor(krr_ctx *ctx, double lambda, krr_factor_info *info);
  * solved against one factorisation.
  *   Y : n x p FP32, leading dimension ldy >= p, host or device (read only).
  *   A : n x p FP32 output, leading dimension lda >= p, host or device.
- * Refinement stops when ||R||_F / ||Y||_F <= ir_tol, when two successive
- * steps fail to halve it, or when a step makes it worse (that step is undone):
- * the floor set by FP32 storage of K and A.  A holds the best iterate.
+ * Refinement stops when ||R||_F / ||Y||_F <= ir_tol, when a step fails to
+ * halve it, or when a step makes it worse (that step is undone): the floor set
+ * by FP32 storage of K and A.  A holds the best iterate.
  * Errors: KRR_ESTATE (no factor), KRR_EINVAL, KRR_ENOCONV (non-finite
  * residual, or ir_max iterations without reaching the tolerance or the
  * floor), KRR_ECUDA.

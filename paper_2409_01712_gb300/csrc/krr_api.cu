@@ -194,8 +194,6 @@ void free_factor(Ctx *c) {
     dev_free(&c->colbuf);
     dev_free(&c->pan_hi);
     dev_free(&c->pan_lo);
-    dev_free(&c->pan_f8);
-    dev_free(&c->colnorm2);
     dev_free(&c->colmax);
     dev_free(&c->precmap);
     c->pool_bytes = 0;
@@ -233,11 +231,6 @@ krr_status ensure_vectors(Ctx *c, int64_t p) {
     if (c->colsum_cap < p) {
         KRR_TRY(dev_alloc(c, &c->colsum, (size_t)p, "column sums"));
         c->colsum_cap = p;
-    }
-    const size_t rp = (size_t)c->nt * c->nt * c->b * (size_t)std::min<int64_t>(p, 32);
-    if (c->res_part_cap < rp) {
-        KRR_TRY(dev_alloc(c, &c->res_part, rp, "residual partials"));
-        c->res_part_cap = rp;
     }
     return KRR_OK;
 }
@@ -281,7 +274,6 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
     const bool refine = mixed(c) && c->opt.ir_max > 0;
     if (refine || info) {
         double best = INFINITY;
-        int stall = 0;
         for (int it = 0;; ++it) {
             int rr = prof_begin(c, KRR_PROF_RESIDUAL);
             KRR_TRY(launch_residual(c, c->ybuf, c->abuf, c->rbuf, p));
@@ -319,14 +311,12 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
                 st = KRR_ENOCONV;
                 break;
             }
-            // stagnation: two successive steps that do not halve the residual
-            if (rel > 0.5 * best) {
-                if (++stall >= 2) {
-                    si.converged = 2;
-                    break;
-                }
-            } else {
-                stall = 0;
+            // stagnation: a step that did not halve the residual shows the
+            // floor set by FP32 storage of K and A; a further step would only
+            // move along it
+            if (it > 0 && rel > 0.5 * best) {
+                si.converged = 2;
+                break;
             }
             best = std::min(best, rel);
             launch_axpy_r(c->rbuf, c->dabuf, cnt, s);
@@ -430,8 +420,11 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->pred_part);
     dev_free(&c->pred_out);
     dev_free(&c->colsum);
-    dev_free(&c->res_part);
     dev_free(&c->sw_flags);
+    dev_free(&c->ts_v0);
+    dev_free(&c->ts_v1);
+    if (c->ts_aux) cudaFree(c->ts_aux);
+    c->ts_aux = nullptr;
     dev_free(&c->g_yt);
     dev_free(&c->g_gp);
     dev_free(&c->g_aw);
@@ -593,9 +586,7 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
             KRR_TRY(dev_alloc(c, &c->colbuf, colt * bb, "column buffer"));
             KRR_TRY(dev_alloc(c, &c->pan_hi, colt * bb, "operand panel"));
             KRR_TRY(dev_alloc(c, &c->pan_lo, colt * bb, "operand panel"));
-            KRR_TRY(dev_alloc(c, &c->pan_f8, colt * bb, "operand panel"));
-            KRR_TRY(dev_alloc(c, &c->colnorm2, colt * 16, "column norms"));
-            KRR_TRY(dev_alloc(c, &c->colmax, colt * 16, "column maxima"));
+            KRR_TRY(dev_alloc(c, &c->colmax, colt * (size_t)tile_max_partials(b), "column maxima"));
         }
     }
     // reset the error record, the precision map and (fp32 mode) the tile

@@ -40,9 +40,14 @@ constexpr int RED_MINPIV = 64;   // nt * (b / 64) block minimum pivots, then nt 
 
 // Storage precision of an off-diagonal factor tile (values of the
 // KRR_PREC_* enum of krr.h).
+// Mixed mode: FP16 and E4M3 tiles hold scale * L; an FP32-class tile holds
+// scale * L as an exact pair of FP16 planes (hi = fp16(x), lo = fp16(x - hi),
+// about 22 significant bits), hi plane first.  An E4M3 tile also has an FP16
+// copy in its trailing slot W(i, k), which is spent once the column is
+// factored.  fp32 mode: every tile is plain FP32 with scale 1.
 struct TileDesc {
     int64_t offset;   // byte offset of the tile in the factor pool
-    float scale;      // stored value = scale * L (power of two; 1 for FP32)
+    float scale;      // stored value = scale * L (power of two)
     int32_t prec;     // KRR_PREC_FP32 / KRR_PREC_FP16 / KRR_PREC_E4M3
 };
 
@@ -95,9 +100,7 @@ struct Ctx {
     TileDesc *ltab = nullptr;  // per strictly-lower tile: where/how L is stored
     float *colbuf = nullptr;   // FP32 TRSM output of one tile column
     __half *pan_hi = nullptr, *pan_lo = nullptr;  // FP16 operand copies of one column
-    uint8_t *pan_f8 = nullptr;                    // E4M3 operand copies of one column
-    double *colnorm2 = nullptr;  // per tile of the column: sum of L^2
-    float *colmax = nullptr;     // per tile of the column: max |L|
+    float *colmax = nullptr;     // per block of the column's tiles: max |L| (panel-solve epilogue)
     uint8_t *precmap = nullptr;  // device copy of the precision map (nt x nt)
     DevErrors *derr = nullptr;
     DevErrors *herr = nullptr;   // pinned host mirror
@@ -110,8 +113,6 @@ struct Ctx {
     float *dabuf = nullptr;                  // n_pad x p correction
     double *red = nullptr;                   // reductions (norms), small; slots RED_*
     double *colsum = nullptr;                // column sums of the current iterate (FP64)
-    float *res_part = nullptr;               // residual partial slots, nt * nt * b * min(p, 32)
-    size_t res_part_cap = 0;
     int64_t colsum_cap = 0;
     double *hred = nullptr;                  // pinned host mirror of red
     int64_t vec_cap = 0;                     // capacity in elements of the n_pad x p buffers
@@ -119,6 +120,10 @@ struct Ctx {
     size_t pred_part_cap = 0;
     int *sw_flags = nullptr;                 // sweep item counter, abort flag, progress counters
     int64_t sw_flags_cap = 0;
+    __half *ts_v0 = nullptr, *ts_v1 = nullptr;  // tensor-core sweep: FP16 pairs of vector blocks
+    size_t ts_vcap = 0;
+    void *ts_aux = nullptr;                  // tensor-core sweep: block scales and counters
+    size_t ts_aux_cap = 0;
     float *pred_out = nullptr;               // reduced predictions, rows_pad x p
     size_t pred_out_cap = 0;
     // hyperparameter gradient buffers (krr_grad_hyper)
@@ -205,8 +210,12 @@ krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT
 // Diagonal step: in-place Cholesky of Wd tile k and its inverse into Linv.
 krr_status diag_step(Ctx *c, int64_t k);
 
+// Number of max |L_ik| partials per panel tile written by the tensor-core
+// panel solve (one per 128 x 256 output block).
+inline int64_t tile_max_partials(int64_t b) { return (b / 128) * (b / 256); }
 // Casts the FP32 TRSM output of column k into the factor pool with the
 // precision chosen by the adaptive rule, plus the operand panels (mixed mode).
+// The tile maxima come from the panel solve (c->colmax).
 // ||K||_F^2 is read from c->red[2] (written by the build).
 void launch_column_cast(Ctx *c, int64_t k);
 
@@ -214,10 +223,12 @@ void launch_column_cast(Ctx *c, int64_t k);
 // (row-major, leading dimension p); tmp is n_pad x p scratch.
 krr_status solve_inplace(Ctx *c, float *x, float *tmp, int64_t p);
 
-// Persistent dataflow sweeps (sweep.cu): the two substitutions of a solve,
-// and the residual r = y - (K + lambda I) a given the column sums of a in
-// c->colsum.
+// Persistent dataflow sweeps (sweep.cu): the two substitutions of a solve
+// on CUDA cores (fp32 mode), and the residual r = y - (K + lambda I) a given
+// the column sums of a in c->colsum.
 krr_status sweep_solve(Ctx *c, float *x, float *tmp, int64_t p);
+// The two substitutions on the tensor cores (tcsweep.cu, mixed mode).
+krr_status tc_sweep_solve(Ctx *c, float *x, float *tmp, int64_t p);
 krr_status sweep_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
 
 // r = y - (K + lambda I) a (FP64 accumulation), norms into c->red.

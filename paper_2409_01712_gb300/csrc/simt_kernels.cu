@@ -721,35 +721,6 @@ krr_status diag_step(Ctx *c, int64_t k) {
 // sqrt(max_r W_kk[r, r]) from the diagonal step.  FP16/E4M3 tiles carry a
 // power-of-two scale so the largest entry sits near the top of the format.
 // ----------------------------------------------------------------------------
-__global__ void column_stats_kernel(const float *col, int64_t bb, int chunks, double *part_ss,
-                                    float *part_max) {
-    const int64_t tile = blockIdx.y, ch = blockIdx.x;
-    const int64_t per = bb / chunks;
-    const float4 *src = reinterpret_cast<const float4 *>(col + tile * bb + ch * per);
-    double ss = 0.0;
-    float mx = 0.f;
-    for (int64_t e = threadIdx.x; e < per / 4; e += blockDim.x) {
-        float4 v = src[e];
-        ss += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
-        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
-    }
-    __shared__ double rs[32];
-    __shared__ float rm[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        ss += __shfl_down_sync(0xffffffffu, ss, o);
-        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    }
-    if ((threadIdx.x & 31) == 0) { rs[threadIdx.x >> 5] = ss; rm[threadIdx.x >> 5] = mx; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0;
-        float m = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { s += rs[w]; m = fmaxf(m, rm[w]); }
-        part_ss[tile * chunks + ch] = s;
-        part_max[tile * chunks + ch] = m;
-    }
-}
-
 __device__ inline float pow2_scale(float mx, float top) {
     if (!(mx > 0.f)) return 1.f;
     int e = (int)floorf(log2f(top / mx));
@@ -760,23 +731,18 @@ __device__ inline float pow2_scale(float mx, float top) {
 }
 
 __global__ void column_decide_kernel(int64_t k, int64_t nt, int64_t bb, int chunks,
-                                     const double *part_ss, const float *part_max, double thresh,
+                                     const float *part_max, double thresh,
                                      const double *lkk_max, int allow_fp8, TileDesc *ltab,
                                      uint8_t *precmap, DevErrors *err) {
     const int64_t tile = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tile >= nt - k - 1) return;
-    double ss = 0;
     float mx = 0;
-    for (int q = 0; q < chunks; ++q) {
-        ss += part_ss[tile * chunks + q];
-        mx = fmaxf(mx, part_max[tile * chunks + q]);
-    }
+    for (int q = 0; q < chunks; ++q) mx = fmaxf(mx, part_max[tile * chunks + q]);
     const double w = (double)mx * lkk_max[k];
     int prec;
     if (allow_fp8 && 0.0625 * w <= thresh) prec = KRR_PREC_E4M3;
     else if (0x1p-11 * w <= thresh) prec = KRR_PREC_FP16;
     else prec = KRR_PREC_FP32;
-    (void)ss;
     const int64_t i = k + 1 + tile;
     TileDesc d;
     d.prec = prec;
@@ -792,11 +758,12 @@ __global__ void column_decide_kernel(int64_t k, int64_t nt, int64_t bb, int chun
 
 // Four consecutive elements per thread: vector loads and stores.
 __global__ void column_write_kernel(int64_t k, int64_t bb, const float *col, const TileDesc *ltab,
-                                    uint8_t *pool, __half *pan_hi, __half *pan_lo,
-                                    uint8_t *pan_f8) {
+                                    uint8_t *pool, __half *pan_hi, __half *pan_lo, __half *wsh) {
     const int64_t tile = blockIdx.y;
     const int64_t i = k + 1 + tile;
     const TileDesc d = ltab[off_index(i, k)];
+    // E4M3 tiles: FP16 copy in the spent trailing slot W(i, k)
+    __half2 *sh = reinterpret_cast<__half2 *>(wsh + off_index(i, k) * bb);
     const float4 *src = reinterpret_cast<const float4 *>(col + tile * bb);
     __half2 *hi = reinterpret_cast<__half2 *>(pan_hi + tile * bb);
     __half2 *lo = reinterpret_cast<__half2 *>(pan_lo + tile * bb);
@@ -813,10 +780,9 @@ __global__ void column_write_kernel(int64_t k, int64_t bb, const float *col, con
                 packed |= (uint32_t)qv << (8 * t);
                 h[t] = __half(__nv_cvt_fp8_to_halfraw(qv, __NV_E4M3));
             }
-            reinterpret_cast<uint32_t *>(pan_f8 + tile * bb)[e4] = packed;
             reinterpret_cast<uint32_t *>(pool + d.offset)[e4] = packed;
-            hi[2 * e4] = __halves2half2(h[0], h[1]);
-            hi[2 * e4 + 1] = __halves2half2(h[2], h[3]);
+            hi[2 * e4] = sh[2 * e4] = __halves2half2(h[0], h[1]);
+            hi[2 * e4 + 1] = sh[2 * e4 + 1] = __halves2half2(h[2], h[3]);
         } else if (d.prec == KRR_PREC_FP16) {
             // the trailing update reads FP16 tiles from the pool itself
             const __half2 a = __floats2half2_rn(sv[0], sv[1]), b2 = __floats2half2_rn(sv[2], sv[3]);
@@ -824,13 +790,17 @@ __global__ void column_write_kernel(int64_t k, int64_t bb, const float *col, con
             pp[2 * e4] = a;
             pp[2 * e4 + 1] = b2;
         } else {
-            reinterpret_cast<float4 *>(pool + d.offset)[e4] = v;
+            // FP32 class: the exact FP16 pair (hi plane, then lo plane)
             const __half2 a = __floats2half2_rn(sv[0], sv[1]), b2 = __floats2half2_rn(sv[2], sv[3]);
-            hi[2 * e4] = a;
-            hi[2 * e4 + 1] = b2;
             const float2 fa = __half22float2(a), fb = __half22float2(b2);
-            lo[2 * e4] = __floats2half2_rn(sv[0] - fa.x, sv[1] - fa.y);
-            lo[2 * e4 + 1] = __floats2half2_rn(sv[2] - fb.x, sv[3] - fb.y);
+            const __half2 la = __floats2half2_rn(sv[0] - fa.x, sv[1] - fa.y);
+            const __half2 lb = __floats2half2_rn(sv[2] - fb.x, sv[3] - fb.y);
+            __half2 *ph = reinterpret_cast<__half2 *>(pool + d.offset);
+            __half2 *pl = ph + bb / 2;
+            hi[2 * e4] = ph[2 * e4] = a;
+            hi[2 * e4 + 1] = ph[2 * e4 + 1] = b2;
+            lo[2 * e4] = pl[2 * e4] = la;
+            lo[2 * e4 + 1] = pl[2 * e4 + 1] = lb;
         }
     }
 }
@@ -839,19 +809,16 @@ void launch_column_cast(Ctx *c, int64_t k) {
     const int64_t u = c->nt - k - 1;
     if (u <= 0) return;
     const int64_t bb = c->b * c->b;
-    const int chunks = 16;
-    double *part_ss = c->colnorm2;
-    float *part_max = c->colmax;
-    count_launch(), column_stats_kernel<<<dim3(chunks, (unsigned)u), 256, 0, c->stream>>>(c->colbuf, bb, chunks,
-                                                                          part_ss, part_max);
+    // per-block max |L_ik| partials written by the panel-solve epilogue
+    const int chunks = (int)tile_max_partials(c->b);
     const double thresh = c->opt.eps * c->lambda;
     const double *lkk = c->red + RED_MINPIV + c->nt * (c->b / 64);
-    count_launch(), column_decide_kernel<<<cdiv(u, 128), 128, 0, c->stream>>>(k, c->nt, bb, chunks, part_ss, part_max,
+    count_launch(), column_decide_kernel<<<cdiv(u, 128), 128, 0, c->stream>>>(k, c->nt, bb, chunks, c->colmax,
                                                                thresh, lkk, c->opt.allow_fp8,
                                                                c->ltab, c->precmap, c->derr);
     count_launch(), column_write_kernel<<<dim3(64, (unsigned)u), 256, 0, c->stream>>>(k, bb, c->colbuf, c->ltab,
                                                                       c->pool, c->pan_hi, c->pan_lo,
-                                                                      c->pan_f8);
+                                                                      (__half *)c->W);
 }
 
 void launch_kernel_sumsq(Ctx *c, double *out) {
@@ -861,394 +828,9 @@ void launch_kernel_sumsq(Ctx *c, double *out) {
     count_launch(), kernel_sumsq_kernel<<<1, 1024, 0, c->stream>>>(c->knorm2, ntri, per, c->n_pad, out);
 }
 
-// ----------------------------------------------------------------------------
-// Tile matrix-vector products on CUDA cores (HBM-bound), p right-hand sides
-// processed in column chunks of at most PC.
-//
-//   gemv_n:  out[r][q] (op)= sum_c M[r][c] x[c][q]   (row-oriented)
-//            each lane covers 4 consecutive columns per 128-column step with
-//            one 16/8/4-byte load (FP32/FP16/E4M3); x is staged transposed in
-//            shared memory so the lanes' float4 reads are conflict-free; one
-//            warp per row at a time, warp-shuffle reduction.
-//   gemv_t:  out[c][q] (op)= sum_r M[r][c] x[r][q]   (column-oriented)
-//            a CTA covers 128 columns; its 8 warps split the rows; lanes cover
-//            4 columns; per-warp partials are summed in a fixed order in
-//            shared memory.
-// M is a b x b row-major tile in its storage precision: value = stored *
-// inv_scale - shift.  Every output element has one owner (no atomics).
-// ----------------------------------------------------------------------------
-constexpr int PC = 32;
-
-__device__ __forceinline__ float load_l(const uint8_t *base, int prec, int64_t e) {
-    if (prec == KRR_PREC_FP32) return reinterpret_cast<const float *>(base)[e];
-    if (prec == KRR_PREC_FP16) return __half2float(reinterpret_cast<const __half *>(base)[e]);
-    __half_raw h = __nv_cvt_fp8_to_halfraw(base[e], __NV_E4M3);
-    return __half2float(__half(h));
-}
-
-template <int PREC>
-__device__ __forceinline__ float4 load4(const uint8_t *base, int64_t e) {
-    if (PREC == KRR_PREC_FP32) return *reinterpret_cast<const float4 *>(base + e * 4);
-    if (PREC == KRR_PREC_FP16) {
-        uint2 u = *reinterpret_cast<const uint2 *>(base + e * 2);
-        float2 a = __half22float2(*reinterpret_cast<__half2 *>(&u.x));
-        float2 b = __half22float2(*reinterpret_cast<__half2 *>(&u.y));
-        return make_float4(a.x, a.y, b.x, b.y);
-    }
-    uint32_t u = *reinterpret_cast<const uint32_t *>(base + e);
-    __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u & 0xffffu), __NV_E4M3);
-    __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u >> 16), __NV_E4M3);
-    float2 a = __half22float2(__half2(lo));
-    float2 b = __half22float2(__half2(hi));
-    return make_float4(a.x, a.y, b.x, b.y);
-}
-
-// Where a gemv launch reads its tiles and writes its outputs.
-enum GemvJob {
-    JOB_DIAG = 0,      // one FP32 tile (Linv_kk or its transpose), out block k, store
-    JOB_FWD = 1,       // factor tiles L_ik, i > k (grid.y = i - k - 1), out block i, subtract
-    JOB_BWD = 2,       // factor tiles L_kj, j < k (grid.y = j), out block j, subtract
-    JOB_RES_N = 3,     // K tiles (i, j), j <= i (grid.y = tri index): partial slot (i, j), store
-    JOB_RES_T = 4      // K tiles (i, j), i > j (grid.y = off index): partial slot (j, i), store
-};
-
-struct GemvArgs {
-    int job;
-    int64_t k, b, nt;
-    const float *diag;       // JOB_DIAG tile
-    const uint8_t *pool;
-    const TileDesc *ltab;
-    const float *Kd;
-    float shift_dummy;
-    const double *shift;     // residual shift (device), JOB_RES_*
-    const float *x;          // input vectors, n_pad x ldx
-    int64_t ldx;
-    float *out;              // output vectors (n_pad x ldx) or partial slots (nt*nt x b x pc)
-    int q0, pc;
-};
-
-__device__ __forceinline__ void gemv_locate(const GemvArgs &g, int64_t y, const uint8_t *&base, int &prec,
-                                            float &inv_scale, float &shift, int64_t &in_blk,
-                                            float *&out, int64_t &ldo) {
-    shift = 0.f;
-    inv_scale = 1.f;
-    prec = KRR_PREC_FP32;
-    ldo = g.ldx;
-    if (g.job == JOB_DIAG) {
-        base = reinterpret_cast<const uint8_t *>(g.diag);
-        in_blk = g.k;
-        out = g.out + g.k * g.b * g.ldx;
-    } else if (g.job == JOB_FWD || g.job == JOB_BWD) {
-        const int64_t i = (g.job == JOB_FWD) ? g.k + 1 + y : g.k;
-        const int64_t j = (g.job == JOB_FWD) ? g.k : y;
-        const TileDesc d = g.ltab[off_index(i, j)];
-        base = g.pool + d.offset;
-        prec = d.prec;
-        if (prec != KRR_PREC_FP32) inv_scale = 1.f / d.scale;
-        in_blk = g.k;
-        out = g.out + ((g.job == JOB_FWD) ? i : j) * g.b * g.ldx;
-    } else {
-        int64_t i, j;  // y is the lower-triangle index of tile (i, j)
-        tri_decode(y, &i, &j);
-        base = reinterpret_cast<const uint8_t *>(g.Kd + tri_index(i, j) * g.b * g.b);
-        shift = (float)*g.shift;
-        in_blk = (g.job == JOB_RES_N) ? j : i;
-        const int64_t slot = (g.job == JOB_RES_N) ? (i * g.nt + j) : (j * g.nt + i);
-        out = g.out + slot * g.b * g.pc;
-        ldo = g.pc;
-    }
-}
-
-// Row-oriented product for RPL rows per lane: CTA = 8 warps x 32 lanes; warp
-// w covers columns [w * b / 8, (w + 1) * b / 8), lane l rows r0 + l + 32 u
-// (u < RPL).  A warp load touches 32 rows (many lines in flight); x rows
-// come from shared memory as broadcasts; the 8 column-slice partials of a
-// row are summed in a fixed order in shared memory.
-template <int PREC, int RPL>
-__device__ __forceinline__ void gemv_n_block(const uint8_t *base, float inv_scale, float shift, int64_t b,
-                                             int64_t r0, const float *xs, int pcp, int pc, float *red,
-                                             float *out, int64_t ldo, int q0, bool subtract) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t cw = b / 8, c0 = warp * cw;
-    float acc[RPL][PC];
-#pragma unroll
-    for (int u = 0; u < RPL; ++u)
-#pragma unroll
-        for (int q = 0; q < PC; ++q) acc[u][q] = 0.f;
-    int64_t re[RPL];
-#pragma unroll
-    for (int u = 0; u < RPL; ++u) re[u] = (r0 + lane + 32 * u) * b;
-    for (int64_t c = c0; c < c0 + cw; c += 8) {
-        float4 v[RPL][2];
-#pragma unroll
-        for (int u = 0; u < RPL; ++u)
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                v[u][h] = load4<PREC>(base, re[u] + c + 4 * h);
-                v[u][h].x -= shift; v[u][h].y -= shift; v[u][h].z -= shift; v[u][h].w -= shift;
-            }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float *xr = xs + (c + 4 * h + e) * pcp;
-#pragma unroll
-                for (int q4 = 0; q4 < PC / 4; ++q4) {
-                    if (q4 * 4 < pc) {
-                        const float4 z = *reinterpret_cast<const float4 *>(xr + q4 * 4);
-#pragma unroll
-                        for (int u = 0; u < RPL; ++u) {
-                            const float vv = (e == 0) ? v[u][h].x : (e == 1) ? v[u][h].y : (e == 2) ? v[u][h].z : v[u][h].w;
-                            acc[u][q4 * 4 + 0] = fmaf(vv, z.x, acc[u][q4 * 4 + 0]);
-                            acc[u][q4 * 4 + 1] = fmaf(vv, z.y, acc[u][q4 * 4 + 1]);
-                            acc[u][q4 * 4 + 2] = fmaf(vv, z.z, acc[u][q4 * 4 + 2]);
-                            acc[u][q4 * 4 + 3] = fmaf(vv, z.w, acc[u][q4 * 4 + 3]);
-                        }
-                    }
-                }
-            }
-        }
-    }
-    // red layout: [warp][32 * RPL rows][pc]; it overlays the x block, so
-    // every warp must be done reading x first
-    constexpr int R = 32 * RPL;
-    __syncthreads();
-#pragma unroll
-    for (int u = 0; u < RPL; ++u)
-#pragma unroll
-        for (int q = 0; q < PC; ++q)
-            if (q < pc) red[(warp * R + lane + 32 * u) * pc + q] = acc[u][q];
-    __syncthreads();
-    for (int t = threadIdx.x; t < R * pc; t += blockDim.x) {
-        const int rr = t / pc, q = t % pc;
-        float sum = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) sum += red[(w * R + rr) * pc + q];
-        float *dst = out + (r0 + rr) * ldo + q0 + q;
-        const float val = sum * inv_scale;
-        if (subtract) *dst -= val;
-        else *dst = val;
-    }
-}
-
-// grid: (b / (32 * rows_per_lane), tasks), 256 threads; dynamic smem:
-// max(b * pcp, 8 * 32 * rows_per_lane * pc) floats (x block, then the
-// column-slice partials in the same space).
-__global__ void __launch_bounds__(256) gemv_n_kernel(GemvArgs g, int rows_per_lane) {
-    extern __shared__ float xs[];
-    const uint8_t *base;
-    int prec;
-    float inv_scale, shift;
-    int64_t in_blk, ldo;
-    float *out;
-    gemv_locate(g, blockIdx.y, base, prec, inv_scale, shift, in_blk, out, ldo);
-    const int pcp = (g.pc + 3) & ~3;
-    const float *xin = g.x + in_blk * g.b * g.ldx + g.q0;
-    {
-        // stage x_k row-major with padded width pcp, no integer division
-        const int bi = (int)g.b, ldx = (int)g.ldx, pc = g.pc;
-        for (int r = threadIdx.x; r < bi; r += blockDim.x) {
-            const float *src = xin + (int64_t)r * ldx;
-            float *dst = xs + r * pcp;
-            for (int q = 0; q < pcp; ++q) dst[q] = (q < pc) ? src[q] : 0.f;
-        }
-    }
-    __syncthreads();
-    float *red = xs;
-    const int64_t r0 = (int64_t)blockIdx.x * 32 * rows_per_lane;
-    const bool sub = (g.job == JOB_FWD || g.job == JOB_BWD);
-    const int q0o = (g.job >= JOB_RES_N) ? 0 : g.q0;
-    if (rows_per_lane == 2) {
-        if (prec == KRR_PREC_FP32) gemv_n_block<KRR_PREC_FP32, 2>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
-        else if (prec == KRR_PREC_FP16) gemv_n_block<KRR_PREC_FP16, 2>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
-        else gemv_n_block<KRR_PREC_E4M3, 2>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
-    } else {
-        if (prec == KRR_PREC_FP32) gemv_n_block<KRR_PREC_FP32, 1>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
-        else if (prec == KRR_PREC_FP16) gemv_n_block<KRR_PREC_FP16, 1>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
-        else gemv_n_block<KRR_PREC_E4M3, 1>(base, inv_scale, shift, g.b, r0, xs, pcp, g.pc, red, out, ldo, q0o, sub);
-    }
-}
-
-template <int PREC>
-__device__ __forceinline__ void gemv_t_cols(const uint8_t *base, float inv_scale, float shift, int64_t b,
-                                            int64_t c0, int64_t ra0, int64_t rows, const float *at, int pcp,
-                                            int pc, float *red, float *out, int64_t ldo, int q0, int mode) {
-    // mode 0: out = v, 1: out -= v (out rows are the tile's columns)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t rows_per_warp = rows / 8;
-    const int64_t ra = ra0 + warp * rows_per_warp, rb = ra + rows_per_warp;
-    const int64_t col = c0 + lane * 4;
-    float acc[4][PC];
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-#pragma unroll
-        for (int q = 0; q < PC; ++q) acc[e][q] = 0.f;
-    for (int64_t r = ra; r < rb; r += 4) {
-        float4 v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            v[u] = load4<PREC>(base, (r + u) * b + col);
-            v[u].x -= shift; v[u].y -= shift; v[u].z -= shift; v[u].w -= shift;
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float *ar = at + (r + u - ra0) * pcp;
-#pragma unroll
-            for (int q4 = 0; q4 < PC / 4; ++q4) {
-                if (q4 * 4 < pc) {
-                    const float4 a = *reinterpret_cast<const float4 *>(ar + q4 * 4);
-                    const float av[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int q = q4 * 4 + t;
-                        acc[0][q] = fmaf(v[u].x, av[t], acc[0][q]);
-                        acc[1][q] = fmaf(v[u].y, av[t], acc[1][q]);
-                        acc[2][q] = fmaf(v[u].z, av[t], acc[2][q]);
-                        acc[3][q] = fmaf(v[u].w, av[t], acc[3][q]);
-                    }
-                }
-            }
-        }
-    }
-    __syncthreads();  // at[] is no longer read: red[] may alias it
-    // red layout: [warp][128 columns][pc]
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-#pragma unroll
-        for (int q = 0; q < PC; ++q)
-            if (q < pc) red[(warp * 128 + lane * 4 + e) * pc + q] = acc[e][q];
-    __syncthreads();
-    for (int t = threadIdx.x; t < 128 * pc; t += blockDim.x) {
-        const int cc = t / pc, q = t % pc;
-        float s = 0.f;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) s += red[(w * 128 + cc) * pc + q];
-        float *dst = out + (c0 + cc) * ldo + q0 + q;
-        const float v = s * inv_scale;
-        if (mode == 1) *dst -= v;
-        else *dst = v;
-    }
-}
-
-// grid: (b / 128, tasks, row chunks), 256 threads; dynamic smem:
-// max((b / chunks) * pcp, 8 * 128 * pc) floats.  With more than one row chunk
-// (JOB_BWD only) each CTA writes its partial to part[(task * chunks + z)][b][pc]
-// and gemv_t_reduce_kernel subtracts the chunk sums in a fixed order.
-__global__ void __launch_bounds__(256) gemv_t_kernel(GemvArgs g, float *part) {
-    extern __shared__ float at[];
-    const uint8_t *base;
-    int prec;
-    float inv_scale, shift;
-    int64_t in_blk, ldo;
-    float *out;
-    int64_t y = blockIdx.y;
-    if (g.job == JOB_RES_T) {
-        // grid.y runs over the strictly-lower tiles: off_index(i, j) =
-        // tri_index(i - 1, j), so decode with the triangle of size nt - 1
-        int64_t i, j;
-        tri_decode(y, &i, &j);
-        y = tri_index(i + 1, j);
-    }
-    gemv_locate(g, y, base, prec, inv_scale, shift, in_blk, out, ldo);
-    const int chunks = gridDim.z, z = blockIdx.z;
-    const int64_t rows = g.b / chunks, ra0 = (int64_t)z * rows;
-    const int pcp = (g.pc + 3) & ~3;
-    const float *xin = g.x + in_blk * g.b * g.ldx + g.q0;
-    {
-        // stage rows [ra0, ra0 + rows) of x_k with padded width pcp, no integer division
-        const int ri = (int)rows, ldx = (int)g.ldx, pc = g.pc;
-        for (int r = threadIdx.x; r < ri; r += blockDim.x) {
-            const float *src = xin + (ra0 + r) * ldx;
-            float *dst = at + r * pcp;
-            for (int q = 0; q < pcp; ++q) dst[q] = (q < pc) ? src[q] : 0.f;
-        }
-    }
-    __syncthreads();
-    const int64_t c0 = (int64_t)blockIdx.x * 128;
-    int mode = (g.job == JOB_FWD || g.job == JOB_BWD) ? 1 : 0;
-    int q0o = (g.job >= JOB_RES_N) ? 0 : g.q0;
-    if (chunks > 1) {  // partial slot of this chunk
-        out = part + ((int64_t)blockIdx.y * chunks + z) * g.b * g.pc;
-        ldo = g.pc;
-        q0o = 0;
-        mode = 0;
-    }
-    if (prec == KRR_PREC_FP32) gemv_t_cols<KRR_PREC_FP32>(base, inv_scale, shift, g.b, c0, ra0, rows, at, pcp, g.pc, at, out, ldo, q0o, mode);
-    else if (prec == KRR_PREC_FP16) gemv_t_cols<KRR_PREC_FP16>(base, inv_scale, shift, g.b, c0, ra0, rows, at, pcp, g.pc, at, out, ldo, q0o, mode);
-    else gemv_t_cols<KRR_PREC_E4M3>(base, inv_scale, shift, g.b, c0, ra0, rows, at, pcp, g.pc, at, out, ldo, q0o, mode);
-}
-
-// out block j (JOB_BWD task j) -= sum over chunks of the partials, fixed order.
-// grid: (b / 8, tasks), block (pc, 8).
-__global__ void gemv_t_reduce_kernel(const float *part, int chunks, int64_t b, int pc, float *x,
-                                     int64_t ldx, int q0) {
-    const int64_t j = blockIdx.y, c = (int64_t)blockIdx.x * 8 + threadIdx.y;
-    const int q = threadIdx.x;
-    float s = 0.f;
-    for (int z = 0; z < chunks; ++z) s += part[((j * chunks + z) * b + c) * pc + q];
-    x[(j * b + c) * ldx + q0 + q] -= s;
-}
-
-static size_t gemv_n_smem(int64_t b, int pc, int rows_per_lane) {
-    return std::max((size_t)b * ((pc + 3) & ~3), (size_t)8 * 32 * rows_per_lane * pc) * sizeof(float);
-}
-static size_t gemv_t_smem(int64_t rows, int pc) {
-    const size_t a = (size_t)rows * ((pc + 3) & ~3), r = (size_t)8 * 128 * pc;
-    return (a > r ? a : r) * sizeof(float);
-}
-
-static void gemv_attrs() {
-    static bool done = false;
-    if (done) return;
-    cudaFuncSetAttribute(gemv_n_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(gemv_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    done = true;
-}
-
-static GemvArgs gemv_args(Ctx *c, int job, int64_t k, const float *x, int64_t ldx, float *out, int q0,
-                          int pc) {
-    GemvArgs g;
-    memset(&g, 0, sizeof(g));
-    g.job = job;
-    g.k = k;
-    g.b = c->b;
-    g.nt = c->nt;
-    g.pool = c->pool;
-    g.ltab = c->ltab;
-    g.Kd = c->Kd;
-    g.shift = c->red + RED_KSHIFT;
-    g.x = x;
-    g.ldx = ldx;
-    g.out = out;
-    g.q0 = q0;
-    g.pc = pc;
-    return g;
-}
-
 // x (n_pad x p) <- (L L^T)^-1 x.  tmp is n_pad x p scratch (ends as Z).
-krr_status solve_inplace(Ctx *c, float *x, float *tmp, int64_t p) { return sweep_solve(c, x, tmp, p); }
-
-// ----------------------------------------------------------------------------
-// Refinement residual r = y - lambda a - K a, K from the FP32 lower-triangle
-// tiles (symmetric use), computed as (K - c 1 1^T) a + c 1 (1^T a): the
-// shifted entries are small, so FP32 products and per-tile FP32 sums lose far
-// less to cancellation; c 1^T a is formed in FP64 (c = the mean off-diagonal
-// entry of K).  Every tile pair (i, j) writes its own partial slot:
-// slot (i, j <= i) = (K_ij - c) a_j from the row pass and slot (j, i > j) =
-// (K_ij - c)^T a_i from the column pass; the slots of a row block are then
-// summed in FP64 in a fixed order.
-// ----------------------------------------------------------------------------
-// grid: (b / 8, nt), block (pc, 8): one thread per (row, column) of a row block.
-__global__ void residual_reduce_kernel(const float *part, int64_t nt, int64_t b, int pc, int q0,
-                                       int64_t p, float lambda, const float *y, const float *a,
-                                       const double *shift, const double *colsum, double *r) {
-    const int64_t i = blockIdx.y, lr = (int64_t)blockIdx.x * 8 + threadIdx.y;
-    const int q = threadIdx.x;
-    const int64_t row = i * b + lr;
-    double s = 0.0;
-    for (int64_t j = 0; j < nt; ++j) s += (double)part[((i * nt + j) * b + lr) * pc + q];
-    const int64_t idx = row * p + q0 + q;
-    r[idx] = (double)y[idx] - (double)lambda * (double)a[idx] - s - (*shift) * colsum[q0 + q];
+krr_status solve_inplace(Ctx *c, float *x, float *tmp, int64_t p) {
+    return c->opt.mode == KRR_MODE_MIXED ? tc_sweep_solve(c, x, tmp, p) : sweep_solve(c, x, tmp, p);
 }
 
 // Column sums of a (n x p) in FP64, one block per column.
@@ -1331,10 +913,18 @@ void launch_copy_rows(const float *src, int64_t lds, float *dst, int64_t ldd, in
 
 void launch_fill_zero(void *p, size_t bytes, cudaStream_t s) { cudaMemsetAsync(p, 0, bytes, s); }
 
+// One stored factor element in its precision (not de-scaled).
+__device__ __forceinline__ float load_l(const uint8_t *base, int prec, int64_t e) {
+    if (prec == KRR_PREC_FP32) return reinterpret_cast<const float *>(base)[e];
+    if (prec == KRR_PREC_FP16) return __half2float(reinterpret_cast<const __half *>(base)[e]);
+    __half_raw h = __nv_cvt_fp8_to_halfraw(base[e], __NV_E4M3);
+    return __half2float(__half(h));
+}
+
 // Dense lower-triangular copy of the stored factor (diagonal tiles from Wd,
 // off-diagonal tiles from the pool in their precision, de-scaled).
 __global__ void factor_to_dense_kernel(const float *Wd, const uint8_t *pool, const TileDesc *ltab,
-                                       int64_t b, int64_t n, float *dst, int64_t ld) {
+                                       int64_t b, int64_t n, int mixed, float *dst, int64_t ld) {
     const int64_t t = blockIdx.y;
     int64_t ti, tj;
     tri_decode(t, &ti, &tj);
@@ -1348,14 +938,22 @@ __global__ void factor_to_dense_kernel(const float *Wd, const uint8_t *pool, con
         const TileDesc d = ltab[off_index(ti, tj)];
         base = pool + d.offset;
         prec = d.prec;
-        if (prec != KRR_PREC_FP32) inv_scale = 1.f / d.scale;
+        inv_scale = 1.f / d.scale;
     }
+    // mixed mode: an FP32-class tile is an FP16 pair (hi plane, lo plane)
+    const bool pair = mixed && ti != tj && prec == KRR_PREC_FP32;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < b * b;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t lr = e / b, lc = e % b;
         const int64_t r = ti * b + lr, q = tj * b + lc;
         if (r >= n || q >= n) continue;
-        float v = load_l(base, prec, e) * inv_scale;
+        float v;
+        if (pair) {
+            const __half *h = reinterpret_cast<const __half *>(base);
+            v = (__half2float(h[e]) + __half2float(h[b * b + e])) * inv_scale;
+        } else {
+            v = load_l(base, prec, e) * inv_scale;
+        }
         if (ti == tj && lc > lr) v = 0.f;
         dst[r * ld + q] = v;
     }
@@ -1364,7 +962,7 @@ __global__ void factor_to_dense_kernel(const float *Wd, const uint8_t *pool, con
 void launch_factor_to_dense(Ctx *c, float *dst, int64_t ld) {
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     count_launch(), factor_to_dense_kernel<<<dim3(64, (unsigned)ntri), 256, 0, c->stream>>>(
-        c->Wd, c->pool, c->ltab, c->b, c->n, dst, ld);
+        c->Wd, c->pool, c->ltab, c->b, c->n, c->opt.mode == KRR_MODE_MIXED ? 1 : 0, dst, ld);
 }
 
 }  // namespace krr

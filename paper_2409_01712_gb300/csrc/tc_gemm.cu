@@ -558,12 +558,27 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
         }
     } else if (OP == OP_TRSM) {
         float *orow = p.colbuf + (w.i - p.k - 1) * b * b + (w.sm * BM + row) * b + w.sn * BN;
+        float mx = 0.f;
         for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
             float v[16];
             tmem_ld16(tacc + ch * 16, v);
             float4 *dst = reinterpret_cast<float4 *>(orow + ch * 16);
 #pragma unroll
             for (int e = 0; e < 4; ++e) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) mx = fmaxf(mx, fabsf(v[e]));
+        }
+        // max |L_ik| of the block for the adaptive-precision rule: warp
+        // maxima, then the eight warps; one partial per block of the tile
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int ew = (threadIdx.x >> 5) - 2;
+        if ((threadIdx.x & 31) == 0) red_s[ew] = (double)mx;
+        epi_bar();
+        if (threadIdx.x == 64) {
+            double m8 = 0.0;
+            for (int q = 0; q < 8; ++q) m8 = fmax(m8, red_s[q]);
+            const int64_t per_tile = (b / BM) * (b / BN);
+            p.part[(w.i - p.k - 1) * per_tile + w.sm * (b / BN) + w.sn] = (float)m8;
         }
     } else {  // OP_UPDATE
         const int64_t k = p.k;
@@ -1139,6 +1154,7 @@ krr_status tc_trsm(Ctx *c, int64_t k) {
     TcParams p = base_params(c);
     p.k = k;
     p.colbuf = c->colbuf;
+    p.part = c->colmax;  // per-block max |L_ik|, read by the column cast
     p.items = (nt - k - 1) * (b / BM) * (b / BN);
     const CUtensorMap &a0 = (k == 0) ? st->hi_map : st->w_map;
     return launch<KIND_F16, OP_TRSM>(c, a0, st->lo_map, st->linv_hi_map, st->linv_lo_map, p);

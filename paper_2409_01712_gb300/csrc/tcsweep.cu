@@ -1,0 +1,834 @@
+// Tensor-core tile sweeps of the solve phase (Alg. 3: forward substitution
+// L z = y, backward substitution L^T x = z) for the mixed-precision factor.
+//
+// Work items (one 128-row slab s of a row block each), as in the paper's tile
+// Cholesky solve, right-looking:
+//   forward   DIAG(j, s)     z_j[s] = Linv_jj[s, :] y_j             (y_j final)
+//             LINK(i, j, s)  y_i[s] -= L_ij[s, :] z_j,  i > j        (row slab of L_ij)
+//   backward  DIAG(j, s)     x_j[s] = (Linv_jj^T)[s, :] z_j
+//             LINK(t, j, s)  z_t[s] -= (L_jt^T)[s, :] x_j,  t < j    (column slab of L_jt)
+// Every item is one tcgen05.mma chain D[128 x NP] = A[128 x b] B[NP x b]^T with
+// FP32 accumulation in TMEM:
+//   A  a 128-row slab of a factor tile in FP16 (K-major by TMA for the forward
+//      sweep; MN-major -- the tile's columns -- for the backward sweep, so no
+//      transposed copy of the factor is kept).  FP32-class tiles are stored as
+//      an exact FP16 pair (hi, lo) and contribute two A phases; E4M3 tiles are
+//      read from their FP16 copy; the diagonal inverses from their FP16 split.
+//   B  the vector block as an FP16 pair (hi, lo) with one power-of-two scale
+//      per block and column, K-major ([column][row]); both halves are
+//      multiplied, so B carries about 22 significant bits.
+// The right-hand side is updated in place; a LINK applies its update after the
+// earlier ones of the same slab (fixed order: deterministic results).  The
+// last slab to finish a block converts that block to the FP16 pair (the
+// "converter"), then publishes it.
+//
+// Items are claimed from a device counter in dependency order (item 0 converts
+// the first block; then for every column c: the S DIAG items of block c and
+// the LINK items that read its result).  An item only waits for items claimed
+// before it by running CTAs; every wait is bounded (%globaltimer) and ends the
+// kernel with KRR_ETIMEOUT.
+//
+// CTA (192 threads, one per SM):
+//   warp 0      producer: claims items, TMA loads of A (16 KB per stage) and B
+//               into a shared-memory ring; B only after the block it reads has
+//               been published (the A loads of the first stages go out first);
+//   warp 1      TMEM allocation and the single MMA-issuing thread;
+//   warps 2..5  epilogue: TMEM -> registers, scales, the in-place update or the
+//               DIAG store, progress counters and block conversions.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#include "krr_internal.h"
+
+namespace krr {
+
+namespace {
+
+constexpr int TS_THREADS = 192;
+constexpr int TS_EPI = 128;
+constexpr int TS_SLAB = 128;             // output rows of an item (MMA M)
+constexpr int TS_KC = 64;                // K elements of a stage (128 bytes of FP16)
+constexpr int TS_ABYTES = TS_SLAB * 128;  // A bytes of a stage
+constexpr int TS_NPMAX = 64;             // right-hand sides per launch
+constexpr int TS_IRING = 4;              // item header slots
+
+enum { TS_FWD = 0, TS_BWD = 1 };
+enum { IT_CONV = 0, IT_DIAG = 1, IT_LINK = 2, IT_END = 3 };
+// A operand maps
+enum { AM_POOL = 0, AM_WSH = 1, AM_LHI = 2, AM_LLO = 3 };
+
+struct TsParams {
+    int job;
+    int64_t b, nt, S, KC, items, n_pad;
+    int np, pc, q0;
+    int64_t ldx;
+    float *rhs;               // FWD: y, BWD: z (updated in place)
+    float *out;               // FWD: z, BWD: x
+    __half *vin, *vout;       // FP16 pairs of rhs / out blocks: [2 np][n_pad] (hi rows, then lo rows)
+    float *sin, *sout;        // their scales, [nt][np]
+    const TileDesc *ltab;
+    int *flags;               // [0] items, [1] abort, cin[nt], cout[nt], done[nt], ready[nt], seq[nt * S]
+    int stages, stage_bytes;
+    uint32_t idesc;
+    uint64_t wait_ns;
+    DevErrors *err;
+};
+
+struct ItemHdr {
+    int type;
+    int blk, slab, src;      // output block and slab; block of the vector read
+    int seqv;                // LINK: updates applied to (blk, slab) before this one
+    int last_link;
+    int nph;                 // A phases (1 or 2)
+    int amap[2];
+    int arow[2];             // first row of the tile (phase) in its map
+    float inv_tscale;        // 1 / tile scale
+};
+
+__device__ __forceinline__ int *cin_ctr(const TsParams &p) { return p.flags + 2; }
+__device__ __forceinline__ int *cout_ctr(const TsParams &p) { return p.flags + 2 + p.nt; }
+__device__ __forceinline__ int *done_ctr(const TsParams &p) { return p.flags + 2 + 2 * p.nt; }
+__device__ __forceinline__ int *ready_ctr(const TsParams &p) { return p.flags + 2 + 3 * p.nt; }
+__device__ __forceinline__ int *seq_ctr(const TsParams &p) { return p.flags + 2 + 4 * p.nt; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
+    return (uint32_t)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *ptr) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ptr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *ptr, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(ptr), "r"(v) : "memory");
+}
+
+// Orders this thread's generic-proxy global accesses with later async-proxy
+// (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void record_timeout(const TsParams &p) {
+    atomicExch(&p.flags[1], 1);
+    atomicCAS(&p.err->code, 0, (int)KRR_ETIMEOUT);
+}
+
+__device__ __forceinline__ bool aborted(const TsParams &p) { return *(volatile int *)&p.flags[1] != 0; }
+
+// Bounded wait on a CTA barrier; false on expiry or when the sweep aborted.
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, const TsParams &p) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31) == 0) {
+            if (aborted(p)) return false;
+            if (globaltimer() - t0 > p.wait_ns) {
+                record_timeout(p);
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded wait until a progress counter reaches `target`.
+__device__ __forceinline__ bool wait_count(const int *ctr, int target, const TsParams &p) {
+    if (ld_acquire(ctr) >= target) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (ld_acquire(ctr) >= target) return true;
+        if ((it & 15) == 0) {
+            if (aborted(p)) return false;
+            if (globaltimer() - t0 > p.wait_ns) {
+                record_timeout(p);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptors, 128-byte swizzle (tcgen05 version 1).
+// K-major: 8-row groups of 128-byte rows, 1024 bytes apart (SBO); the
+// leading offset is unused.
+__device__ __forceinline__ uint64_t desc_kmajor(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+// MN-major: every 128-byte row holds 64 consecutive M elements of one K
+// index; 8-row K groups are 1024 bytes apart (SBO) and the two 64-wide M
+// halves of the slab are 8192 bytes apart (LBO, one TMA box each).
+__device__ __forceinline__ uint64_t desc_mnmajor(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(8192 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(r[e]);
+}
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Items.  Item 0 converts the first block of the right-hand side; then column
+// c (0..nt-1) holds S DIAG items and S * (nt - 1 - c) LINK items and starts
+// at 1 + S * (c * nt - c (c - 1) / 2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t col_start(int64_t S, int64_t nt, int64_t c) {
+    return S * (c * nt - c * (c - 1) / 2);
+}
+
+__device__ void decode_item(const TsParams &p, int64_t t, ItemHdr &h) {
+    const int64_t S = p.S, nt = p.nt, b = p.b;
+    const bool fwd = (p.job == TS_FWD);
+    h.seqv = 0;
+    h.last_link = 0;
+    h.inv_tscale = 1.f;
+    h.nph = 0;
+    h.amap[0] = h.amap[1] = 0;
+    h.arow[0] = h.arow[1] = 0;
+    if (t == 0) {
+        h.type = IT_CONV;
+        h.blk = fwd ? 0 : (int)(nt - 1);
+        h.slab = 0;
+        h.src = h.blk;
+        return;
+    }
+    const int64_t u = t - 1;
+    int64_t lo = 0, hi = nt - 1;  // largest c with col_start(c) <= u
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (col_start(S, nt, mid) <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t c = lo, r = u - col_start(S, nt, c);
+    const int64_t j = fwd ? c : nt - 1 - c;
+    h.src = (int)j;
+    if (r < S) {
+        h.type = IT_DIAG;
+        h.blk = (int)j;
+        h.slab = (int)r;
+        h.nph = 2;
+        h.amap[0] = AM_LHI;
+        h.amap[1] = AM_LLO;
+        h.arow[0] = h.arow[1] = (int)(j * b);
+        return;
+    }
+    const int64_t m = (r - S) / S;
+    h.type = IT_LINK;
+    h.slab = (int)((r - S) % S);
+    const int64_t blk = fwd ? j + 1 + m : j - 1 - m;
+    h.blk = (int)blk;
+    h.seqv = (int)(fwd ? j : nt - 1 - j);
+    h.last_link = fwd ? (j == blk - 1) : (j == blk + 1);
+    // forward reads L_{blk, j}, backward L_{j, blk}
+    const int64_t ti = fwd ? blk : j, tj = fwd ? j : blk;
+    const int64_t off = off_index(ti, tj);
+    const TileDesc d = p.ltab[off];
+    h.inv_tscale = 1.f / d.scale;
+    if (d.prec == KRR_PREC_E4M3) {
+        // FP16 copy of the E4M3 tile in the tile's (spent) trailing slot
+        h.nph = 1;
+        h.amap[0] = AM_WSH;
+        h.arow[0] = (int)(off * b);
+    } else {
+        const int row0 = (int)(d.offset / (2 * b));
+        h.amap[0] = h.amap[1] = AM_POOL;
+        h.arow[0] = row0;
+        h.arow[1] = row0 + (int)b;  // FP32 class: the lo half follows the hi half
+        h.nph = (d.prec == KRR_PREC_FP32) ? 2 : 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block conversion (128 epilogue threads): v rows [blk b, +b), columns
+// [q0, q0 + pc) -> FP16 pair with the power-of-two scale s_q putting the
+// column maximum in [4096, 8192) (8x headroom below the FP16 maximum):
+// hi = fp16(s v), lo = fp16(s v - hi); padding columns [pc, np) are zero.
+// ---------------------------------------------------------------------------
+__device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __half *vb, float *sv,
+                              float *smax, float *sscale, int tid) {
+    const int64_t b = p.b, n_pad = p.n_pad;
+    const int pc = p.pc, np = p.np;
+    float mx[TS_NPMAX];
+#pragma unroll
+    for (int q = 0; q < TS_NPMAX; ++q) mx[q] = 0.f;
+    for (int64_t r = tid; r < b; r += TS_EPI) {
+        const float *row = v + (blk * b + r) * p.ldx + p.q0;
+#pragma unroll
+        for (int q = 0; q < TS_NPMAX; ++q)
+            if (q < pc) mx[q] = fmaxf(mx[q], fabsf(__ldcg(row + q)));
+    }
+    const int wq = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < TS_NPMAX; ++q) {
+        if (q < pc) {
+            float m = mx[q];
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) smax[wq * TS_NPMAX + q] = m;
+        }
+    }
+    epi_sync();
+    if (tid < np) {
+        float s = 1.f;
+        if (tid < pc) {
+            const float m = fmaxf(fmaxf(smax[tid], smax[TS_NPMAX + tid]),
+                                  fmaxf(smax[2 * TS_NPMAX + tid], smax[3 * TS_NPMAX + tid]));
+            if (m > 0.f && m < 3.0e38f) {
+                int e;
+                frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
+                s = ldexpf(1.f, max(-126, min(126, 13 - e)));
+            }
+        }
+        sscale[tid] = s;
+        sv[blk * np + tid] = s;
+    }
+    epi_sync();
+    for (int64_t r = tid; r < b; r += TS_EPI) {
+        const int64_t grow = blk * b + r;
+        const float *row = v + grow * p.ldx + p.q0;
+#pragma unroll
+        for (int q = 0; q < TS_NPMAX; ++q) {
+            if (q < np) {
+                const float x = (q < pc) ? __ldcg(row + q) * sscale[q] : 0.f;
+                const __half h = __float2half_rn(x);
+                vb[(int64_t)q * n_pad + grow] = h;
+                vb[(int64_t)(np + q) * n_pad + grow] = __float2half_rn(x - __half2float(h));
+            }
+        }
+    }
+    // the block is read next by TMA (async proxy) on other SMs
+    fence_proxy_async_global();
+    __threadfence();
+    epi_sync();
+}
+
+__global__ void __launch_bounds__(TS_THREADS, 1)
+    tcsweep_kernel(const __grid_constant__ CUtensorMap mPool, const __grid_constant__ CUtensorMap mWsh,
+                   const __grid_constant__ CUtensorMap mLhi, const __grid_constant__ CUtensorMap mLlo,
+                   const __grid_constant__ CUtensorMap mVin, const __grid_constant__ CUtensorMap mVout,
+                   const TsParams p) {
+    extern __shared__ __align__(1024) uint8_t ts_smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ts_smem_raw) + 1023) & ~uintptr_t(1023));
+    const int NS = p.stages, SB = p.stage_bytes;
+    ItemHdr *hdrs = reinterpret_cast<ItemHdr *>(smem + NS * SB);
+    float *smax = reinterpret_cast<float *>(hdrs + TS_IRING);    // [4][TS_NPMAX]
+    float *sscale = smax + 4 * TS_NPMAX;                          // [TS_NPMAX]
+    float *smul = sscale + TS_NPMAX;                              // [TS_NPMAX]
+    int *sflag = reinterpret_cast<int *>(smul + TS_NPMAX);        // [4]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sflag + 4);
+    uint64_t *full = bars, *empty = bars + NS, *tfull = bars + 2 * NS, *tempty = bars + 2 * NS + 2,
+             *ifull = bars + 2 * NS + 4, *iempty = bars + 2 * NS + 4 + TS_IRING,
+             *drain = bars + 2 * NS + 4 + 2 * TS_IRING;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int np = p.np;
+    const uint32_t tcols = (np * 2 <= 32) ? 32u : (np * 2 <= 64 ? 64u : 128u);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], TS_EPI / 32);
+        }
+        for (int q = 0; q < TS_IRING; ++q) {
+            mbar_init(&ifull[q], 1);
+            mbar_init(&iempty[q], TS_EPI / 32);
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mPool)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mWsh)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mLhi)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mLlo)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mVin)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mVout)) : "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const bool fwd = (p.job == TS_FWD);
+    const uint32_t bbytes = (uint32_t)(2 * np * 128);
+    const int KC = (int)p.KC;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------ producer ------------------------------
+            const CUtensorMap *amaps[4] = {&mPool, &mWsh, &mLhi, &mLlo};
+            int s = 0;
+            uint32_t ph = 0;
+            int slot = 0;
+            uint32_t sph = 0;
+            int issued = 0;
+            bool ok = true;
+            // A chunk c of the item (phase c / KC, K chunk c % KC) into stage st
+            auto load_a = [&](const ItemHdr &h, int c, uint8_t *st, uint64_t *bar) {
+                const int q = c / KC, kc = c % KC;
+                const CUtensorMap *m = amaps[h.amap[q]];
+                if (fwd) {
+                    tma_load_2d(st, m, kc * TS_KC, h.arow[q] + h.slab * TS_SLAB, bar);
+                } else {
+                    const int y = h.arow[q] + kc * TS_KC;
+                    tma_load_2d(st, m, h.slab * TS_SLAB, y, bar);
+                    tma_load_2d(st + TS_ABYTES / 2, m, h.slab * TS_SLAB + 64, y, bar);
+                }
+            };
+            auto load_b = [&](const ItemHdr &h, int c, uint8_t *st, uint64_t *bar) {
+                const int kc = c % KC;
+                const CUtensorMap *m = (h.type == IT_DIAG) ? &mVin : &mVout;
+                tma_load_2d(st + TS_ABYTES, m, (int)(h.src * p.b) + kc * TS_KC, 0, bar);
+            };
+            while (ok) {
+                int64_t t = atomicAdd(&p.flags[0], 1);
+                ItemHdr h;
+                if (t >= p.items) {
+                    memset(&h, 0, sizeof(h));
+                    h.type = IT_END;
+                } else {
+                    decode_item(p, t, h);
+                }
+                if (!wait_bar(&iempty[slot], sph ^ 1, p)) { ok = false; break; }
+                hdrs[slot] = h;
+                mbar_arrive(&ifull[slot]);
+                if (++slot == TS_IRING) { slot = 0; sph ^= 1; }
+                if (h.type == IT_END) break;
+                if (h.type == IT_CONV) continue;
+                const int nch = h.nph * KC;
+                // the first stages' A loads go out before the dependency wait
+                const int npre = min(NS, nch);
+                int pst[8];
+                for (int c = 0; c < npre && ok; ++c) {
+                    if (!wait_bar(&empty[s], ph ^ 1, p)) { ok = false; break; }
+                    uint8_t *st = smem + s * SB;
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)TS_ABYTES + bbytes);
+                    load_a(h, c, st, &full[s]);
+                    pst[c] = s;
+                    ++issued;
+                    if (++s == NS) { s = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                const int *dep = (h.type == IT_DIAG) ? done_ctr(p) + h.blk : ready_ctr(p) + h.src;
+                ok = wait_count(dep, 1, p);
+                fence_proxy_async_global();
+                // (after an abort too, so every issued stage completes and can be drained)
+                for (int c = 0; c < npre; ++c) load_b(h, c, smem + pst[c] * SB, &full[pst[c]]);
+                for (int c = npre; c < nch && ok; ++c) {
+                    if (!wait_bar(&empty[s], ph ^ 1, p)) { ok = false; break; }
+                    uint8_t *st = smem + s * SB;
+                    mbar_arrive_expect_tx(&full[s], (uint32_t)TS_ABYTES + bbytes);
+                    load_a(h, c, st, &full[s]);
+                    load_b(h, c, st, &full[s]);
+                    ++issued;
+                    if (++s == NS) { s = 0; ph ^= 1; }
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the loads of the last stages to land
+                const int n = issued < NS ? issued : NS;
+                int ss = s;
+                uint32_t pp = ph;
+                for (int e = 0; e < n; ++e) {
+                    if (--ss < 0) { ss = NS - 1; pp ^= 1; }
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < p.wait_ns) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------ MMA issuer ------------------------------
+            int s = 0;
+            uint32_t ph = 0;
+            int slot = 0;
+            uint32_t sph = 0;
+            int acc = 0;
+            uint32_t aph = 0;
+            bool ok = true, any = false;
+            const uint32_t bhalf = (uint32_t)(np * 128);
+            while (ok) {
+                if (!wait_bar(&ifull[slot], sph, p)) { ok = false; break; }
+                const ItemHdr h = hdrs[slot];
+                if (++slot == TS_IRING) { slot = 0; sph ^= 1; }
+                if (h.type == IT_END) break;
+                if (h.type == IT_CONV) continue;
+                if (!wait_bar(&tempty[acc], aph ^ 1, p)) { ok = false; break; }
+                tmem_fence_after();
+                const uint32_t tacc = tmem_base + (uint32_t)(acc * np);
+                const int nch = h.nph * KC;
+                for (int c = 0; c < nch; ++c) {
+                    if (!wait_bar(&full[s], ph, p)) { ok = false; break; }
+                    tmem_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * SB), sb = sa + TS_ABYTES;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = fwd ? desc_kmajor(sa + kk * 32) : desc_mnmajor(sa + kk * 2048);
+                        mma_f16(tacc, ad, desc_kmajor(sb + kk * 32), p.idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                        mma_f16(tacc, ad, desc_kmajor(sb + bhalf + kk * 32), p.idesc, 1u);
+                    }
+                    any = true;
+                    mma_commit(&empty[s]);
+                    if (++s == NS) { s = 0; ph ^= 1; }
+                }
+                if (!ok) break;
+                mma_commit(&tfull[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1; }
+            }
+            if (!ok && any) {
+                mma_commit(drain);
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < p.wait_ns) {}
+            }
+        }
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int tid = threadIdx.x - 64;
+        const int row = ((warp & 3) << 5) + lane;  // TMEM lane quarter of this warp
+        int slot = 0;
+        uint32_t sph = 0;
+        int acc = 0;
+        uint32_t aph = 0;
+        const int pc = p.pc;
+        const int64_t b = p.b, S = p.S;
+        // one thread waits, the group follows its decision
+        auto group_wait_bar = [&](uint64_t *bar, uint32_t parity) -> bool {
+            if (tid == 0) sflag[0] = wait_bar(bar, parity, p) ? 1 : 0;
+            epi_sync();
+            const bool r = sflag[0] != 0;
+            epi_sync();
+            return r;
+        };
+        while (true) {
+            if (!group_wait_bar(&ifull[slot], sph)) break;
+            const ItemHdr h = hdrs[slot];
+            epi_sync();
+            if (lane == 0) mbar_arrive(&iempty[slot]);
+            if (++slot == TS_IRING) { slot = 0; sph ^= 1; }
+            if (h.type == IT_END) break;
+            if (h.type == IT_CONV) {
+                convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid);
+                if (tid == 0) st_release(done_ctr(p) + h.blk, 1);
+                continue;
+            }
+            if (!group_wait_bar(&tfull[acc], aph)) break;
+            tmem_fence_after();
+            float v[TS_NPMAX];
+            const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * np);
+#pragma unroll
+            for (int c16 = 0; c16 < TS_NPMAX / 16; ++c16)
+                if (c16 * 16 < np) tmem_ld16(tacc + c16 * 16, v + c16 * 16);
+            tmem_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+            if (++acc == 2) { acc = 0; aph ^= 1; }
+            // column multipliers: 1 / (tile scale * vector block scale)
+            const float *sv = (h.type == IT_DIAG) ? p.sin + (int64_t)h.blk * np : p.sout + (int64_t)h.src * np;
+            if (tid < pc) smul[tid] = h.inv_tscale / __ldcg(sv + tid);
+            const int64_t grow = (int64_t)h.blk * b + (int64_t)h.slab * TS_SLAB + row;
+            if (h.type == IT_DIAG) {
+                epi_sync();
+                float *o = p.out + grow * p.ldx + p.q0;
+#pragma unroll
+                for (int q = 0; q < TS_NPMAX; ++q)
+                    if (q < pc) __stcg(o + q, v[q] * smul[q]);
+                __threadfence();
+                epi_sync();
+                if (tid == 0) sflag[1] = (atomicAdd(cout_ctr(p) + h.blk, 1) == (int)S - 1) ? 1 : 0;
+                epi_sync();
+                if (sflag[1]) {
+                    __threadfence();
+                    convert_block(p, p.out, h.blk, p.vout, p.sout, smax, sscale, tid);
+                    if (tid == 0) st_release(ready_ctr(p) + h.blk, 1);
+                }
+            } else {
+                // LINK: after the earlier updates of this slab
+                int *sq = seq_ctr(p) + (int64_t)h.blk * S + h.slab;
+                if (tid == 0) sflag[2] = wait_count(sq, h.seqv, p) ? 1 : 0;
+                epi_sync();
+                if (!sflag[2]) break;
+                float *y = p.rhs + grow * p.ldx + p.q0;
+#pragma unroll
+                for (int q = 0; q < TS_NPMAX; ++q)
+                    if (q < pc) __stcg(y + q, __ldcg(y + q) - v[q] * smul[q]);
+                __threadfence();
+                epi_sync();
+                if (tid == 0) {
+                    atomicAdd(sq, 1);
+                    sflag[1] = (h.last_link && atomicAdd(cin_ctr(p) + h.blk, 1) == (int)S - 1) ? 1 : 0;
+                }
+                epi_sync();
+                if (sflag[1]) {
+                    __threadfence();
+                    convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid);
+                    if (tid == 0) st_release(done_ctr(p) + h.blk, 1);
+                }
+            }
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tmem_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tcols) : "memory");
+    }
+}
+
+// Encoder of TMA descriptors (driver entry point, looked up once).
+typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encoder(Ctx *c) {
+    static EncodeFn fn = nullptr;
+    if (fn) return fn;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !f) {
+        cudaGetLastError();
+        c->last_error = "cuTensorMapEncodeTiled is not available from the driver";
+        return nullptr;
+    }
+    fn = (EncodeFn)f;
+    return fn;
+}
+
+// FP16 row-major matrix (rows x cols), boxes of 64 columns (128 bytes) x
+// box_rows, 128-byte swizzle.
+krr_status map_f16(Ctx *c, CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int box_rows) {
+    EncodeFn enc = encoder(c);
+    if (!enc) return KRR_ECUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(cols * 2)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->last_error = "cuTensorMapEncodeTiled (tensor-core sweep) failed with code " + std::to_string((int)r);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
+}
+
+constexpr size_t ts_smem_limit() { return 227 * 1024; }
+
+size_t ts_smem_bytes(int stages, int stage_bytes) {
+    return (size_t)stages * stage_bytes + TS_IRING * sizeof(ItemHdr) + (6 * TS_NPMAX + 4) * 4 +
+           (size_t)(2 * stages + 5 + 2 * TS_IRING) * 8 + 16 + 1024;
+}
+
+int64_t ts_flag_count(const Ctx *c) { return 2 + 4 * c->nt + c->nt * (c->b / TS_SLAB); }
+
+krr_status ensure_ts_buffers(Ctx *c) {
+    const size_t vbytes = (size_t)2 * TS_NPMAX * c->n_pad * sizeof(__half);
+    if (c->ts_vcap < vbytes) {
+        for (__half **v : {&c->ts_v0, &c->ts_v1}) {
+            if (*v) cudaFree(*v);
+            *v = nullptr;
+            if (cudaMalloc((void **)v, vbytes) != cudaSuccess) {
+                cudaGetLastError();
+                c->ts_vcap = 0;
+                c->last_error = "cudaMalloc failed for the sweep vector blocks";
+                return KRR_ENOMEM;
+            }
+        }
+        c->ts_vcap = vbytes;
+    }
+    const size_t sbytes = (size_t)2 * c->nt * TS_NPMAX * sizeof(float);
+    const size_t fbytes = (size_t)ts_flag_count(c) * sizeof(int);
+    if (c->ts_aux_cap < sbytes + fbytes) {
+        if (c->ts_aux) cudaFree(c->ts_aux);
+        c->ts_aux = nullptr;
+        if (cudaMalloc(&c->ts_aux, sbytes + fbytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->ts_aux_cap = 0;
+            c->last_error = "cudaMalloc failed for the sweep counters";
+            return KRR_ENOMEM;
+        }
+        c->ts_aux_cap = sbytes + fbytes;
+    }
+    return KRR_OK;
+}
+
+krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
+    const int64_t b = c->b, nt = c->nt;
+    if (b % TS_SLAB != 0) {
+        c->last_error = "tensor-core sweep: the tile edge must be a multiple of 128";
+        return KRR_EINVAL;
+    }
+    KRR_TRY(ensure_ts_buffers(c));
+    const bool fwd = (job == TS_FWD);
+    const int abox = fwd ? 128 : 64;
+    const int64_t noff = nt * (nt - 1) / 2;
+    CUtensorMap mp, mw, mlh, mll, mvi, mvo;
+    KRR_TRY(map_f16(c, &mp, c->pool, (int64_t)(c->pool_bytes / (2 * b)), b, abox));
+    // the E4M3 copies live in the trailing tiles (only read when such tiles exist)
+    KRR_TRY(map_f16(c, &mw, noff > 0 ? c->W : c->Linv_hi, (noff > 0 ? noff : 1) * b, b, abox));
+    KRR_TRY(map_f16(c, &mlh, c->Linv_hi, nt * b, b, abox));
+    KRR_TRY(map_f16(c, &mll, c->Linv_lo, nt * b, b, abox));
+    float *sbase = (float *)c->ts_aux;
+    int *flags = (int *)(sbase + 2 * nt * TS_NPMAX);
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(tcsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_limit());
+        if (e != cudaSuccess) {
+            c->last_error = std::string("cudaFuncSetAttribute (tensor-core sweep): ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+        attr = true;
+    }
+    for (int64_t q0 = 0; q0 < p; q0 += TS_NPMAX) {
+        TsParams sp;
+        memset(&sp, 0, sizeof(sp));
+        sp.job = job;
+        sp.b = b;
+        sp.nt = nt;
+        sp.S = b / TS_SLAB;
+        sp.KC = b / TS_KC;
+        sp.n_pad = c->n_pad;
+        sp.items = 1 + sp.S * nt * (nt + 1) / 2;
+        sp.pc = (int)std::min<int64_t>(TS_NPMAX, p - q0);
+        sp.np = (sp.pc + 15) & ~15;
+        sp.q0 = (int)q0;
+        sp.ldx = p;
+        sp.rhs = rhs;
+        sp.out = out;
+        sp.vin = c->ts_v0;
+        sp.vout = c->ts_v1;
+        sp.sin = sbase;
+        sp.sout = sbase + nt * TS_NPMAX;
+        sp.ltab = c->ltab;
+        sp.flags = flags;
+        sp.stage_bytes = TS_ABYTES + 2 * sp.np * 128;
+        int stages = 8;
+        while (stages > 2 && ts_smem_bytes(stages, sp.stage_bytes) > ts_smem_limit()) --stages;
+        sp.stages = stages;
+        // kind::f16, D = F32, A = B = F16, A K-major (forward) or MN-major
+        // (backward), B K-major, N = np, M = 128
+        sp.idesc = (1u << 4) | ((fwd ? 0u : 1u) << 15) | ((uint32_t)(sp.np >> 3) << 17) |
+                   ((uint32_t)(TS_SLAB >> 4) << 24);
+        sp.wait_ns = (uint64_t)c->opt.wait_budget_ns;
+        sp.err = c->derr;
+        KRR_TRY(map_f16(c, &mvi, c->ts_v0, 2 * sp.np, c->n_pad, 2 * sp.np));
+        KRR_TRY(map_f16(c, &mvo, c->ts_v1, 2 * sp.np, c->n_pad, 2 * sp.np));
+        KRR_CUDA_TRY(c, cudaMemsetAsync(flags, 0, (size_t)ts_flag_count(c) * sizeof(int), c->stream));
+        const size_t smem = ts_smem_bytes(stages, sp.stage_bytes);
+        const int64_t grid = std::min<int64_t>(sp.items, c->num_sms);
+        count_launch(), tcsweep_kernel<<<(unsigned)grid, TS_THREADS, smem, c->stream>>>(mp, mw, mlh, mll, mvi, mvo, sp);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            c->last_error = std::string("tensor-core sweep launch: ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+    }
+    return KRR_OK;
+}
+
+}  // namespace
+
+// x (n_pad x p) <- (L L^T)^-1 x with the stored mixed-precision factor on the
+// tensor cores: the forward sweep updates x in place and writes z to tmp, the
+// backward sweep updates tmp in place and writes the solution to x.
+krr_status tc_sweep_solve(Ctx *c, float *x, float *tmp, int64_t p) {
+    KRR_TRY(run_ts(c, TS_FWD, x, tmp, p));
+    return run_ts(c, TS_BWD, tmp, x, p);
+}
+
+}  // namespace krr
