@@ -75,10 +75,15 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 }
 
 // Bounded wait (one thread) until *c >= target; false on expiry / abort.
+// Polls back off exponentially (32 ns up to 256 ns) so that many waiting
+// CTAs do not flood the L2 slice holding the counters.
 __device__ bool wait_ge(const int *c, int target, const DiagParams &p) {
     if (ld_acquire(c) >= target) return true;
     const uint64_t t0 = globaltimer();
+    uint32_t nap = 32;
     for (uint32_t it = 1;; ++it) {
+        __nanosleep(nap);
+        if (nap < 256) nap <<= 1;
         if (ld_acquire(c) >= target) return true;
         if ((it & 15) == 0) {
             if (*(volatile int *)&p.ctr[1]) return false;
@@ -232,59 +237,171 @@ __device__ __forceinline__ void store_blk(float *C, int64_t ld, const float (&ac
 }
 
 // ---------------------------------------------------------------------------
-// P(q): Cholesky and inverse of the 64 x 64 diagonal block in shared memory
-// (right-looking, one column per step).  A pivot that is not positive is
-// recorded (first one wins) and replaced by 1 so the rest stays finite.
+// P(q): Cholesky and inverse of the 64 x 64 diagonal block in shared memory,
+// blocked by 16 (a pivot that is not positive is recorded, first one wins,
+// and replaced by 1 so the rest stays finite):
+//   for each 16-block q of the diagonal:
+//     warp 0 factors A_qq and inverts L_qq in registers (lane l owns row l;
+//     columns and rows are broadcast by warp shuffles);
+//     L_iq = A_iq X_qq^T for the 16-row blocks below (all threads);
+//     A_ij -= L_iq L_jq^T on the trailing lower triangle (all threads, 16 x 16
+//     thread grid, rows of L_iq / L_jq held in registers);
+//   then X = L^-1 below the diagonal blocks, by block diagonals:
+//     X_iq = -X_ii (sum_{k=q}^{i-1} L_ik X_kq).
+// a holds A on entry and L on exit, x receives X; tmp is 3 x 16 x 17 floats.
 // ---------------------------------------------------------------------------
+__device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17], float *dinv,
+                                            int &bad, float &mpiv) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const unsigned FULL = 0xffffffffu;
+    for (int e = t; e < 64 * 64; e += 256) x[e >> 6][e & 63] = 0.f;
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+        const int o = 16 * q;
+        if (warp == 0) {
+            const int l = lane & 15;
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = (j <= l) ? a[o + l][o + j] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                float d = __shfl_sync(FULL, v[c], c);
+                if (!(d > 0.f)) {
+                    if (bad < 0) bad = o + c;
+                    d = 1.f;
+                }
+                const float lcc = sqrtf(d), inv = 1.f / lcc;
+                mpiv = fminf(mpiv, lcc);
+                if (l == c) {
+                    v[c] = lcc;
+                    if (lane == c) dinv[o + c] = inv;
+                } else if (l > c) {
+                    v[c] *= inv;
+                }
+#pragma unroll
+                for (int j = c + 1; j < 16; ++j) {
+                    const float ljc = __shfl_sync(FULL, v[c], j);
+                    if (l >= j) v[j] = fmaf(-v[c], ljc, v[j]);
+                }
+            }
+            float xr[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) xr[k] = (k == l) ? 1.f : 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const float invc = 1.f / __shfl_sync(FULL, v[c], c);
+                if (l == c) {
+#pragma unroll
+                    for (int k = 0; k <= c; ++k) xr[k] *= invc;
+                }
+#pragma unroll
+                for (int k = 0; k <= c; ++k) {
+                    const float xck = __shfl_sync(FULL, xr[k], c);
+                    if (l > c) xr[k] = fmaf(-v[c], xck, xr[k]);
+                }
+            }
+            if (lane < 16) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (j <= l) {
+                        a[o + l][o + j] = v[j];
+                        x[o + l][o + j] = xr[j];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        const int rows = 64 - o - 16;
+        if (rows > 0) {
+            const int tc = t & 15, tr = t >> 4;
+            float res[3];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int rr = tr + 16 * u;
+                if (rr < rows) {
+                    const int i = o + 16 + rr, c = o + tc;
+                    float acc = 0.f;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) acc = fmaf(a[i][o + k], x[c][o + k], acc);
+                    res[u] = acc;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                const int rr = tr + 16 * u;
+                if (rr < rows) a[o + 16 + rr][o + tc] = res[u];
+            }
+            __syncthreads();
+            const int nb = rows / 16;
+            float li[3][16], lj[3][16];
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+                if (u < nb) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        li[u][k] = a[o + 16 + tr + 16 * u][o + k];
+                        lj[u][k] = a[o + 16 + tc + 16 * u][o + k];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+#pragma unroll
+                for (int w = 0; w < 3; ++w) {
+                    if (u < nb && w <= u) {
+                        const int i = o + 16 + tr + 16 * u, j = o + 16 + tc + 16 * w;
+                        if (i >= j) {
+                            float acc = 0.f;
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) acc = fmaf(li[u][k], lj[w][k], acc);
+                            a[i][j] -= acc;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // off-diagonal blocks of X = L^-1: X_iq = -X_ii sum_{k=q}^{i-1} L_ik X_kq
+    const int tc = t & 15, tr = t >> 4;
+    for (int dd = 1; dd < 4; ++dd) {
+        const int npair = 4 - dd;
+        for (int qq = 0; qq < npair; ++qq) {
+            const int ib = qq + dd;
+            float acc = 0.f;
+            for (int kb = qq; kb < ib; ++kb) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) acc = fmaf(a[16 * ib + tr][16 * kb + k], x[16 * kb + k][16 * qq + tc], acc);
+            }
+            tmp[qq][tr][tc] = acc;
+        }
+        __syncthreads();
+        for (int qq = 0; qq < npair; ++qq) {
+            const int ib = qq + dd;
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc = fmaf(x[16 * ib + tr][16 * ib + k], tmp[qq][k][tc], acc);
+            x[16 * ib + tr][16 * qq + tc] = -acc;
+        }
+        __syncthreads();
+    }
+}
+
 __device__ void potrf_inv_block(const DiagParams &p, int q, BlkSmem &s) {
     float (*a)[DB + 1] = s.a;
     float (*x)[DB + 1] = s.b;
     const int64_t b = p.b;
     float *blk = p.W + (int64_t)q * DB * b + q * DB;
-    __shared__ int bad;
-    __shared__ float mpiv;
+    __shared__ float dinv[DB];
+    __shared__ float tmp[3][16][17];
     const int tx = threadIdx.x & (DB - 1), ty = threadIdx.x / DB;  // 4 row groups
     constexpr int RS = DT / DB;
-    for (int r = ty; r < DB; r += RS) {
-        a[r][tx] = __ldcg(blk + (int64_t)r * b + tx);
-        x[r][tx] = (r == tx) ? 1.f : 0.f;
-    }
-    if (threadIdx.x == 0) {
-        bad = -1;
-        mpiv = 3.0e38f;
-    }
+    for (int r = ty; r < DB; r += RS) a[r][tx] = __ldcg(blk + (int64_t)r * b + tx);
     __syncthreads();
-    for (int c = 0; c < DB; ++c) {
-        if (threadIdx.x == 0) {
-            float d = a[c][c];
-            if (!(d > 0.f)) {
-                if (bad < 0) bad = c;
-                d = 1.f;
-            }
-            a[c][c] = sqrtf(d);
-            mpiv = fminf(mpiv, a[c][c]);
-        }
-        __syncthreads();
-        if (ty == 0 && tx > c) a[tx][c] /= a[c][c];
-        __syncthreads();
-        if (tx > c) {
-            const float lsc = a[tx][c];
-            for (int r = ty; r < DB; r += RS)
-                if (r >= tx) a[r][tx] -= a[r][c] * lsc;
-        }
-        __syncthreads();
-    }
-    // inverse: row c of X is final after the division; then rows r > c
-    for (int c = 0; c < DB; ++c) {
-        if (ty == 0 && tx <= c) x[c][tx] /= a[c][c];
-        __syncthreads();
-        if (tx <= c) {
-            const float xc = x[c][tx];
-            for (int r = ty; r < DB; r += RS)
-                if (r > c) x[r][tx] -= a[r][c] * xc;
-        }
-        __syncthreads();
-    }
+    int bad = -1;
+    float mpiv = 3.0e38f;
+    chol_inv_64(a, x, tmp, dinv, bad, mpiv);
     float *iblk = p.X + (int64_t)q * DB * b + q * DB;
     for (int r = ty; r < DB; r += RS) {
         __stcg(blk + (int64_t)r * b + tx, (tx <= r) ? a[r][tx] : 0.f);

@@ -217,6 +217,10 @@ bool mixed(const Ctx *c) { return c->opt.mode == KRR_MODE_MIXED; }
 }  // namespace
 
 namespace {
+// Scratch of the residual-norm reduction: the last norm_partial_count()
+// doubles of the reduction buffer.
+double *red_norm_part(Ctx *c) { return c->red + c->red_cap - norm_partial_count(); }
+
 // Allocates (or keeps) the n_pad x p work vectors of the solve.
 krr_status ensure_vectors(Ctx *c, int64_t p) {
     const int64_t cnt = c->n_pad * p;
@@ -266,7 +270,7 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
             launch_add_scaled(c->abuf, c->dabuf, 1.0f, cnt, s);
         }
         KRR_TRY(launch_residual(c, c->ybuf, c->abuf, c->rbuf, p));
-        launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
+        launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, red_norm_part(c), s);
         KRR_TRY(check_launch(c, "refinement (graph mode)"));
         if (info) *info = si;
         return KRR_OK;
@@ -277,7 +281,7 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
         for (int it = 0;; ++it) {
             int rr = prof_begin(c, KRR_PROF_RESIDUAL);
             KRR_TRY(launch_residual(c, c->ybuf, c->abuf, c->rbuf, p));
-            launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, s);
+            launch_reduce_norms(c->rbuf, c->ybuf, c->n_pad, p, c->red + RED_RNORM, red_norm_part(c), s);
             // the lower-triangle K tiles are read once by the row pass and
             // once by the column pass
             prof_end(c, rr, 2.0 * (double)c->n_pad * c->n_pad * p, 2.0 * (double)c->kd_bytes);
@@ -510,7 +514,7 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
     c->nt = nt;
     c->n_pad = n_pad;
     c->gamma = gamma;
-    const size_t red_count = RED_MINPIV + (size_t)nt * (b / 64) + (size_t)nt + 16;
+    const size_t red_count = RED_MINPIV + (size_t)nt * (b / 64) + (size_t)nt + 16 + (size_t)norm_partial_count();
     if (c->red_cap < red_count) {
         KRR_TRY(dev_alloc(c, &c->red, red_count, "reduction buffer"));
         c->red_cap = red_count;

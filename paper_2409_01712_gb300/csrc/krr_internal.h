@@ -229,6 +229,8 @@ krr_status solve_inplace(Ctx *c, float *x, float *tmp, int64_t p);
 krr_status sweep_solve(Ctx *c, float *x, float *tmp, int64_t p);
 // The two substitutions on the tensor cores (tcsweep.cu, mixed mode).
 krr_status tc_sweep_solve(Ctx *c, float *x, float *tmp, int64_t p);
+// The refinement residual on the tensor cores (tcsweep.cu, mixed mode).
+krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
 krr_status sweep_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p);
 
 // r = y - (K + lambda I) a (FP64 accumulation), norms into c->red.
@@ -240,7 +242,10 @@ void launch_factor_init(Ctx *c);
 
 // Small helpers.
 void launch_fill_zero(void *p, size_t bytes, cudaStream_t s);
-void launch_reduce_norms(const double *r, const float *y, int64_t n, int64_t p, double *out,
+// part: norm_partial_count() doubles of scratch (the context's reduction buffer
+// keeps them after its other slots, see red_norm_part()).
+constexpr int64_t norm_partial_count() { return 2 * 256; }
+void launch_reduce_norms(const double *r, const float *y, int64_t n, int64_t p, double *out, double *part,
                          cudaStream_t s);
 void launch_axpy_r(const double *r, float *dst, int64_t count, cudaStream_t s);
 void launch_add_scaled(float *a, const float *da, float alpha, int64_t count, cudaStream_t s);

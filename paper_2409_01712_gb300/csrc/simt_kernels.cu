@@ -851,16 +851,41 @@ __global__ void colsum_kernel(const float *a, int64_t n, int64_t p, double *out)
 
 krr_status launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
     count_launch(), colsum_kernel<<<(unsigned)p, 512, 0, c->stream>>>(a, c->n_pad, p, c->colsum);
-    return sweep_residual(c, y, a, r, p);
+    return c->opt.mode == KRR_MODE_MIXED ? tc_residual(c, y, a, r, p) : sweep_residual(c, y, a, r, p);
 }
 
-// ||r||_F^2 and ||y||_F^2 into out[0], out[1] (deterministic single block).
-__global__ void reduce_norms_kernel(const double *r, const float *y, int64_t count, double *out) {
+// ||r||_F^2 and ||y||_F^2 into out[0], out[1]: fixed per-block partial sums
+// (NORM_BLOCKS blocks, grid-stride), then one block adds them in order, so
+// the result is deterministic.
+constexpr int NORM_BLOCKS = 256;
+
+__global__ void norm_partial_kernel(const double *r, const float *y, int64_t count, double *part) {
     __shared__ double s1[32], s2[32];
     double a = 0, bsum = 0;
-    for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
         a += r[e] * r[e];
         bsum += (double)y[e] * (double)y[e];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        bsum += __shfl_down_sync(0xffffffffu, bsum, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s1[threadIdx.x >> 5] = a; s2[threadIdx.x >> 5] = bsum; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, z = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { x += s1[w]; z += s2[w]; }
+        part[blockIdx.x] = x;
+        part[gridDim.x + blockIdx.x] = z;
+    }
+}
+
+__global__ void norm_final_kernel(const double *part, int nb, double *out) {
+    __shared__ double s1[32], s2[32];
+    double a = 0, bsum = 0;
+    for (int e = threadIdx.x; e < nb; e += blockDim.x) {
+        a += part[e];
+        bsum += part[nb + e];
     }
     for (int o = 16; o > 0; o >>= 1) {
         a += __shfl_down_sync(0xffffffffu, a, o);
@@ -876,9 +901,10 @@ __global__ void reduce_norms_kernel(const double *r, const float *y, int64_t cou
     }
 }
 
-void launch_reduce_norms(const double *r, const float *y, int64_t n, int64_t p, double *out,
+void launch_reduce_norms(const double *r, const float *y, int64_t n, int64_t p, double *out, double *part,
                          cudaStream_t s) {
-    count_launch(), reduce_norms_kernel<<<1, 1024, 0, s>>>(r, y, n * p, out);
+    count_launch(), norm_partial_kernel<<<NORM_BLOCKS, 256, 0, s>>>(r, y, n * p, part);
+    count_launch(), norm_final_kernel<<<1, 256, 0, s>>>(part, NORM_BLOCKS, out);
 }
 
 __global__ void d2f_kernel(const double *r, float *dst, int64_t count) {

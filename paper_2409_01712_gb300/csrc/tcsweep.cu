@@ -54,7 +54,7 @@ constexpr int TS_EPI = 128;
 constexpr int TS_SLAB = 128;             // output rows of an item (MMA M)
 constexpr int TS_KC = 64;                // K elements of a stage (128 bytes of FP16)
 constexpr int TS_ABYTES = TS_SLAB * 128;  // A bytes of a stage
-constexpr int TS_NPMAX = 64;             // right-hand sides per launch
+constexpr int TS_NPMAX = 32;             // right-hand sides per launch
 constexpr int TS_IRING = 4;              // item header slots
 
 enum { TS_FWD = 0, TS_BWD = 1 };
@@ -171,10 +171,15 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, const T
 }
 
 // Bounded wait until a progress counter reaches `target`.
+// Polls back off exponentially (32 ns up to 256 ns) so that many waiting
+// CTAs do not flood the L2 slice holding the counter.
 __device__ __forceinline__ bool wait_count(const int *ctr, int target, const TsParams &p) {
     if (ld_acquire(ctr) >= target) return true;
     const uint64_t t0 = globaltimer();
+    uint32_t nap = 32;
     for (uint32_t it = 1;; ++it) {
+        __nanosleep(nap);
+        if (nap < 256) nap <<= 1;
         if (ld_acquire(ctr) >= target) return true;
         if ((it & 15) == 0) {
             if (aborted(p)) return false;
@@ -324,12 +329,16 @@ __device__ void decode_item(const TsParams &p, int64_t t, ItemHdr &h) {
 
 // ---------------------------------------------------------------------------
 // Block conversion (128 epilogue threads): v rows [blk b, +b), columns
-// [q0, q0 + pc) -> FP16 pair with the power-of-two scale s_q putting the
+// [q0, q0 + pc) -> FP16 terms with the power-of-two scale s_q putting the
 // column maximum in [4096, 8192) (8x headroom below the FP16 maximum):
-// hi = fp16(s v), lo = fp16(s v - hi); padding columns [pc, np) are zero.
+// two terms hi = fp16(s v), lo = fp16(s v - hi) (about 22 significant bits),
+// or three, hi, mid = fp16(s v - hi), lo = fp16(s v - hi - mid), which hold
+// an FP32 value exactly down to 2^-14 of the column maximum (below that the
+// absolute error stays under 2^-38 of the maximum).  Planes of np rows each;
+// padding columns [pc, np) are zero.
 // ---------------------------------------------------------------------------
 __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __half *vb, float *sv,
-                              float *smax, float *sscale, int tid) {
+                              float *smax, float *sscale, int tid, int terms = 2) {
     const int64_t b = p.b, n_pad = p.n_pad;
     const int pc = p.pc, np = p.np;
     float mx[TS_NPMAX];
@@ -369,20 +378,31 @@ __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __
     for (int64_t r = tid; r < b; r += TS_EPI) {
         const int64_t grow = blk * b + r;
         const float *row = v + grow * p.ldx + p.q0;
+        // the row's loads first (the FP16 stores below may alias them)
+        float xv[TS_NPMAX];
+#pragma unroll
+        for (int q = 0; q < TS_NPMAX; ++q)
+            if (q < pc) xv[q] = __ldcg(row + q);
 #pragma unroll
         for (int q = 0; q < TS_NPMAX; ++q) {
             if (q < np) {
-                const float x = (q < pc) ? __ldcg(row + q) * sscale[q] : 0.f;
+                const float x = (q < pc) ? xv[q] * sscale[q] : 0.f;
                 const __half h = __float2half_rn(x);
+                const float r1 = x - __half2float(h);  // exact
+                const __half m = __float2half_rn(r1);
                 vb[(int64_t)q * n_pad + grow] = h;
-                vb[(int64_t)(np + q) * n_pad + grow] = __float2half_rn(x - __half2float(h));
+                vb[(int64_t)(np + q) * n_pad + grow] = m;
+                if (terms == 3) vb[(int64_t)(2 * np + q) * n_pad + grow] = __float2half_rn(r1 - __half2float(m));
             }
         }
     }
-    // the block is read next by TMA (async proxy) on other SMs
-    fence_proxy_async_global();
-    __threadfence();
+    // publish: the block is read next by TMA (async proxy) on other SMs; the
+    // caller's thread 0 releases the flag after this barrier
     epi_sync();
+    if (tid == 0) {
+        __threadfence();
+        fence_proxy_async_global();
+    }
 }
 
 __global__ void __launch_bounds__(TS_THREADS, 1)
@@ -406,7 +426,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int np = p.np;
-    const uint32_t tcols = (np * 2 <= 32) ? 32u : (np * 2 <= 64 ? 64u : 128u);
+    // two accumulators of 2 np columns: products with the hi half of B, then
+    // with the lo half (one MMA of N = 2 np per K step reads A once)
+    const uint32_t tcols = (np * 4 <= 32) ? 32u : (np * 4 <= 64 ? 64u : (np * 4 <= 128 ? 128u : 256u));
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
@@ -418,7 +440,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         }
         for (int q = 0; q < TS_IRING; ++q) {
             mbar_init(&ifull[q], 1);
-            mbar_init(&iempty[q], TS_EPI / 32);
+            mbar_init(&iempty[q], TS_EPI / 32 + 1);  // epilogue warps and the MMA thread
         }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -539,16 +561,16 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             int acc = 0;
             uint32_t aph = 0;
             bool ok = true, any = false;
-            const uint32_t bhalf = (uint32_t)(np * 128);
             while (ok) {
                 if (!wait_bar(&ifull[slot], sph, p)) { ok = false; break; }
                 const ItemHdr h = hdrs[slot];
+                mbar_arrive(&iempty[slot]);
                 if (++slot == TS_IRING) { slot = 0; sph ^= 1; }
                 if (h.type == IT_END) break;
                 if (h.type == IT_CONV) continue;
                 if (!wait_bar(&tempty[acc], aph ^ 1, p)) { ok = false; break; }
                 tmem_fence_after();
-                const uint32_t tacc = tmem_base + (uint32_t)(acc * np);
+                const uint32_t tacc = tmem_base + (uint32_t)(acc * 2 * np);
                 const int nch = h.nph * KC;
                 for (int c = 0; c < nch; ++c) {
                     if (!wait_bar(&full[s], ph, p)) { ok = false; break; }
@@ -557,8 +579,8 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk) {
                         const uint64_t ad = fwd ? desc_kmajor(sa + kk * 32) : desc_mnmajor(sa + kk * 2048);
+                        // B rows [0, np) = hi half, [np, 2 np) = lo half
                         mma_f16(tacc, ad, desc_kmajor(sb + kk * 32), p.idesc, (c > 0 || kk > 0) ? 1u : 0u);
-                        mma_f16(tacc, ad, desc_kmajor(sb + bhalf + kk * 32), p.idesc, 1u);
                     }
                     any = true;
                     mma_commit(&empty[s]);
@@ -607,10 +629,17 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             if (!group_wait_bar(&tfull[acc], aph)) break;
             tmem_fence_after();
             float v[TS_NPMAX];
-            const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * np);
+            const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * 2 * np);
 #pragma unroll
-            for (int c16 = 0; c16 < TS_NPMAX / 16; ++c16)
-                if (c16 * 16 < np) tmem_ld16(tacc + c16 * 16, v + c16 * 16);
+            for (int c16 = 0; c16 < TS_NPMAX / 16; ++c16) {
+                if (c16 * 16 < np) {
+                    float hv[16], lv[16];
+                    tmem_ld16(tacc + c16 * 16, hv);
+                    tmem_ld16(tacc + np + c16 * 16, lv);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[c16 * 16 + e] = hv[e] + lv[e];
+                }
+            }
             tmem_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
@@ -625,12 +654,15 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 #pragma unroll
                 for (int q = 0; q < TS_NPMAX; ++q)
                     if (q < pc) __stcg(o + q, v[q] * smul[q]);
-                __threadfence();
                 epi_sync();
-                if (tid == 0) sflag[1] = (atomicAdd(cout_ctr(p) + h.blk, 1) == (int)S - 1) ? 1 : 0;
+                if (tid == 0) {
+                    __threadfence();
+                    const bool last = atomicAdd(cout_ctr(p) + h.blk, 1) == (int)S - 1;
+                    if (last) __threadfence();  // the other slabs' rows are read next
+                    sflag[1] = last ? 1 : 0;
+                }
                 epi_sync();
                 if (sflag[1]) {
-                    __threadfence();
                     convert_block(p, p.out, h.blk, p.vout, p.sout, smax, sscale, tid);
                     if (tid == 0) st_release(ready_ctr(p) + h.blk, 1);
                 }
@@ -641,18 +673,25 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 epi_sync();
                 if (!sflag[2]) break;
                 float *y = p.rhs + grow * p.ldx + p.q0;
+                // all loads of the row first: the stores may alias them, so
+                // interleaving would serialise the L2 round trips
+                float yv[TS_NPMAX];
 #pragma unroll
                 for (int q = 0; q < TS_NPMAX; ++q)
-                    if (q < pc) __stcg(y + q, __ldcg(y + q) - v[q] * smul[q]);
-                __threadfence();
+                    if (q < pc) yv[q] = __ldcg(y + q);
+#pragma unroll
+                for (int q = 0; q < TS_NPMAX; ++q)
+                    if (q < pc) __stcg(y + q, yv[q] - v[q] * smul[q]);
                 epi_sync();
                 if (tid == 0) {
+                    __threadfence();
                     atomicAdd(sq, 1);
-                    sflag[1] = (h.last_link && atomicAdd(cin_ctr(p) + h.blk, 1) == (int)S - 1) ? 1 : 0;
+                    const bool last = h.last_link && atomicAdd(cin_ctr(p) + h.blk, 1) == (int)S - 1;
+                    if (last) __threadfence();  // the other slabs' rows are read next
+                    sflag[1] = last ? 1 : 0;
                 }
                 epi_sync();
                 if (sflag[1]) {
-                    __threadfence();
                     convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid);
                     if (tid == 0) st_release(done_ctr(p) + h.blk, 1);
                 }
@@ -665,6 +704,379 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
         tmem_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tcols) : "memory");
     }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement residual on the tensor cores:
+//   r = y - lambda a - sum_j (K_ij - c) a_j - c 1 (1^T a)      (FP64 output)
+// with K the FP32 kernel tiles (lower triangle; block row i reads the row
+// slabs of tiles (i, j <= i) and the column slabs of tiles (j > i, i)) and c
+// the shift (mean off-diagonal entry of K), which keeps the products small.
+// Item (i, s) = 128 rows of block i, one accumulation per tile j:
+//   warp 0      producer: TMA of the FP32 K chunk (128 x 64 rows x columns, or
+//               64 x 128 for a column slab) into a staging ring, and of the
+//               FP16 pair of a_j (B) into the operand ring;
+//   warps 6..9  converters: (K - c) 2^12 -> FP16 pair (hi, lo) in the operand
+//               ring, in the MMA's K-major or MN-major 128-byte-swizzled layout;
+//   warp 1      MMA: A_hi x [B_hi; B_mid; B_lo] (N = 3 np) and A_lo x [B_hi;
+//               B_mid] (N = 2 np); a is split into three FP16 terms (exact for
+//               FP32 values), K - c into two (about 22 bits of a quantity
+//               already small); the dropped products are below 2^-33;
+//   warps 2..5  epilogue: per 64-wide chunk, the three FP32 accumulator
+//               parts are summed, de-scaled exactly (powers of two) and added
+//               to a two-term FP32 (TwoSum) accumulator, so each FP32 sum in
+//               TMEM spans only 64 products.
+// Operands exactly representing the FP32 inputs, exact FP16 products and
+// FP32 accumulation: the residual keeps FP32 accuracy.
+// Every wait is bounded and ends the kernel with KRR_ETIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int RS_THREADS = 320;
+constexpr int RS_STG = 32768;      // FP32 chunk: 128 x 64 or 64 x 128
+constexpr int RS_NSTG = 3;
+constexpr int RS_NOP = 2;
+constexpr float RS_KSCALE = 4096.f;  // (K - c) * 2^12 in FP16 (|K - c| <= 1)
+
+struct RsParams {
+    int64_t b, nt, S, KC, items, n_pad;
+    int np, pc, q0;
+    int64_t ldx;
+    const float *y, *a;
+    double *r;
+    const double *shift, *colsum;
+    float lambda;
+    const float *sa;        // scales of the FP16 pair of a, [nt][np]
+    int *flags;             // [0] item counter, [1] abort
+    int op_bytes;
+    uint32_t idesc_k, idesc_mn, idesc_k2, idesc_mn2;  // N = 3 np and N = 2 np
+    uint64_t wait_ns;
+    DevErrors *err;
+};
+
+__device__ __forceinline__ bool rs_aborted(const RsParams &p) { return *(volatile int *)&p.flags[1] != 0; }
+
+__device__ __forceinline__ bool rs_wait(uint64_t *bar, uint32_t parity, const RsParams &p) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31) == 0) {
+            if (rs_aborted(p)) return false;
+            if (globaltimer() - t0 > p.wait_ns) {
+                atomicExch(&p.flags[1], 1);
+                atomicCAS(&p.err->code, 0, (int)KRR_ETIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS, 1)
+    tcres_kernel(const __grid_constant__ CUtensorMap mK128, const __grid_constant__ CUtensorMap mK64,
+                 const __grid_constant__ CUtensorMap mA, const RsParams p) {
+    extern __shared__ __align__(1024) uint8_t rs_smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(rs_smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *stg = smem;                                   // RS_NSTG x 32 KB
+    uint8_t *ops = smem + RS_NSTG * RS_STG;                // RS_NOP x op_bytes
+    int64_t *items = reinterpret_cast<int64_t *>(ops + RS_NOP * p.op_bytes);  // item ring
+    uint64_t *bars = reinterpret_cast<uint64_t *>(items + TS_IRING);
+    uint64_t *sfull = bars, *sempty = bars + RS_NSTG, *ofull = bars + 2 * RS_NSTG,
+             *oempty = bars + 2 * RS_NSTG + RS_NOP, *tfull = bars + 2 * RS_NSTG + 2 * RS_NOP,
+             *tempty = tfull + 2, *ifull = tempty + 2, *iempty = ifull + TS_IRING, *drain = iempty + TS_IRING;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int np = p.np;
+    const uint32_t tcols = (np * 6 <= 128) ? 128u : 256u;  // two accumulators of 3 np columns
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < RS_NSTG; ++q) {
+            mbar_init(&sfull[q], 1);
+            mbar_init(&sempty[q], 4);      // converter warps
+        }
+        for (int q = 0; q < RS_NOP; ++q) {
+            mbar_init(&ofull[q], 1 + 4);   // producer (B bytes) + converter warps (A)
+            mbar_init(&oempty[q], 1);      // MMA commit
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);      // epilogue warps
+        }
+        for (int q = 0; q < TS_IRING; ++q) {
+            mbar_init(&ifull[q], 1);
+            mbar_init(&iempty[q], 4 + 4 + 1);  // epilogue, converter warps, MMA thread
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mK128)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mK64)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA)) : "memory");
+    }
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int64_t b = p.b, nt = p.nt, S = p.S;
+    const int KC = (int)p.KC;
+    const uint32_t bbytes = (uint32_t)(3 * np * 128);
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------ producer ------------------------------
+            int ss = 0, os = 0, slot = 0;
+            uint32_t sph = 0, oph = 0, iph = 0;
+            int issued_s = 0, issued_o = 0;
+            bool ok = true;
+            while (ok) {
+                const int64_t t = atomicAdd(&p.flags[0], 1);
+                if (!rs_wait(&iempty[slot], iph ^ 1, p)) { ok = false; break; }
+                items[slot] = (t < p.items) ? t : -1;
+                mbar_arrive(&ifull[slot]);
+                if (++slot == TS_IRING) { slot = 0; iph ^= 1; }
+                if (t >= p.items) break;
+                const int64_t i = t / S, sl = t % S;
+                for (int64_t j = 0; j < nt && ok; ++j) {
+                    for (int kc = 0; kc < KC && ok; ++kc) {
+                        if (!rs_wait(&sempty[ss], sph ^ 1, p)) { ok = false; break; }
+                        uint8_t *st = stg + ss * RS_STG;
+                        mbar_arrive_expect_tx(&sfull[ss], RS_STG);
+                        if (j <= i) {
+                            // row slab of tile (i, j): rows [sl 128, +128), columns [kc 64, +64)
+                            const int y = (int)(tri_index(i, j) * b + sl * TS_SLAB);
+                            tma_load_2d(st, &mK128, kc * 64, y, &sfull[ss]);
+                            tma_load_2d(st + RS_STG / 2, &mK128, kc * 64 + 32, y, &sfull[ss]);
+                        } else {
+                            // column slab of tile (j, i): rows [kc 64, +64), columns [sl 128, +128)
+                            const int y = (int)(tri_index(j, i) * b + kc * 64);
+                            for (int e = 0; e < 4; ++e)
+                                tma_load_2d(st + e * (RS_STG / 4), &mK64, (int)(sl * TS_SLAB) + 32 * e, y, &sfull[ss]);
+                        }
+                        ++issued_s;
+                        if (++ss == RS_NSTG) { ss = 0; sph ^= 1; }
+                        if (!rs_wait(&oempty[os], oph ^ 1, p)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&ofull[os], bbytes);
+                        tma_load_2d(ops + os * p.op_bytes + 32768, &mA, (int)(j * b) + kc * 64, 0, &ofull[os]);
+                        ++issued_o;
+                        if (++os == RS_NOP) { os = 0; oph ^= 1; }
+                    }
+                }
+            }
+            if (!ok) {
+                // drain the copies in flight (bounded)
+                int n = issued_s < RS_NSTG ? issued_s : RS_NSTG;
+                int q = ss;
+                uint32_t pp = sph;
+                for (int e = 0; e < n; ++e) {
+                    if (--q < 0) { q = RS_NSTG - 1; pp ^= 1; }
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&sfull[q], pp) && globaltimer() - t0 < p.wait_ns) {}
+                }
+                n = issued_o < RS_NOP ? issued_o : RS_NOP;
+                q = os;
+                pp = oph;
+                for (int e = 0; e < n; ++e) {
+                    if (--q < 0) { q = RS_NOP - 1; pp ^= 1; }
+                    const uint64_t t0 = globaltimer();
+                    // the B bytes of the stage (its converter arrivals may be missing)
+                    while (!mbar_try_wait(&ofull[q], pp) && globaltimer() - t0 < p.wait_ns) {}
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------ MMA issuer ------------------------------
+            int os = 0, slot = 0, acc = 0;
+            uint32_t oph = 0, iph = 0, aph = 0;
+            bool ok = true, any = false;
+            while (ok) {
+                if (!rs_wait(&ifull[slot], iph, p)) { ok = false; break; }
+                const int64_t t = items[slot];
+                mbar_arrive(&iempty[slot]);
+                if (++slot == TS_IRING) { slot = 0; iph ^= 1; }
+                if (t < 0) break;
+                const int64_t i = t / S;
+                for (int64_t j = 0; j < nt && ok; ++j) {
+                    const bool kmaj = (j <= i);
+                    for (int kc = 0; kc < KC; ++kc) {
+                        // one accumulation per 64-wide chunk, folded into FP64
+                        // by the epilogue: the FP32 sums in TMEM stay short
+                        if (!rs_wait(&tempty[acc], aph ^ 1, p)) { ok = false; break; }
+                        tmem_fence_after();
+                        const uint32_t tacc = tmem_base + (uint32_t)(acc * 3 * np);
+                        if (!rs_wait(&ofull[os], oph, p)) { ok = false; break; }
+                        tmem_fence_after();
+                        const uint32_t sa = smem_u32(ops + os * p.op_bytes), sb = sa + 32768;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t bd = desc_kmajor(sb + kk * 32);
+                            if (kmaj) {
+                                mma_f16(tacc, desc_kmajor(sa + kk * 32), bd, p.idesc_k, kk > 0 ? 1u : 0u);
+                                mma_f16(tacc, desc_kmajor(sa + 16384 + kk * 32), bd, p.idesc_k2, 1u);
+                            } else {
+                                mma_f16(tacc, desc_mnmajor(sa + kk * 2048), bd, p.idesc_mn, kk > 0 ? 1u : 0u);
+                                mma_f16(tacc, desc_mnmajor(sa + 16384 + kk * 2048), bd, p.idesc_mn2, 1u);
+                            }
+                        }
+                        any = true;
+                        mma_commit(&oempty[os]);
+                        if (++os == RS_NOP) { os = 0; oph ^= 1; }
+                        mma_commit(&tfull[acc]);
+                        if (++acc == 2) { acc = 0; aph ^= 1; }
+                    }
+                }
+            }
+            if (!ok && any) {
+                mma_commit(drain);
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < p.wait_ns) {}
+            }
+        }
+    } else if (warp >= 6) {
+        // ------------------------------ converters ------------------------------
+        const int ct = threadIdx.x - 192;
+        const float c = (float)*p.shift;
+        int ss = 0, os = 0, slot = 0;
+        uint32_t sph = 0, oph = 0, iph = 0;
+        bool ok = true;
+        while (ok) {
+            if (!__all_sync(0xffffffffu, rs_wait(&ifull[slot], iph, p))) break;
+            const int64_t t = items[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&iempty[slot]);
+            if (++slot == TS_IRING) { slot = 0; iph ^= 1; }
+            if (t < 0) break;
+            const int64_t i = t / S;
+            for (int64_t j = 0; j < nt && ok; ++j) {
+                const bool kmaj = (j <= i);
+                // thread -> (row r of the staged chunk, 64-value half h)
+                const int r = kmaj ? ct : (ct >> 1), h = kmaj ? 0 : (ct & 1);
+                const int boxb = kmaj ? RS_STG / 2 : RS_STG / 4;
+                for (int kc = 0; kc < KC; ++kc) {
+                    if (!__all_sync(0xffffffffu, rs_wait(&sfull[ss], sph, p))) { ok = false; break; }
+                    if (!__all_sync(0xffffffffu, rs_wait(&oempty[os], oph ^ 1, p))) { ok = false; break; }
+                    const uint8_t *src = stg + ss * RS_STG + r * 128;
+                    uint8_t *dst = ops + os * p.op_bytes + h * 8192 + r * 128;
+                    float v[64];
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float4 f = *reinterpret_cast<const float4 *>(src + (2 * h + e) * boxb + ((u ^ (r & 7)) << 4));
+                            v[e * 32 + 4 * u] = f.x; v[e * 32 + 4 * u + 1] = f.y;
+                            v[e * 32 + 4 * u + 2] = f.z; v[e * 32 + 4 * u + 3] = f.w;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        uint4 hv, lv;
+                        __half2 *hh = reinterpret_cast<__half2 *>(&hv), *ll = reinterpret_cast<__half2 *>(&lv);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float x0 = (v[8 * u + 2 * e] - c) * RS_KSCALE, x1 = (v[8 * u + 2 * e + 1] - c) * RS_KSCALE;
+                            const __half2 hx = __floats2half2_rn(x0, x1);
+                            const float2 hf = __half22float2(hx);
+                            hh[e] = hx;
+                            ll[e] = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+                        }
+                        const int off = (u ^ (r & 7)) << 4;
+                        *reinterpret_cast<uint4 *>(dst + off) = hv;
+                        *reinterpret_cast<uint4 *>(dst + 16384 + off) = lv;
+                    }
+                    // generic-proxy writes, read next by the tensor cores
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(&ofull[os]);
+                        mbar_arrive(&sempty[ss]);
+                    }
+                    if (++ss == RS_NSTG) { ss = 0; sph ^= 1; }
+                    if (++os == RS_NOP) { os = 0; oph ^= 1; }
+                }
+            }
+        }
+    } else {
+        // ------------------------------ epilogue ------------------------------
+        const int row = ((warp & 3) << 5) + lane;
+        int slot = 0, acc = 0;
+        uint32_t iph = 0, aph = 0;
+        const int pc = p.pc;
+        while (true) {
+            if (!__all_sync(0xffffffffu, rs_wait(&ifull[slot], iph, p))) break;
+            const int64_t t = items[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&iempty[slot]);
+            if (++slot == TS_IRING) { slot = 0; iph ^= 1; }
+            if (t < 0) break;
+            const int64_t i = t / S, sl = t % S;
+            // per column a two-term FP32 sum (hi, lo) grown by error-free
+            // transformations (TwoSum): about 48 significant bits without
+            // FP64 arithmetic, which runs at a small fraction of the FP32 rate
+            float ahi[TS_NPMAX], alo[TS_NPMAX];
+#pragma unroll
+            for (int q = 0; q < TS_NPMAX; ++q) ahi[q] = alo[q] = 0.f;
+            bool ok = true;
+            for (int64_t jc = 0; jc < nt * KC; ++jc) {
+                const int64_t j = jc / KC;
+                if (!__all_sync(0xffffffffu, rs_wait(&tfull[acc], aph, p))) { ok = false; break; }
+                tmem_fence_after();
+                const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * 3 * np);
+                float v[TS_NPMAX];
+#pragma unroll
+                for (int c16 = 0; c16 < TS_NPMAX / 16; ++c16) {
+                    if (c16 * 16 < np) {
+                        float hv[16], mv[16], lv[16];
+                        tmem_ld16(tacc + c16 * 16, hv);
+                        tmem_ld16(tacc + np + c16 * 16, mv);
+                        tmem_ld16(tacc + 2 * np + c16 * 16, lv);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[c16 * 16 + e] = hv[e] + (mv[e] + lv[e]);
+                    }
+                }
+                tmem_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1; }
+                const float *sv = p.sa + j * np;
+#pragma unroll
+                for (int q = 0; q < TS_NPMAX; ++q) {
+                    if (q < pc) {
+                        const float xq = v[q] * (1.f / (RS_KSCALE * __ldg(sv + q)));  // exact: powers of two
+                        const float s2 = ahi[q] + xq, bp = s2 - ahi[q];
+                        alo[q] += (ahi[q] - (s2 - bp)) + (xq - bp);
+                        ahi[q] = s2;
+                    }
+                }
+            }
+            if (!ok) break;
+            const int64_t grow = i * b + sl * TS_SLAB + row;
+            const int64_t gi = grow * p.ldx + p.q0;
+            const double c = *p.shift;
+#pragma unroll
+            for (int q = 0; q < TS_NPMAX; ++q)
+                if (q < pc)
+                    p.r[gi + q] = ((double)p.y[gi + q] - (double)p.lambda * (double)p.a[gi + q]) -
+                                  ((double)ahi[q] + (double)alo[q]) - c * p.colsum[p.q0 + q];
+        }
+    }
+    tmem_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tmem_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(tcols) : "memory");
+    }
+}
+
+// FP16 pairs of every block of v (one CTA of 128 threads per block).
+__global__ void __launch_bounds__(TS_EPI) convert_all_kernel(const TsParams p, const float *v, __half *vb, float *sv,
+                                                              int terms) {
+    __shared__ float smax[4 * TS_NPMAX], sscale[TS_NPMAX];
+    convert_block(p, v, blockIdx.x, vb, sv, smax, sscale, threadIdx.x, terms);
 }
 
 // Encoder of TMA descriptors (driver entry point, looked up once).
@@ -716,7 +1128,7 @@ size_t ts_smem_bytes(int stages, int stage_bytes) {
 int64_t ts_flag_count(const Ctx *c) { return 2 + 4 * c->nt + c->nt * (c->b / TS_SLAB); }
 
 krr_status ensure_ts_buffers(Ctx *c) {
-    const size_t vbytes = (size_t)2 * TS_NPMAX * c->n_pad * sizeof(__half);
+    const size_t vbytes = (size_t)3 * TS_NPMAX * c->n_pad * sizeof(__half);
     if (c->ts_vcap < vbytes) {
         for (__half **v : {&c->ts_v0, &c->ts_v1}) {
             if (*v) cudaFree(*v);
@@ -801,8 +1213,8 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
         while (stages > 2 && ts_smem_bytes(stages, sp.stage_bytes) > ts_smem_limit()) --stages;
         sp.stages = stages;
         // kind::f16, D = F32, A = B = F16, A K-major (forward) or MN-major
-        // (backward), B K-major, N = np, M = 128
-        sp.idesc = (1u << 4) | ((fwd ? 0u : 1u) << 15) | ((uint32_t)(sp.np >> 3) << 17) |
+        // (backward), B K-major, N = 2 np (hi and lo halves), M = 128
+        sp.idesc = (1u << 4) | ((fwd ? 0u : 1u) << 15) | ((uint32_t)((2 * sp.np) >> 3) << 17) |
                    ((uint32_t)(TS_SLAB >> 4) << 24);
         sp.wait_ns = (uint64_t)c->opt.wait_budget_ns;
         sp.err = c->derr;
@@ -829,6 +1241,107 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
 krr_status tc_sweep_solve(Ctx *c, float *x, float *tmp, int64_t p) {
     KRR_TRY(run_ts(c, TS_FWD, x, tmp, p));
     return run_ts(c, TS_BWD, tmp, x, p);
+}
+
+namespace {
+
+// FP32 row-major matrix, boxes of 32 columns (128 bytes) x box_rows, 128-byte swizzle.
+krr_status map_f32(Ctx *c, CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int box_rows) {
+    EncodeFn enc = encoder(c);
+    if (!enc) return KRR_ECUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(cols * 4)};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        c->last_error = "cuTensorMapEncodeTiled (tensor-core residual) failed with code " + std::to_string((int)r);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
+}
+
+size_t rs_smem_bytes(int op_bytes) {
+    return (size_t)RS_NSTG * RS_STG + (size_t)RS_NOP * op_bytes + TS_IRING * 8 +
+           (size_t)(2 * RS_NSTG + 2 * RS_NOP + 4 + 2 * TS_IRING + 1) * 8 + 16 + 1024;
+}
+
+}  // namespace
+
+// r = y - (K + lambda I) a on the tensor cores (mixed mode), given the column
+// sums of a in c->colsum and the shift in c->red[RED_KSHIFT].
+krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
+    const int64_t b = c->b, nt = c->nt;
+    KRR_TRY(ensure_ts_buffers(c));
+    float *sbase = (float *)c->ts_aux;
+    int *flags = (int *)(sbase + 2 * nt * TS_NPMAX);
+    const int64_t ntri = nt * (nt + 1) / 2;
+    CUtensorMap mk128, mk64, ma;
+    KRR_TRY(map_f32(c, &mk128, c->Kd, ntri * b, b, 128));
+    KRR_TRY(map_f32(c, &mk64, c->Kd, ntri * b, b, 64));
+    static bool attr = false;
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(tcres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_limit());
+        if (e != cudaSuccess) {
+            c->last_error = std::string("cudaFuncSetAttribute (tensor-core residual): ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+        attr = true;
+    }
+    for (int64_t q0 = 0; q0 < p; q0 += TS_NPMAX) {
+        // the FP16 pair of a with per-block scales (B operand)
+        TsParams cp;
+        memset(&cp, 0, sizeof(cp));
+        cp.b = b;
+        cp.nt = nt;
+        cp.n_pad = c->n_pad;
+        cp.pc = (int)std::min<int64_t>(TS_NPMAX, p - q0);
+        cp.np = (cp.pc + 15) & ~15;
+        cp.q0 = (int)q0;
+        cp.ldx = p;
+        count_launch(), convert_all_kernel<<<(unsigned)nt, TS_EPI, 0, c->stream>>>(cp, a, c->ts_v0, sbase, 3);
+        KRR_TRY(map_f16(c, &ma, c->ts_v0, 3 * cp.np, c->n_pad, 3 * cp.np));
+        RsParams rp;
+        memset(&rp, 0, sizeof(rp));
+        rp.b = b;
+        rp.nt = nt;
+        rp.S = b / TS_SLAB;
+        rp.KC = b / TS_KC;
+        rp.items = nt * rp.S;
+        rp.n_pad = c->n_pad;
+        rp.np = cp.np;
+        rp.pc = cp.pc;
+        rp.q0 = cp.q0;
+        rp.ldx = p;
+        rp.y = y;
+        rp.a = a;
+        rp.r = r;
+        rp.shift = c->red + RED_KSHIFT;
+        rp.colsum = c->colsum;
+        rp.lambda = (float)c->lambda;
+        rp.sa = sbase;
+        rp.flags = flags;
+        rp.op_bytes = 32768 + 3 * rp.np * 128;
+        rp.idesc_k = (1u << 4) | ((uint32_t)((3 * rp.np) >> 3) << 17) | ((uint32_t)(TS_SLAB >> 4) << 24);
+        rp.idesc_mn = rp.idesc_k | (1u << 15);
+        rp.idesc_k2 = (1u << 4) | ((uint32_t)((2 * rp.np) >> 3) << 17) | ((uint32_t)(TS_SLAB >> 4) << 24);
+        rp.idesc_mn2 = rp.idesc_k2 | (1u << 15);
+        rp.wait_ns = (uint64_t)c->opt.wait_budget_ns;
+        rp.err = c->derr;
+        KRR_CUDA_TRY(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
+        const size_t smem = rs_smem_bytes(rp.op_bytes);
+        const int64_t grid = std::min<int64_t>(rp.items, c->num_sms);
+        count_launch(), tcres_kernel<<<(unsigned)grid, RS_THREADS, smem, c->stream>>>(mk128, mk64, ma, rp);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            c->last_error = std::string("tensor-core residual launch: ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+    }
+    return KRR_OK;
 }
 
 }  // namespace krr
