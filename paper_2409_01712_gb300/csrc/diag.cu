@@ -260,7 +260,7 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
         const int o = 16 * q;
         if (warp == 0) {
             const int l = lane & 15;
-            float v[16];
+            float v[16], ivs[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = (j <= l) ? a[o + l][o + j] : 0.f;
 #pragma unroll
@@ -270,7 +270,12 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
                     if (bad < 0) bad = o + c;
                     d = 1.f;
                 }
-                const float lcc = sqrtf(d), inv = 1.f / lcc;
+                // 1 / sqrt(d): hardware estimate refined by one Newton-Raphson
+                // step for the reciprocal square root, x <- x (3 - d x^2) / 2
+                float inv = rsqrtf(d);
+                inv = inv * fmaf(-0.5f * d * inv, inv, 1.5f);
+                const float lcc = d * inv;
+                ivs[c] = inv;
                 mpiv = fminf(mpiv, lcc);
                 if (l == c) {
                     v[c] = lcc;
@@ -278,10 +283,13 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
                 } else if (l > c) {
                     v[c] *= inv;
                 }
+                // constant loop bounds (j > c as a condition) keep v in registers
 #pragma unroll
-                for (int j = c + 1; j < 16; ++j) {
-                    const float ljc = __shfl_sync(FULL, v[c], j);
-                    if (l >= j) v[j] = fmaf(-v[c], ljc, v[j]);
+                for (int j = 1; j < 16; ++j) {
+                    if (j > c) {
+                        const float ljc = __shfl_sync(FULL, v[c], j);
+                        if (l >= j) v[j] = fmaf(-v[c], ljc, v[j]);
+                    }
                 }
             }
             float xr[16];
@@ -289,7 +297,7 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
             for (int k = 0; k < 16; ++k) xr[k] = (k == l) ? 1.f : 0.f;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                const float invc = 1.f / __shfl_sync(FULL, v[c], c);
+                const float invc = ivs[c];  // 1 / L[c][c] from the factorisation
                 if (l == c) {
 #pragma unroll
                     for (int k = 0; k <= c; ++k) xr[k] *= invc;

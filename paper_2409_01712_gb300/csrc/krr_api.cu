@@ -426,6 +426,7 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->colsum);
     dev_free(&c->sw_flags);
     dev_free(&c->ts_v0);
+    dev_free(&c->ts_xt);
     dev_free(&c->ts_v1);
     if (c->ts_aux) cudaFree(c->ts_aux);
     c->ts_aux = nullptr;

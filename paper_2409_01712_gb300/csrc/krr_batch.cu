@@ -51,7 +51,7 @@ krr_status issue(krr_ctx *c, const krr_batch_problem &pr, int64_t m, int64_t p) 
 
 // Wall time (ms) of one eager pipeline of problem pr with tile b.
 krr_status trial_ms(const krr_options &base, cudaStream_t s, const krr_batch_problem &pr, int64_t m, int64_t p,
-                    int64_t b, double *ms) {
+                    int64_t b, double *ms, std::string *why) {
     krr_options o = base;
     o.tile = b;
     krr_ctx *c = nullptr;
@@ -65,6 +65,7 @@ krr_status trial_ms(const krr_options &base, cudaStream_t s, const krr_batch_pro
         cudaStreamSynchronize(s);
         *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
+    if (st != KRR_OK && why) *why = krr_last_error(c);
     krr_destroy(c);
     return st;
 }
@@ -112,8 +113,10 @@ extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, 
             for (int64_t b : cand) {
                 if (b > 2 * ((problems[probes[q]].n + 255) / 256 * 256) && b != 256) continue;
                 double ms = 0.0;
-                krr_status st = trial_ms(bt->opt, bt->main, problems[probes[q]], m, p, b, &ms);
-                if (st != KRR_OK) return fail(st, "krr_batch_create: autotune trial failed");
+                std::string why;
+                krr_status st = trial_ms(bt->opt, bt->main, problems[probes[q]], m, p, b, &ms, &why);
+                if (st != KRR_OK)
+                    return fail(st, "krr_batch_create: autotune trial (tile " + std::to_string(b) + ") failed: " + why);
                 if (ms < best) {
                     best = ms;
                     best_b[q] = b;

@@ -122,8 +122,10 @@ struct Ctx {
     int64_t sw_flags_cap = 0;
     __half *ts_v0 = nullptr, *ts_v1 = nullptr;  // tensor-core sweep: FP16 pairs of vector blocks
     size_t ts_vcap = 0;
-    void *ts_aux = nullptr;                  // tensor-core sweep: block scales and counters
+    void *ts_aux = nullptr;                  // tensor-core sweep: block scales, slab maxima, counters
     size_t ts_aux_cap = 0;
+    float *ts_xt = nullptr;                  // tensor-core sweep: column-major copy of the right-hand sides
+    size_t ts_xcap = 0;
     float *pred_out = nullptr;               // reduced predictions, rows_pad x p
     size_t pred_out_cap = 0;
     // hyperparameter gradient buffers (krr_grad_hyper)

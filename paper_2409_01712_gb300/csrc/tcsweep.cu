@@ -66,9 +66,10 @@ struct TsParams {
     int job;
     int64_t b, nt, S, KC, items, n_pad;
     int np, pc, q0;
-    int64_t ldx;
+    int64_t rs, cs;           // vector element (row, column q0 + q) at row * rs + (q0 + q) * cs
     float *rhs;               // FWD: y, BWD: z (updated in place)
     float *out;               // FWD: z, BWD: x
+    float *mx_in, *mx_out;    // per-slab column maxima of rhs / out blocks, [nt][S][TS_NPMAX]
     __half *vin, *vout;       // FP16 pairs of rhs / out blocks: [2 np][n_pad] (hi rows, then lo rows)
     float *sin, *sout;        // their scales, [nt][np]
     const TileDesc *ltab;
@@ -338,25 +339,39 @@ __device__ void decode_item(const TsParams &p, int64_t t, ItemHdr &h) {
 // padding columns [pc, np) are zero.
 // ---------------------------------------------------------------------------
 __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __half *vb, float *sv,
-                              float *smax, float *sscale, int tid, int terms = 2) {
-    const int64_t b = p.b, n_pad = p.n_pad;
+                              float *smax, float *sscale, int tid, int terms = 2, const float *slabmax = nullptr) {
+    const int64_t b = p.b, n_pad = p.n_pad, rs = p.rs, cs = p.cs;
     const int pc = p.pc, np = p.np;
-    float mx[TS_NPMAX];
+    if (slabmax) {
+        // column maxima published by the slabs of the block
+        if (tid < pc) {
+            float m = 0.f;
+            for (int64_t sl = 0; sl < p.S; ++sl) m = fmaxf(m, __ldcg(slabmax + (blk * p.S + sl) * TS_NPMAX + tid));
+            smax[tid] = m;
+            smax[TS_NPMAX + tid] = smax[2 * TS_NPMAX + tid] = smax[3 * TS_NPMAX + tid] = 0.f;
+        }
+    } else {
+        float mx[TS_NPMAX];
 #pragma unroll
-    for (int q = 0; q < TS_NPMAX; ++q) mx[q] = 0.f;
-    for (int64_t r = tid; r < b; r += TS_EPI) {
-        const float *row = v + (blk * b + r) * p.ldx + p.q0;
+        for (int q = 0; q < TS_NPMAX; ++q) mx[q] = 0.f;
+        for (int64_t r = tid; r < b; r += TS_EPI) {
+            const float *row = v + (blk * b + r) * rs + p.q0 * cs;
 #pragma unroll
-        for (int q = 0; q < TS_NPMAX; ++q)
-            if (q < pc) mx[q] = fmaxf(mx[q], fabsf(__ldcg(row + q)));
-    }
-    const int wq = tid >> 5, lane = tid & 31;
+            for (int q = 0; q < TS_NPMAX; ++q) {
+                if (q < pc) {
+                    mx[q] = fmaxf(mx[q], fabsf(__ldcg(row)));
+                    row += cs;
+                }
+            }
+        }
+        const int wq = tid >> 5, lane = tid & 31;
 #pragma unroll
-    for (int q = 0; q < TS_NPMAX; ++q) {
-        if (q < pc) {
-            float m = mx[q];
-            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-            if (lane == 0) smax[wq * TS_NPMAX + q] = m;
+        for (int q = 0; q < TS_NPMAX; ++q) {
+            if (q < pc) {
+                float m = mx[q];
+                for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+                if (lane == 0) smax[wq * TS_NPMAX + q] = m;
+            }
         }
     }
     epi_sync();
@@ -377,12 +392,16 @@ __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __
     epi_sync();
     for (int64_t r = tid; r < b; r += TS_EPI) {
         const int64_t grow = blk * b + r;
-        const float *row = v + grow * p.ldx + p.q0;
+        const float *row = v + grow * rs + p.q0 * cs;
         // the row's loads first (the FP16 stores below may alias them)
         float xv[TS_NPMAX];
 #pragma unroll
-        for (int q = 0; q < TS_NPMAX; ++q)
-            if (q < pc) xv[q] = __ldcg(row + q);
+        for (int q = 0; q < TS_NPMAX; ++q) {
+            if (q < pc) {
+                xv[q] = __ldcg(row);
+                row += cs;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < TS_NPMAX; ++q) {
             if (q < np) {
@@ -403,6 +422,23 @@ __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __
         __threadfence();
         fence_proxy_async_global();
     }
+}
+
+// Column maxima of |x| over the 128 rows of a slab (x one row per thread) into
+// dst[TS_NPMAX] (one block of the per-slab array).
+__device__ __forceinline__ void slab_max(const float (&x)[TS_NPMAX], int pc, float *smax, int tid, float *dst) {
+    const int wq = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < TS_NPMAX; ++q) {
+        if (q < pc) {
+            float m = fabsf(x[q]);
+            for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0) smax[wq * TS_NPMAX + q] = m;
+        }
+    }
+    epi_sync();
+    if (tid < pc)
+        dst[tid] = fmaxf(fmaxf(smax[tid], smax[TS_NPMAX + tid]), fmaxf(smax[2 * TS_NPMAX + tid], smax[3 * TS_NPMAX + tid]));
 }
 
 __global__ void __launch_bounds__(TS_THREADS, 1)
@@ -650,10 +686,19 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             const int64_t grow = (int64_t)h.blk * b + (int64_t)h.slab * TS_SLAB + row;
             if (h.type == IT_DIAG) {
                 epi_sync();
-                float *o = p.out + grow * p.ldx + p.q0;
+                float *o = p.out + grow * p.rs + p.q0 * p.cs;
+                {
+                    float *op = o;
 #pragma unroll
-                for (int q = 0; q < TS_NPMAX; ++q)
-                    if (q < pc) __stcg(o + q, v[q] * smul[q]);
+                    for (int q = 0; q < TS_NPMAX; ++q) {
+                        if (q < pc) {
+                            v[q] *= smul[q];
+                            __stcg(op, v[q]);
+                            op += p.cs;
+                        }
+                    }
+                }
+                slab_max(v, pc, smax, tid, p.mx_out + ((int64_t)h.blk * S + h.slab) * TS_NPMAX);
                 epi_sync();
                 if (tid == 0) {
                     __threadfence();
@@ -663,7 +708,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 }
                 epi_sync();
                 if (sflag[1]) {
-                    convert_block(p, p.out, h.blk, p.vout, p.sout, smax, sscale, tid);
+                    convert_block(p, p.out, h.blk, p.vout, p.sout, smax, sscale, tid, 2, p.mx_out);
                     if (tid == 0) st_release(ready_ctr(p) + h.blk, 1);
                 }
             } else {
@@ -672,16 +717,30 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 if (tid == 0) sflag[2] = wait_count(sq, h.seqv, p) ? 1 : 0;
                 epi_sync();
                 if (!sflag[2]) break;
-                float *y = p.rhs + grow * p.ldx + p.q0;
+                float *y = p.rhs + grow * p.rs + p.q0 * p.cs;
                 // all loads of the row first: the stores may alias them, so
                 // interleaving would serialise the L2 round trips
                 float yv[TS_NPMAX];
+                {
+                    const float *yp = y;
 #pragma unroll
-                for (int q = 0; q < TS_NPMAX; ++q)
-                    if (q < pc) yv[q] = __ldcg(y + q);
+                    for (int q = 0; q < TS_NPMAX; ++q) {
+                        if (q < pc) {
+                            yv[q] = __ldcg(yp);
+                            yp += p.cs;
+                        }
+                    }
+                    float *ys = y;
 #pragma unroll
-                for (int q = 0; q < TS_NPMAX; ++q)
-                    if (q < pc) __stcg(y + q, yv[q] - v[q] * smul[q]);
+                    for (int q = 0; q < TS_NPMAX; ++q) {
+                        if (q < pc) {
+                            yv[q] -= v[q] * smul[q];
+                            __stcg(ys, yv[q]);
+                            ys += p.cs;
+                        }
+                    }
+                }
+                if (h.last_link) slab_max(yv, pc, smax, tid, p.mx_in + ((int64_t)h.blk * S + h.slab) * TS_NPMAX);
                 epi_sync();
                 if (tid == 0) {
                     __threadfence();
@@ -692,7 +751,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 }
                 epi_sync();
                 if (sflag[1]) {
-                    convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid);
+                    convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid, 2, p.mx_in);
                     if (tid == 0) st_release(done_ctr(p) + h.blk, 1);
                 }
             }
@@ -783,6 +842,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
              *oempty = bars + 2 * RS_NSTG + RS_NOP, *tfull = bars + 2 * RS_NSTG + 2 * RS_NOP,
              *tempty = tfull + 2, *ifull = tempty + 2, *iempty = ifull + TS_IRING, *drain = iempty + TS_IRING;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    // epilogue: low halves of the two-term column sums, [TS_NPMAX][128 threads]
+    float *alo_s = reinterpret_cast<float *>(tmem_slot + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int np = p.np;
     const uint32_t tcols = (np * 6 <= 128) ? 128u : 256u;  // two accumulators of 3 np columns
@@ -1017,9 +1078,13 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             // per column a two-term FP32 sum (hi, lo) grown by error-free
             // transformations (TwoSum): about 48 significant bits without
             // FP64 arithmetic, which runs at a small fraction of the FP32 rate
-            float ahi[TS_NPMAX], alo[TS_NPMAX];
+            const int et = threadIdx.x - 64;  // epilogue thread 0..127
+            float ahi[TS_NPMAX];
 #pragma unroll
-            for (int q = 0; q < TS_NPMAX; ++q) ahi[q] = alo[q] = 0.f;
+            for (int q = 0; q < TS_NPMAX; ++q) {
+                ahi[q] = 0.f;
+                alo_s[q * 128 + et] = 0.f;
+            }
             bool ok = true;
             for (int64_t jc = 0; jc < nt * KC; ++jc) {
                 const int64_t j = jc / KC;
@@ -1048,7 +1113,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                     if (q < pc) {
                         const float xq = v[q] * (1.f / (RS_KSCALE * __ldg(sv + q)));  // exact: powers of two
                         const float s2 = ahi[q] + xq, bp = s2 - ahi[q];
-                        alo[q] += (ahi[q] - (s2 - bp)) + (xq - bp);
+                        alo_s[q * 128 + et] += (ahi[q] - (s2 - bp)) + (xq - bp);
                         ahi[q] = s2;
                     }
                 }
@@ -1061,7 +1126,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             for (int q = 0; q < TS_NPMAX; ++q)
                 if (q < pc)
                     p.r[gi + q] = ((double)p.y[gi + q] - (double)p.lambda * (double)p.a[gi + q]) -
-                                  ((double)ahi[q] + (double)alo[q]) - c * p.colsum[p.q0 + q];
+                                  ((double)ahi[q] + (double)alo_s[q * 128 + et]) - c * p.colsum[p.q0 + q];
         }
     }
     tmem_fence_before();
@@ -1127,7 +1192,13 @@ size_t ts_smem_bytes(int stages, int stage_bytes) {
 
 int64_t ts_flag_count(const Ctx *c) { return 2 + 4 * c->nt + c->nt * (c->b / TS_SLAB); }
 
-krr_status ensure_ts_buffers(Ctx *c) {
+// Auxiliary buffer: block scales of the two FP16 vector buffers ([nt][TS_NPMAX]
+// each), per-slab column maxima of the two ([nt][S][TS_NPMAX] each), then the
+// progress counters.
+int64_t ts_scale_count(const Ctx *c) { return c->nt * TS_NPMAX; }
+int64_t ts_max_count(const Ctx *c) { return c->nt * (c->b / TS_SLAB) * TS_NPMAX; }
+
+krr_status ensure_ts_buffers(Ctx *c, int64_t p) {
     const size_t vbytes = (size_t)3 * TS_NPMAX * c->n_pad * sizeof(__half);
     if (c->ts_vcap < vbytes) {
         for (__half **v : {&c->ts_v0, &c->ts_v1}) {
@@ -1142,20 +1213,56 @@ krr_status ensure_ts_buffers(Ctx *c) {
         }
         c->ts_vcap = vbytes;
     }
-    const size_t sbytes = (size_t)2 * c->nt * TS_NPMAX * sizeof(float);
-    const size_t fbytes = (size_t)ts_flag_count(c) * sizeof(int);
-    if (c->ts_aux_cap < sbytes + fbytes) {
+    const size_t abytes = (size_t)(2 * ts_scale_count(c) + 2 * ts_max_count(c)) * sizeof(float) +
+                          (size_t)ts_flag_count(c) * sizeof(int);
+    if (c->ts_aux_cap < abytes) {
         if (c->ts_aux) cudaFree(c->ts_aux);
         c->ts_aux = nullptr;
-        if (cudaMalloc(&c->ts_aux, sbytes + fbytes) != cudaSuccess) {
+        if (cudaMalloc(&c->ts_aux, abytes) != cudaSuccess) {
             cudaGetLastError();
             c->ts_aux_cap = 0;
             c->last_error = "cudaMalloc failed for the sweep counters";
             return KRR_ENOMEM;
         }
-        c->ts_aux_cap = sbytes + fbytes;
+        c->ts_aux_cap = abytes;
+    }
+    const size_t xbytes = (size_t)c->n_pad * p * sizeof(float);
+    if (p > 0 && c->ts_xcap < xbytes) {
+        if (c->ts_xt) cudaFree(c->ts_xt);
+        c->ts_xt = nullptr;
+        if (cudaMalloc((void **)&c->ts_xt, xbytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->ts_xcap = 0;
+            c->last_error = "cudaMalloc failed for the sweep vector copy";
+            return KRR_ENOMEM;
+        }
+        c->ts_xcap = xbytes;
     }
     return KRR_OK;
+}
+
+float *ts_scales(Ctx *c) { return (float *)c->ts_aux; }
+float *ts_maxima(Ctx *c) { return ts_scales(c) + 2 * ts_scale_count(c); }
+int *ts_flags(Ctx *c) { return (int *)(ts_maxima(c) + 2 * ts_max_count(c)); }
+
+// dst (cols x rows, row-major) = src^T, src rows x cols row-major.
+__global__ void transpose_kernel(const float *__restrict__ src, int64_t rows, int64_t cols, float *__restrict__ dst) {
+    __shared__ float t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t r = r0 + k, cc = c0 + threadIdx.x;
+        if (r < rows && cc < cols) t[k][threadIdx.x] = src[r * cols + cc];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t cc = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && cc < cols) dst[cc * rows + r] = t[threadIdx.x][k];
+    }
+}
+
+void launch_transpose(const float *src, int64_t rows, int64_t cols, float *dst, cudaStream_t s) {
+    const dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    count_launch(), transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(src, rows, cols, dst);
 }
 
 krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
@@ -1164,7 +1271,7 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
         c->last_error = "tensor-core sweep: the tile edge must be a multiple of 128";
         return KRR_EINVAL;
     }
-    KRR_TRY(ensure_ts_buffers(c));
+    KRR_TRY(ensure_ts_buffers(c, p));
     const bool fwd = (job == TS_FWD);
     const int abox = fwd ? 128 : 64;
     const int64_t noff = nt * (nt - 1) / 2;
@@ -1174,8 +1281,8 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
     KRR_TRY(map_f16(c, &mw, noff > 0 ? c->W : c->Linv_hi, (noff > 0 ? noff : 1) * b, b, abox));
     KRR_TRY(map_f16(c, &mlh, c->Linv_hi, nt * b, b, abox));
     KRR_TRY(map_f16(c, &mll, c->Linv_lo, nt * b, b, abox));
-    float *sbase = (float *)c->ts_aux;
-    int *flags = (int *)(sbase + 2 * nt * TS_NPMAX);
+    float *sbase = ts_scales(c);
+    int *flags = ts_flags(c);
     static bool attr = false;
     if (!attr) {
         const cudaError_t e =
@@ -1199,13 +1306,18 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
         sp.pc = (int)std::min<int64_t>(TS_NPMAX, p - q0);
         sp.np = (sp.pc + 15) & ~15;
         sp.q0 = (int)q0;
-        sp.ldx = p;
+        // column-major vectors ([p][n_pad]): one row per epilogue thread gives
+        // coalesced accesses for every column
+        sp.rs = 1;
+        sp.cs = c->n_pad;
         sp.rhs = rhs;
         sp.out = out;
+        sp.mx_in = ts_maxima(c);
+        sp.mx_out = ts_maxima(c) + ts_max_count(c);
         sp.vin = c->ts_v0;
         sp.vout = c->ts_v1;
         sp.sin = sbase;
-        sp.sout = sbase + nt * TS_NPMAX;
+        sp.sout = sbase + ts_scale_count(c);
         sp.ltab = c->ltab;
         sp.flags = flags;
         sp.stage_bytes = TS_ABYTES + 2 * sp.np * 128;
@@ -1239,8 +1351,19 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
 // tensor cores: the forward sweep updates x in place and writes z to tmp, the
 // backward sweep updates tmp in place and writes the solution to x.
 krr_status tc_sweep_solve(Ctx *c, float *x, float *tmp, int64_t p) {
-    KRR_TRY(run_ts(c, TS_FWD, x, tmp, p));
-    return run_ts(c, TS_BWD, tmp, x, p);
+    KRR_TRY(ensure_ts_buffers(c, p));
+    // the sweeps work on column-major copies: x^T in ts_xt, z^T in tmp
+    float *xt = c->ts_xt;
+    launch_transpose(x, c->n_pad, p, xt, c->stream);
+    KRR_TRY(run_ts(c, TS_FWD, xt, tmp, p));
+    KRR_TRY(run_ts(c, TS_BWD, tmp, xt, p));
+    launch_transpose(xt, p, c->n_pad, x, c->stream);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->last_error = std::string("sweep transposes: ") + cudaGetErrorString(e);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
 }
 
 namespace {
@@ -1265,7 +1388,7 @@ krr_status map_f32(Ctx *c, CUtensorMap *m, const void *base, int64_t rows, int64
 
 size_t rs_smem_bytes(int op_bytes) {
     return (size_t)RS_NSTG * RS_STG + (size_t)RS_NOP * op_bytes + TS_IRING * 8 +
-           (size_t)(2 * RS_NSTG + 2 * RS_NOP + 4 + 2 * TS_IRING + 1) * 8 + 16 + 1024;
+           (size_t)(2 * RS_NSTG + 2 * RS_NOP + 4 + 2 * TS_IRING + 1) * 8 + 16 + (size_t)TS_NPMAX * 128 * 4 + 1024;
 }
 
 }  // namespace
@@ -1274,9 +1397,9 @@ size_t rs_smem_bytes(int op_bytes) {
 // sums of a in c->colsum and the shift in c->red[RED_KSHIFT].
 krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {
     const int64_t b = c->b, nt = c->nt;
-    KRR_TRY(ensure_ts_buffers(c));
-    float *sbase = (float *)c->ts_aux;
-    int *flags = (int *)(sbase + 2 * nt * TS_NPMAX);
+    KRR_TRY(ensure_ts_buffers(c, 0));
+    float *sbase = ts_scales(c);
+    int *flags = ts_flags(c);
     const int64_t ntri = nt * (nt + 1) / 2;
     CUtensorMap mk128, mk64, ma;
     KRR_TRY(map_f32(c, &mk128, c->Kd, ntri * b, b, 128));
@@ -1301,7 +1424,9 @@ krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_
         cp.pc = (int)std::min<int64_t>(TS_NPMAX, p - q0);
         cp.np = (cp.pc + 15) & ~15;
         cp.q0 = (int)q0;
-        cp.ldx = p;
+        cp.S = b / TS_SLAB;
+        cp.rs = p;  // a is row-major here
+        cp.cs = 1;
         count_launch(), convert_all_kernel<<<(unsigned)nt, TS_EPI, 0, c->stream>>>(cp, a, c->ts_v0, sbase, 3);
         KRR_TRY(map_f16(c, &ma, c->ts_v0, 3 * cp.np, c->n_pad, 3 * cp.np));
         RsParams rp;
