@@ -406,10 +406,10 @@ __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __
         for (int q = 0; q < TS_NPMAX; ++q) {
             if (q < np) {
                 const float x = (q < pc) ? xv[q] * sscale[q] : 0.f;
-                const __half h = __float2half_rn(x);
-                const float r1 = x - __half2float(h);  // exact
+                const __half hh = __float2half_rn(x);
+                const float r1 = x - __half2float(hh);  // exact
                 const __half m = __float2half_rn(r1);
-                vb[(int64_t)q * n_pad + grow] = h;
+                vb[(int64_t)q * n_pad + grow] = hh;
                 vb[(int64_t)(np + q) * n_pad + grow] = m;
                 if (terms == 3) vb[(int64_t)(2 * np + q) * n_pad + grow] = __float2half_rn(r1 - __half2float(m));
             }
@@ -662,6 +662,26 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 if (tid == 0) st_release(done_ctr(p) + h.blk, 1);
                 continue;
             }
+            const int64_t grow = (int64_t)h.blk * b + (int64_t)h.slab * TS_SLAB + row;
+            // LINK: once the earlier updates of this slab are in, load the rows
+            // to update before waiting for the accumulator (the L2 round trip
+            // overlaps the MMAs)
+            float yv[TS_NPMAX];
+            float *y = p.rhs + grow * p.rs + p.q0 * p.cs;
+            int *sq = seq_ctr(p) + (int64_t)h.blk * S + h.slab;
+            if (h.type == IT_LINK) {
+                if (tid == 0) sflag[2] = wait_count(sq, h.seqv, p) ? 1 : 0;
+                epi_sync();
+                if (!sflag[2]) break;
+                const float *yp = y;
+#pragma unroll
+                for (int q = 0; q < TS_NPMAX; ++q) {
+                    if (q < pc) {
+                        yv[q] = __ldcg(yp);
+                        yp += p.cs;
+                    }
+                }
+            }
             if (!group_wait_bar(&tfull[acc], aph)) break;
             tmem_fence_after();
             float v[TS_NPMAX];
@@ -683,7 +703,6 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             // column multipliers: 1 / (tile scale * vector block scale)
             const float *sv = (h.type == IT_DIAG) ? p.sin + (int64_t)h.blk * np : p.sout + (int64_t)h.src * np;
             if (tid < pc) smul[tid] = h.inv_tscale / __ldcg(sv + tid);
-            const int64_t grow = (int64_t)h.blk * b + (int64_t)h.slab * TS_SLAB + row;
             if (h.type == IT_DIAG) {
                 epi_sync();
                 float *o = p.out + grow * p.rs + p.q0 * p.cs;
@@ -712,24 +731,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                     if (tid == 0) st_release(ready_ctr(p) + h.blk, 1);
                 }
             } else {
-                // LINK: after the earlier updates of this slab
-                int *sq = seq_ctr(p) + (int64_t)h.blk * S + h.slab;
-                if (tid == 0) sflag[2] = wait_count(sq, h.seqv, p) ? 1 : 0;
-                epi_sync();
-                if (!sflag[2]) break;
-                float *y = p.rhs + grow * p.rs + p.q0 * p.cs;
-                // all loads of the row first: the stores may alias them, so
-                // interleaving would serialise the L2 round trips
-                float yv[TS_NPMAX];
+                // LINK: the rows were loaded before the accumulator wait
+                epi_sync();  // smul
                 {
-                    const float *yp = y;
-#pragma unroll
-                    for (int q = 0; q < TS_NPMAX; ++q) {
-                        if (q < pc) {
-                            yv[q] = __ldcg(yp);
-                            yp += p.cs;
-                        }
-                    }
                     float *ys = y;
 #pragma unroll
                     for (int q = 0; q < TS_NPMAX; ++q) {
@@ -774,7 +778,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 // Item (i, s) = 128 rows of block i, one accumulation per tile j:
 //   warp 0      producer: TMA of the FP32 K chunk (128 x 64 rows x columns, or
 //               64 x 128 for a column slab) into a staging ring, and of the
-//               FP16 pair of a_j (B) into the operand ring;
+//               FP16 terms of a_j (B) into a ring of their own;
 //   warps 6..9  converters: (K - c) 2^12 -> FP16 pair (hi, lo) in the operand
 //               ring, in the MMA's K-major or MN-major 128-byte-swizzled layout;
 //   warp 1      MMA: A_hi x [B_hi; B_mid; B_lo] (N = 3 np) and A_lo x [B_hi;
@@ -791,8 +795,9 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 320;
 constexpr int RS_STG = 32768;      // FP32 chunk: 128 x 64 or 64 x 128
-constexpr int RS_NSTG = 3;
-constexpr int RS_NOP = 2;
+constexpr int RS_NSTG = 3;         // staging ring (FP32 K chunks, TMA)
+constexpr int RS_NOP = 2;          // A ring (FP16 pair of (K - c) 2^12, converters)
+constexpr int RS_NB = 3;           // B ring (FP16 terms of a, TMA): loads run ahead of the A ring
 constexpr float RS_KSCALE = 4096.f;  // (K - c) * 2^12 in FP16 (|K - c| <= 1)
 
 struct RsParams {
@@ -805,7 +810,7 @@ struct RsParams {
     float lambda;
     const float *sa;        // scales of the FP16 pair of a, [nt][np]
     int *flags;             // [0] item counter, [1] abort
-    int op_bytes;
+    int b_bytes;            // one B chunk: 3 np rows of 128 bytes
     uint32_t idesc_k, idesc_mn, idesc_k2, idesc_mn2;  // N = 3 np and N = 2 np
     uint64_t wait_ns;
     DevErrors *err;
@@ -835,12 +840,14 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     extern __shared__ __align__(1024) uint8_t rs_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(rs_smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *stg = smem;                                   // RS_NSTG x 32 KB
-    uint8_t *ops = smem + RS_NSTG * RS_STG;                // RS_NOP x op_bytes
-    int64_t *items = reinterpret_cast<int64_t *>(ops + RS_NOP * p.op_bytes);  // item ring
+    uint8_t *ops = smem + RS_NSTG * RS_STG;                // RS_NOP x 32 KB (A hi, A lo)
+    uint8_t *bst = ops + RS_NOP * 32768;                   // RS_NB x b_bytes
+    int64_t *items = reinterpret_cast<int64_t *>(bst + RS_NB * p.b_bytes);  // item ring
     uint64_t *bars = reinterpret_cast<uint64_t *>(items + TS_IRING);
     uint64_t *sfull = bars, *sempty = bars + RS_NSTG, *ofull = bars + 2 * RS_NSTG,
-             *oempty = bars + 2 * RS_NSTG + RS_NOP, *tfull = bars + 2 * RS_NSTG + 2 * RS_NOP,
-             *tempty = tfull + 2, *ifull = tempty + 2, *iempty = ifull + TS_IRING, *drain = iempty + TS_IRING;
+             *oempty = bars + 2 * RS_NSTG + RS_NOP, *bfull = oempty + RS_NOP, *bempty = bfull + RS_NB,
+             *tfull = bempty + RS_NB, *tempty = tfull + 2, *ifull = tempty + 2, *iempty = ifull + TS_IRING,
+             *drain = iempty + TS_IRING;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     // epilogue: low halves of the two-term column sums, [TS_NPMAX][128 threads]
     float *alo_s = reinterpret_cast<float *>(tmem_slot + 4);
@@ -853,8 +860,12 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             mbar_init(&sempty[q], 4);      // converter warps
         }
         for (int q = 0; q < RS_NOP; ++q) {
-            mbar_init(&ofull[q], 1 + 4);   // producer (B bytes) + converter warps (A)
+            mbar_init(&ofull[q], 4);       // converter warps
             mbar_init(&oempty[q], 1);      // MMA commit
+        }
+        for (int q = 0; q < RS_NB; ++q) {
+            mbar_init(&bfull[q], 1);       // producer (B bytes)
+            mbar_init(&bempty[q], 1);      // MMA commit
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
@@ -885,7 +896,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     const uint32_t tmem_base = *tmem_slot;
     const int64_t b = p.b, nt = p.nt, S = p.S;
     const int KC = (int)p.KC;
-    const uint32_t bbytes = (uint32_t)(3 * np * 128);
+    const uint32_t bbytes = (uint32_t)p.b_bytes;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -920,11 +931,11 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         }
                         ++issued_s;
                         if (++ss == RS_NSTG) { ss = 0; sph ^= 1; }
-                        if (!rs_wait(&oempty[os], oph ^ 1, p)) { ok = false; break; }
-                        mbar_arrive_expect_tx(&ofull[os], bbytes);
-                        tma_load_2d(ops + os * p.op_bytes + 32768, &mA, (int)(j * b) + kc * 64, 0, &ofull[os]);
+                        if (!rs_wait(&bempty[os], oph ^ 1, p)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&bfull[os], bbytes);
+                        tma_load_2d(bst + os * p.b_bytes, &mA, (int)(j * b) + kc * 64, 0, &bfull[os]);
                         ++issued_o;
-                        if (++os == RS_NOP) { os = 0; oph ^= 1; }
+                        if (++os == RS_NB) { os = 0; oph ^= 1; }
                     }
                 }
             }
@@ -938,22 +949,21 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                     const uint64_t t0 = globaltimer();
                     while (!mbar_try_wait(&sfull[q], pp) && globaltimer() - t0 < p.wait_ns) {}
                 }
-                n = issued_o < RS_NOP ? issued_o : RS_NOP;
+                n = issued_o < RS_NB ? issued_o : RS_NB;
                 q = os;
                 pp = oph;
                 for (int e = 0; e < n; ++e) {
-                    if (--q < 0) { q = RS_NOP - 1; pp ^= 1; }
+                    if (--q < 0) { q = RS_NB - 1; pp ^= 1; }
                     const uint64_t t0 = globaltimer();
-                    // the B bytes of the stage (its converter arrivals may be missing)
-                    while (!mbar_try_wait(&ofull[q], pp) && globaltimer() - t0 < p.wait_ns) {}
+                    while (!mbar_try_wait(&bfull[q], pp) && globaltimer() - t0 < p.wait_ns) {}
                 }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------ MMA issuer ------------------------------
-            int os = 0, slot = 0, acc = 0;
-            uint32_t oph = 0, iph = 0, aph = 0;
+            int os = 0, bs = 0, slot = 0, acc = 0;
+            uint32_t oph = 0, bph = 0, iph = 0, aph = 0;
             bool ok = true, any = false;
             while (ok) {
                 if (!rs_wait(&ifull[slot], iph, p)) { ok = false; break; }
@@ -971,8 +981,9 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         tmem_fence_after();
                         const uint32_t tacc = tmem_base + (uint32_t)(acc * 3 * np);
                         if (!rs_wait(&ofull[os], oph, p)) { ok = false; break; }
+                        if (!rs_wait(&bfull[bs], bph, p)) { ok = false; break; }
                         tmem_fence_after();
-                        const uint32_t sa = smem_u32(ops + os * p.op_bytes), sb = sa + 32768;
+                        const uint32_t sa = smem_u32(ops + os * 32768), sb = smem_u32(bst + bs * p.b_bytes);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint64_t bd = desc_kmajor(sb + kk * 32);
@@ -986,7 +997,9 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         }
                         any = true;
                         mma_commit(&oempty[os]);
+                        mma_commit(&bempty[bs]);
                         if (++os == RS_NOP) { os = 0; oph ^= 1; }
+                        if (++bs == RS_NB) { bs = 0; bph ^= 1; }
                         mma_commit(&tfull[acc]);
                         if (++acc == 2) { acc = 0; aph ^= 1; }
                     }
@@ -1022,7 +1035,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                     if (!__all_sync(0xffffffffu, rs_wait(&sfull[ss], sph, p))) { ok = false; break; }
                     if (!__all_sync(0xffffffffu, rs_wait(&oempty[os], oph ^ 1, p))) { ok = false; break; }
                     const uint8_t *src = stg + ss * RS_STG + r * 128;
-                    uint8_t *dst = ops + os * p.op_bytes + h * 8192 + r * 128;
+                    uint8_t *dst = ops + os * 32768 + h * 8192 + r * 128;
                     float v[64];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
@@ -1086,8 +1099,10 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 alo_s[q * 128 + et] = 0.f;
             }
             bool ok = true;
+            float mlane = 0.f;  // lane q: 1 / (2^12 * scale of column q of a_j)
             for (int64_t jc = 0; jc < nt * KC; ++jc) {
                 const int64_t j = jc / KC;
+                if (jc % KC == 0) mlane = (lane < pc) ? 1.f / (RS_KSCALE * __ldg(p.sa + j * np + lane)) : 0.f;
                 if (!__all_sync(0xffffffffu, rs_wait(&tfull[acc], aph, p))) { ok = false; break; }
                 tmem_fence_after();
                 const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * 3 * np);
@@ -1107,11 +1122,11 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[acc]);
                 if (++acc == 2) { acc = 0; aph ^= 1; }
-                const float *sv = p.sa + j * np;
 #pragma unroll
                 for (int q = 0; q < TS_NPMAX; ++q) {
+                    const float mq = __shfl_sync(0xffffffffu, mlane, q);
                     if (q < pc) {
-                        const float xq = v[q] * (1.f / (RS_KSCALE * __ldg(sv + q)));  // exact: powers of two
+                        const float xq = v[q] * mq;  // exact: powers of two
                         const float s2 = ahi[q] + xq, bp = s2 - ahi[q];
                         alo_s[q * 128 + et] += (ahi[q] - (s2 - bp)) + (xq - bp);
                         ahi[q] = s2;
@@ -1386,9 +1401,10 @@ krr_status map_f32(Ctx *c, CUtensorMap *m, const void *base, int64_t rows, int64
     return KRR_OK;
 }
 
-size_t rs_smem_bytes(int op_bytes) {
-    return (size_t)RS_NSTG * RS_STG + (size_t)RS_NOP * op_bytes + TS_IRING * 8 +
-           (size_t)(2 * RS_NSTG + 2 * RS_NOP + 4 + 2 * TS_IRING + 1) * 8 + 16 + (size_t)TS_NPMAX * 128 * 4 + 1024;
+size_t rs_smem_bytes(int b_bytes) {
+    return (size_t)RS_NSTG * RS_STG + (size_t)RS_NOP * 32768 + (size_t)RS_NB * b_bytes + TS_IRING * 8 +
+           (size_t)(2 * RS_NSTG + 2 * RS_NOP + 2 * RS_NB + 4 + 2 * TS_IRING + 1) * 8 + 16 +
+           (size_t)TS_NPMAX * 128 * 4 + 1024;
 }
 
 }  // namespace
@@ -1449,7 +1465,7 @@ krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_
         rp.lambda = (float)c->lambda;
         rp.sa = sbase;
         rp.flags = flags;
-        rp.op_bytes = 32768 + 3 * rp.np * 128;
+        rp.b_bytes = 3 * rp.np * 128;
         rp.idesc_k = (1u << 4) | ((uint32_t)((3 * rp.np) >> 3) << 17) | ((uint32_t)(TS_SLAB >> 4) << 24);
         rp.idesc_mn = rp.idesc_k | (1u << 15);
         rp.idesc_k2 = (1u << 4) | ((uint32_t)((2 * rp.np) >> 3) << 17) | ((uint32_t)(TS_SLAB >> 4) << 24);
@@ -1457,7 +1473,7 @@ krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_
         rp.wait_ns = (uint64_t)c->opt.wait_budget_ns;
         rp.err = c->derr;
         KRR_CUDA_TRY(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
-        const size_t smem = rs_smem_bytes(rp.op_bytes);
+        const size_t smem = rs_smem_bytes(rp.b_bytes);
         const int64_t grid = std::min<int64_t>(rp.items, c->num_sms);
         count_launch(), tcres_kernel<<<(unsigned)grid, RS_THREADS, smem, c->stream>>>(mk128, mk64, ma, rp);
         const cudaError_t e = cudaGetLastError();
