@@ -183,31 +183,6 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         : "memory");
 }
 
-// L2 policy for data touched once per launch (the trailing update's target
-// blocks): evicted first, so the column panel that every target reuses stays.
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ void tma_load_2d_hint(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar,
-                                                 uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
-__device__ __forceinline__ void tma_store_2d_hint(const CUtensorMap *map, int x, int y, const void *src,
-                                                  uint64_t pol) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(x), "r"(y), "r"(smem_u32(src)), "l"(pol)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
@@ -926,8 +901,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 mbar_arrive_expect_tx(cfull, (uint32_t)PairCfg<PAIR>::cbuf_bytes);
                 const int y = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
                 for (int bx = 0; bx < BN / 64; ++bx)
-                    tma_load_2d_hint(cbuf + bx * (BM * 128), &mB1, (int)(w.sn * BN + bx * 64), y, cfull,
-                                     policy_evict_first());
+                    tma_load_2d(cbuf + bx * (BM * 128), &mB1, (int)(w.sn * BN + bx * 64), y, cfull);
                 cload_pending = true;
             }
             epi_bar();
@@ -957,8 +931,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 if (threadIdx.x == 64) {
                     const int y = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
                     for (int bx = 0; bx < BN / 64; ++bx)
-                        tma_store_2d_hint(&mB1, (int)(w.sn * BN + bx * 64), y, cbuf + bx * (BM * 128),
-                                          policy_evict_first());
+                        tma_store_2d(&mB1, (int)(w.sn * BN + bx * 64), y, cbuf + bx * (BM * 128));
                     bulk_commit();
                 }
             }
