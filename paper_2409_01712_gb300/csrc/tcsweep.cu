@@ -70,6 +70,7 @@ struct TsParams {
     float *rhs;               // FWD: y, BWD: z (updated in place)
     float *out;               // FWD: z, BWD: x
     float *mx_in, *mx_out;    // per-slab column maxima of rhs / out blocks, [nt][S][TS_NPMAX]
+    float *bm_in, *bm_out;    // their block column maxima, [nt][TS_NPMAX]
     __half *vin, *vout;       // FP16 pairs of rhs / out blocks: [2 np][n_pad] (hi rows, then lo rows)
     float *sin, *sout;        // their scales, [nt][np]
     const TileDesc *ltab;
@@ -339,7 +340,8 @@ __device__ void decode_item(const TsParams &p, int64_t t, ItemHdr &h) {
 // padding columns [pc, np) are zero.
 // ---------------------------------------------------------------------------
 __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __half *vb, float *sv,
-                              float *smax, float *sscale, int tid, int terms = 2, const float *slabmax = nullptr) {
+                              float *smax, float *sscale, int tid, int terms = 2, const float *slabmax = nullptr,
+                              float *bmax = nullptr) {
     const int64_t b = p.b, n_pad = p.n_pad, rs = p.rs, cs = p.cs;
     const int pc = p.pc, np = p.np;
     if (slabmax) {
@@ -385,6 +387,7 @@ __device__ void convert_block(const TsParams &p, const float *v, int64_t blk, __
                 frexpf(m, &e);  // m = f 2^e, f in [0.5, 1)
                 s = ldexpf(1.f, max(-126, min(126, 13 - e)));
             }
+            if (bmax) bmax[blk * TS_NPMAX + tid] = m;
         }
         sscale[tid] = s;
         sv[blk * np + tid] = s;
@@ -439,6 +442,60 @@ __device__ __forceinline__ void slab_max(const float (&x)[TS_NPMAX], int pc, flo
     epi_sync();
     if (tid < pc)
         dst[tid] = fmaxf(fmaxf(smax[tid], smax[TS_NPMAX + tid]), fmaxf(smax[2 * TS_NPMAX + tid], smax[3 * TS_NPMAX + tid]));
+}
+
+// Predicted scale of a block from the column maximum m of the block before
+// it in the sweep: puts m in [256, 512).  Blocks of one vector have similar
+// magnitudes, so each slab converts its own rows with this scale as soon as
+// they are final; the block keeps it if its own maximum lands in
+// [PRED_LO, PRED_HI) (about 22 significant bits relative to the maximum, as
+// with the exact scale, and 2x headroom below the FP16 maximum), else the last
+// slab converts the whole block again with the exact scale.
+constexpr float PRED_LO = 8.f, PRED_HI = 32768.f;
+
+__device__ __forceinline__ float pred_scale(float m) {
+    if (!(m > 0.f) || !(m < 3.0e38f)) return 1.f;
+    int e;
+    frexpf(m, &e);
+    return ldexpf(1.f, max(-126, min(126, 9 - e)));
+}
+
+// One row (one element per column, already final) as an FP16 pair with the
+// per-column scales sscale: planes q (hi) and np + q (lo); padding columns zero.
+__device__ __forceinline__ void store_pair_row(const TsParams &p, __half *vb, int64_t grow, const float (&x)[TS_NPMAX],
+                                               const float *sscale) {
+    const int pc = p.pc, np = p.np;
+    const int64_t n_pad = p.n_pad;
+#pragma unroll
+    for (int q = 0; q < TS_NPMAX; ++q) {
+        if (q < np) {
+            const float xs = (q < pc) ? x[q] * sscale[q] : 0.f;
+            const __half hh = __float2half_rn(xs);
+            vb[(int64_t)q * n_pad + grow] = hh;
+            vb[(int64_t)(np + q) * n_pad + grow] = __float2half_rn(xs - __half2float(hh));
+        }
+    }
+}
+
+// Last slab of a block (128 epilogue threads): block column maxima from the
+// slab maxima into bmax; true (for every thread) if the predicted scales in
+// sscale hold for every column, and then they become the block's scales sv.
+__device__ bool accept_block(const TsParams &p, const float *slabmax, int64_t blk, const float *sscale, float *sv,
+                             float *bmax, int *sflag, int tid) {
+    if (tid == 0) sflag[3] = 1;
+    epi_sync();
+    if (tid < p.pc) {
+        float m = 0.f;
+        for (int64_t sl = 0; sl < p.S; ++sl) m = fmaxf(m, __ldcg(slabmax + (blk * p.S + sl) * TS_NPMAX + tid));
+        bmax[blk * TS_NPMAX + tid] = m;
+        const float ms = m * sscale[tid];
+        if (!(m == 0.f || (ms >= PRED_LO && ms < PRED_HI))) sflag[3] = 0;
+    }
+    epi_sync();
+    const bool ok = sflag[3] != 0;
+    if (ok && tid < p.np) sv[blk * p.np + tid] = sscale[tid];
+    epi_sync();
+    return ok;
 }
 
 __global__ void __launch_bounds__(TS_THREADS, 1)
@@ -658,7 +715,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             if (++slot == TS_IRING) { slot = 0; sph ^= 1; }
             if (h.type == IT_END) break;
             if (h.type == IT_CONV) {
-                convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid);
+                convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid, 2, nullptr, p.bm_in);
                 if (tid == 0) st_release(done_ctr(p) + h.blk, 1);
                 continue;
             }
@@ -703,6 +760,17 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             // column multipliers: 1 / (tile scale * vector block scale)
             const float *sv = (h.type == IT_DIAG) ? p.sin + (int64_t)h.blk * np : p.sout + (int64_t)h.src * np;
             if (tid < pc) smul[tid] = h.inv_tscale / __ldcg(sv + tid);
+            // predicted scale of the block this item finishes: from the block
+            // before it in the sweep (the right-hand side's own block for the
+            // first solution block)
+            const int64_t prev = fwd ? (int64_t)h.blk - 1 : (int64_t)h.blk + 1;
+            const bool first = fwd ? (h.blk == 0) : (h.blk == p.nt - 1);
+            if ((h.type == IT_DIAG || h.last_link) && tid < np) {
+                const float *bm = (h.type == IT_LINK) ? p.bm_in + prev * TS_NPMAX
+                                  : first            ? p.bm_in + (int64_t)h.blk * TS_NPMAX
+                                                     : p.bm_out + prev * TS_NPMAX;
+                sscale[tid] = (tid < pc) ? pred_scale(__ldcg(bm + tid)) : 1.f;
+            }
             if (h.type == IT_DIAG) {
                 epi_sync();
                 float *o = p.out + grow * p.rs + p.q0 * p.cs;
@@ -717,18 +785,24 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                         }
                     }
                 }
+                store_pair_row(p, p.vout, grow, v, sscale);
                 slab_max(v, pc, smax, tid, p.mx_out + ((int64_t)h.blk * S + h.slab) * TS_NPMAX);
                 epi_sync();
                 if (tid == 0) {
                     __threadfence();
+                    fence_proxy_async_global();  // the FP16 rows are read by TMA on other SMs
                     const bool last = atomicAdd(cout_ctr(p) + h.blk, 1) == (int)S - 1;
-                    if (last) __threadfence();  // the other slabs' rows are read next
+                    if (last) __threadfence();  // the other slabs' rows and maxima are read next
                     sflag[1] = last ? 1 : 0;
                 }
                 epi_sync();
                 if (sflag[1]) {
-                    convert_block(p, p.out, h.blk, p.vout, p.sout, smax, sscale, tid, 2, p.mx_out);
-                    if (tid == 0) st_release(ready_ctr(p) + h.blk, 1);
+                    if (!accept_block(p, p.mx_out, h.blk, sscale, p.sout, p.bm_out, sflag, tid))
+                        convert_block(p, p.out, h.blk, p.vout, p.sout, smax, sscale, tid, 2, p.mx_out, p.bm_out);
+                    if (tid == 0) {
+                        __threadfence();
+                        st_release(ready_ctr(p) + h.blk, 1);
+                    }
                 }
             } else {
                 // LINK: the rows were loaded before the accumulator wait
@@ -744,10 +818,14 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                         }
                     }
                 }
-                if (h.last_link) slab_max(yv, pc, smax, tid, p.mx_in + ((int64_t)h.blk * S + h.slab) * TS_NPMAX);
+                if (h.last_link) {
+                    store_pair_row(p, p.vin, grow, yv, sscale);
+                    slab_max(yv, pc, smax, tid, p.mx_in + ((int64_t)h.blk * S + h.slab) * TS_NPMAX);
+                }
                 epi_sync();
                 if (tid == 0) {
                     __threadfence();
+                    if (h.last_link) fence_proxy_async_global();
                     atomicAdd(sq, 1);
                     const bool last = h.last_link && atomicAdd(cin_ctr(p) + h.blk, 1) == (int)S - 1;
                     if (last) __threadfence();  // the other slabs' rows are read next
@@ -755,8 +833,12 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 }
                 epi_sync();
                 if (sflag[1]) {
-                    convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid, 2, p.mx_in);
-                    if (tid == 0) st_release(done_ctr(p) + h.blk, 1);
+                    if (!accept_block(p, p.mx_in, h.blk, sscale, p.sin, p.bm_in, sflag, tid))
+                        convert_block(p, p.rhs, h.blk, p.vin, p.sin, smax, sscale, tid, 2, p.mx_in, p.bm_in);
+                    if (tid == 0) {
+                        __threadfence();
+                        st_release(done_ctr(p) + h.blk, 1);
+                    }
                 }
             }
         }
@@ -1208,8 +1290,8 @@ size_t ts_smem_bytes(int stages, int stage_bytes) {
 int64_t ts_flag_count(const Ctx *c) { return 2 + 4 * c->nt + c->nt * (c->b / TS_SLAB); }
 
 // Auxiliary buffer: block scales of the two FP16 vector buffers ([nt][TS_NPMAX]
-// each), per-slab column maxima of the two ([nt][S][TS_NPMAX] each), then the
-// progress counters.
+// each), per-slab column maxima of the two ([nt][S][TS_NPMAX] each), their
+// block column maxima ([nt][TS_NPMAX] each), then the progress counters.
 int64_t ts_scale_count(const Ctx *c) { return c->nt * TS_NPMAX; }
 int64_t ts_max_count(const Ctx *c) { return c->nt * (c->b / TS_SLAB) * TS_NPMAX; }
 
@@ -1228,7 +1310,7 @@ krr_status ensure_ts_buffers(Ctx *c, int64_t p) {
         }
         c->ts_vcap = vbytes;
     }
-    const size_t abytes = (size_t)(2 * ts_scale_count(c) + 2 * ts_max_count(c)) * sizeof(float) +
+    const size_t abytes = (size_t)(4 * ts_scale_count(c) + 2 * ts_max_count(c)) * sizeof(float) +
                           (size_t)ts_flag_count(c) * sizeof(int);
     if (c->ts_aux_cap < abytes) {
         if (c->ts_aux) cudaFree(c->ts_aux);
@@ -1258,7 +1340,8 @@ krr_status ensure_ts_buffers(Ctx *c, int64_t p) {
 
 float *ts_scales(Ctx *c) { return (float *)c->ts_aux; }
 float *ts_maxima(Ctx *c) { return ts_scales(c) + 2 * ts_scale_count(c); }
-int *ts_flags(Ctx *c) { return (int *)(ts_maxima(c) + 2 * ts_max_count(c)); }
+float *ts_block_maxima(Ctx *c) { return ts_maxima(c) + 2 * ts_max_count(c); }
+int *ts_flags(Ctx *c) { return (int *)(ts_block_maxima(c) + 2 * ts_scale_count(c)); }
 
 // dst (cols x rows, row-major) = src^T, src rows x cols row-major.
 __global__ void transpose_kernel(const float *__restrict__ src, int64_t rows, int64_t cols, float *__restrict__ dst) {
@@ -1329,6 +1412,8 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
         sp.out = out;
         sp.mx_in = ts_maxima(c);
         sp.mx_out = ts_maxima(c) + ts_max_count(c);
+        sp.bm_in = ts_block_maxima(c);
+        sp.bm_out = ts_block_maxima(c) + ts_scale_count(c);
         sp.vin = c->ts_v0;
         sp.vout = c->ts_v1;
         sp.sin = sbase;
