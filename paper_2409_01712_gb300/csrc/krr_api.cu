@@ -728,13 +728,21 @@ krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt,
     float *aw = c->dabuf;  // padded copy of the weights
     KRR_TRY(load_rows_f32(c, A, c->n, p, lda, c->n_pad, aw));
     float *out = c->pred_out;
+    if (mx && c->colsum_cap < p) {
+        KRR_TRY(dev_alloc(c, &c->colsum, (size_t)p, "column sums"));
+        c->colsum_cap = p;
+    }
     int pr = prof_begin(c, KRR_PROF_PREDICT);
     if (mx) {
+        // products of the shifted kernel K - c, then + c (1^T A) in FP64
+        const double *shift = c->red + RED_KSHIFT;
+        launch_colsum(aw, c->n_pad, p, c->colsum, c->stream);
         // the tensor-core epilogue holds at most 32 weight columns: chunk p
         for (int64_t q0 = 0; q0 < p; q0 += 32) {
             const int64_t pc = std::min<int64_t>(32, p - q0);
-            KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows_pad, aw + q0, p, pc, c->pred_part));
-            launch_predict_reduce(c->pred_part, nblk, rows_pad, n_test, pc, out + q0, p, c->stream);
+            KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows_pad, aw + q0, p, pc, c->pred_part, shift));
+            launch_predict_reduce(c->pred_part, nblk, rows_pad, n_test, pc, out + q0, p, c->stream, shift,
+                                  c->colsum + q0);
         }
     } else {
         launch_predict_simt(c, (const float *)c->t8, c->tnorms, n_test, rows_pad, aw, p,
@@ -950,9 +958,15 @@ extern "C" krr_status krr_grad_hyper(krr_ctx *c, const int8_t *T, int64_t n_test
     KRR_TRY(pack(c, T, n_test, c->m, ldt, rows, c->t8, nullptr, c->tnorms));
     KRR_TRY(load_rows_f32(c, A, c->n, p, lda, npad, c->g_aw));
     KRR_TRY(load_rows_f32(c, Yt, n_test, p, ldy, rows, c->g_yt));
-    // 2. Yhat = K_t A (Alg. 4)
-    KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows, c->g_aw, p, p, c->g_part));
-    launch_predict_reduce(c->g_part, npad / 128, rows, n_test, p, c->pred_out, p, s);
+    // 2. Yhat = K_t A (Alg. 4), as in krr_predict: (K - c) A + c (1^T A)
+    if (c->colsum_cap < p) {
+        KRR_TRY(dev_alloc(c, &c->colsum, (size_t)p, "column sums"));
+        c->colsum_cap = p;
+    }
+    launch_colsum(c->g_aw, npad, p, c->colsum, s);
+    KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows, c->g_aw, p, p, c->g_part, c->red + RED_KSHIFT));
+    launch_predict_reduce(c->g_part, npad / 128, rows, n_test, p, c->pred_out, p, s, c->red + RED_KSHIFT,
+                          c->colsum);
     // 3. G_p = d loss / d Yhat and the loss
     launch_grad_prep(c->pred_out, c->g_yt, n_test, p, rows, c->g_gp, c->g_sq, s);
     launch_sum_f64(c->g_sq, rows * p, c->g_scal + 0, s);

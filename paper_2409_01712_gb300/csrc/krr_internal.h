@@ -251,8 +251,13 @@ void launch_reduce_norms(const double *r, const float *y, int64_t n, int64_t p, 
                          cudaStream_t s);
 void launch_axpy_r(const double *r, float *dst, int64_t count, cudaStream_t s);
 void launch_add_scaled(float *a, const float *da, float alpha, int64_t count, cudaStream_t s);
+// Yt = sum of the per-block partials; when shift is given the partials are of
+// (K - c) A and c (1^T A) is added (c = *shift rounded to FP32, colsum = 1^T A).
 void launch_predict_reduce(const float *part, int64_t nblk, int64_t rows_pad, int64_t n_test,
-                           int64_t p, float *out, int64_t ldo, cudaStream_t s);
+                           int64_t p, float *out, int64_t ldo, cudaStream_t s, const double *shift = nullptr,
+                           const double *colsum = nullptr);
+// out[q] = sum of column q of a (n x p, row-major), FP64.
+void launch_colsum(const float *a, int64_t n, int64_t p, double *out, cudaStream_t s);
 void launch_copy_rows(const float *src, int64_t lds, float *dst, int64_t ldd, int64_t rows,
                       int64_t cols, int64_t rows_pad, cudaStream_t s);
 // out[0] = ||K||_F^2, out[1] = sum of K, out[2] = mean off-diagonal entry.
@@ -276,8 +281,11 @@ krr_status tc_trsm(Ctx *c, int64_t k);       // panel TRSM of column k (FP16 spl
 krr_status tc_update(Ctx *c, int64_t k);     // trailing update of step k
 // Predict partial products for weight columns A[:, 0:p] (p <= 32, leading
 // dimension lda): part is (n_pad / 128) x rows_pad x p.
+// With kshift the partials are of (K - c) A, c = *kshift (the reduction adds
+// c (1^T A) back).
 krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
-                      int64_t rows_pad, const float *A, int64_t lda, int64_t p, float *part);
+                      int64_t rows_pad, const float *A, int64_t lda, int64_t p, float *part,
+                      const double *kshift = nullptr);
 // B = K_test^T G_p (roles swapped): part is (2 * test_rows256 / 256) x n_pad x p.
 krr_status tc_predict_t(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
                         int64_t test_rows256, const float *gp, int64_t ldgp, int64_t p, float *part);

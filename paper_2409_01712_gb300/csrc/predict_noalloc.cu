@@ -34,7 +34,8 @@ constexpr size_t NA_TN = NA_T8 + align256(NA_MAX_TEST * NA_MAX_MPAD);           
 constexpr size_t NA_AW = NA_TN + align256(NA_MAX_TEST * 4);                     // padded weights
 constexpr size_t NA_PART = NA_AW + align256(NA_MAX_NPAD * NA_MAX_P * 4);        // partial products
 constexpr size_t NA_OUT = NA_PART + align256((NA_MAX_NPAD / 128) * NA_MAX_TEST * NA_MAX_P * 4);
-constexpr size_t NA_BYTES = NA_OUT + align256(NA_MAX_TEST * NA_MAX_P * 4);
+constexpr size_t NA_CSUM = NA_OUT + align256(NA_MAX_TEST * NA_MAX_P * 4);   // FP64 column sums of the weights
+constexpr size_t NA_BYTES = NA_CSUM + align256(NA_MAX_P * 8);
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[NA_BYTES];
 
@@ -106,14 +107,17 @@ extern "C" krr_status krr_predict_noalloc(krr_ctx *ctx, const int8_t *T, int64_t
     float *aw = reinterpret_cast<float *>(base + NA_AW);
     float *part = reinterpret_cast<float *>(base + NA_PART);
     float *out = reinterpret_cast<float *>(base + NA_OUT);
+    double *csum = reinterpret_cast<double *>(base + NA_CSUM);
+    const double *shift = c->red + krr::RED_KSHIFT;
     const int64_t rows_pad = (n_test + 127) / 128 * 128;
     // Every scratch element read below is written first in this call (the
     // packing and the weight copy zero their padding; the partials and the
     // output are written in full), so nothing needs clearing.
     krr::launch_pack_genotypes(T, n_test, c->m, ldt, rows_pad, c->m_pad, t8, nullptr, tn, c->stream);
     krr::launch_copy_rows(A, lda, aw, p, c->n, p, c->n_pad, c->stream);
-    KRR_TRY(krr::tc_predict(c, t8, tn, n_test, rows_pad, aw, p, p, part));
-    krr::launch_predict_reduce(part, c->n_pad / 128, rows_pad, n_test, p, out, p, c->stream);
+    krr::launch_colsum(aw, c->n_pad, p, csum, c->stream);
+    KRR_TRY(krr::tc_predict(c, t8, tn, n_test, rows_pad, aw, p, p, part, shift));
+    krr::launch_predict_reduce(part, c->n_pad / 128, rows_pad, n_test, p, out, p, c->stream, shift, csum);
     krr::launch_copy_rows(out, p, Yt, ldyt, n_test, p, n_test, c->stream);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -472,22 +472,27 @@ void launch_predict_simt(Ctx *c, const float *tf, const int32_t *tn, int64_t n_t
         tf, tn, n_test, c->gf, c->norms, c->n, c->m_pad, ncb, (float)c->gamma, A, p, rows_pad, part);
 }
 
-// Sum of partial products over column blocks in a fixed order.
+// Sum of partial products over column blocks in a fixed order; with a shift
+// c (the partials hold (K - c) A), plus c (1^T A) from the FP64 column sums.
 __global__ void predict_reduce_kernel(const float *part, int64_t nblk, int64_t rows_pad,
-                                      int64_t n_test, int64_t p, float *out, int64_t ldo) {
+                                      int64_t n_test, int64_t p, float *out, int64_t ldo,
+                                      const double *shift, const double *colsum) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= n_test * p) return;
     int64_t r = e / p, q = e % p;
     double s = 0.0;
     for (int64_t c = 0; c < nblk; ++c) s += (double)part[(c * rows_pad + r) * p + q];
+    if (shift) s += (double)(float)*shift * colsum[q];
     out[r * ldo + q] = (float)s;
 }
 
 void launch_predict_reduce(const float *part, int64_t nblk, int64_t rows_pad, int64_t n_test,
-                           int64_t p, float *out, int64_t ldo, cudaStream_t s) {
+                           int64_t p, float *out, int64_t ldo, cudaStream_t s, const double *shift,
+                           const double *colsum) {
     count_launch(), predict_reduce_kernel<<<cdiv(n_test * p, 256), 256, 0, s>>>(part, nblk, rows_pad, n_test, p,
-                                                               out, ldo);
+                                                               out, ldo, shift, colsum);
 }
+
 
 // ----------------------------------------------------------------------------
 // Diagonal-tile Cholesky, blocked by NB = 64 inside the b x b tile.
@@ -847,6 +852,10 @@ __global__ void colsum_kernel(const float *a, int64_t n, int64_t p, double *out)
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
         out[q] = t;
     }
+}
+
+void launch_colsum(const float *a, int64_t n, int64_t p, double *out, cudaStream_t s) {
+    count_launch(), colsum_kernel<<<(unsigned)p, 512, 0, s>>>(a, n, p, out);
 }
 
 krr_status launch_residual(Ctx *c, const float *y, const float *a, double *r, int64_t p) {

@@ -68,7 +68,7 @@ constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >
 // A stage is 32 KB instead of 48 KB.
 template <int PAIR>
 struct PairCfg {
-    static constexpr int stages = (PAIR == 2) ? 4 : STAGES;
+    static constexpr int stages = (PAIR == 2) ? 5 : STAGES;
     // pair mode (trailing update): the FP16 target block (128 x 256) is staged
     // in shared memory by TMA, updated there and stored back by TMA
     static constexpr int cbuf_bytes = (PAIR == 2) ? BM * BN * 2 : 0;
@@ -97,6 +97,7 @@ struct TcParams {
     const float *zw;   // OP_GRADK: Z = (K + lambda I)^-1 K_t^T G_p, n_pad x ldaw
     const float *gp;   // OP_GRADT: G_p, padded test rows x ldaw
     double *gpart;     // OP_GRADT / OP_GRADK: one partial sum per block
+    const double *kshift;  // OP_PREDICT: shift c subtracted from every K entry (nullptr: none)
     uint64_t wait_ns;
     DevErrors *err;
 };
@@ -294,6 +295,12 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // Every role calls this with the same arguments, so all agree on the number
 // of slabs of every block (zero for skipped blocks).
 // ---------------------------------------------------------------------------
+// Descriptor of factor tile (k + 1 + e, k): staged in shared memory, or read
+// from the global table (pair mode, whose shared memory holds a fifth stage).
+__device__ __forceinline__ TileDesc col_tile(const TcParams &p, const TileDesc *col_desc, int64_t e) {
+    return col_desc ? col_desc[e] : p.ltab[off_index(p.k + 1 + e, p.k)];
+}
+
 template <int OP>
 __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, const TileDesc *col_desc) {
     const int64_t b = p.b;
@@ -377,8 +384,8 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
         // panel of the column, 2 = FP16 lo panel.  FP16 tiles are read from the
         // pool directly; FP32 tiles use the hi/lo split, E4M3 tiles their FP16
         // shadow in the hi panel.
-        const TileDesc di = col_desc[w.i - k - 1];
-        const TileDesc dj = col_desc[w.j - k - 1];
+        const TileDesc di = col_tile(p, col_desc, w.i - k - 1);
+        const TileDesc dj = col_tile(p, col_desc, w.j - k - 1);
         const int ahi_map = (di.prec == KRR_PREC_FP16) ? 0 : 1;
         const int bhi_map = (dj.prec == KRR_PREC_FP16) ? 0 : 1;
         const int ahi_row = (int)((di.prec == KRR_PREC_FP16 ? di.offset / (2 * b) : (w.i - k - 1) * b) + w.sm * BM);
@@ -502,6 +509,11 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
 #pragma unroll
         for (int q = 0; q < PRED_MAX_P; ++q) acc[q] = 0.f;
         const int pp = (int)p.p;
+        // K - c: the entries of K concentrate around their mean, so the
+        // shifted products are small and their FP32 sums lose far less to
+        // cancellation; the reduction adds c (1^T A) back in FP64.  Padding
+        // columns hold zero weights.
+        const float kc = p.kshift ? (float)*p.kshift : 0.f;
         for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
             float v[16];
             tmem_ld16(tacc + ch * 16, v);
@@ -510,7 +522,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                 const int c = ch * 16 + e;
                 const int64_t gj = w.j * BN + c;
                 const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
-                const float kv = (gi < p.n_test && gj < p.n) ? expf(-p.gamma * (float)d) : 0.f;
+                const float kv = (gi < p.n_test && gj < p.n) ? expf(-p.gamma * (float)d) - kc : 0.f;
                 const float *ar = aw_s + c * PRED_MAX_P;
 #pragma unroll
                 for (int q = 0; q < PRED_MAX_P; ++q)
@@ -591,7 +603,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
         }
     } else {  // OP_UPDATE
         const int64_t k = p.k;
-        const float sc = 1.f / (col_desc[w.i - k - 1].scale * col_desc[w.j - k - 1].scale);
+        const float sc = 1.f / (col_tile(p, col_desc, w.i - k - 1).scale * col_tile(p, col_desc, w.j - k - 1).scale);
         if (cbuf) {
             // FP16 target staged in shared memory as 4 boxes of 64 columns x
             // 128 rows, 128-byte swizzled: update in place
@@ -735,8 +747,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 16);
     float *aw_s = reinterpret_cast<float *>(nb_s + BN);
     // trailing update: descriptors of factor column k, staged once (aw_s is
-    // unused by that op; 32 KB hold 2048 descriptors)
-    TileDesc *col_desc = reinterpret_cast<TileDesc *>(aw_s);
+    // unused by that op; 32 KB hold 2048 descriptors); pair mode reads them
+    // from the global table instead
+    TileDesc *col_desc = (PAIR == 2) ? nullptr : reinterpret_cast<TileDesc *>(aw_s);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = (PAIR == 2) ? cluster_rank() : 0u;
@@ -780,7 +793,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB0)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB1)) : "memory");
     }
-    if (OP == OP_UPDATE) {
+    if (OP == OP_UPDATE && col_desc) {
         const int64_t ncol = p.nt - p.k - 1;
         for (int64_t e = threadIdx.x; e < ncol; e += blockDim.x) col_desc[e] = p.ltab[off_index(p.k + 1 + e, p.k)];
     }
@@ -963,11 +976,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 // Shared memory: ring + barriers/slots + norms + predict weights + alignment slack.
 constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 256 + BN * 4 + BN * PRED_MAX_P * 4 + 1024;
+// Pair mode (trailing update only) needs no norms, weights or staged
+// descriptors: ring, target block, barriers and slots.
 template <int PAIR>
 constexpr size_t smem_bytes_of() {
-    return (size_t)PairCfg<PAIR>::stages * PairCfg<PAIR>::stage_bytes + PairCfg<PAIR>::cbuf_bytes + 256 + BN * 4 +
-           BN * PRED_MAX_P * 4 + 1024;
+    return (PAIR == 2) ? (size_t)PairCfg<PAIR>::stages * PairCfg<PAIR>::stage_bytes + PairCfg<PAIR>::cbuf_bytes + 256 + 1024
+                       : (size_t)PairCfg<PAIR>::stages * PairCfg<PAIR>::stage_bytes + PairCfg<PAIR>::cbuf_bytes + 256 +
+                             BN * 4 + BN * PRED_MAX_P * 4 + 1024;
 }
+static_assert(smem_bytes_of<2>() <= 227 * 1024, "pair-mode shared memory");
 
 __global__ void split_col0_kernel(const float *Kd, int64_t nt, int64_t b, __half *hi, __half *lo) {
     const int64_t tile = 1 + blockIdx.y;  // tile row i >= 1 of column 0
@@ -1256,7 +1273,8 @@ krr_status tc_grad_terms(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n
 }
 
 krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
-                      int64_t rows_pad, const float *A, int64_t lda, int64_t p_cols, float *part) {
+                      int64_t rows_pad, const float *A, int64_t lda, int64_t p_cols, float *part,
+                      const double *kshift) {
     TcState *st = (TcState *)c->tc;
     if (p_cols < 1 || p_cols > PRED_MAX_P) {
         c->last_error = "tc_predict: at most 32 weight columns per launch";
@@ -1274,6 +1292,7 @@ krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_te
     p.ldaw = lda;
     p.p = p_cols;
     p.part = part;
+    p.kshift = kshift;
     p.items = (rows_pad / BM) * (c->n_pad / BN);
     return launch<KIND_F8, OP_PREDICT>(c, t_map, t_map, st->g_map, st->g_map, p);
 }

@@ -271,10 +271,13 @@ class KRR:
         self._check(self._lib.krr_get_distances(self._ctx, ctypes.c_void_p(out.ctypes.data), self.n))
         return out
 
-    def kernel(self) -> np.ndarray:
-        """FP32 kernel matrix of the lower-triangle tiles (upper tiles left 0)."""
-        out = np.zeros((self.n, self.n), dtype=np.float32)
-        self._check(self._lib.krr_get_kernel(self._ctx, ctypes.c_void_p(out.ctypes.data), self.n))
+    def kernel(self, out=None):
+        """FP32 kernel matrix of the lower-triangle tiles into ``out`` (an n x n
+        host array or device tensor; its strictly-upper tiles are left as they
+        are), or into a new zeroed host array."""
+        if out is None:
+            out = np.zeros((self.n, self.n), dtype=np.float32)
+        self._check(self._lib.krr_get_kernel(self._ctx, ctypes.c_void_p(_ptr(out)), _ld(out)))
         return out
 
     def set_profiling(self, on: bool = True):
