@@ -23,8 +23,8 @@
 // "converter"), then publishes it.
 //
 // Items are claimed from a device counter in dependency order (item 0 converts
-// the first block; then for every column c: the S DIAG items of block c and
-// the LINK items that read its result).  An item only waits for items claimed
+// the first block; then, per column, its S DIAG items, its head LINK items
+// and the LINK items of the column before; see "Items" below).  An item only waits for items claimed
 // before it by running CTAs; every wait is bounded (%globaltimer) and ends the
 // kernel with KRR_ETIMEOUT.
 //
@@ -259,12 +259,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
-// Items.  Item 0 converts the first block of the right-hand side; then column
-// c (0..nt-1) holds S DIAG items and S * (nt - 1 - c) LINK items and starts
-// at 1 + S * (c * nt - c (c - 1) / 2).
+// Items.  Positions count from the start of the sweep: block position c is
+// block c (forward) or nt - 1 - c (backward); LINK(c', p) applies column c'
+// to block position p > c'.  Item 0 converts the first block of the
+// right-hand side; then section c (0..nt-1) lists, S slabs each:
+//   DIAG(c);
+//   LINK(c - 1, c + 1)                 (1 <= c <= nt - 2)
+//   LINK(c, c + 1), the head           (c <= nt - 2)
+//   LINK(c - 1, p) for p = c + 2 .. nt - 1.
+// The updates of a slab apply in column order, the head last, as with a plain
+// column-by-column order; but DIAG(c + 1) is claimed before the bulk of
+// column c's updates (listed one section later), so the chain DIAG -> head ->
+// DIAG of consecutive columns does not wait for those to be claimed.  Every
+// item depends only on items listed before it.  Section sizes: 2S (c = 0,
+// nt > 1), S (nt + 1 - c) (0 < c < nt - 1), S (c = nt - 1).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t col_start(int64_t S, int64_t nt, int64_t c) {
-    return S * (c * nt - c * (c - 1) / 2);
+__device__ __forceinline__ int64_t sec_start(int64_t S, int64_t nt, int64_t c) {
+    if (c == 0) return 0;
+    const int64_t first = (nt > 1) ? 2 * S : S;
+    return first + S * ((c - 1) * (nt + 1) - (c - 1) * c / 2);
 }
 
 __device__ void decode_item(const TsParams &p, int64_t t, ItemHdr &h) {
@@ -284,18 +297,19 @@ __device__ void decode_item(const TsParams &p, int64_t t, ItemHdr &h) {
         return;
     }
     const int64_t u = t - 1;
-    int64_t lo = 0, hi = nt - 1;  // largest c with col_start(c) <= u
+    int64_t lo = 0, hi = nt - 1;  // largest c with sec_start(c) <= u
     while (lo < hi) {
         const int64_t mid = (lo + hi + 1) >> 1;
-        if (col_start(S, nt, mid) <= u) lo = mid;
+        if (sec_start(S, nt, mid) <= u) lo = mid;
         else hi = mid - 1;
     }
-    const int64_t c = lo, r = u - col_start(S, nt, c);
-    const int64_t j = fwd ? c : nt - 1 - c;
-    h.src = (int)j;
+    const int64_t c = lo;
+    int64_t r = u - sec_start(S, nt, c);
     if (r < S) {
+        const int64_t j = fwd ? c : nt - 1 - c;
         h.type = IT_DIAG;
         h.blk = (int)j;
+        h.src = (int)j;
         h.slab = (int)r;
         h.nph = 2;
         h.amap[0] = AM_LHI;
@@ -303,13 +317,28 @@ __device__ void decode_item(const TsParams &p, int64_t t, ItemHdr &h) {
         h.arow[0] = h.arow[1] = (int)(j * b);
         return;
     }
-    const int64_t m = (r - S) / S;
+    r -= S;
+    int64_t col, pos, slab;  // LINK: column and block positions
+    const bool pre = (c >= 1 && c <= nt - 2), head = (c <= nt - 2);
+    if (pre && r < S) {
+        col = c - 1, pos = c + 1, slab = r;
+    } else {
+        if (pre) r -= S;
+        if (head && r < S) {
+            col = c, pos = c + 1, slab = r;
+        } else {
+            if (head) r -= S;
+            col = c - 1, pos = c + 2 + r / S, slab = r % S;
+        }
+    }
+    const int64_t j = fwd ? col : nt - 1 - col;  // block of the vector read
+    const int64_t blk = fwd ? pos : nt - 1 - pos;
     h.type = IT_LINK;
-    h.slab = (int)((r - S) % S);
-    const int64_t blk = fwd ? j + 1 + m : j - 1 - m;
+    h.src = (int)j;
     h.blk = (int)blk;
-    h.seqv = (int)(fwd ? j : nt - 1 - j);
-    h.last_link = fwd ? (j == blk - 1) : (j == blk + 1);
+    h.slab = (int)slab;
+    h.seqv = (int)col;
+    h.last_link = (col == pos - 1) ? 1 : 0;
     // forward reads L_{blk, j}, backward L_{j, blk}
     const int64_t ti = fwd ? blk : j, tj = fwd ? j : blk;
     const int64_t off = off_index(ti, tj);
@@ -1400,7 +1429,7 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
         sp.S = b / TS_SLAB;
         sp.KC = b / TS_KC;
         sp.n_pad = c->n_pad;
-        sp.items = 1 + sp.S * nt * (nt + 1) / 2;
+        sp.items = 1 + sp.S * nt * (nt + 1) / 2;  // sum of the section sizes
         sp.pc = (int)std::min<int64_t>(TS_NPMAX, p - q0);
         sp.np = (sp.pc + 15) & ~15;
         sp.q0 = (int)q0;
