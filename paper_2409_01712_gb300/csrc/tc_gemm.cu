@@ -66,12 +66,15 @@ constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >
 // cta_group::2 over a 256 x 256 block, M = 256: each CTA stages its own 128 A
 // rows and one 128-row half of B, and keeps its 128 output rows in its TMEM.
 // A stage is 32 KB instead of 48 KB.
+constexpr int BOX_BYTES = BM * 128;     // one 64-column box of an FP16 target block
+
 template <int PAIR>
 struct PairCfg {
-    static constexpr int stages = (PAIR == 2) ? 5 : STAGES;
-    // pair mode (trailing update): the FP16 target block (128 x 256) is staged
-    // in shared memory by TMA, updated there and stored back by TMA
-    static constexpr int cbuf_bytes = (PAIR == 2) ? BM * BN * 2 : 0;
+    static constexpr int stages = (PAIR == 2) ? 6 : STAGES;
+    // pair mode (trailing update): the FP16 target block (128 x 256) passes
+    // through shared memory as four 64-column boxes in two buffers (TMA load,
+    // update in place, TMA store)
+    static constexpr int cbuf_bytes = (PAIR == 2) ? 2 * BOX_BYTES : 0;
     static constexpr int stage_bytes = (PAIR == 2) ? 2 * A_BYTES : STAGE_BYTES;
     static constexpr uint32_t idesc = (PAIR == 2)
         ? (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)((2 * BM) >> 4) << 24)
@@ -182,6 +185,14 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
         : "memory");
+}
+
+// L2 prefetch of a tensor-map box (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y)
+                 : "memory");
 }
 
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, const void *src) {
@@ -444,7 +455,7 @@ __device__ __forceinline__ void epilogue_prefetch(const TcParams &p, const Work 
 template <int OP>
 __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row, int half,
                                          int32_t *nb_s, float *aw_s, double *red_s,
-                                         const TileDesc *col_desc, uint8_t *cbuf = nullptr) {
+                                         const TileDesc *col_desc) {
     const int64_t b = p.b;
     const int ch0 = half * CH_PER_HALF;
     if (OP == OP_DIST) {
@@ -604,32 +615,6 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
     } else {  // OP_UPDATE
         const int64_t k = p.k;
         const float sc = 1.f / (col_tile(p, col_desc, w.i - k - 1).scale * col_tile(p, col_desc, w.j - k - 1).scale);
-        if (cbuf) {
-            // FP16 target staged in shared memory as 4 boxes of 64 columns x
-            // 128 rows, 128-byte swizzled: update in place
-#pragma unroll
-            for (int cc = 0; cc < CH_PER_HALF; ++cc) {
-                float v[16];
-                tmem_ld16(tacc + (ch0 + cc) * 16, v);
-                const int col = half * 128 + cc * 16, u0 = (col & 63) >> 3;
-                uint8_t *rp = cbuf + (col >> 6) * (BM * 128) + row * 128;
-                uint4 *q0 = reinterpret_cast<uint4 *>(rp + ((u0 ^ (row & 7)) << 4));
-                uint4 *q1 = reinterpret_cast<uint4 *>(rp + (((u0 + 1) ^ (row & 7)) << 4));
-                uint4 u[2] = {*q0, *q1};
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    __half2 *h2 = reinterpret_cast<__half2 *>(&u[e]);
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        const float2 f = __half22float2(h2[qq]);
-                        h2[qq] = __floats2half2_rn(f.x - v[8 * e + 2 * qq] * sc, f.y - v[8 * e + 2 * qq + 1] * sc);
-                    }
-                }
-                *q0 = u[0];
-                *q1 = u[1];
-            }
-            return;
-        }
         const int64_t lr = w.sm * BM + row;
         const bool diag = (w.i == w.j);
         const float *cin32 = nullptr;
@@ -693,6 +678,34 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
     }
 }
 
+// Trailing update, FP16 target: box bx (columns [64 bx, 64 bx + 64)) of the
+// block, staged 128-byte swizzled in `box` (128 rows of 128 bytes), is
+// updated in place from the accumulator: thread `row` takes columns
+// [32 hh, 32 hh + 32) of the box.
+__device__ __forceinline__ void update_box(uint32_t tacc, int row, int hh, int bx, uint8_t *box, float sc) {
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+        const int col = hh * 32 + cc * 16, u0 = col >> 3;
+        float v[16];
+        tmem_ld16(tacc + bx * 64 + col, v);
+        uint8_t *rp = box + row * 128;
+        uint4 *q0 = reinterpret_cast<uint4 *>(rp + ((u0 ^ (row & 7)) << 4));
+        uint4 *q1 = reinterpret_cast<uint4 *>(rp + (((u0 + 1) ^ (row & 7)) << 4));
+        uint4 u[2] = {*q0, *q1};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            __half2 *h2 = reinterpret_cast<__half2 *>(&u[e]);
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const float2 f = __half22float2(h2[qq]);
+                h2[qq] = __floats2half2_rn(f.x - v[8 * e + 2 * qq] * sc, f.y - v[8 * e + 2 * qq + 1] * sc);
+            }
+        }
+        *q0 = u[0];
+        *q1 = u[1];
+    }
+}
+
 // Per-block epilogue inputs staged in shared memory by the epilogue warps.
 template <int OP>
 __device__ __forceinline__ void epilogue_stage(const TcParams &p, const Work &w, int row,
@@ -741,7 +754,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NST * SBYTES + PairCfg<PAIR>::cbuf_bytes);
     uint64_t *full = bars, *empty = bars + NST, *tfull = bars + 2 * NST,
              *tempty = bars + 2 * NST + 2, *drain = bars + 2 * NST + 4, *cfull = bars + 2 * NST + 5;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NST + 6);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * NST + 7);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     double *red_s = reinterpret_cast<double *>(tmem_slot + 2);
     int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 16);
@@ -767,7 +780,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mbar_init(&tempty[a], PAIR * (EPI_THREADS / 32));  // one arrival per epilogue warp
         }
         mbar_init(drain, 1);
-        mbar_init(cfull, 1);
+        mbar_init(&cfull[0], 1);
+        mbar_init(&cfull[1], 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -899,37 +913,69 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // ---------------- epilogue warps ----------------
         const int row = ((warp & 3) << 5) + lane;  // TMEM lane quarter of this warp
         const int half = (warp - 2) >> 2;          // column half of the block
+        const int hh = (warp - 2) >> 2;            // 32-column half of a target box
         int acc = 0;
-        uint32_t aph = 0, cph = 0;
-        bool cload_pending = false;  // thread 64: a staging load was issued and not waited for
+        uint32_t aph = 0, cph = 0;                 // cph: phases of the two box buffers
+        uint32_t cload_pending = 0;  // thread 64: box buffers with a load issued and not waited for
         for (int64_t u = ustart; u < nunits; u += ustep) {
             Work w;
             decode<OP>(p, unit_item(u), w, col_desc);
             if (w.nph * w.nkb == 0) continue;
-            // pair mode, FP16 target: stage it by TMA while the MMAs run (the
-            // previous block's store must have read the buffer first)
+            // pair mode, FP16 target: the block goes through shared memory box by
+            // box; the first two boxes load while the MMAs run (once the previous
+            // block's stores have read the buffers), the other two are prefetched
+            // into L2
             const bool cstage = (PAIR == 2 && OP == OP_UPDATE) && p.k > 0 && w.i != w.j;
+            const int ybox = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
             if (cstage && threadIdx.x == 64) {
                 bulk_wait_read();
-                mbar_arrive_expect_tx(cfull, (uint32_t)PairCfg<PAIR>::cbuf_bytes);
-                const int y = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
-                for (int bx = 0; bx < BN / 64; ++bx)
-                    tma_load_2d(cbuf + bx * (BM * 128), &mB1, (int)(w.sn * BN + bx * 64), y, cfull);
-                cload_pending = true;
+                for (int bx = 0; bx < 2; ++bx) {
+                    mbar_arrive_expect_tx(&cfull[bx], (uint32_t)BOX_BYTES);
+                    tma_load_2d(cbuf + bx * BOX_BYTES, &mB1, (int)(w.sn * BN + bx * 64), ybox, &cfull[bx]);
+                }
+                for (int bx = 2; bx < BN / 64; ++bx) tma_prefetch_2d(&mB1, (int)(w.sn * BN + bx * 64), ybox);
+                cload_pending = 3u;
             }
             epi_bar();
             epilogue_stage<OP>(p, w, threadIdx.x - 64, nb_s, aw_s);
             if (!cstage) epilogue_prefetch<OP>(p, w, row, half);
             epi_bar();
             if (!wait_bar(&tfull[acc], aph, budget, abort_flag, p.err)) break;
-            if (cstage) {
-                if (!wait_bar(cfull, cph, budget, abort_flag, p.err)) break;
-                cph ^= 1;
-                cload_pending = false;
-            }
             tmem_fence_after();
             const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * BN);
-            epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc, cstage ? cbuf : nullptr);
+            if (cstage) {
+                const float sc = 1.f / (col_tile(p, col_desc, w.i - p.k - 1).scale *
+                                        col_tile(p, col_desc, w.j - p.k - 1).scale);
+                bool ok = true;
+                for (int bx = 0; bx < BN / 64; ++bx) {
+                    const int bi = bx & 1;
+                    // every thread reaches the barrier, then all take the same
+                    // decision (a wait that ran out set the abort flag)
+                    wait_bar(&cfull[bi], (cph >> bi) & 1u, budget, abort_flag, p.err);
+                    epi_bar();
+                    if (*abort_flag) { ok = false; break; }
+                    cph ^= 1u << bi;
+                    if (threadIdx.x == 64) cload_pending &= ~(1u << bi);
+                    update_box(tacc, row, hh, bx, cbuf + bi * BOX_BYTES, sc);
+                    // generic-proxy writes become visible to the TMA store
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    epi_bar();
+                    if (threadIdx.x == 64) {
+                        tma_store_2d(&mB1, (int)(w.sn * BN + bx * 64), ybox, cbuf + bi * BOX_BYTES);
+                        bulk_commit();
+                        if (bx + 2 < BN / 64) {
+                            bulk_wait_read();  // the store has read the buffer
+                            mbar_arrive_expect_tx(&cfull[bi], (uint32_t)BOX_BYTES);
+                            tma_load_2d(cbuf + bi * BOX_BYTES, &mB1, (int)(w.sn * BN + (bx + 2) * 64), ybox,
+                                        &cfull[bi]);
+                            cload_pending |= 1u << bi;
+                        }
+                    }
+                }
+                if (!ok) break;
+            } else {
+                epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc);
+            }
             tmem_fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -937,23 +983,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 else mbar_arrive(&tempty[acc]);
             }
             if (++acc == 2) { acc = 0; aph ^= 1; }
-            if (cstage) {
-                // generic-proxy writes become visible to the TMA store
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                epi_bar();
-                if (threadIdx.x == 64) {
-                    const int y = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
-                    for (int bx = 0; bx < BN / 64; ++bx)
-                        tma_store_2d(&mB1, (int)(w.sn * BN + bx * 64), y, cbuf + bx * (BM * 128));
-                    bulk_commit();
-                }
-            }
         }
         if (PAIR == 2 && threadIdx.x == 64) {
             bulk_wait_all();  // stores finished before the CTA leaves
-            if (cload_pending) {  // aborted with a staging load in flight
-                const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(cfull, cph) && globaltimer() - t0 < budget) {}
+            for (int bi = 0; bi < 2; ++bi) {
+                if (cload_pending & (1u << bi)) {  // aborted with a box load in flight
+                    const uint64_t t0 = globaltimer();
+                    while (!mbar_try_wait(&cfull[bi], (cph >> bi) & 1u) && globaltimer() - t0 < budget) {}
+                }
             }
         }
     }
