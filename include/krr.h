@@ -57,7 +57,7 @@ typedef enum krr_mode {
 enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_FP16 = 2, KRR_PREC_E4M3 = 3 };
 
 typedef struct krr_options {
-    int64_t tile;            /* b: tile edge, a multiple of 256 (default 1024) */
+    int64_t tile;            /* b: tile edge, a power of two in [256, 4096] (default 1024) */
     int32_t mode;            /* krr_mode (default KRR_MODE_MIXED) */
     int32_t allow_fp8;       /* 1: E4M3 allowed for factor tiles (default 1) */
     double eps;              /* adaptive-precision threshold: a factor tile L_ik may be stored
@@ -98,8 +98,8 @@ void krr_default_options(krr_options *opt);
 /*
  * Creates a context bound to the current CUDA device and to `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  opt may be NULL for
- * the defaults.  Returns KRR_EINVAL for a tile edge that is not a positive
- * multiple of 256 or an unknown mode.
+ * the defaults.  Returns KRR_EINVAL for a tile edge that is not a power of
+ * two in [256, 4096] or an unknown mode.
  */
 krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream);
 

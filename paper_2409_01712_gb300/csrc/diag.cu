@@ -16,11 +16,16 @@
 //                 split of X (operands of the tensor-core panel solve), per
 //                 64-row block.
 // Progress counters: upd[i][j] (updates applied to block (i, j)), pdone[q],
-// tdone[i][q], the number of finished factor items, and finished items per
-// inverse step.  An item only waits for items claimed before it by running
-// CTAs, so the kernel always progresses; every wait is bounded
-// (%globaltimer) and ends the kernel with KRR_ETIMEOUT.  Blocks written by
-// other CTAs are read through L2 (ld.global.cg).
+// tdone[i][q], and finished items of each inverse pair (step 1 and step 2
+// separately).  Inverse items wait only for the blocks they read: a step-1
+// item for its row of L_21 (T items) and for X_11 (the pair's first half),
+// a step-2 item for X_22 and the pair's step-1 products, a finishing item for
+// the pairs whose second half holds its rows; so the inverse of the leading
+// blocks runs while the factorisation of the trailing ones goes on.  An item
+// only waits for items claimed before it by running CTAs, so the kernel always
+// progresses; every wait is bounded (%globaltimer) and ends the kernel with
+// KRR_ETIMEOUT.  Blocks written by other CTAs are read through L2
+// (ld.global.cg).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -41,7 +46,7 @@ struct DiagParams {
     float *X;          // inverse (zeroed before the launch)
     float *XT;         // transpose of the inverse
     __half *hi, *lo;   // FP16 split of the inverse (or null)
-    float *tmp;        // b * b / 2 floats: products of the inverse step
+    float *tmp;        // b * b / 2 floats: products of the inverse steps, one region per level
     int64_t b;
     int NB, levels;
     int64_t tile_k;
@@ -53,14 +58,22 @@ struct DiagParams {
     uint64_t wait_ns;
 };
 
-// counter layout: [0] item counter, [1] abort, [2] finished factor items,
-// [3 .. 3 + 2 * levels) finished items per inverse step, then pdone[NB],
-// tdone[NB * NB], upd[NB * NB]
-__device__ __forceinline__ int *ctr_fdone(const DiagParams &p) { return p.ctr + 2; }
-__device__ __forceinline__ int *ctr_phase(const DiagParams &p, int ph) { return p.ctr + 3 + ph; }
-__device__ __forceinline__ int *ctr_pdone(const DiagParams &p) { return p.ctr + 3 + 2 * p.levels; }
+// counter layout: [0] item counter, [1] abort, then pdone[NB], tdone[NB * NB],
+// upd[NB * NB], and per inverse pair (all levels, fewer than NB pairs) the
+// finished step-1 items i1done[NB] and step-2 items i2done[NB]
+__device__ __forceinline__ int *ctr_pdone(const DiagParams &p) { return p.ctr + 2; }
 __device__ __forceinline__ int *ctr_tdone(const DiagParams &p) { return ctr_pdone(p) + p.NB; }
 __device__ __forceinline__ int *ctr_upd(const DiagParams &p) { return ctr_tdone(p) + p.NB * p.NB; }
+__device__ __forceinline__ int *ctr_i1done(const DiagParams &p) { return ctr_upd(p) + p.NB * p.NB; }
+__device__ __forceinline__ int *ctr_i2done(const DiagParams &p) { return ctr_i1done(p) + p.NB; }
+
+// Slot of pair `pr` of inverse level l (levels before it hold NB / 2,
+// NB / 4, ... pairs).
+__device__ __forceinline__ int pair_slot(const DiagParams &p, int l, int pr) {
+    int base = 0;
+    for (int q = 0; q < l; ++q) base += p.NB >> (q + 1);
+    return base + pr;
+}
 
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
@@ -449,13 +462,28 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
                 ok = wait_ge(tdone + it.i * NB + it.q, 1, p) && wait_ge(tdone + it.j * NB + it.q, 1, p) &&
                      wait_ge(upd + it.i * NB + it.j, it.q, p);
             } else if (it.kind == K_I1 || it.kind == K_I2) {
-                ok = (it.phase == 0) ? wait_ge(ctr_fdone(p), (int)p.n_factor, p)
-                                     : wait_ge(ctr_phase(p, it.phase - 1),
-                                               (int)inv_step_items(NB, (it.phase - 1) / 2), p);
+                const int nb = 1 << it.level, r0 = 2 * it.pair * nb, half = nb / 2;
+                // X of the pair's first (I1) or second (I2) half: the P item at
+                // level 0, else all step-2 items of that half one level down
+                const int sub = (it.kind == K_I1) ? 0 : 1;
+                ok = (it.level == 0) ? wait_ge(pdone + r0 + sub, 1, p)
+                                     : wait_ge(ctr_i2done(p) + pair_slot(p, it.level - 1, 2 * it.pair + sub),
+                                               half * half, p);
+                if (it.kind == K_I1) {
+                    // row a of L_21, columns c .. nb - 1
+                    for (int k = it.c; k < nb && ok; ++k) ok = wait_ge(tdone + (r0 + nb + it.a) * NB + r0 + k, 1, p);
+                } else {
+                    ok = ok && wait_ge(ctr_i1done(p) + pair_slot(p, it.level, it.pair), nb * nb, p);
+                }
             } else {
-                ok = (p.levels == 0) ? wait_ge(ctr_fdone(p), (int)p.n_factor, p)
-                                     : wait_ge(ctr_phase(p, 2 * p.levels - 1),
-                                               (int)inv_step_items(NB, p.levels - 1), p);
+                // row block r of X: its diagonal block, and the step-2 items of
+                // every pair whose second half holds it
+                const int r = it.i;
+                ok = wait_ge(pdone + r, 1, p);
+                for (int l = 0; l < p.levels && ok; ++l) {
+                    const int nb = 1 << l;
+                    if (r % (2 * nb) >= nb) ok = wait_ge(ctr_i2done(p) + pair_slot(p, l, r / (2 * nb)), nb * nb, p);
+                }
             }
             ok_s = ok ? 1 : 0;
         }
@@ -487,7 +515,9 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
             store_blk(p.W + (int64_t)it.i * DB * b + it.j * DB, b, acc, -1.f, 1.f);
         } else if (it.kind == K_I1 || it.kind == K_I2) {
             const int64_t nb = (int64_t)1 << it.level, sz = nb * DB, base = 2 * it.pair * sz;
-            float *tp = p.tmp + (int64_t)it.pair * sz * sz;
+            // products of level l after those of levels 0 .. l - 1 (each level
+            // NB * 2^l * DB * DB / 2 floats): levels run concurrently
+            float *tp = p.tmp + (int64_t)p.NB * (nb - 1) * (DB * DB / 2) + (int64_t)it.pair * sz * sz;
             if (it.kind == K_I1) {
                 // T_p[a][c] = sum_{k >= c} L21[a][k] X11[k][c]
                 for (int64_t kk = it.c; kk < nb; ++kk) {
@@ -540,10 +570,11 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
                 signal(ctr_tdone(p) + it.i * NB + it.q);
             } else if (it.kind == K_U) {
                 signal(ctr_upd(p) + it.i * NB + it.j);
-            } else if (it.kind == K_I1 || it.kind == K_I2) {
-                signal(ctr_phase(p, it.phase));
+            } else if (it.kind == K_I1) {
+                signal(ctr_i1done(p) + pair_slot(p, it.level, it.pair));
+            } else if (it.kind == K_I2) {
+                signal(ctr_i2done(p) + pair_slot(p, it.level, it.pair));
             }
-            if (it.kind <= K_U) atomicAdd(ctr_fdone(p), 1);  // ordered after the signal's fence
         }
     }
 }
@@ -552,9 +583,7 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
 
 int64_t diag_counter_count(int64_t b) {
     const int64_t NB = b / DB;
-    int levels = 0;
-    while (((int64_t)DB << levels) < b) ++levels;
-    return 3 + 2 * levels + NB + 2 * NB * NB;
+    return 2 + NB + 2 * NB * NB + 2 * NB;
 }
 
 // Factor + inverse of diagonal tile k in FP32 (W in place, Linv, LinvT and

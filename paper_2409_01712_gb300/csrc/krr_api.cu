@@ -156,8 +156,13 @@ krr_status store_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, flo
         launch_copy_rows(src, cols, dst, ld, n, cols, n, c->stream);
         return check_launch(c, "copy rows");
     }
-    KRR_CUDA_TRY(c, cudaMemcpy2DAsync(dst, ld * sizeof(float), src, cols * sizeof(float),
-                                      cols * sizeof(float), n, cudaMemcpyDeviceToHost, c->stream));
+    if (ld == cols) {  // contiguous rows: one linear copy
+        KRR_CUDA_TRY(c, cudaMemcpyAsync(dst, src, (size_t)n * cols * sizeof(float), cudaMemcpyDeviceToHost,
+                                        c->stream));
+    } else {
+        KRR_CUDA_TRY(c, cudaMemcpy2DAsync(dst, ld * sizeof(float), src, cols * sizeof(float),
+                                          cols * sizeof(float), n, cudaMemcpyDeviceToHost, c->stream));
+    }
     KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return KRR_OK;
 }
@@ -169,8 +174,13 @@ krr_status pack(Ctx *c, const int8_t *g, int64_t n, int64_t m, int64_t ldg, int6
     const int8_t *dg = g;
     if (!is_device_ptr(g)) {
         KRR_TRY(stage(c, (size_t)n * m));
-        KRR_CUDA_TRY(c, cudaMemcpy2DAsync(c->stage, m, g, ldg, m, n, cudaMemcpyHostToDevice,
-                                          c->stream));
+        // one linear copy when the rows are contiguous (a pitched copy of short
+        // rows runs far below the host link's rate)
+        if (ldg == m) {
+            KRR_CUDA_TRY(c, cudaMemcpyAsync(c->stage, g, (size_t)n * m, cudaMemcpyHostToDevice, c->stream));
+        } else {
+            KRR_CUDA_TRY(c, cudaMemcpy2DAsync(c->stage, m, g, ldg, m, n, cudaMemcpyHostToDevice, c->stream));
+        }
         dg = (const int8_t *)c->stage;
         ldg = m;
     }
@@ -361,8 +371,10 @@ krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
     krr_options o;
     krr_default_options(&o);
     if (opt) o = *opt;
-    if (o.tile < 256 || o.tile % 256 != 0 || o.tile > 4096) {
-        g_create_error = "tile must be a multiple of 256 in [256, 4096]";
+    // a power of two: the diagonal step inverts the factor by recursive
+    // doubling over 64-wide blocks
+    if (o.tile < 256 || o.tile > 4096 || (o.tile & (o.tile - 1)) != 0) {
+        g_create_error = "tile must be a power of two in [256, 4096]";
         return KRR_EINVAL;
     }
     if (o.mode != KRR_MODE_MIXED && o.mode != KRR_MODE_FP32) {

@@ -149,9 +149,10 @@ def test_errors():
         model.factor(0.1)
         a, info = model.solve(_to(prob["Y"]))
         assert info["converged"]
-    with pytest.raises(KRRError) as e:
-        KRR(tile=300)
-    assert e.value.status == krrmod.EINVAL
+    for bad_tile in (300, 768):  # a power of two in [256, 4096] only
+        with pytest.raises(KRRError) as e:
+            KRR(tile=bad_tile)
+        assert e.value.status == krrmod.EINVAL
 
 
 @pytest.mark.parametrize("mode", MODES)
