@@ -728,10 +728,19 @@ __device__ __forceinline__ void epilogue_stage(const TcParams &p, const Work &w,
         }
     } else if (OP == OP_PREDICT || OP == OP_GRADT) {
         for (int c = row; c < BN; c += EPI_THREADS) nb_s[c] = p.norms_b[w.j * BN + c];
-        for (int e = row; e < BN * PRED_MAX_P; e += EPI_THREADS) {
-            const int c = e / PRED_MAX_P, q = e % PRED_MAX_P;
-            aw_s[e] = (q < p.p) ? p.aw[(w.j * BN + c) * p.ldaw + q] : 0.f;
+        // weights of the block's 256 rows: thread `row` takes element q = row %
+        // 32 of rows row / 32 + 8 k; all 32 loads are in flight before the
+        // (bank-conflict-free) stores
+        constexpr int PER = BN * PRED_MAX_P / EPI_THREADS;
+        const int q = row % PRED_MAX_P;
+        float v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int c = row / PRED_MAX_P + k * (EPI_THREADS / PRED_MAX_P);
+            v[k] = (q < p.p) ? __ldg(p.aw + (w.j * BN + c) * p.ldaw + q) : 0.f;
         }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) aw_s[row + k * EPI_THREADS] = v[k];
     }
 }
 
