@@ -148,6 +148,23 @@ def dist_env():
     return world, rank, local
 
 
+def slowest_ms(ms, dist=None, device=None):
+    """The job's time per step: the largest of the ranks' times (replicas run
+    independently; the job ends with the slowest)."""
+    if dist is None:
+        return ms
+    import torch
+
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(world, ops_per_rank, ms):
+    """Whole-job TOp/s: every rank's operations over the slowest rank's time."""
+    return world * ops_per_rank / (ms / 1e3) / 1e12
+
+
 def cpu_sample(cfg, n_sample, g_host=None, y_host=None):
     """Times the oracle's build + factor + solve on the first n_sample rows."""
     import oracle
@@ -252,12 +269,9 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     prof = model.profile(reset=True)
     model.set_profiling(False)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = slowest_ms(ms, dist, dev)
     ops = metric_ops(n, m, p)
-    value = world * ops / (ms / 1e3) / 1e12
+    value = job_value(world, ops, ms)
     fi, si = infos[-1]
 
     pk, pk_kind = peaks()
@@ -330,13 +344,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         wall = (time.perf_counter() - w0) / args.steps
         ems = max(e0.elapsed_time(e1) / args.steps, wall * 1e3)
-        if dist:
-            tt = torch.tensor([ems], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ems = float(tt.item())
+        ems = slowest_ms(ems, dist, dev)
         h2d = n * m + n * p * 4 + n_test * m + n * p * 4
         d2h = n * p * 4 + n_test * p * 4
-        line["e2e"] = {"value": world * ops / (ems / 1e3) / 1e12, "unit": "TOp/s", "ms_per_step": ems,
+        line["e2e"] = {"value": job_value(world, ops, ems), "unit": "TOp/s", "ms_per_step": ems,
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # ---- sampled accuracy check against the oracle (outside the timing)
