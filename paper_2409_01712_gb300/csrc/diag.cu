@@ -4,17 +4,22 @@
 //
 // Items, claimed from a device counter in an order that respects their
 // dependencies:
-//   factor, for q = 0 .. NB-1 (NB = b / 64):
-//     P(q)        L_qq = chol(A_qq) and X_qq = inv(L_qq) in shared memory
-//     T(i, q)     L_iq = A_iq X_qq^T                     (i > q)
-//     U(i, j, q)  A_ij -= L_iq L_jq^T                    (q < j <= i)
+//   factor (NB = b / 64):
+//     P(q)        for q >= 1 first L_q,q-1 = A_q,q-1 X_q-1,q-1^T (published at
+//                 once) and A_qq -= L_q,q-1 L_q,q-1^T, then L_qq = chol(A_qq)
+//                 and X_qq = inv(L_qq) in shared memory: the chain from one
+//                 diagonal block to the next is a single item
+//     T(i, q)     L_iq = A_iq X_qq^T                     (i > q + 1)
+//     U(i, j, q)  A_ij -= L_iq L_jq^T                    (q < j <= i, i > q + 1)
+//   listed as P(0), then for q = 0 .. NB-2: P(q + 1) and the T and U items of
+//   column q;
 //   inverse X = L^-1 by recursive doubling, for s = 64, 128, ..., b / 2 and
 //   every pair of diagonal s-blocks:
 //     step 1      T_p = L_21 X_11                        (one 64 x 64 output block per item)
 //     step 2      X_21 = -X_22 T_p
 //   finish        X^T (for the backward substitution) and the FP16 hi/lo
 //                 split of X (operands of the tensor-core panel solve), per
-//                 64-row block.
+//                 64 x 64 block, as soon as that block of X is final.
 // Progress counters: upd[i][j] (updates applied to block (i, j)), pdone[q],
 // tdone[i][q], and finished items of each inverse pair (step 1 and step 2
 // separately).  Inverse items wait only for the blocks they read: a step-1
@@ -127,12 +132,16 @@ struct DItem {
     int phase;       // inverse step index 2 * level + (0 | 1)
 };
 
+// Items of factor group q (0 <= q <= NB - 2): P(q + 1), then for every row
+// i = q + 2 .. NB - 1 the items T(i, q), U(i, q + 1 .. i, q).
+__host__ __device__ inline int64_t factor_group_items(int NB, int q) {
+    const int64_t m = NB - q - 1;  // rows below block q
+    return m + m * (m + 1) / 2 - 1;
+}
+
 __host__ __device__ inline int64_t factor_items_for(int NB) {
-    int64_t n = 0;
-    for (int q = 0; q < NB; ++q) {
-        const int64_t m = NB - q - 1;
-        n += 1 + m + m * (m + 1) / 2;
-    }
+    int64_t n = 1;  // P(0)
+    for (int q = 0; q + 1 < NB; ++q) n += factor_group_items(NB, q);
     return n;
 }
 
@@ -146,21 +155,27 @@ __host__ __device__ inline int64_t inv_step_items(int NB, int l) {
 __device__ void decode_item(const DiagParams &p, int64_t t, DItem &it) {
     const int NB = p.NB;
     if (t < p.n_factor) {
-        // walk the q groups: 1 P, then rows i = q+1.. with T(i, q) and U(i, j, q)
-        int64_t r = t;
-        for (int q = 0; q < NB; ++q) {
-            const int64_t m = NB - q - 1, g = 1 + m + m * (m + 1) / 2;
+        if (t == 0) {
+            it.kind = K_P;
+            it.q = 0;
+            return;
+        }
+        // walk the q groups: P(q + 1), then rows i = q + 2.. with T(i, q) and U(i, j, q)
+        int64_t r = t - 1;
+        for (int q = 0; q + 1 < NB; ++q) {
+            const int64_t g = factor_group_items(NB, q);
             if (r >= g) {
                 r -= g;
                 continue;
             }
-            it.q = q;
             if (r == 0) {
                 it.kind = K_P;
+                it.q = q + 1;
                 return;
             }
+            it.q = q;
             --r;
-            for (int i = q + 1; i < NB; ++i) {
+            for (int i = q + 2; i < NB; ++i) {
                 const int64_t row = 1 + (i - q);  // T + U(i, q+1..i)
                 if (r < row) {
                     it.i = i;
@@ -194,7 +209,8 @@ __device__ void decode_item(const DiagParams &p, int64_t t, DItem &it) {
         }
     }
     it.kind = K_FIN;
-    it.i = (int)r;  // 64-row block of the inverse
+    it.i = (int)(r / NB);  // block (i, j) of the inverse
+    it.j = (int)(r % NB);
 }
 
 // ---------------------------------------------------------------------------
@@ -409,7 +425,9 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
     }
 }
 
-__device__ void potrf_inv_block(const DiagParams &p, int q, BlkSmem &s) {
+// sub (optional): a product to subtract from A_qq first, held as the 16 x 16
+// thread grid of mac_blk holds it.
+__device__ void potrf_inv_block(const DiagParams &p, int q, BlkSmem &s, const float (*sub)[4] = nullptr) {
     float (*a)[DB + 1] = s.a;
     float (*x)[DB + 1] = s.b;
     const int64_t b = p.b;
@@ -420,6 +438,14 @@ __device__ void potrf_inv_block(const DiagParams &p, int q, BlkSmem &s) {
     constexpr int RS = DT / DB;
     for (int r = ty; r < DB; r += RS) a[r][tx] = __ldcg(blk + (int64_t)r * b + tx);
     __syncthreads();
+    if (sub) {
+        const int gx = threadIdx.x & 15, gy = threadIdx.x >> 4;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) a[gy + 16 * u][gx + 16 * v] -= sub[u][v];
+        __syncthreads();
+    }
     int bad = -1;
     float mpiv = 3.0e38f;
     chol_inv_64(a, x, tmp, dinv, bad, mpiv);
@@ -455,7 +481,11 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
             bool ok = true;
             int *upd = ctr_upd(p), *tdone = ctr_tdone(p), *pdone = ctr_pdone(p);
             if (it.kind == K_P) {
-                ok = wait_ge(upd + it.q * NB + it.q, it.q, p);
+                // P(q), q >= 1: X_q-1,q-1, and blocks (q, q-1) and (q, q) with the
+                // updates of columns 0 .. q-2
+                if (it.q > 0)
+                    ok = wait_ge(pdone + it.q - 1, 1, p) && wait_ge(upd + it.q * NB + it.q - 1, it.q - 1, p) &&
+                         wait_ge(upd + it.q * NB + it.q, it.q - 1, p);
             } else if (it.kind == K_T) {
                 ok = wait_ge(pdone + it.q, 1, p) && wait_ge(upd + it.i * NB + it.q, it.q, p);
             } else if (it.kind == K_U) {
@@ -475,16 +505,14 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
                 } else {
                     ok = ok && wait_ge(ctr_i1done(p) + pair_slot(p, it.level, it.pair), nb * nb, p);
                 }
-            } else {
-                // row block r of X: its diagonal block, and the step-2 items of
-                // every pair whose second half holds it
-                const int r = it.i;
-                ok = wait_ge(pdone + r, 1, p);
-                for (int l = 0; l < p.levels && ok; ++l) {
-                    const int nb = 1 << l;
-                    if (r % (2 * nb) >= nb) ok = wait_ge(ctr_i2done(p) + pair_slot(p, l, r / (2 * nb)), nb * nb, p);
-                }
-            }
+            } else if (it.j == it.i) {
+                ok = wait_ge(pdone + it.i, 1, p);  // diagonal block of X
+            } else if (it.j < it.i) {
+                // block (i, j) of X is written by the step-2 items of the pair in
+                // which i and j first fall into different halves
+                const int l = 31 - __clz(it.i ^ it.j), nb = 1 << l;
+                ok = wait_ge(ctr_i2done(p) + pair_slot(p, l, it.i >> (l + 1)), nb * nb, p);
+            }  // blocks above the diagonal are zero from the start
             ok_s = ok ? 1 : 0;
         }
         __syncthreads();
@@ -495,7 +523,34 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
         if (it.kind == K_P) {
-            potrf_inv_block(p, it.q, s);
+            if (it.q > 0) {
+                // L_q,q-1 = A_q,q-1 X_q-1,q-1^T, published for the U items of column q-1
+                const int q = it.q;
+                float *c = p.W + (int64_t)q * DB * b + (q - 1) * DB;
+                load_blk(s.a, c, b, false);
+                load_blk(s.b, p.X + (int64_t)(q - 1) * DB * b + (q - 1) * DB, b, true);
+                __syncthreads();
+                mac_blk(s, acc);
+                __syncthreads();
+                store_blk(c, b, acc, 1.f, 0.f);
+                // L_q,q-1 into s.a and, transposed, into s.b; then L L^T
+                const int gx = threadIdx.x & 15, gy = threadIdx.x >> 4;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        s.a[gy + 16 * u][gx + 16 * v] = acc[u][v];
+                        s.b[gx + 16 * v][gy + 16 * u] = acc[u][v];
+                        acc[u][v] = 0.f;
+                    }
+                __syncthreads();
+                if (threadIdx.x == 0) signal(ctr_tdone(p) + q * NB + q - 1);
+                mac_blk(s, acc);
+                __syncthreads();
+                potrf_inv_block(p, q, s, acc);
+            } else {
+                potrf_inv_block(p, it.q, s);
+            }
         } else if (it.kind == K_T) {
             // L_iq = A_iq X_qq^T, in place
             float *c = p.W + (int64_t)it.i * DB * b + it.q * DB;
@@ -540,25 +595,22 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
                 store_blk(p.X + (base + sz + it.a * DB) * b + base + it.c * DB, b, acc, -1.f, 0.f);
             }
         } else {
-            // 64-row block r of X: transpose into X^T and the FP16 split
-            const int r = it.i;
-            for (int cb = 0; cb < NB; ++cb) {
-                const float *src = p.X + (int64_t)r * DB * b + cb * DB;
-                load_blk(s.a, src, b, false);
-                __syncthreads();
-                for (int e = threadIdx.x; e < DB * DB; e += DT) {
-                    const int rr = e / DB, cc = e % DB;
-                    // X^T block (cb, r): element (cc, rr) = X (rr, cc)
-                    __stcg(p.XT + ((int64_t)cb * DB + rr) * b + r * DB + cc, s.a[cc][rr]);
-                    if (p.hi) {
-                        const float v = s.a[rr][cc];
-                        const __half h = __float2half_rn(v);
-                        const int64_t o = ((int64_t)r * DB + rr) * b + cb * DB + cc;
-                        p.hi[o] = h;
-                        p.lo[o] = __float2half_rn(v - __half2float(h));
-                    }
+            // block (r, cb) of X: transpose into X^T and the FP16 split
+            const int r = it.i, cb = it.j;
+            const float *src = p.X + (int64_t)r * DB * b + cb * DB;
+            load_blk(s.a, src, b, false);
+            __syncthreads();
+            for (int e = threadIdx.x; e < DB * DB; e += DT) {
+                const int rr = e / DB, cc = e % DB;
+                // X^T block (cb, r): element (cc, rr) = X (rr, cc)
+                __stcg(p.XT + ((int64_t)cb * DB + rr) * b + r * DB + cc, s.a[cc][rr]);
+                if (p.hi) {
+                    const float v = s.a[rr][cc];
+                    const __half h = __float2half_rn(v);
+                    const int64_t o = ((int64_t)r * DB + rr) * b + cb * DB + cc;
+                    p.hi[o] = h;
+                    p.lo[o] = __float2half_rn(v - __half2float(h));
                 }
-                __syncthreads();
             }
         }
         __syncthreads();
@@ -613,7 +665,7 @@ krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT
     p.n_factor = factor_items_for(p.NB);
     int64_t inv = 0;
     for (int l = 0; l < levels; ++l) inv += 2 * inv_step_items(p.NB, l);
-    p.items = p.n_factor + inv + p.NB;
+    p.items = p.n_factor + inv + (int64_t)p.NB * p.NB;
     p.ctr = ctr;
     p.minpiv = minpiv;
     p.err = c->derr;
