@@ -1229,7 +1229,8 @@ krr_status tc_trsm(Ctx *c, int64_t k) {
     p.part = c->colmax;  // per-block max |L_ik|, read by the column cast
     p.items = (nt - k - 1) * (b / BM) * (b / BN);
     const CUtensorMap &a0 = (k == 0) ? st->hi_map : st->w_map;
-    return launch<KIND_F16, OP_TRSM>(c, a0, st->lo_map, st->linv_hi_map, st->linv_lo_map, p);
+    // CTA pairs (M = 256) share the B operand (the diagonal inverse), as in the update
+    return launch<KIND_F16, OP_TRSM, 2>(c, a0, st->lo_map, st->linv_hi_map, st->linv_lo_map, p);
 }
 
 krr_status tc_update(Ctx *c, int64_t k) {
