@@ -307,7 +307,9 @@ enum {
  * Measurement report: CUDA events recorded on the context's stream around
  * every region of a class while profiling is on.  flops / bytes are the
  * algorithmic operation counts and compulsory HBM bytes of the timed
- * regions (definitions in the design doc of the repository), not counter values.
+ * regions (for the trailing update 2 b^3 per off-diagonal target tile and
+ * b^3 per diagonal target; for the build 2 M per lower-triangle entry), not
+ * counter values.
  * launches counts the kernels this library launched (all contexts) since the
  * last reset.
  */

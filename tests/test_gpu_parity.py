@@ -1,11 +1,11 @@
 """Parity of the CUDA path (through the C ABI) against the CPU oracle.
 
-Tolerances (stated here, derived in the design doc):
+Tolerances:
 * squared distances: bit-exact (integers);
 * kernel entries: |K_gpu - K_ref| <= 4e-7 (FP32 storage + expf, a few ulp);
 * mixed mode after refinement: ||Yt - Yt*||_F / ||Yt*||_F <= 1e-4 (the
-  spec bound), relative residual <= 1e-5 (the floor of FP32 storage of
-  K and A is ~1e-6 at these sizes);
+  end-to-end accuracy target), relative residual <= 1e-5 (the floor of FP32
+  storage of K and A is ~1e-6 at these sizes);
 * plain FP32 mode (no refinement): ||Yt - Yt*|| / ||Yt*|| <= 1e-3.
 """
 import numpy as np
