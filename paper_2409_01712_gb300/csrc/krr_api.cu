@@ -98,6 +98,18 @@ void dev_free(T **p) {
     *p = nullptr;
 }
 
+// Device address of page-locked host memory (the GPU reads it over the host
+// link, no staging copy), or nullptr for anything else.
+const void *pinned_host_alias(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost) ? a.devicePointer : nullptr;
+}
+
 bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -172,7 +184,10 @@ krr_status store_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, flo
 krr_status pack(Ctx *c, const int8_t *g, int64_t n, int64_t m, int64_t ldg, int64_t rows_pad,
                 uint8_t *out8, float *outf, int32_t *norms) {
     const int8_t *dg = g;
-    if (!is_device_ptr(g)) {
+    const void *alias = is_device_ptr(g) ? nullptr : pinned_host_alias(g);
+    if (alias) {
+        dg = (const int8_t *)alias;  // page-locked: the pack kernel reads it in place
+    } else if (!is_device_ptr(g)) {
         KRR_TRY(stage(c, (size_t)n * m));
         // one linear copy when the rows are contiguous (a pitched copy of short
         // rows runs far below the host link's rate)

@@ -100,12 +100,16 @@ def test_fit_predict_matches_oracle(mode, n, m, p, tile):
 
 
 @pytest.mark.parametrize("mode", MODES)
-def test_host_buffers_and_multiple_rhs(mode):
+@pytest.mark.parametrize("pinned", [False, True])
+def test_host_buffers_and_multiple_rhs(mode, pinned):
     prob = _problem(600, 200, 4, 100, seed=77)
     gamma, lam = 1.0 / 200, 0.3
     _, a_ref, yt_ref = oracle.krr(gamma, lam, prob["G"], prob["Y"].astype(np.float64), prob["T"])
     with KRR(tile=256, mode=mode) as model:
-        model.build_kernel(prob["G"], gamma)  # host numpy in
+        if pinned:  # page-locked host genotypes are read in place by the pack kernel
+            model.build_kernel(torch.from_numpy(prob["G"]).pin_memory(), gamma)
+        else:
+            model.build_kernel(prob["G"], gamma)  # host numpy in (staged)
         model.factor(lam)
         a, _ = model.solve(prob["Y"])  # host in, host out
         assert isinstance(a, np.ndarray)
