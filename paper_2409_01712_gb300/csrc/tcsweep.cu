@@ -890,8 +890,11 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 //   warp 0      producer: TMA of the FP32 K chunk (128 x 64 rows x columns, or
 //               64 x 128 for a column slab) into a staging ring, and of the
 //               FP16 terms of a_j (B) into a ring of their own;
-//   warps 6..9  converters: (K - c) 2^12 -> FP16 pair (hi, lo) in the operand
-//               ring, in the MMA's K-major or MN-major 128-byte-swizzled layout;
+//   warps 6..9  converters: (K - c) 2^12 -> FP16 pair (hi, lo), written in
+//               place over the staged FP32 chunk (each thread overwrites only
+//               the bytes its own warp read) in the MMA's K-major or MN-major
+//               128-byte-swizzled layout, so the staging ring is also the
+//               operand ring;
 //   warp 1      MMA: A_hi x [B_hi; B_mid; B_lo] (N = 3 np) and A_lo x [B_hi;
 //               B_mid] (N = 2 np); a is split into three FP16 terms (exact for
 //               FP32 values), K - c into two (about 22 bits of a quantity
@@ -906,8 +909,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
 // ---------------------------------------------------------------------------
 constexpr int RS_THREADS = 320;
 constexpr int RS_STG = 32768;      // FP32 chunk: 128 x 64 or 64 x 128
-constexpr int RS_NSTG = 3;         // staging ring (FP32 K chunks, TMA)
-constexpr int RS_NOP = 2;          // A ring (FP16 pair of (K - c) 2^12, converters)
+constexpr int RS_NSTG = 5;         // staging ring (FP32 K chunks by TMA, converted in place)
 constexpr int RS_NB = 3;           // B ring (FP16 terms of a, TMA): loads run ahead of the A ring
 constexpr float RS_KSCALE = 4096.f;  // (K - c) * 2^12 in FP16 (|K - c| <= 1)
 
@@ -951,12 +953,12 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     extern __shared__ __align__(1024) uint8_t rs_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(rs_smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *stg = smem;                                   // RS_NSTG x 32 KB
-    uint8_t *ops = smem + RS_NSTG * RS_STG;                // RS_NOP x 32 KB (A hi, A lo)
-    uint8_t *bst = ops + RS_NOP * 32768;                   // RS_NB x b_bytes
+    uint8_t *bst = smem + RS_NSTG * RS_STG;                // RS_NB x b_bytes
     int64_t *items = reinterpret_cast<int64_t *>(bst + RS_NB * p.b_bytes);  // item ring
     uint64_t *bars = reinterpret_cast<uint64_t *>(items + TS_IRING);
-    uint64_t *sfull = bars, *sempty = bars + RS_NSTG, *ofull = bars + 2 * RS_NSTG,
-             *oempty = bars + 2 * RS_NSTG + RS_NOP, *bfull = oempty + RS_NOP, *bempty = bfull + RS_NB,
+    // sfull: FP32 chunk landed; cfull: converted in place; sempty: MMAs done
+    uint64_t *sfull = bars, *sempty = bars + RS_NSTG, *cfull = bars + 2 * RS_NSTG,
+             *bfull = cfull + RS_NSTG, *bempty = bfull + RS_NB,
              *tfull = bempty + RS_NB, *tempty = tfull + 2, *ifull = tempty + 2, *iempty = ifull + TS_IRING,
              *drain = iempty + TS_IRING;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
@@ -968,11 +970,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int q = 0; q < RS_NSTG; ++q) {
             mbar_init(&sfull[q], 1);
-            mbar_init(&sempty[q], 4);      // converter warps
-        }
-        for (int q = 0; q < RS_NOP; ++q) {
-            mbar_init(&ofull[q], 4);       // converter warps
-            mbar_init(&oempty[q], 1);      // MMA commit
+            mbar_init(&sempty[q], 1);      // MMA commit
+            mbar_init(&cfull[q], 4);       // converter warps
         }
         for (int q = 0; q < RS_NB; ++q) {
             mbar_init(&bfull[q], 1);       // producer (B bytes)
@@ -1073,8 +1072,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------ MMA issuer ------------------------------
-            int os = 0, bs = 0, slot = 0, acc = 0;
-            uint32_t oph = 0, bph = 0, iph = 0, aph = 0;
+            int ss = 0, bs = 0, slot = 0, acc = 0;
+            uint32_t sph = 0, bph = 0, iph = 0, aph = 0;
             bool ok = true, any = false;
             while (ok) {
                 if (!rs_wait(&ifull[slot], iph, p)) { ok = false; break; }
@@ -1091,10 +1090,10 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         if (!rs_wait(&tempty[acc], aph ^ 1, p)) { ok = false; break; }
                         tmem_fence_after();
                         const uint32_t tacc = tmem_base + (uint32_t)(acc * 3 * np);
-                        if (!rs_wait(&ofull[os], oph, p)) { ok = false; break; }
+                        if (!rs_wait(&cfull[ss], sph, p)) { ok = false; break; }
                         if (!rs_wait(&bfull[bs], bph, p)) { ok = false; break; }
                         tmem_fence_after();
-                        const uint32_t sa = smem_u32(ops + os * 32768), sb = smem_u32(bst + bs * p.b_bytes);
+                        const uint32_t sa = smem_u32(stg + ss * RS_STG), sb = smem_u32(bst + bs * p.b_bytes);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             const uint64_t bd = desc_kmajor(sb + kk * 32);
@@ -1107,9 +1106,9 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                             }
                         }
                         any = true;
-                        mma_commit(&oempty[os]);
+                        mma_commit(&sempty[ss]);  // the stage takes the next TMA load
                         mma_commit(&bempty[bs]);
-                        if (++os == RS_NOP) { os = 0; oph ^= 1; }
+                        if (++ss == RS_NSTG) { ss = 0; sph ^= 1; }
                         if (++bs == RS_NB) { bs = 0; bph ^= 1; }
                         mma_commit(&tfull[acc]);
                         if (++acc == 2) { acc = 0; aph ^= 1; }
@@ -1126,8 +1125,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
         // ------------------------------ converters ------------------------------
         const int ct = threadIdx.x - 192;
         const float c = (float)*p.shift;
-        int ss = 0, os = 0, slot = 0;
-        uint32_t sph = 0, oph = 0, iph = 0;
+        int ss = 0, slot = 0;
+        uint32_t sph = 0, iph = 0;
         bool ok = true;
         while (ok) {
             if (!__all_sync(0xffffffffu, rs_wait(&ifull[slot], iph, p))) break;
@@ -1144,9 +1143,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 const int boxb = kmaj ? RS_STG / 2 : RS_STG / 4;
                 for (int kc = 0; kc < KC; ++kc) {
                     if (!__all_sync(0xffffffffu, rs_wait(&sfull[ss], sph, p))) { ok = false; break; }
-                    if (!__all_sync(0xffffffffu, rs_wait(&oempty[os], oph ^ 1, p))) { ok = false; break; }
                     const uint8_t *src = stg + ss * RS_STG + r * 128;
-                    uint8_t *dst = ops + os * 32768 + h * 8192 + r * 128;
+                    uint8_t *dst = stg + ss * RS_STG + h * 8192 + r * 128;
                     float v[64];
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
@@ -1157,6 +1155,9 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                             v[e * 32 + 4 * u + 2] = f.z; v[e * 32 + 4 * u + 3] = f.w;
                         }
                     }
+                    // the FP16 rows overwrite FP32 rows that lanes of this warp
+                    // read (thread (r, 0) writes over box 2 row r of thread (r, 1))
+                    __syncwarp();
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         uint4 hv, lv;
@@ -1176,12 +1177,8 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                     // generic-proxy writes, read next by the tensor cores
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
-                    if (lane == 0) {
-                        mbar_arrive(&ofull[os]);
-                        mbar_arrive(&sempty[ss]);
-                    }
+                    if (lane == 0) mbar_arrive(&cfull[ss]);
                     if (++ss == RS_NSTG) { ss = 0; sph ^= 1; }
-                    if (++os == RS_NOP) { os = 0; oph ^= 1; }
                 }
             }
         }
@@ -1516,8 +1513,8 @@ krr_status map_f32(Ctx *c, CUtensorMap *m, const void *base, int64_t rows, int64
 }
 
 size_t rs_smem_bytes(int b_bytes) {
-    return (size_t)RS_NSTG * RS_STG + (size_t)RS_NOP * 32768 + (size_t)RS_NB * b_bytes + TS_IRING * 8 +
-           (size_t)(2 * RS_NSTG + 2 * RS_NOP + 2 * RS_NB + 4 + 2 * TS_IRING + 1) * 8 + 16 +
+    return (size_t)RS_NSTG * RS_STG + (size_t)RS_NB * b_bytes + TS_IRING * 8 +
+           (size_t)(3 * RS_NSTG + 2 * RS_NB + 4 + 2 * TS_IRING + 1) * 8 + 16 +
            (size_t)TS_NPMAX * 128 * 4 + 1024;
 }
 
