@@ -3,10 +3,11 @@
 // One persistent, warp-specialised kernel template computes 128 x 256 output
 // blocks of C = A B^T with both operands K-major in global memory:
 //   warp 0      TMA producer: 128-byte-swizzled A (128 rows) and B (256 rows)
-//               slabs of 128 bytes along K into a 4-stage shared-memory ring;
+//               slabs of 128 bytes along K into a shared-memory ring (4 stages
+//               of 48 KB; 6 of 32 KB in pair mode, below);
 //   warp 1      TMEM allocator and MMA issuer (one thread): tcgen05.mma
 //               M = 128, N = 256 into one of two TMEM accumulators;
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, fused per-op math,
+//   warps 2..9  epilogue: tcgen05.ld of the accumulator, fused per-op math,
 //               stores to global memory.
 // Every mbarrier wait is bounded by the context's wait budget
 // (%globaltimer); on expiry the kernel records KRR_ETIMEOUT, drains its own
@@ -62,10 +63,10 @@ constexpr int PRED_MAX_P = 32;
 constexpr uint32_t IDESC = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) |
                            ((uint32_t)(BM >> 4) << 24);
 
-// Pair mode (PAIR = 2): two CTAs of a cluster run one tcgen05.mma with
-// cta_group::2 over a 256 x 256 block, M = 256: each CTA stages its own 128 A
-// rows and one 128-row half of B, and keeps its 128 output rows in its TMEM.
-// A stage is 32 KB instead of 48 KB.
+// Pair mode (PAIR = 2; the panel solve and the trailing update): two CTAs of a
+// cluster run one tcgen05.mma with cta_group::2 over a 256 x 256 block,
+// M = 256: each CTA stages its own 128 A rows and one 128-row half of B, and
+// keeps its 128 output rows in its TMEM.  A stage is 32 KB instead of 48 KB.
 constexpr int BOX_BYTES = BM * 128;     // one 64-column box of an FP16 target block
 
 template <int PAIR>

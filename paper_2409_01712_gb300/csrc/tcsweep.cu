@@ -18,15 +18,18 @@
 //      per block and column, K-major ([column][row]); both halves are
 //      multiplied, so B carries about 22 significant bits.
 // The right-hand side is updated in place; a LINK applies its update after the
-// earlier ones of the same slab (fixed order: deterministic results).  The
-// last slab to finish a block converts that block to the FP16 pair (the
-// "converter"), then publishes it.
+// earlier ones of the same slab (fixed order: deterministic results).  A slab
+// whose rows become final (a DIAG slab, the last LINK of a slab) writes them
+// at once as the FP16 pair with a scale predicted from the previous block; the
+// last slab of the block checks the prediction against the block's maximum
+// (converting the whole block again with the exact scale if it fails) and
+// publishes the block.
 //
 // Items are claimed from a device counter in dependency order (item 0 converts
-// the first block; then, per column, its S DIAG items, its head LINK items
-// and the LINK items of the column before; see "Items" below).  An item only waits for items claimed
-// before it by running CTAs; every wait is bounded (%globaltimer) and ends the
-// kernel with KRR_ETIMEOUT.
+// the first block; then, per column, its S DIAG items, its head LINK items and
+// the LINK items of the column before; see "Items" below).  An item only waits
+// for items claimed before it by running CTAs; every wait is bounded
+// (%globaltimer) and ends the kernel with KRR_ETIMEOUT.
 //
 // CTA (192 threads, one per SM):
 //   warp 0      producer: claims items, TMA loads of A (16 KB per stage) and B
