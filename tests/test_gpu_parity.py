@@ -199,3 +199,38 @@ def test_fp64_diagonal_option():
     assert np.all(np.diag(pmap) == 0)  # diagonal tiles report FP64
     err = np.linalg.norm(yt.cpu().numpy() - yt_ref) / np.linalg.norm(yt_ref)
     assert err <= 1e-4, (err, info)
+
+
+def test_empty_inputs_rejected():
+    prob = _problem(300, 64, 2, 10, seed=9)
+    with KRR(tile=256, mode="mixed") as model:
+        with pytest.raises(KRRError) as e:
+            model.build_kernel(_to(prob["G"][:0]), 1.0 / 64)  # no rows
+        assert e.value.status == krrmod.EINVAL
+        model.build_kernel(_to(prob["G"]), 1.0 / 64)
+        model.factor(0.1)
+        with pytest.raises(KRRError) as e:
+            model.solve(_to(prob["Y"][:, :0]))  # no phenotypes
+        assert e.value.status == krrmod.EINVAL
+        a, _ = model.solve(_to(prob["Y"]))
+        with pytest.raises(KRRError) as e:
+            model.predict(_to(prob["T"][:0]), a)  # no held-out rows
+        assert e.value.status == krrmod.EINVAL
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_single_row_closed_form(mode):
+    # N = 1: K = [1], so A = Y / (1 + lambda) exactly; the other 255 rows of
+    # the tile are padding (identity rows of K, zero right-hand side)
+    g = np.zeros((1, 64), np.int8)
+    g[0, ::3] = 2
+    y = np.array([[2.0, -0.5]], np.float32)
+    lam = 0.25
+    with KRR(tile=256, mode=mode) as model:
+        model.build_kernel(_to(g), 1.0 / 64)
+        model.factor(lam)
+        a, _ = model.solve(_to(y))
+        yt = model.predict(_to(g), a)
+    assert np.allclose(a.cpu().numpy(), y / (1 + lam), rtol=1e-6, atol=1e-7)
+    # predicting the training row: K A = Y - lambda A
+    assert np.allclose(yt.cpu().numpy(), y - lam * y / (1 + lam), rtol=1e-5, atol=1e-6)
