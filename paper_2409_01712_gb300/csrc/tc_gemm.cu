@@ -453,6 +453,35 @@ __device__ __forceinline__ void epilogue_prefetch(const TcParams &p, const Work 
     for (int o = 0; o < bytes; o += 128) prefetch_l2(ptr + o);
 }
 
+// Predict: the thread's test row against 128 training columns of the block,
+// exp(-gamma d) - c times the staged weights, NQ (>= p) weight columns.
+template <int NQ>
+__device__ __forceinline__ void predict_half(const TcParams &p, uint32_t tacc, int ch0, int64_t gi, int64_t j0,
+                                             const int32_t *nb_s, const float *aw_s, float kc, float *dst) {
+    const int32_t ni = p.norms_a[gi];
+    const bool real_row = gi < p.n_test;
+    float acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
+    for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
+        float v[16];
+        tmem_ld16(tacc + ch * 16, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int c = ch * 16 + e;
+            const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
+            const float kv = (real_row && j0 + c < p.n) ? expf(-p.gamma * (float)d) - kc : 0.f;
+            const float *ar = aw_s + c * PRED_MAX_P;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) acc[q] = fmaf(kv, ar[q], acc[q]);
+        }
+    }
+    const int pp = (int)p.p;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        if (q < pp) dst[q] = acc[q];
+}
+
 template <int OP>
 __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row, int half,
                                          int32_t *nb_s, float *aw_s, double *red_s,
@@ -516,34 +545,24 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
         }
     } else if (OP == OP_PREDICT) {
         const int64_t gi = w.i * BM + row;  // test row
-        const int32_t ni = p.norms_a[gi];
-        float acc[PRED_MAX_P];
-#pragma unroll
-        for (int q = 0; q < PRED_MAX_P; ++q) acc[q] = 0.f;
         const int pp = (int)p.p;
         // K - c: the entries of K concentrate around their mean, so the
         // shifted products are small and their FP32 sums lose far less to
         // cancellation; the reduction adds c (1^T A) back in FP64.  Padding
         // columns hold zero weights.
         const float kc = p.kshift ? (float)*p.kshift : 0.f;
-        for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
-            float v[16];
-            tmem_ld16(tacc + ch * 16, v);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int c = ch * 16 + e;
-                const int64_t gj = w.j * BN + c;
-                const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
-                const float kv = (gi < p.n_test && gj < p.n) ? expf(-p.gamma * (float)d) - kc : 0.f;
-                const float *ar = aw_s + c * PRED_MAX_P;
-#pragma unroll
-                for (int q = 0; q < PRED_MAX_P; ++q)
-                    if (q < pp) acc[q] = fmaf(kv, ar[q], acc[q]);
-            }
-        }
         // partials: [128-column block][padded test row][p]
         float *dst = p.part + ((2 * w.j + half) * p.test_rows + gi) * p.p;
-        for (int q = 0; q < pp; ++q) dst[q] = acc[q];
+        // as many weight columns as the call has, rounded up to 8 (the staged
+        // weights beyond p are zero)
+        if (pp <= 8)
+            predict_half<8>(p, tacc, ch0, gi, w.j * BN, nb_s, aw_s, kc, dst);
+        else if (pp <= 16)
+            predict_half<16>(p, tacc, ch0, gi, w.j * BN, nb_s, aw_s, kc, dst);
+        else if (pp <= 24)
+            predict_half<24>(p, tacc, ch0, gi, w.j * BN, nb_s, aw_s, kc, dst);
+        else
+            predict_half<32>(p, tacc, ch0, gi, w.j * BN, nb_s, aw_s, kc, dst);
     } else if (OP == OP_GRADT || OP == OP_GRADK) {
         // d K-weighted contractions for the hyperparameter gradient
         const bool kterm = (OP == OP_GRADK);
