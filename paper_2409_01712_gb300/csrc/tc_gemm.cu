@@ -482,6 +482,50 @@ __device__ __forceinline__ void predict_half(const TcParams &p, uint32_t tacc, i
         if (q < pp) dst[q] = acc[q];
 }
 
+// Gradient contractions: sum over 128 columns of d exp(-gamma d) times the
+// staged A (and, for the training tiles, Z) columns, NQ (>= p) of them, then
+// the thread's dot products with its own row; returns the warp's sum.
+template <int NQ, bool KTERM>
+__device__ __forceinline__ double grad_half(const TcParams &p, const Work &w, uint32_t tacc, int ch0, int64_t gi,
+                                            int64_t j0, const int32_t *nb_s, const float *aw_s) {
+    const int64_t a_real = KTERM ? p.n : p.n_test;
+    const int32_t ni = p.norms_a[gi];
+    const int pp = (int)p.p;
+    float accA[NQ], accZ[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) accA[q] = accZ[q] = 0.f;
+    for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
+        float v[16];
+        tmem_ld16(tacc + ch * 16, v);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int c = ch * 16 + e;
+            const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
+            const float sv = (gi < a_real && j0 + c < p.n) ? (float)d * expf(-p.gamma * (float)d) : 0.f;
+            const float *ar = aw_s + c * PRED_MAX_P;  // columns beyond p are zero
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                accA[q] = fmaf(sv, ar[q], accA[q]);
+                if (KTERM) accZ[q] = fmaf(sv, ar[GRAD_MAX_P + q], accZ[q]);
+            }
+        }
+    }
+    double val = 0.0;
+    if (gi < a_real) {
+        const float *own = KTERM ? p.zw : p.gp;  // Z_i or G_p,t
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+            if (q < pp) val += (double)own[gi * p.ldaw + q] * (double)accA[q];
+        if (KTERM && w.i != w.j) {  // mirror entry (j, i) of an off-diagonal tile
+#pragma unroll
+            for (int q = 0; q < NQ; ++q)
+                if (q < pp) val += (double)p.aw[gi * p.ldaw + q] * (double)accZ[q];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+    return val;
+}
+
 template <int OP>
 __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row, int half,
                                          int32_t *nb_s, float *aw_s, double *red_s,
@@ -565,41 +609,11 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
             predict_half<32>(p, tacc, ch0, gi, w.j * BN, nb_s, aw_s, kc, dst);
     } else if (OP == OP_GRADT || OP == OP_GRADK) {
         // d K-weighted contractions for the hyperparameter gradient
-        const bool kterm = (OP == OP_GRADK);
+        constexpr bool kterm = (OP == OP_GRADK);
         const int64_t gi = kterm ? w.i * b + w.sm * BM + row : w.i * BM + row;
-        const int64_t a_real = kterm ? p.n : p.n_test;
-        const int32_t ni = p.norms_a[gi];
-        const int pp = (int)p.p;
-        float accA[GRAD_MAX_P], accZ[GRAD_MAX_P];
-#pragma unroll
-        for (int q = 0; q < GRAD_MAX_P; ++q) accA[q] = accZ[q] = 0.f;
-        for (int ch = ch0; ch < ch0 + CH_PER_HALF; ++ch) {
-            float v[16];
-            tmem_ld16(tacc + ch * 16, v);
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int c = ch * 16 + e;
-                const int64_t gj = kterm ? w.j * b + w.sn * BN + c : w.j * BN + c;
-                const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
-                const float sv = (gi < a_real && gj < p.n) ? (float)d * expf(-p.gamma * (float)d) : 0.f;
-                const float *ar = aw_s + c * PRED_MAX_P;
-#pragma unroll
-                for (int q = 0; q < GRAD_MAX_P; ++q) {
-                    if (q < pp) {
-                        accA[q] = fmaf(sv, ar[q], accA[q]);
-                        if (kterm) accZ[q] = fmaf(sv, ar[GRAD_MAX_P + q], accZ[q]);
-                    }
-                }
-            }
-        }
-        double val = 0.0;
-        if (gi < a_real) {
-            const float *own = kterm ? p.zw : p.gp;  // Z_i or G_p,t
-            for (int q = 0; q < pp; ++q) val += (double)own[gi * p.ldaw + q] * (double)accA[q];
-            if (kterm && w.i != w.j)  // mirror entry (j, i) of an off-diagonal tile
-                for (int q = 0; q < pp; ++q) val += (double)p.aw[gi * p.ldaw + q] * (double)accZ[q];
-        }
-        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+        const int64_t j0 = kterm ? w.j * b + w.sn * BN : w.j * BN;
+        const double val = (p.p <= 8) ? grad_half<8, kterm>(p, w, tacc, ch0, gi, j0, nb_s, aw_s)
+                                      : grad_half<GRAD_MAX_P, kterm>(p, w, tacc, ch0, gi, j0, nb_s, aw_s);
         const int ew = (threadIdx.x >> 5) - 2;
         if ((threadIdx.x & 31) == 0) red_s[ew] = val;
         epi_bar();
