@@ -483,9 +483,9 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
             if (it.kind == K_P) {
                 // P(q), q >= 1: X_q-1,q-1, and blocks (q, q-1) and (q, q) with the
                 // updates of columns 0 .. q-2
-                if (it.q > 0)
-                    ok = wait_ge(pdone + it.q - 1, 1, p) && wait_ge(upd + it.q * NB + it.q - 1, it.q - 1, p) &&
-                         wait_ge(upd + it.q * NB + it.q, it.q - 1, p);
+                // (the other two inputs are awaited in the item body, after the
+                // first block is loaded)
+                if (it.q > 0) ok = wait_ge(upd + it.q * NB + it.q - 1, it.q - 1, p);
             } else if (it.kind == K_T) {
                 ok = wait_ge(pdone + it.q, 1, p) && wait_ge(upd + it.i * NB + it.q, it.q, p);
             } else if (it.kind == K_U) {
@@ -527,7 +527,14 @@ __global__ void __launch_bounds__(DT) diag_kernel(const DiagParams p) {
                 // L_q,q-1 = A_q,q-1 X_q-1,q-1^T, published for the U items of column q-1
                 const int q = it.q;
                 float *c = p.W + (int64_t)q * DB * b + (q - 1) * DB;
+                // A_q,q-1 (final since the updates of columns 0 .. q-2) comes in
+                // while P(q-1) may still be running
                 load_blk(s.a, c, b, false);
+                __syncthreads();  // every thread has read the previous ok_s
+                if (threadIdx.x == 0)
+                    ok_s = (wait_ge(ctr_pdone(p) + q - 1, 1, p) && wait_ge(ctr_upd(p) + q * NB + q, q - 1, p)) ? 1 : 0;
+                __syncthreads();
+                if (!ok_s) break;
                 load_blk(s.b, p.X + (int64_t)(q - 1) * DB * b + (q - 1) * DB, b, true);
                 __syncthreads();
                 mac_blk(s, acc);
