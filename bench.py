@@ -178,13 +178,19 @@ def cpu_sample(cfg, n_sample, g_host=None, y_host=None):
     y = np.ascontiguousarray(y_host[:n_sample]).astype(np.float64)
     t0 = time.perf_counter()
     k = oracle.build_kernel(1.0 / m, g)
+    t1 = time.perf_counter()
     oracle.associate(LAMBDA, k, y)
     dt = time.perf_counter() - t0
     ops = metric_ops(n_sample, m, p)
+    # the plain loops scale as N^2 M (distances) and N^3 (factorisation)
+    scale = n / n_sample
+    extrap = (t1 - t0) * scale ** 2 + (dt - (t1 - t0)) * scale ** 3
     return {"value": ops / dt / 1e12, "unit": "TOp/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {n_sample} rows of the {cfg} workload (M={m}, P={p}): brute-force "
                       f"distances, FP64 Cholesky, substitution; {dt:.2f} s",
-            "seconds": dt}
+            "seconds": dt, "build_s": t1 - t0, "associate_s": dt - (t1 - t0),
+            "extrapolated_full_s": extrap,
+            "extrapolation": f"labelled extrapolation to N={n}: build x (N/{n_sample})^2, associate x (N/{n_sample})^3"}
 
 
 def run_reference(args):
@@ -192,7 +198,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = args.config if args.config in CONFIGS else "c3"
-    n_sample = args.cpu_rows
+    n_sample = args.ref_rows
     times = []
     res = None
     for i in range(args.warmup + args.steps):
@@ -208,10 +214,41 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(cfg), "sample_rows": n_sample},
             "cpu_baseline": {"value": value, "unit": "TOp/s", "cores": res["cores"], "kind": "oracle",
-                             "sample": res["sample"]},
+                             "sample": res["sample"], "extrapolated_full_s": res["extrapolated_full_s"],
+                             "extrapolation": res["extrapolation"]},
             "e2e": {"value": value, "unit": "TOp/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def subproblem_accuracy(args, g, y, t, gamma, tile, stream):
+    """The first sub_rows rows of the workload (same held-out rows) through the
+    same mixed path, against the full FP64 oracle solution of that
+    subproblem (float64 library Gram products and factorisation)."""
+    import oracle
+    from paper_2409_01712_gb300 import KRR
+
+    ns = args.sub_rows
+    gs, ys = g[:ns].contiguous(), y[:ns].contiguous()
+    with KRR(tile=tile, mode=args.mode, stream=stream.cuda_stream) as sub:
+        sub.build_kernel(gs, gamma)
+        fi = sub.factor(LAMBDA)
+        a_s, si = sub.solve(ys)
+        yt_s = sub.predict(t, a_s)
+    g_h, y_h, t_h = gs.cpu().numpy(), ys.double().cpu().numpy(), t.cpu().numpy()
+    a_h, yt_h = a_s.double().cpu().numpy(), yt_s.double().cpu().numpy()
+    t0 = time.perf_counter()
+    k_ref, a_ref, yt_ref = oracle.krr(gamma, LAMBDA, g_h, y_h, t_h, method="lapack")
+    osec = time.perf_counter() - t0
+    res = y_h - LAMBDA * a_h - k_ref @ a_h
+    return {"rows": ns, "held_out_rows": int(t.shape[0]),
+            "rel_err_yt": float(np.linalg.norm(yt_h - yt_ref) / np.linalg.norm(yt_ref)),
+            "rel_err_a": float(np.linalg.norm(a_h - a_ref) / np.linalg.norm(a_ref)),
+            "rel_residual_fp64": float(np.linalg.norm(res) / np.linalg.norm(y_h)),
+            "rel_residual_device": si["rel_residual"], "iterations": si["iterations"],
+            "tiles_fp32_fp16_e4m3": [fi["tiles_fp32"], fi["tiles_fp16"], fi["tiles_e4m3"]],
+            "oracle": "FP64, float64 library Gram product + LAPACK Cholesky / triangular solves",
+            "oracle_s": osec}
 
 
 def run_ours(args):
@@ -363,6 +400,8 @@ def run_ours(args):
         line["accuracy"] = {"sampled_rows": int(args.check_rows),
                             "rel_residual_fp64_oracle_rows": float(np.linalg.norm(r) / np.linalg.norm(yh_np[rows])),
                             "rel_residual_device": si["rel_residual"]}
+        if args.sub_rows > 0 and args.sub_rows < n:
+            line["accuracy"]["subproblem"] = subproblem_accuracy(args, g, y, t, gamma, tile, stream)
 
     # ---- plain FP32 comparator: the same engine with every step in FP32 on CUDA cores
     if not args.no_compare and args.mode == "mixed":
@@ -377,22 +416,29 @@ def run_ours(args):
             cmp_model.solve(y, out=a_out)
             cmp_model.predict(t, a_out, out=yt_out)
 
+        # one untimed step allocates the FP32 tiles and sets up the kernels,
+        # then the timed steps (the mixed arm's own warm-up runs before its timing)
+        for _ in range(args.fp32_warmup):
+            step32()
         torch.cuda.synchronize()
         c0 = torch.cuda.Event(enable_timing=True)
         c1 = torch.cuda.Event(enable_timing=True)
         c0.record(stream)
-        step32()
+        for _ in range(args.fp32_steps):
+            step32()
         c1.record(stream)
         torch.cuda.synchronize()
-        cms = c0.elapsed_time(c1)
+        cms = c0.elapsed_time(c1) / args.fp32_steps
         line["fp32_comparator"] = {"ms_per_step": cms, "value": ops / (cms / 1e3) / 1e12, "unit": "TOp/s",
-                                   "steps": 1, "speedup_mixed_over_fp32": cms / ms}
+                                   "steps": args.fp32_steps, "warmup": args.fp32_warmup,
+                                   "speedup_mixed_over_fp32": cms / ms}
         cmp_model.close()
 
     # ---- CPU baseline: the oracle on this host's cores, bounded sample
     if not args.no_cpu and rank == 0:
         res = cpu_sample(cfg, args.cpu_rows, g.cpu().numpy(), y.cpu().numpy())
-        res.pop("seconds")
+        for key in ("seconds", "build_s", "associate_s"):
+            res.pop(key)
         line["cpu_baseline"] = res
 
     if rank == 0:
@@ -472,7 +518,12 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparator step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline and sampled check")
-    ap.add_argument("--cpu-rows", type=int, default=2048, help="rows of the oracle sample")
+    ap.add_argument("--cpu-rows", type=int, default=4096, help="rows of the oracle sample (cpu_baseline)")
+    ap.add_argument("--ref-rows", type=int, default=2048, help="rows of each --impl reference step")
+    ap.add_argument("--sub-rows", type=int, default=16384,
+                    help="rows of the subproblem compared with the full FP64 oracle (0: skip)")
+    ap.add_argument("--fp32-warmup", type=int, default=1)
+    ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--check-rows", type=int, default=32, help="rows of the sampled oracle residual")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -202,9 +202,10 @@ krr_status krr_get_factor(krr_ctx *ctx, float *L, int64_t ldl);
 /*
  * Predict without allocating.  The paper has no counterpart: this entry point
  * exists for callers that must not allocate device memory at call time --
- * code recorded into a CUDA graph, processes whose device memory is owned up
- * front by another allocator, or latency-critical callers that must not enter
- * the driver's allocator.  It computes the same Yt = K_test A as
+ * processes whose device memory is owned up front by another allocator (a
+ * pool or arena that has to account for every byte), or latency-critical
+ * callers that must not enter the driver's allocator, whose calls can block
+ * and synchronise the device.  It computes the same Yt = K_test A as
  * krr_predict() with the same kernels, but every working buffer lives in one
  * file-scope device array of fixed size (about 16.8 MB, present on every GPU
  * that loads the library until the process exits), so it calls no

@@ -16,6 +16,16 @@ int64 / IEEE double:
   and log lambda, from the adjoint closed form (the paper has no gradient;
   the formula is derived in ``hyper_gradient``'s docstring).
 
+Large cases (the 16384-row subproblem of the N = 131072 workload, the
+gradient at N = 16384) would take the plain loops many minutes on the host,
+so the functions that carry the O(N^2 M) Gram product and the O(N^3)
+factorisation also take ``method="lapack"``: the same definitions with a
+library primitive as the step -- the Gram product G1 G2^T as a float64
+matrix product (every partial sum is an integer below 2^53, so it is exact),
+LAPACK's Cholesky and triangular solves in float64.  The tests pin each of
+them against the plain loops (equal integers, and agreement to float64
+rounding).
+
 Pins (tests/test_oracle_*.py) tie each function to something other than
 itself: brute force on tiny inputs, the paper's 3x2 worked example, closed
 forms (gamma = 0, K = I, lambda -> infinity, min(i,j) Cholesky), invariants
@@ -107,12 +117,23 @@ def sqdist(g1, g2=None, method: str = "bruteforce") -> np.ndarray:
 
     ``method="bruteforce"`` sums ``(g1_ik - g2_jk)^2`` term by term (the
     definition used by Alg. 5); ``method="gram"`` uses the norm-plus-Gram
-    identity of the paper's distance section (Sec. IV-B).  Both are exact.
+    identity of the paper's distance section (Sec. IV-B).  ``method="blas"``
+    is the same identity with the Gram product G1 G2^T taken by a float64
+    library matrix product: its entries and partial sums are integers of at
+    most 4 m < 2^53, so it is exact too.  All three are exact.
     """
     a = _geno(g1)
     b = a if g2 is None else _geno(g2)
     if a.shape[1] != b.shape[1]:
         raise ValueError("SNP counts differ")
+    if method == "blas":
+        af = a.astype(np.float64)
+        bf = af if g2 is None else b.astype(np.float64)
+        s = af @ bf.T                        # s_ij = sum_k g1_ik g2_jk (exact)
+        n1 = (af * af).sum(axis=1)
+        n2 = n1 if g2 is None else (bf * bf).sum(axis=1)
+        d = n1[:, None] + n2[None, :] - 2.0 * s
+        return d.astype(np.int64)
     out = np.empty((a.shape[0], b.shape[0]), dtype=np.int64)
     fn = {"bruteforce": _load().oracle_sqdist_bruteforce, "gram": _load().oracle_sqdist_gram}[method]
     fn(_ptr(a, _i8p), a.shape[0], a.shape[1], _ptr(b, _i8p), b.shape[0], b.shape[1], a.shape[1],
@@ -128,9 +149,9 @@ def gaussian_kernel(d: np.ndarray, gamma: float) -> np.ndarray:
     return out
 
 
-def build_kernel(gamma: float, g1, g2=None) -> np.ndarray:
+def build_kernel(gamma: float, g1, g2=None, method: str = "bruteforce") -> np.ndarray:
     """Alg. 2: ``K[i, j] = KernelMatrix('Gaussian', gamma, G1[i, :], G2[j, :])``."""
-    return gaussian_kernel(sqdist(g1, g2), gamma)
+    return gaussian_kernel(sqdist(g1, g2, method=method), gamma)
 
 
 class NotPositiveDefinite(ArithmeticError):
@@ -139,8 +160,16 @@ class NotPositiveDefinite(ArithmeticError):
         self.column = column
 
 
-def cholesky(a: np.ndarray) -> np.ndarray:
-    """Alg. 3 "Factorize": lower-triangular L with ``L L^T = a`` (double)."""
+def cholesky(a: np.ndarray, method: str = "plain") -> np.ndarray:
+    """Alg. 3 "Factorize": lower-triangular L with ``L L^T = a`` (double).
+
+    ``method="lapack"`` takes LAPACK's float64 Cholesky as the step (the
+    failing column is not reported then: ``column`` is -1)."""
+    if method == "lapack":
+        try:
+            return np.linalg.cholesky(np.asarray(a, dtype=np.float64))
+        except np.linalg.LinAlgError:
+            raise NotPositiveDefinite(-1) from None
     l = np.array(a, dtype=np.float64, order="C", copy=True)
     n = l.shape[0]
     if l.shape != (n, n):
@@ -151,16 +180,26 @@ def cholesky(a: np.ndarray) -> np.ndarray:
     return l
 
 
-def forward_subst(l: np.ndarray, y: np.ndarray) -> np.ndarray:
+def forward_subst(l: np.ndarray, y: np.ndarray, method: str = "plain") -> np.ndarray:
     """Solve ``L Z = Y`` by forward substitution (Y is n x p)."""
+    if method == "lapack":
+        import scipy.linalg
+
+        yy = np.asarray(y, dtype=np.float64).reshape(len(l), -1)
+        return scipy.linalg.solve_triangular(l, yy, lower=True)
     l = np.ascontiguousarray(l, dtype=np.float64)
     z = np.array(y, dtype=np.float64, order="C", copy=True).reshape(l.shape[0], -1)
     _load().oracle_forward_subst(_ptr(l, _f64p), l.shape[0], _ptr(z, _f64p), z.shape[1])
     return z
 
 
-def backward_subst(l: np.ndarray, z: np.ndarray) -> np.ndarray:
+def backward_subst(l: np.ndarray, z: np.ndarray, method: str = "plain") -> np.ndarray:
     """Solve ``L^T X = Z`` by backward substitution (Z is n x p)."""
+    if method == "lapack":
+        import scipy.linalg
+
+        zz = np.asarray(z, dtype=np.float64).reshape(len(l), -1)
+        return scipy.linalg.solve_triangular(l, zz, lower=True, trans="T")
     l = np.ascontiguousarray(l, dtype=np.float64)
     x = np.array(z, dtype=np.float64, order="C", copy=True).reshape(l.shape[0], -1)
     _load().oracle_backward_subst(_ptr(l, _f64p), l.shape[0], _ptr(x, _f64p), x.shape[1])
@@ -177,25 +216,42 @@ def matmul(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     return c
 
 
-def associate(alpha: float, k: np.ndarray, y: np.ndarray, return_factor: bool = False):
+def _lin(method: str) -> str:
+    """Method of the linear-algebra steps that goes with a distance method."""
+    return "lapack" if method in ("lapack", "blas") else "plain"
+
+
+def _dist(method: str) -> str:
+    """Method of the distance step that goes with a method name."""
+    return "blas" if method in ("lapack", "blas") else method
+
+
+def associate(alpha: float, k: np.ndarray, y: np.ndarray, return_factor: bool = False,
+              method: str = "plain"):
     """Alg. 3: ``K~ = Factorize(K + alpha I)``; ``W = Solve(K~, P_h)``."""
     a = np.array(k, dtype=np.float64, copy=True)
     a[np.diag_indices_from(a)] += alpha
-    l = cholesky(a)
-    w = backward_subst(l, forward_subst(l, y))
+    lm = _lin(method)
+    l = cholesky(a, method=lm)
+    del a
+    w = backward_subst(l, forward_subst(l, y, method=lm), method=lm)
     return (w, l) if return_factor else w
 
 
-def predict(gamma: float, g, t, w: np.ndarray) -> np.ndarray:
+def predict(gamma: float, g, t, w: np.ndarray, method: str = "bruteforce") -> np.ndarray:
     """Alg. 4: ``K = Build(gamma, T, G)`` (N_P2 x N_P1), ``P_r = K W``."""
-    return matmul(build_kernel(gamma, t, g), w)
+    return matmul(build_kernel(gamma, t, g, method=_dist(method)), w)
 
 
-def krr(gamma: float, alpha: float, g, y, t):
-    """Alg. 1: Build, Associate, Predict.  Returns (K, W, P_r)."""
-    k = build_kernel(gamma, g)
-    w = associate(alpha, k, y)
-    return k, w, predict(gamma, g, t, w)
+def krr(gamma: float, alpha: float, g, y, t, method: str = "plain"):
+    """Alg. 1: Build, Associate, Predict.  Returns (K, W, P_r).
+
+    ``method="lapack"``: Gram product and factorisation by library routines
+    (see the module docstring); the same definitions otherwise."""
+    dm = "bruteforce" if method == "plain" else _dist(method)
+    k = build_kernel(gamma, g, method=dm)
+    w = associate(alpha, k, y, method=method)
+    return k, w, predict(gamma, g, t, w, method=dm)
 
 
 def kernel_rows(gamma: float, g1, rows, g2) -> np.ndarray:
@@ -216,7 +272,7 @@ def held_out_loss(gamma: float, lam: float, g, y, t, y_t) -> float:
     return float((r * r).sum() / r.size)
 
 
-def hyper_gradient(gamma: float, lam: float, g, y, t, y_t):
+def hyper_gradient(gamma: float, lam: float, g, y, t, y_t, method: str = "plain"):
     """Gradient of the held-out MSE with respect to log gamma and log lambda.
 
     With M = K + lambda I, A = M^-1 Y, Yhat = K_t A and
@@ -231,22 +287,25 @@ def hyper_gradient(gamma: float, lam: float, g, y, t, y_t):
                                    - sum_tj D_tj K_tj (G_p A^T)_tj ).
 
     Returns (loss, dloss/dlog gamma, dloss/dlog lambda), all double.
+    ``method="lapack"``: Gram products and factorisation by library routines.
     """
     g = _geno(g)
     t = _geno(t)
     y = np.asarray(y, dtype=np.float64).reshape(len(g), -1)
     y_t = np.asarray(y_t, dtype=np.float64).reshape(len(t), -1)
-    d = sqdist(g)
+    dm = "bruteforce" if method == "plain" else _dist(method)
+    lm = _lin(method)
+    d = sqdist(g, method=dm)
     k = gaussian_kernel(d, gamma)
-    a, l = associate(lam, k, y, return_factor=True)
-    d_t = sqdist(t, g)
+    a, l = associate(lam, k, y, return_factor=True, method=method)
+    d_t = sqdist(t, g, method=dm)
     k_t = gaussian_kernel(d_t, gamma)
     yhat = matmul(k_t, a)
     r = yhat - y_t
     loss = float((r * r).sum() / r.size)
     g_p = 2.0 * r / r.size
     b = matmul(k_t.T, g_p)
-    z = backward_subst(l, forward_subst(l, b))
+    z = backward_subst(l, forward_subst(l, b, method=lm), method=lm)
     dlog_lam = -lam * float((z * a).sum())
     za = matmul(z, a.T)
     ga = matmul(g_p, a.T)

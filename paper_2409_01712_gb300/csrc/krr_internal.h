@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/krr.h"
@@ -150,6 +151,26 @@ struct Ctx {
     // solve / predict, fixed refinement count (used by the batch runner)
     int graph_mode = 0;
     size_t red_cap = 0;
+};
+
+// One-time set-up per device: cudaFuncSetAttribute and the occupancy queries
+// act on the current device only, so a process that drives several GPUs
+// repeats them on each.  Objects of this type live in static storage (zero
+// initialised); two threads racing on the same device only repeat an
+// idempotent set-up call.  Devices past MAX_DEVICES are set up on every call.
+constexpr int MAX_DEVICES = 64;
+struct PerDevice {
+    std::atomic<int> done[MAX_DEVICES];
+    std::atomic<int> value[MAX_DEVICES];
+    bool has(int dev) const {
+        return dev >= 0 && dev < MAX_DEVICES && done[dev].load(std::memory_order_acquire) != 0;
+    }
+    int get(int dev) const { return value[dev].load(std::memory_order_relaxed); }
+    void put(int dev, int v = 1) {
+        if (dev < 0 || dev >= MAX_DEVICES) return;
+        value[dev].store(v, std::memory_order_relaxed);
+        done[dev].store(1, std::memory_order_release);
+    }
 };
 
 // Kernel launch counter of the whole library (reported by krr_get_profile).

@@ -1,10 +1,11 @@
 // Predict (Alg. 4) for callers that cannot allocate device memory.
 //
 // krr_predict() sizes its own working buffers with cudaMalloc on first use.
-// Some callers cannot allow that: code running inside a CUDA graph capture,
-// host processes whose device memory is reserved up front by another
-// allocator (a pool or arena that must see every byte), or real-time callers
-// that must not hit the driver's allocator on the hot path.  This file gives
+// Some callers cannot allow that: host processes whose device memory is
+// reserved up front by another allocator (a pool or arena that must see
+// every byte), or real-time callers that must not hit the driver's
+// allocator on the hot path (cudaMalloc and cudaFree can block and
+// synchronise the device).  This file gives
 // them krr_predict_noalloc(), the same computation on the same kernels, with
 // every working buffer carved out of one file-scope device array of fixed
 // size instead of context-owned allocations.

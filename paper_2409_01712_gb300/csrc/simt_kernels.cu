@@ -664,10 +664,13 @@ static void diag_factor_tile(Ctx *c, T *W, T *Winv, T *tmp, int64_t k, double *m
     cudaStream_t s = c->stream;
     cudaMemsetAsync(Winv, 0, sizeof(T) * b * b, s);
     const size_t pb_smem = 2 * sizeof(T) * DNB * (DNB + 1);
-    static bool pb_attr = false;
-    if (!pb_attr) {
-        cudaFuncSetAttribute(potrf_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb_smem);
-        pb_attr = true;
+    static PerDevice pb_attr;
+    if (!pb_attr.has(c->device)) {
+        if (cudaFuncSetAttribute(potrf_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pb_smem) ==
+            cudaSuccess)
+            pb_attr.put(c->device);
+        else
+            cudaGetLastError();  // the launch below reports the failure
     }
     for (int q = 0; q < nq; ++q) {
         count_launch(), potrf_block_kernel<T><<<1, PB_THREADS, pb_smem, s>>>(W, Winv, b, q, k, c->derr, minpiv + k * nq);

@@ -786,15 +786,15 @@ size_t smem_bytes(int stages, int64_t stage_bytes, int pcp) {
 
 template <int NQ>
 krr_status launch_nq(Ctx *c, const CUtensorMap (&m)[4], const SweepParams &p, size_t smem) {
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    if (!attr.has(c->device)) {
         const cudaError_t e =
             cudaFuncSetAttribute(sweep_kernel<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit());
         if (e != cudaSuccess) {
             c->last_error = std::string("cudaFuncSetAttribute (sweep): ") + cudaGetErrorString(e);
             return KRR_ECUDA;
         }
-        attr = true;
+        attr.put(c->device);
     }
     const int64_t grid = std::min<int64_t>(p.items, c->num_sms);
     count_launch(), sweep_kernel<NQ><<<(unsigned)grid, SW_THREADS, smem, c->stream>>>(m[0], m[1], m[2], m[3], p);

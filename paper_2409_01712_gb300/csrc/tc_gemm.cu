@@ -1118,16 +1118,15 @@ template <int KIND, int OP, int PAIR = 1>
 krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
                   const CUtensorMap &b1, TcParams &p) {
     if (p.items <= 0) return KRR_OK;
-    static bool attr = false;
-    static int max_clusters = 0;
-    if (!attr) {
+    static PerDevice attr, clusters_of;  // per device: smem opt-in done; clusters that fit at once
+    if (!attr.has(c->device)) {
         cudaError_t e = cudaFuncSetAttribute(tc_kernel<KIND, OP, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_bytes_of<PAIR>());
         if (e != cudaSuccess) {
             c->last_error = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
             return KRR_ECUDA;
         }
-        attr = true;
+        attr.put(c->device);
     }
     p.wait_ns = (uint64_t)c->opt.wait_budget_ns;
     p.err = c->derr;
@@ -1147,6 +1146,7 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
         cfg.stream = c->stream;
         cfg.attrs = at;
         cfg.numAttrs = 1;
+        int max_clusters = clusters_of.has(c->device) ? clusters_of.get(c->device) : 0;
         if (max_clusters == 0) {
             // clusters that fit at once (SMs of a cluster share a GPC); the
             // kernel is persistent, so the grid never exceeds them
@@ -1157,6 +1157,7 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
                 n = 1;
             }
             max_clusters = n;
+            clusters_of.put(c->device, n);
         }
         const int64_t units = p.items / PAIR;
         const int64_t clusters = units < max_clusters ? units : max_clusters;

@@ -1410,15 +1410,15 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
     KRR_TRY(map_f16(c, &mll, c->Linv_lo, nt * b, b, abox));
     float *sbase = ts_scales(c);
     int *flags = ts_flags(c);
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    if (!attr.has(c->device)) {
         const cudaError_t e =
             cudaFuncSetAttribute(tcsweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_limit());
         if (e != cudaSuccess) {
             c->last_error = std::string("cudaFuncSetAttribute (tensor-core sweep): ") + cudaGetErrorString(e);
             return KRR_ECUDA;
         }
-        attr = true;
+        attr.put(c->device);
     }
     for (int64_t q0 = 0; q0 < p; q0 += TS_NPMAX) {
         TsParams sp;
@@ -1534,15 +1534,15 @@ krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_
     CUtensorMap mk128, mk64, ma;
     KRR_TRY(map_f32(c, &mk128, c->Kd, ntri * b, b, 128));
     KRR_TRY(map_f32(c, &mk64, c->Kd, ntri * b, b, 64));
-    static bool attr = false;
-    if (!attr) {
+    static PerDevice attr;
+    if (!attr.has(c->device)) {
         const cudaError_t e =
             cudaFuncSetAttribute(tcres_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ts_smem_limit());
         if (e != cudaSuccess) {
             c->last_error = std::string("cudaFuncSetAttribute (tensor-core residual): ") + cudaGetErrorString(e);
             return KRR_ECUDA;
         }
-        attr = true;
+        attr.put(c->device);
     }
     for (int64_t q0 = 0; q0 < p; q0 += TS_NPMAX) {
         // the FP16 pair of a with per-block scales (B operand)

@@ -265,10 +265,14 @@ class KRR:
                                                     ctypes.byref(nt)))
         return out
 
-    def distances(self) -> np.ndarray:
-        """Squared distances of the lower-triangle tiles (needs keep_distances=True)."""
-        out = np.zeros((self.n, self.n), dtype=np.uint32)
-        self._check(self._lib.krr_get_distances(self._ctx, ctypes.c_void_p(out.ctypes.data), self.n))
+    def distances(self, out=None):
+        """Squared distances of the lower-triangle tiles (needs keep_distances=True)
+        into ``out`` (an n x n host array or device tensor of 4-byte integers;
+        its strictly-upper tiles are left as they are), or into a new zeroed
+        host uint32 array."""
+        if out is None:
+            out = np.zeros((self.n, self.n), dtype=np.uint32)
+        self._check(self._lib.krr_get_distances(self._ctx, ctypes.c_void_p(_ptr(out)), _ld(out)))
         return out
 
     def kernel(self, out=None):

@@ -55,3 +55,42 @@ def test_gradient_matches_finite_differences_and_autograd():
     fd_l = (f(lg.item(), ll.item() + h) - f(lg.item(), ll.item() - h)) / (2 * h)
     assert lg.grad.item() == pytest.approx(fd_g, rel=2e-2, abs=1e-3 * float(loss))
     assert ll.grad.item() == pytest.approx(fd_l, rel=2e-2, abs=1e-3 * float(loss))
+
+
+def test_gradient_at_differentiation_workload_size():
+    """The differentiation workload: N_train = 16384, N_test = 4096, M = 8192,
+    P = 8, gamma = 1/M, lambda = 0.1, tile 1024.  The adjoint gradient
+    (reusing the Cholesky factor) against the FP64 oracle's closed form
+    (float64 library Gram products and factorisation) and against central
+    differences of the GPU loss with h = 1e-3 in log space."""
+    n, n_test, m, p, tile = 16384, 4096, 8192, 8, 1024
+    gamma, lam = 1.0 / m, 0.1
+    prob = inputs.problem(n, m, p, n_test, seed=2409017125, device=DEV)
+    g, y, t, yt = prob["G"], prob["Y"], prob["T"], prob["Yt"]
+    with KRR(tile=tile, mode="mixed") as model:
+        model.build_kernel(g, gamma)
+        model.factor(lam)
+        a, _ = model.solve(y)
+        loss, dg, dl = model.grad_hyper(t, yt, a)
+
+    def gpu_loss(log_g, log_l):
+        with KRR(tile=tile, mode="mixed") as mdl:
+            mdl.build_kernel(g, math.exp(log_g))
+            mdl.factor(math.exp(log_l))
+            aa, _ = mdl.solve(y)
+            pr = mdl.predict(t, aa)
+        return float(((pr.double() - yt.double()) ** 2).mean())
+
+    h = 1e-3
+    lg0, ll0 = math.log(gamma), math.log(lam)
+    fd_g = (gpu_loss(lg0 + h, ll0) - gpu_loss(lg0 - h, ll0)) / (2 * h)
+    fd_l = (gpu_loss(lg0, ll0 + h) - gpu_loss(lg0, ll0 - h)) / (2 * h)
+    rloss, rdg, rdl = oracle.hyper_gradient(gamma, lam, g.cpu().numpy(), y.cpu().numpy(), t.cpu().numpy(),
+                                            yt.cpu().numpy(), method="lapack")
+    print(f"\ngradient N={n}: loss {loss:.6e} (oracle {rloss:.6e}); d/dlog gamma {dg:.6e} (oracle {rdg:.6e}, "
+          f"fd {fd_g:.6e}); d/dlog lambda {dl:.6e} (oracle {rdl:.6e}, fd {fd_l:.6e})")
+    assert loss == pytest.approx(rloss, rel=1e-4)
+    assert dl == pytest.approx(rdl, rel=2e-3)
+    assert dg == pytest.approx(rdg, rel=2e-3, abs=2e-3 * abs(rloss))
+    assert dg == pytest.approx(fd_g, rel=2e-2, abs=1e-3 * rloss)
+    assert dl == pytest.approx(fd_l, rel=2e-2, abs=1e-3 * rloss)

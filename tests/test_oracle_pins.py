@@ -261,3 +261,57 @@ def test_input_generator_recipe():
     # mean genotype matches 2 p_j on a larger draw
     big = inputs.genotypes(4000, 64, seed=2).double()
     assert torch.allclose(big.mean(0), 2 * inputs.allele_freqs(64, 2), atol=0.08)
+
+
+# ---------------------------------------------------------------- library-primitive methods
+
+def test_blas_distances_equal_bruteforce():
+    """The float64 Gram product gives the same integers as the term-by-term sum,
+    including the largest value (all-0 against all-2 rows: 4 m)."""
+    for seed, (n1, n2, m) in enumerate([(1, 1, 1), (7, 5, 3), (33, 64, 300), (64, 17, 129)]):
+        a = _rand_geno(n1, m, seed + 200)
+        b = _rand_geno(n2, m, seed + 300)
+        assert np.array_equal(oracle.sqdist(a, b, method="blas"), oracle.sqdist(a, b))
+        assert np.array_equal(oracle.sqdist(a, method="blas"), oracle.sqdist(a))
+    m = 20000
+    g = np.zeros((3, m), np.int8)
+    g[1] = 2
+    g[2, ::2] = 1
+    d = oracle.sqdist(g, method="blas")
+    assert d[1, 0] == 4 * m and d[0, 1] == 4 * m
+    assert np.array_equal(d, oracle.sqdist(g))
+
+
+def test_lapack_factor_and_solves_equal_plain_loops():
+    rng = np.random.default_rng(31)
+    for n in (1, 17, 200):
+        x = rng.standard_normal((n, n))
+        a = x @ x.T + n * np.eye(n)
+        l0 = oracle.cholesky(a)
+        l1 = oracle.cholesky(a, method="lapack")
+        assert np.allclose(l1, l0, rtol=1e-12, atol=1e-12)
+        y = rng.standard_normal((n, 3))
+        z0 = oracle.forward_subst(l0, y)
+        z1 = oracle.forward_subst(l0, y, method="lapack")
+        assert np.allclose(z1, z0, rtol=1e-11, atol=1e-12)
+        assert np.allclose(oracle.backward_subst(l0, z0, method="lapack"), oracle.backward_subst(l0, z0),
+                           rtol=1e-11, atol=1e-12)
+    with pytest.raises(oracle.NotPositiveDefinite):
+        oracle.cholesky(np.diag([4.0, 1.0, -1.0, 2.0]), method="lapack")
+
+
+def test_lapack_krr_and_gradient_equal_plain():
+    g = _rand_geno(150, 90, 33)
+    t = _rand_geno(40, 90, 34)
+    rng = np.random.default_rng(33)
+    y = rng.standard_normal((150, 3))
+    yt = rng.standard_normal((40, 3))
+    gamma, lam = 1 / 90, 0.1
+    k0, a0, p0 = oracle.krr(gamma, lam, g, y, t)
+    k1, a1, p1 = oracle.krr(gamma, lam, g, y, t, method="lapack")
+    assert np.array_equal(k0, k1)
+    assert np.allclose(a1, a0, rtol=1e-9, atol=1e-10)
+    assert np.allclose(p1, p0, rtol=1e-9, atol=1e-10)
+    r0 = oracle.hyper_gradient(gamma, lam, g, y, t, yt)
+    r1 = oracle.hyper_gradient(gamma, lam, g, y, t, yt, method="lapack")
+    assert np.allclose(r1, r0, rtol=1e-8, atol=1e-13)

@@ -69,6 +69,6 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     called = []
     monkeypatch.setattr(bench, "cpu_sample", lambda *a, **k: called.append(1))
-    args = types.SimpleNamespace(config="c3", cpu_rows=64, warmup=0, steps=1)
+    args = types.SimpleNamespace(config="c3", ref_rows=64, warmup=0, steps=1)
     assert bench.run_reference(args) == 0
     assert not called

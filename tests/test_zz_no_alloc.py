@@ -1,8 +1,10 @@
 """krr_predict_noalloc: prediction for callers that must not allocate device
-memory at call time (graph capture, a pre-reserved device arena, latency-
-critical paths).  It keeps its working buffers in one fixed-size device array
-of the library instead of cudaMalloc'd buffers.  Called here through the C
-ABI and compared with krr_predict on two calls in a row.
+memory at call time (a process whose device memory is reserved up front by
+another allocator, or a latency-critical path that must not enter the
+driver's allocator).  It keeps its working buffers in one fixed-size device
+array of the library instead of cudaMalloc'd buffers.  Called here through
+the C ABI and compared with krr_predict on two calls in a row; the free
+device memory is the same before and after a call.
 
 This file is collected last on purpose, so a stop-at-first-failure run has
 already run every other test when it gets here."""
@@ -46,6 +48,16 @@ def test_predict_noalloc_matches_predict():
             assert st == krrmod.OK, lib.krr_last_error(model._ctx)
             err = (torch.linalg.norm(out.double() - ref.double()) / torch.linalg.norm(ref.double())).item()
             assert err <= RTOL_YT, err
+        # after a warm call (the array's address is looked up), a call takes
+        # no device memory: cudaMalloc works in 2 MB pages, so any allocation
+        # would show in the free bytes
+        out = torch.empty((n_test, p), device=dev)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        st = _call(lib, model, t, a, out)
+        torch.cuda.synchronize()
+        assert st == krrmod.OK
+        assert torch.cuda.mem_get_info()[0] == free0
         # limits are checked, nothing is written on refusal
         big = torch.zeros((300, m), dtype=torch.int8, device=dev)
         out = torch.zeros((300, p), device=dev)
