@@ -37,7 +37,11 @@ CONFIGS = {
     "c3": (131072, 16384, 20, 4096, 1024),
     # small case for ncu captures (about 1.5 GB on the device, K tiles > L2)
     "p1": (16384, 4096, 8, 1024, 1024),
+    # FP8-dominant regime: the precision workload's shapes on structured cohorts
+    "c2s": (32768, 8192, 10, 4096, 1024),
 }
+# structured cohorts (Balding-Nichols subpopulations) and gamma = gamma_m / M
+STRUCTURED = {"c2s": {"populations": 8, "fst": 0.3, "gamma_m": 8.0}}
 # batching workload: 64 problems = 16 cohorts x 4 lambdas, N ~ U[1024, 16384]
 C4 = {"problems": 64, "cohorts": 16, "n_lo": 1024, "n_hi": 16384, "m": 4096, "p": 4, "n_test": 512,
       "lambdas": (1e-3, 1e-2, 1e-1, 1.0)}
@@ -54,8 +58,37 @@ def metric_ops(n, m, p):
 
 def workload_name(cfg):
     n, m, p, nt, b = CONFIGS[cfg]
+    if cfg in STRUCTURED:
+        st = STRUCTURED[cfg]
+        return (f"{cfg}: N={n} M={m} P={p} N_test={nt} tile={b} gamma={st['gamma_m']:g}/M lambda={LAMBDA}, "
+                f"{st['populations']} Balding-Nichols cohorts F={st['fst']} around p_j~U(0.05,0.5), "
+                f"phenotypes 20 SNP-pair products + N(0,0.5)")
     return (f"{cfg}: N={n} M={m} P={p} N_test={nt} tile={b} gamma=1/M lambda={LAMBDA}, "
             f"genotypes Binomial(2,p_j) p_j~U(0.05,0.5), phenotypes 20 SNP-pair products + N(0,0.5)")
+
+
+def gamma_of(cfg):
+    m = CONFIGS[cfg][1]
+    return STRUCTURED[cfg]["gamma_m"] / m if cfg in STRUCTURED else 1.0 / m
+
+
+def make_problem(cfg, n, m, p, n_test, seed, device="cpu"):
+    from paper_2409_01712_gb300 import inputs
+
+    if cfg in STRUCTURED:
+        st = STRUCTURED[cfg]
+        return inputs.structured_problem(n, m, p, n_test, seed=seed, populations=st["populations"], fst=st["fst"],
+                                         device=device)
+    return inputs.problem(n, m, p, n_test, seed=seed, device=device)
+
+
+PREC_CHARS = {0: "D", 1: "S", 2: "h", 3: "8", 255: " "}
+
+
+def heatmap_rows(pmap):
+    """The precision mosaic as text rows: D = FP64 diagonal, S = FP32 class,
+    h = FP16, 8 = E4M3 (row i lists tiles (i, 0..i))."""
+    return ["".join(PREC_CHARS.get(int(v), "?") for v in pmap[i, : i + 1]) for i in range(pmap.shape[0])]
 
 
 def peaks():
@@ -172,12 +205,12 @@ def cpu_sample(cfg, n_sample, g_host=None, y_host=None):
 
     n, m, p, _, _ = CONFIGS[cfg]
     if g_host is None:
-        prob = inputs.problem(n_sample, m, p, 1, seed=SEED)
+        prob = make_problem(cfg, n_sample, m, p, 1, seed=SEED)
         g_host, y_host = prob["G"].numpy(), prob["Y"].numpy()
     g = np.ascontiguousarray(g_host[:n_sample])
     y = np.ascontiguousarray(y_host[:n_sample]).astype(np.float64)
     t0 = time.perf_counter()
-    k = oracle.build_kernel(1.0 / m, g)
+    k = oracle.build_kernel(gamma_of(cfg), g)
     t1 = time.perf_counter()
     oracle.associate(LAMBDA, k, y)
     dt = time.perf_counter() - t0
@@ -266,16 +299,16 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     cfg = args.config
     n, m, p, n_test, tile = CONFIGS[cfg]
-    gamma = 1.0 / m
+    gamma = gamma_of(cfg)
 
-    prob = inputs.problem(n, m, p, n_test, seed=SEED + rank, device=dev)
+    prob = make_problem(cfg, n, m, p, n_test, seed=SEED + rank, device=dev)
     g, y, t = prob["G"], prob["Y"], prob["T"]
     torch.cuda.synchronize()
     a_out = torch.empty((n, p), dtype=torch.float32, device=dev)
     yt_out = torch.empty((n_test, p), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    model = KRR(tile=tile, mode=args.mode, stream=stream.cuda_stream)
+    model = KRR(tile=tile, mode=args.mode, stream=stream.cuda_stream, prec_rule=args.prec_rule, eps=args.eps)
 
     def step():
         model.build_kernel(g, gamma)
@@ -348,6 +381,9 @@ def run_ours(args):
             "phases": phases,
             "factor": {k: fi[k] for k in ("tiles_fp32", "tiles_fp16", "tiles_e4m3", "factor_bytes",
                                           "min_pivot")},
+            "precision_map": ({"legend": "D FP64/FP32 diagonal, S FP32 class, h FP16, 8 E4M3; row i = tiles (i, 0..i)",
+                               "rows": heatmap_rows(model.precision_map())} if fi["nt"] <= 32 else
+                              {"note": f"{fi['nt']} x {fi['nt']} tiles: counts under factor"}),
             "solve": {"iterations": si["iterations"], "rel_residual": si["rel_residual"],
                       "converged": si["converged"], "history": si["history"]}}
     if roof:
@@ -513,6 +549,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--config", default="c3", choices=sorted(CONFIGS) + ["c4"])
+    ap.add_argument("--prec-rule", default="lambda", choices=["lambda", "knorm"])
+    ap.add_argument("--eps", type=float, default=None, help="threshold of the precision rule")
     ap.add_argument("--mode", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparator step")

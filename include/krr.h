@@ -56,17 +56,30 @@ typedef enum krr_mode {
 /* Tile precisions reported by krr_get_precision_map(). */
 enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_FP16 = 2, KRR_PREC_E4M3 = 3 };
 
+/* Adaptive-precision rules (krr_options.prec_rule) for an off-diagonal factor
+ * tile (i, k), stored at the lowest unit roundoff u of {E4M3 2^-4, FP16
+ * 2^-11} the rule admits, else at FP32 accuracy:
+ *   KRR_RULE_LAMBDA: u max|L_ik| max|L_kk| <= eps * lambda -- the rounding of
+ *     L_ik perturbs L L^T by about u |L_ik| |L_kk|, which stays below the
+ *     smallest eigenvalue K + lambda I can have (default);
+ *   KRR_RULE_KNORM: u ||K_ik||_F <= eps ||K||_F / NT -- the Frobenius-norm
+ *     rule on the tiles of K of the adaptive-precision Cholesky the paper
+ *     cites (Sec. IV-C, "Precision Heatmaps"), with ||K_ik||_F from the
+ *     build. */
+enum { KRR_RULE_LAMBDA = 0, KRR_RULE_KNORM = 1 };
+
 typedef struct krr_options {
     int64_t tile;            /* b: tile edge, a power of two in [256, 4096] (default 1024) */
     int32_t mode;            /* krr_mode (default KRR_MODE_MIXED) */
     int32_t allow_fp8;       /* 1: E4M3 allowed for factor tiles (default 1) */
-    double eps;              /* adaptive-precision threshold: a factor tile L_ik may be stored
-                                at unit roundoff u when u max|L_ik| max|L_kk| <= eps * lambda
-                                (default 6e-4) */
+    double eps;              /* adaptive-precision threshold of prec_rule (default 6e-4) */
     double ir_tol;           /* refinement stops at ||R||_F / ||Y||_F <= ir_tol (default 1e-7) */
     int32_t ir_max;          /* maximum refinement iterations (default 30; 0 = none) */
     int32_t diag_fp64;       /* 1: diagonal-tile Cholesky in FP64, 0: FP32 (default 0) */
     int64_t wait_budget_ns;  /* limit of every bounded device wait (default 2e9) */
+    int32_t prec_rule;       /* KRR_RULE_LAMBDA (default) or KRR_RULE_KNORM; eps is the
+                                threshold of either rule */
+    int32_t reserved;        /* 0 */
 } krr_options;
 
 /* Per-call reports; valid when the call returns. */

@@ -375,6 +375,8 @@ void krr_default_options(krr_options *opt) {
     opt->ir_max = 30;
     opt->diag_fp64 = 0;
     opt->wait_budget_ns = 2000000000LL;
+    opt->prec_rule = KRR_RULE_LAMBDA;
+    opt->reserved = 0;
 }
 
 krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
@@ -398,6 +400,10 @@ krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
     }
     if (!(o.eps > 0.0) || !(o.ir_tol > 0.0) || o.ir_max < 0 || o.ir_max > 1000) {
         g_create_error = "eps and ir_tol must be positive, ir_max in [0, 1000]";
+        return KRR_EINVAL;
+    }
+    if (o.prec_rule != KRR_RULE_LAMBDA && o.prec_rule != KRR_RULE_KNORM) {
+        g_create_error = "unknown precision rule";
         return KRR_EINVAL;
     }
     krr_ctx *c = new (std::nothrow) krr_ctx();

@@ -769,14 +769,18 @@ krr_status diag_step(Ctx *c, int64_t k) {
 
 // ----------------------------------------------------------------------------
 // Adaptive precision of one factor column (mixed mode).
-// Tile (i, k), i > k, is stored at unit roundoff u_p when
-//     u_p * max|L_ik| * max|L_kk| <= eps * lambda,
-// the lowest allowed of E4M3 (u = 2^-4) and FP16 (u = 2^-11), else FP32.
-// Rounding L_ik perturbs L L^T in block (i, k) by about u_p |L_ik| |L_kk|;
-// the refinement converges while that stays well below lambda, the smallest
-// possible eigenvalue of K + lambda I.  max|L_kk| is bounded by
-// sqrt(max_r W_kk[r, r]) from the diagonal step.  FP16/E4M3 tiles carry a
-// power-of-two scale so the largest entry sits near the top of the format.
+// Tile (i, k), i > k, is stored at the lowest unit roundoff u_p of E4M3
+// (u = 2^-4) and FP16 (u = 2^-11) that the rule admits, else FP32:
+//   lambda rule:  u_p * max|L_ik| * max|L_kk| <= eps * lambda.
+//     Rounding L_ik perturbs L L^T in block (i, k) by about u_p |L_ik| |L_kk|;
+//     the refinement converges while that stays well below lambda, the
+//     smallest possible eigenvalue of K + lambda I.  max|L_kk| is bounded by
+//     sqrt(max_r W_kk[r, r]) from the diagonal step.
+//   K-norm rule (the Frobenius rule on the tiles of K of the adaptive-
+//     precision Cholesky the paper cites, Sec. IV-C):
+//     u_p * ||K_ik||_F <= eps * ||K||_F / NT, both norms from the build.
+// FP16/E4M3 tiles carry a power-of-two scale so the largest entry sits near
+// the top of the format.
 // ----------------------------------------------------------------------------
 __device__ inline float pow2_scale(float mx, float top) {
     if (!(mx > 0.f)) return 1.f;
@@ -789,18 +793,30 @@ __device__ inline float pow2_scale(float mx, float top) {
 
 __global__ void column_decide_kernel(int64_t k, int64_t nt, int64_t bb, int chunks,
                                      const float *part_max, double thresh,
-                                     const double *lkk_max, int allow_fp8, TileDesc *ltab,
+                                     const double *lkk_max, int allow_fp8, int rule, double eps,
+                                     const double *knorm_part, int64_t knorm_per_tile,
+                                     const double *knorm2_total, TileDesc *ltab,
                                      uint8_t *precmap, DevErrors *err) {
     const int64_t tile = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (tile >= nt - k - 1) return;
+    const int64_t i = k + 1 + tile;
     float mx = 0;
     for (int q = 0; q < chunks; ++q) mx = fmaxf(mx, part_max[tile * chunks + q]);
-    const double w = (double)mx * lkk_max[k];
+    double w, thr;
+    if (rule == KRR_RULE_KNORM) {
+        const double *tp = knorm_part + tri_index(i, k) * knorm_per_tile;
+        double s2 = 0.0;
+        for (int64_t q = 0; q < knorm_per_tile; ++q) s2 += tp[q];
+        w = sqrt(s2);
+        thr = eps * sqrt(*knorm2_total) / (double)nt;
+    } else {
+        w = (double)mx * lkk_max[k];
+        thr = thresh;
+    }
     int prec;
-    if (allow_fp8 && 0.0625 * w <= thresh) prec = KRR_PREC_E4M3;
-    else if (0x1p-11 * w <= thresh) prec = KRR_PREC_FP16;
+    if (allow_fp8 && 0.0625 * w <= thr) prec = KRR_PREC_E4M3;
+    else if (0x1p-11 * w <= thr) prec = KRR_PREC_FP16;
     else prec = KRR_PREC_FP32;
-    const int64_t i = k + 1 + tile;
     TileDesc d;
     d.prec = prec;
     d.scale = (prec == KRR_PREC_E4M3) ? pow2_scale(mx, 448.f) : pow2_scale(mx, 32768.f);
@@ -870,9 +886,11 @@ void launch_column_cast(Ctx *c, int64_t k) {
     const int chunks = (int)tile_max_partials(c->b);
     const double thresh = c->opt.eps * c->lambda;
     const double *lkk = c->red + RED_MINPIV + c->nt * (c->b / 64);
-    count_launch(), column_decide_kernel<<<cdiv(u, 128), 128, 0, c->stream>>>(k, c->nt, bb, chunks, c->colmax,
-                                                               thresh, lkk, c->opt.allow_fp8,
-                                                               c->ltab, c->precmap, c->derr);
+    // K-norm rule: sums of K^2 per 128 x 256 block of every lower-triangle tile (build epilogue)
+    const int64_t kper = (c->b / 128) * (c->b / 256);
+    count_launch(), column_decide_kernel<<<cdiv(u, 128), 128, 0, c->stream>>>(
+        k, c->nt, bb, chunks, c->colmax, thresh, lkk, c->opt.allow_fp8, c->opt.prec_rule, c->opt.eps, c->knorm2, kper,
+        c->red + RED_KNORM2, c->ltab, c->precmap, c->derr);
     count_launch(), column_write_kernel<<<dim3(64, (unsigned)u), 256, 0, c->stream>>>(k, bb, c->colbuf, c->ltab,
                                                                       c->pool, c->pan_hi, c->pan_lo,
                                                                       (__half *)c->W);

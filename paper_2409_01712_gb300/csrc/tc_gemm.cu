@@ -29,7 +29,10 @@
 //              sum_ij d_ij K_ij <Z_i, A_j> (both triangles through symmetry).
 //   OP_UPDATE  Factorize (Alg. 3), trailing update of step k:
 //              W_ij -= L_ik L_jk^T for k < j <= i, FP16 operands (hi/lo
-//              phases for tiles stored at FP32 accuracy), FP32 accumulation.
+//              phases for tiles stored at FP32 accuracy), FP32 accumulation;
+//              a block whose two factor tiles are both stored E4M3 runs as
+//              kind::f8f6f4 on the stored E4M3 bytes (twice the FP16 rate,
+//              half the operand bytes, the same exact products).
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -109,6 +112,7 @@ struct TcParams {
 // One 128 x 256 output block: up to three operand phases, each nkb slabs.
 struct Work {
     int nph, nkb;
+    int kind8;  // pair-mode update: both operands E4M3 (kind::f8f6f4, 128 K per stage)
     int amap[3], bmap[3];
     int arow[3], brow[3];
     // epilogue coordinates
@@ -258,6 +262,16 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bd
     }
 }
 
+// Pair mode, both operands E4M3 (the trailing update of two E4M3 tiles):
+// the same descriptors and instruction descriptor (E4M3 encodes as 0, like
+// F16), 32 bytes of K per instruction = 32 elements.
+__device__ __forceinline__ void mma_pair_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(PairCfg<2>::idesc), "r"(acc));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -318,6 +332,7 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
     const int64_t b = p.b;
     const int64_t sub_cols = b / BN, sub_per_tile = (b / BM) * sub_cols;
     w.t = t;
+    w.kind8 = 0;
     if (OP == OP_DIST || OP == OP_GRADK) {
         const int64_t tile = t / sub_per_tile, sub = t % sub_per_tile;
         tri_decode(tile, &w.i, &w.j);
@@ -393,11 +408,23 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
             return;
         }
         // operand maps: 0 = factor pool viewed as FP16 rows of b, 1 = FP16 (hi)
-        // panel of the column, 2 = FP16 lo panel.  FP16 tiles are read from the
-        // pool directly; FP32 tiles use the hi/lo split, E4M3 tiles their FP16
-        // shadow in the hi panel.
+        // panel of the column, 2 = FP16 lo panel, 4 = factor pool viewed as
+        // E4M3 rows of b bytes.  Two E4M3 tiles meet in one kind::f8f6f4
+        // phase on their stored bytes (a stage holds 128 of their columns);
+        // otherwise FP16 tiles are read from the pool directly, FP32 tiles
+        // use the hi/lo split, E4M3 tiles their FP16 shadow in the hi panel.
         const TileDesc di = col_tile(p, col_desc, w.i - k - 1);
         const TileDesc dj = col_tile(p, col_desc, w.j - k - 1);
+        if (di.prec == KRR_PREC_E4M3 && dj.prec == KRR_PREC_E4M3) {
+            w.kind8 = 1;
+            w.nph = 1;
+            w.nkb = (int)(b / SLAB);
+            w.amap[0] = 4;
+            w.arow[0] = (int)(di.offset / b + w.sm * BM);
+            w.bmap[0] = 4;
+            w.brow[0] = (int)(dj.offset / b + w.sn * BN);
+            return;
+        }
         const int ahi_map = (di.prec == KRR_PREC_FP16) ? 0 : 1;
         const int bhi_map = (dj.prec == KRR_PREC_FP16) ? 0 : 1;
         const int ahi_row = (int)((di.prec == KRR_PREC_FP16 ? di.offset / (2 * b) : (w.i - k - 1) * b) + w.sm * BM);
@@ -788,7 +815,7 @@ template <int KIND, int OP, int PAIR>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
               const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1,
-              const TcParams p) {
+              const __grid_constant__ CUtensorMap mX, const TcParams p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     constexpr int NST = PairCfg<PAIR>::stages, SBYTES = PairCfg<PAIR>::stage_bytes;
@@ -849,6 +876,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mA1)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB0)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mB1)) : "memory");
+        if (OP == OP_UPDATE)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mX)) : "memory");
     }
     if (OP == OP_UPDATE && col_desc) {
         const int64_t ncol = p.nt - p.k - 1;
@@ -864,7 +893,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
-            const CUtensorMap *maps[4] = {&mA0, &mA1, &mB0, &mB1};
+            const CUtensorMap *maps[5] = {&mA0, &mA1, &mB0, &mB1, &mX};
             int s = 0;
             uint32_t ph = 0;
             int issued = 0;
@@ -877,7 +906,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         if (!wait_bar(&empty[s], ph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
                         uint8_t *sa = stage_base + s * SBYTES;
                         uint8_t *sb = sa + A_BYTES;
-                        const int x = (KIND == KIND_F16) ? kb * (SLAB / 2) : kb * SLAB;
+                        const int x = (KIND == KIND_F16 && !w.kind8) ? kb * (SLAB / 2) : kb * SLAB;
                         if (PAIR == 2) {
                             // rank 0 expects both CTAs' bytes; B rows [rank * 128, +128)
                             const uint32_t fbar = map_to_rank(&full[s], 0);
@@ -930,10 +959,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     tmem_fence_after();
                     const uint32_t sa = smem_u32(stage_base + s * SBYTES);
                     const uint32_t sb = sa + A_BYTES;
+                    if (PAIR == 2 && w.kind8) {
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        mma<KIND, PAIR>(tacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma_pair_f8(tacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
                                         (it > 0 || kk > 0) ? 1u : 0u);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            mma<KIND, PAIR>(tacc, smem_desc_sw128(sa + kk * 32), smem_desc_sw128(sb + kk * 32),
+                                            (it > 0 || kk > 0) ? 1u : 0u);
                     }
                     any = true;
                     if (PAIR == 2) mma_commit_pair(&empty[s]);  // frees the stage in both CTAs
@@ -1093,6 +1128,7 @@ struct TcState {
     CUtensorMap g_map;                     // packed training genotypes
     CUtensorMap w_map, hi_map, lo_map;     // trailing tiles, column panels
     CUtensorMap pool_map;                  // factor pool viewed as FP16 rows of b
+    CUtensorMap pool8_map;                 // factor pool viewed as E4M3 rows of b bytes
     CUtensorMap linv_hi_map, linv_lo_map;  // diagonal inverse splits
     bool factor_maps = false;
 };
@@ -1116,7 +1152,8 @@ krr_status make_map(Ctx *c, CUtensorMap *map, const void *base, CUtensorMapDataT
 
 template <int KIND, int OP, int PAIR = 1>
 krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
-                  const CUtensorMap &b1, TcParams &p) {
+                  const CUtensorMap &b1, TcParams &p, const CUtensorMap *x = nullptr) {
+    const CUtensorMap &mx = x ? *x : a0;  // fifth map: only the trailing update reads one
     if (p.items <= 0) return KRR_OK;
     static PerDevice attr, clusters_of;  // per device: smem opt-in done; clusters that fit at once
     if (!attr.has(c->device)) {
@@ -1132,7 +1169,7 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
     p.err = c->derr;
     if (PAIR == 1) {
         const int64_t grid = p.items < c->num_sms ? p.items : c->num_sms;
-        count_launch(), tc_kernel<KIND, OP, 1><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, c->stream>>>(a0, a1, b0, b1, p);
+        count_launch(), tc_kernel<KIND, OP, 1><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, c->stream>>>(a0, a1, b0, b1, mx, p);
     } else {
         cudaLaunchConfig_t cfg;
         memset(&cfg, 0, sizeof(cfg));
@@ -1163,7 +1200,7 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
         const int64_t clusters = units < max_clusters ? units : max_clusters;
         cfg.gridDim = dim3((unsigned)(clusters * PAIR));
         count_launch();
-        cudaError_t e = cudaLaunchKernelEx(&cfg, tc_kernel<KIND, OP, PAIR>, a0, a1, b0, b1, p);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, tc_kernel<KIND, OP, PAIR>, a0, a1, b0, b1, mx, p);
         if (e != cudaSuccess) {
             cudaGetLastError();
             c->last_error = std::string("tensor-core cluster launch: ") + cudaGetErrorString(e);
@@ -1199,6 +1236,7 @@ krr_status ensure_factor_maps(Ctx *c) {
     KRR_TRY(make_map(c, &st->hi_map, c->pan_hi, f16, 2, (nt - 1) * b, b));
     KRR_TRY(make_map(c, &st->lo_map, c->pan_lo, f16, 2, (nt - 1) * b, b));
     KRR_TRY(make_map(c, &st->pool_map, c->pool, f16, 2, (int64_t)(c->pool_bytes / (2 * b)), b));
+    KRR_TRY(make_map(c, &st->pool8_map, c->pool, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, (int64_t)(c->pool_bytes / b), b));
     KRR_TRY(make_map(c, &st->linv_hi_map, c->Linv_hi, f16, 2, nt * b, b));
     KRR_TRY(make_map(c, &st->linv_lo_map, c->Linv_lo, f16, 2, nt * b, b));
     st->factor_maps = true;
@@ -1280,8 +1318,9 @@ krr_status tc_update(Ctx *c, int64_t k) {
     p.Wd = c->Wd;
     p.ltab = c->ltab;
     p.items = u * (u + 1) / 2 * (b / BM) * (b / BN);
-    // mB1 = the FP16 trailing tiles: staged target blocks (TMA load and store)
-    return launch<KIND_F16, OP_UPDATE, 2>(c, st->pool_map, st->hi_map, st->lo_map, st->w_map, p);
+    // mB1 = the FP16 trailing tiles: staged target blocks (TMA load and store);
+    // the fifth map reads E4M3 tiles for kind::f8f6f4 blocks
+    return launch<KIND_F16, OP_UPDATE, 2>(c, st->pool_map, st->hi_map, st->lo_map, st->w_map, p, &st->pool8_map);
 }
 
 // B = K_test^T G_p: the predict kernel with the roles of the two genotype

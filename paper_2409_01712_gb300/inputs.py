@@ -18,9 +18,19 @@ these draws stand in for them with the same value range and shapes):
   ``y_ic = sum_t w_ct g_{i,a_t} g_{i,b_t} + e_ic``, accumulated in float64 and
   stored float32;
 * held-out rows are further rows of the same genotype stream (same p_j).
+
+Structured cohorts (``structured_problem``; the FP8-dominant regime): the
+rows come from ``populations`` subpopulations under the Balding-Nichols
+model -- ancestral ``p_j ~ U(0.05, 0.5)`` as above, population ``k`` draws
+``p_kj ~ Beta(p_j (1 - F) / F, (1 - p_j) (1 - F) / F)`` (mean ``p_j``,
+variance ``F p_j (1 - p_j)``, ``F`` the fixation index) from a numpy
+generator seeded with ``seed + 3``; training rows are grouped by population
+in equal contiguous blocks, held-out rows likewise; genotypes and phenotypes
+then follow the recipe above with each row's own population frequencies.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 N_PAIRS = 20
@@ -75,3 +85,52 @@ def problem(n: int, m: int, n_pheno: int, n_test: int, seed: int, device="cpu"):
     y_all = phenotypes(g_all, n_pheno, seed)
     return {"G": g_all[:n].contiguous(), "Y": y_all[:n].contiguous(),
             "T": g_all[n:].contiguous(), "Yt": y_all[n:].contiguous()}
+
+
+def population_freqs(m: int, populations: int, fst: float, seed: int) -> torch.Tensor:
+    """populations x m allele frequencies under the Balding-Nichols model."""
+    p0 = allele_freqs(m, seed).numpy()
+    rng = np.random.default_rng(int(seed) + 3)
+    shape = (1.0 - fst) / fst
+    pk = rng.beta(p0 * shape, (1.0 - p0) * shape, size=(populations, m))
+    return torch.from_numpy(pk)
+
+
+def _population_of(rows: int, populations: int) -> torch.Tensor:
+    """Equal contiguous blocks: row r belongs to population r * populations // rows."""
+    return torch.arange(rows, dtype=torch.int64) * populations // max(rows, 1)
+
+
+def structured_genotypes(n: int, m: int, seed: int, pk: torch.Tensor, pop: torch.Tensor, device="cpu",
+                         chunk_rows: int = 8192) -> torch.Tensor:
+    """n x m int8 genotypes, row r drawn with the frequencies of population pop[r]."""
+    device = torch.device(device)
+    pkd = pk.to(device=device, dtype=torch.float32)
+    popd = pop.to(device)
+    gen = torch.Generator(device=device).manual_seed(int(seed) + 1)
+    out = torch.empty((n, m), dtype=torch.int8, device=device)
+    for r0 in range(0, n, chunk_rows):
+        r1 = min(n, r0 + chunk_rows)
+        pr = pkd[popd[r0:r1]]
+        u = torch.rand((r1 - r0, m), generator=gen, device=device, dtype=torch.float32)
+        blk = (u < pr).to(torch.int8)
+        torch.rand((r1 - r0, m), generator=gen, device=device, dtype=torch.float32, out=u)
+        blk += (u < pr).to(torch.int8)
+        out[r0:r1] = blk
+        del u, blk, pr
+    return out
+
+
+def structured_problem(n: int, m: int, n_pheno: int, n_test: int, seed: int, populations: int = 8,
+                       fst: float = 0.3, device="cpu"):
+    """Training and held-out data of ``populations`` structured cohorts.
+
+    Returns the keys of ``problem`` plus ``pop`` and ``pop_test`` (the
+    population index of every training and held-out row)."""
+    pk = population_freqs(m, populations, fst, seed)
+    pop = _population_of(n, populations)
+    pop_t = _population_of(n_test, populations)
+    g_all = structured_genotypes(n + n_test, m, seed, pk, torch.cat([pop, pop_t]), device=device)
+    y_all = phenotypes(g_all, n_pheno, seed)
+    return {"G": g_all[:n].contiguous(), "Y": y_all[:n].contiguous(),
+            "T": g_all[n:].contiguous(), "Yt": y_all[n:].contiguous(), "pop": pop, "pop_test": pop_t}

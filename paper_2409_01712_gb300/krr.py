@@ -26,6 +26,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOTPD, ENOCONV, ETIMEOUT, ESTATE = range(8)
 STATUS_NAMES = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA", 4: "KRR_ENOTPD",
                 5: "KRR_ENOCONV", 6: "KRR_ETIMEOUT", 7: "KRR_ESTATE"}
 MODES = {"mixed": 0, "fp32": 1}
+RULES = {"lambda": 0, "knorm": 1}
 PREC_NAMES = {0: "fp64", 1: "fp32", 2: "fp16", 3: "e4m3", 255: "-"}
 
 # Every symbol include/krr.h declares (checked by the CPU test suite).
@@ -40,7 +41,8 @@ PROF_CLASSES = ["pack", "build", "diag", "trsm", "cast", "update", "solve", "res
 class Options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int64), ("mode", ctypes.c_int32), ("allow_fp8", ctypes.c_int32),
                 ("eps", ctypes.c_double), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int32),
-                ("diag_fp64", ctypes.c_int32), ("wait_budget_ns", ctypes.c_int64)]
+                ("diag_fp64", ctypes.c_int32), ("wait_budget_ns", ctypes.c_int64), ("prec_rule", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class FactorInfo(ctypes.Structure):
@@ -167,13 +169,17 @@ class KRR:
 
     def __init__(self, tile: int = 1024, mode: str = "mixed", eps: float | None = None,
                  ir_tol: float | None = None, ir_max: int | None = None, allow_fp8: bool = True,
-                 diag_fp64: bool = False, stream=None):
+                 diag_fp64: bool = False, prec_rule: str = "lambda", wait_budget_ns: int | None = None,
+                 stream=None):
         lib = load_library()
         o = default_options()
         o.tile = tile
         o.mode = MODES[mode]
         o.allow_fp8 = int(allow_fp8)
         o.diag_fp64 = int(diag_fp64)
+        o.prec_rule = RULES[prec_rule]
+        if wait_budget_ns is not None:
+            o.wait_budget_ns = int(wait_budget_ns)
         if eps is not None:
             o.eps = eps
         if ir_tol is not None:
