@@ -68,6 +68,18 @@ enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_FP16 = 2, KRR_PREC_E4M3 = 
  *     build. */
 enum { KRR_RULE_LAMBDA = 0, KRR_RULE_KNORM = 1 };
 
+/* Kernel functions of Alg. 5 (krr_options.kernel):
+ *   KRR_KERNEL_GAUSSIAN: K_ij = exp(-gamma ||g_i - g_j||^2) (default);
+ *   KRR_KERNEL_IBS: identity by state, K_ij = (g_i ~ g_j) / M with
+ *     (g_i ~ g_j) = sum_k (2 - |g_ik - g_jk|) the number of alleles the two
+ *     patients share at the M loci (K_ii = 2; gamma is not used).  It is
+ *     computed on the same integer-exact tensor-core Gram machinery: each
+ *     genotype becomes the two indicators [g >= 1], [g >= 2], whose squared
+ *     Euclidean distance is the L1 distance |g_i - g_j|_1, and
+ *     (g_i ~ g_j) = 2M - |g_i - g_j|_1.  krr_get_distances() then returns the
+ *     L1 distances.  m <= 2^21. */
+enum { KRR_KERNEL_GAUSSIAN = 0, KRR_KERNEL_IBS = 1 };
+
 typedef struct krr_options {
     int64_t tile;            /* b: tile edge, a power of two in [256, 4096] (default 1024) */
     int32_t mode;            /* krr_mode (default KRR_MODE_MIXED) */
@@ -79,7 +91,7 @@ typedef struct krr_options {
     int64_t wait_budget_ns;  /* limit of every bounded device wait (default 2e9) */
     int32_t prec_rule;       /* KRR_RULE_LAMBDA (default) or KRR_RULE_KNORM; eps is the
                                 threshold of either rule */
-    int32_t reserved;        /* 0 */
+    int32_t kernel;          /* KRR_KERNEL_GAUSSIAN (default) or KRR_KERNEL_IBS */
 } krr_options;
 
 /* Per-call reports; valid when the call returns. */

@@ -88,6 +88,9 @@ def _load():
             lib.oracle_matmul.restype = None
             lib.oracle_matmul.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, _f64p,
                                           ctypes.c_int64, _f64p]
+            lib.oracle_ibs_count.restype = None
+            lib.oracle_ibs_count.argtypes = [_i8p, ctypes.c_int64, ctypes.c_int64, _i8p, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_int64, _i64p]
             lib.oracle_kernel_rows.restype = None
             lib.oracle_kernel_rows.argtypes = [_i8p, ctypes.c_int64, _i64p, ctypes.c_int64, _i8p,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -149,8 +152,48 @@ def gaussian_kernel(d: np.ndarray, gamma: float) -> np.ndarray:
     return out
 
 
-def build_kernel(gamma: float, g1, g2=None, method: str = "bruteforce") -> np.ndarray:
-    """Alg. 2: ``K[i, j] = KernelMatrix('Gaussian', gamma, G1[i, :], G2[j, :])``."""
+# Alleles shared identical by state at one locus, by genotype (copies of the
+# minor allele): row a, column b.
+IBS_TABLE = np.array([[2, 1, 0], [1, 2, 1], [0, 1, 2]], dtype=np.int64)
+
+
+def ibs_count(g1, g2=None, method: str = "bruteforce") -> np.ndarray:
+    """``(g1_i ~ g2_j)``: alleles shared identical by state, summed over the loci (int64).
+
+    ``method="bruteforce"`` adds ``2 - |a - b|`` locus by locus;
+    ``method="blas"`` writes each genotype as its one-hot indicator (a row of
+    the 3 x 3 sharing table picks the count) and sums the table lookups of all
+    loci with one float64 library matrix product (integers below 2^53:
+    exact)."""
+    a = _geno(g1)
+    b = a if g2 is None else _geno(g2)
+    if a.shape[1] != b.shape[1]:
+        raise ValueError("SNP counts differ")
+    if method == "blas":
+        m = a.shape[1]
+        ea = np.zeros((a.shape[0], m, 3), np.float64)
+        np.put_along_axis(ea, a.astype(np.int64)[:, :, None], 1.0, axis=2)
+        eb = np.zeros((b.shape[0], m, 3), np.float64)
+        np.put_along_axis(eb, b.astype(np.int64)[:, :, None], 1.0, axis=2)
+        ebw = eb @ IBS_TABLE.astype(np.float64)  # row of the table for each genotype of g2
+        return (ea.reshape(a.shape[0], -1) @ ebw.reshape(b.shape[0], -1).T).astype(np.int64)
+    out = np.empty((a.shape[0], b.shape[0]), dtype=np.int64)
+    _load().oracle_ibs_count(_ptr(a, _i8p), a.shape[0], a.shape[1], _ptr(b, _i8p), b.shape[0], b.shape[1],
+                             a.shape[1], _ptr(out, _i64p))
+    return out
+
+
+def ibs_kernel(g1, g2=None, method: str = "bruteforce") -> np.ndarray:
+    """Alg. 5, IBS branch: ``K_ij = (g1_i ~ g2_j) / N_S`` in double (K_ii = 2)."""
+    m = _geno(g1).shape[1]
+    return ibs_count(g1, g2, method=method).astype(np.float64) / float(m)
+
+
+def build_kernel(gamma: float, g1, g2=None, method: str = "bruteforce", kernel: str = "gaussian") -> np.ndarray:
+    """Alg. 2: ``K[i, j] = KernelMatrix(type, gamma, G1[i, :], G2[j, :])`` (type
+    ``"gaussian"`` or ``"ibs"``; gamma unused for IBS)."""
+    if kernel == "ibs":
+        return ibs_kernel(g1, g2, method="blas" if method in ("blas", "lapack") else "bruteforce")
     return gaussian_kernel(sqdist(g1, g2, method=method), gamma)
 
 
@@ -238,20 +281,21 @@ def associate(alpha: float, k: np.ndarray, y: np.ndarray, return_factor: bool = 
     return (w, l) if return_factor else w
 
 
-def predict(gamma: float, g, t, w: np.ndarray, method: str = "bruteforce") -> np.ndarray:
+def predict(gamma: float, g, t, w: np.ndarray, method: str = "bruteforce", kernel: str = "gaussian") -> np.ndarray:
     """Alg. 4: ``K = Build(gamma, T, G)`` (N_P2 x N_P1), ``P_r = K W``."""
-    return matmul(build_kernel(gamma, t, g, method=_dist(method)), w)
+    return matmul(build_kernel(gamma, t, g, method=_dist(method), kernel=kernel), w)
 
 
-def krr(gamma: float, alpha: float, g, y, t, method: str = "plain"):
+def krr(gamma: float, alpha: float, g, y, t, method: str = "plain", kernel: str = "gaussian"):
     """Alg. 1: Build, Associate, Predict.  Returns (K, W, P_r).
 
     ``method="lapack"``: Gram product and factorisation by library routines
-    (see the module docstring); the same definitions otherwise."""
+    (see the module docstring); the same definitions otherwise.  ``kernel``:
+    the Alg. 5 kernel type, ``"gaussian"`` or ``"ibs"``."""
     dm = "bruteforce" if method == "plain" else _dist(method)
-    k = build_kernel(gamma, g, method=dm)
+    k = build_kernel(gamma, g, method=dm, kernel=kernel)
     w = associate(alpha, k, y, method=method)
-    return k, w, predict(gamma, g, t, w, method=dm)
+    return k, w, predict(gamma, g, t, w, method=dm, kernel=kernel)
 
 
 def kernel_rows(gamma: float, g1, rows, g2) -> np.ndarray:

@@ -193,3 +193,29 @@ void oracle_kernel_rows(const int8_t *g1, int64_t ld1, const int64_t *rows,
         }
     }
 }
+
+/*
+ * Identity-by-state allele counts (Alg. 5, second branch): for each pair of
+ * rows, the number of alleles the two patients share identical by state,
+ * summed over the m loci.  At one locus genotypes a and b (copies of the
+ * minor allele, 0..2) share 2 - |a - b| alleles: the same genotype shares
+ * both, genotypes one apart share one, opposite homozygotes share none.
+ * Exact in int64.
+ */
+void oracle_ibs_count(const int8_t *g1, int64_t n1, int64_t ld1,
+                      const int8_t *g2, int64_t n2, int64_t ld2,
+                      int64_t m, int64_t *out) {
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n1; ++i) {
+        const int8_t *a = g1 + i * ld1;
+        for (int64_t j = 0; j < n2; ++j) {
+            const int8_t *b = g2 + j * ld2;
+            int64_t s = 0;
+            for (int64_t k = 0; k < m; ++k) {
+                int64_t t = (int64_t)a[k] - (int64_t)b[k];
+                s += 2 - (t < 0 ? -t : t);
+            }
+            out[i * n2 + j] = s;
+        }
+    }
+}

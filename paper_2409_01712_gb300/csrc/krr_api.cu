@@ -199,7 +199,7 @@ krr_status pack(Ctx *c, const int8_t *g, int64_t n, int64_t m, int64_t ldg, int6
         dg = (const int8_t *)c->stage;
         ldg = m;
     }
-    launch_pack_genotypes(dg, n, m, ldg, rows_pad, c->m_pad, out8, outf, norms, c->stream);
+    launch_pack_genotypes(dg, n, m, ldg, rows_pad, c->m_pad, out8, outf, norms, c->stream, is_ibs(c) ? 1 : 0);
     return check_launch(c, "pack genotypes");
 }
 
@@ -376,7 +376,7 @@ void krr_default_options(krr_options *opt) {
     opt->diag_fp64 = 0;
     opt->wait_budget_ns = 2000000000LL;
     opt->prec_rule = KRR_RULE_LAMBDA;
-    opt->reserved = 0;
+    opt->kernel = KRR_KERNEL_GAUSSIAN;
 }
 
 krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
@@ -404,6 +404,10 @@ krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
     }
     if (o.prec_rule != KRR_RULE_LAMBDA && o.prec_rule != KRR_RULE_KNORM) {
         g_create_error = "unknown precision rule";
+        return KRR_EINVAL;
+    }
+    if (o.kernel != KRR_KERNEL_GAUSSIAN && o.kernel != KRR_KERNEL_IBS) {
+        g_create_error = "unknown kernel function";
         return KRR_EINVAL;
     }
     krr_ctx *c = new (std::nothrow) krr_ctx();
@@ -507,10 +511,10 @@ krr_status krr_set_keep_distances(krr_ctx *c, int32_t keep) {
 krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, int64_t ldg,
                             double gamma) {
     if (!c) return KRR_EINVAL;
-    if (!G || n < 1 || m < 1 || m > (int64_t(1) << 22) || ldg < m || !(gamma > 0.0) ||
-        !isfinite(gamma)) {
-        c->last_error = "krr_build_kernel: need G != NULL, n >= 1, 1 <= m <= 2^22, ldg >= m, "
-                        "0 < gamma < inf";
+    if (!G || n < 1 || m < 1 || m > (int64_t(1) << (is_ibs(c) ? 21 : 22)) || ldg < m ||
+        (!is_ibs(c) && (!(gamma > 0.0) || !isfinite(gamma)))) {
+        c->last_error = "krr_build_kernel: need G != NULL, n >= 1, 1 <= m <= 2^22 (IBS: 2^21), ldg >= m, "
+                        "0 < gamma < inf (Gaussian kernel)";
         return KRR_EINVAL;
     }
     c->built = false;
@@ -519,7 +523,7 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
     const int64_t nt = (n + b - 1) / b;
     if (nt != c->nt || b != c->b) free_factor(c);  // factor buffers depend on the tile grid
     const int64_t n_pad = nt * b;
-    const int64_t m_pad = (m + 127) / 128 * 128;
+    const int64_t m_pad = (encoded_width(c, m) + 127) / 128 * 128;
     const size_t g_bytes = (size_t)n_pad * m_pad * (mixed(c) ? 1 : 4);
     const int64_t ntri = nt * (nt + 1) / 2;
     const size_t kd_bytes = (size_t)ntri * b * b * sizeof(float);
@@ -542,7 +546,7 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
         c->dd_bytes = dd_bytes;
     }
     c->n = n;
-    c->m = m;
+    c->m = m;  // set before packing: the IBS encoding and kernel function read it
     c->m_pad = m_pad;
     c->b = b;
     c->nt = nt;
@@ -569,8 +573,9 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
         launch_build_simt(c);
     }
     // algorithmic work: 2 M multiply-adds per entry of the lower-triangle
-    // tiles; compulsory bytes: the K tiles written once (FP32)
-    prof_end(c, pr, 2.0 * (double)ntri * b * b * (double)m, (double)kd_bytes);
+    // tiles (2 x 2M for the IBS encoding); compulsory bytes: the K tiles
+    // written once (FP32)
+    prof_end(c, pr, 2.0 * (double)ntri * b * b * (double)encoded_width(c, m), (double)kd_bytes);
     KRR_TRY(check_launch(c, "build"));
     launch_kernel_sumsq(c, c->red + RED_KNORM2);
     KRR_TRY(check_launch(c, "kernel norm"));
@@ -782,7 +787,7 @@ krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt,
                             c->pred_part);
         launch_predict_reduce(c->pred_part, nblk, rows_pad, n_test, p, out, p, c->stream);
     }
-    prof_end(c, pr, 2.0 * (double)n_test * c->n * c->m + 2.0 * (double)n_test * c->n * p, 0.0);
+    prof_end(c, pr, 2.0 * (double)n_test * c->n * encoded_width(c, c->m) + 2.0 * (double)n_test * c->n * p, 0.0);
     KRR_TRY(check_launch(c, "predict"));
     return store_rows_f32(c, out, n_test, p, Yt, ldyt);
 }
@@ -934,8 +939,8 @@ extern "C" krr_status krr_grad_hyper(krr_ctx *c, const int8_t *T, int64_t n_test
         c->last_error = "krr_grad_hyper: no factorisation";
         return KRR_ESTATE;
     }
-    if (!mixed(c) || !c->tc) {
-        c->last_error = "krr_grad_hyper: needs a context in KRR_MODE_MIXED";
+    if (!mixed(c) || !c->tc || is_ibs(c)) {
+        c->last_error = "krr_grad_hyper: needs a context in KRR_MODE_MIXED with the Gaussian kernel";
         return KRR_EINVAL;
     }
     if (!T || !Yt || !A || !out || n_test < 1 || ldt < c->m || p < 1 || p > 16 || ldy < p || lda < p) {

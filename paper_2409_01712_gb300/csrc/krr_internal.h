@@ -32,6 +32,18 @@ __host__ __device__ inline void tri_decode(int64_t t, int64_t *i, int64_t *j) {
     *j = t - r * (r + 1) / 2;
 }
 
+// Kernel function of Alg. 5 applied to the exact integer distance d of the
+// encoded rows: Gaussian exp(-gamma d) on the squared Euclidean distance, or
+// IBS (2M - d) / M on the L1 distance (the encoded rows' squared distance),
+// one correctly rounded division of exact integers.
+struct KernelFn {
+    int ibs;
+    float two_m, m;
+    __device__ __forceinline__ float value(float gamma, int32_t d) const {
+        return ibs ? __fdiv_rn(two_m - (float)d, m) : expf(-gamma * (float)d);
+    }
+};
+
 // Slots of the small FP64 reduction buffer Ctx::red.
 constexpr int RED_RNORM = 0;     // [0] ||R||_F^2, [1] ||Y||_F^2 of the last residual
 constexpr int RED_KNORM2 = 2;    // ||K||_F^2
@@ -153,6 +165,17 @@ struct Ctx {
     size_t red_cap = 0;
 };
 
+inline bool is_ibs(const Ctx *c) { return c->opt.kernel == KRR_KERNEL_IBS; }
+inline KernelFn kernel_fn(const Ctx *c) {
+    KernelFn f;
+    f.ibs = is_ibs(c) ? 1 : 0;
+    f.two_m = (float)(2 * c->m);
+    f.m = (float)c->m;
+    return f;
+}
+// Width of the packed operand rows before padding: M, or 2M for IBS.
+inline int64_t encoded_width(const Ctx *c, int64_t m) { return is_ibs(c) ? 2 * m : m; }
+
 // One-time set-up per device: cudaFuncSetAttribute and the occupancy queries
 // act on the current device only, so a process that drives several GPUs
 // repeats them on each.  Objects of this type live in static storage (zero
@@ -197,9 +220,11 @@ void count_launch();
 // ---------------------------------------------------------------------------
 // Pack int8 genotypes: E4M3 bytes (mixed) or FP32 (fp32) with zero padding to
 // n_pad x m_pad, plus exact squared row norms.
+// thermo = 1: the IBS encoding (two indicators per genotype, m_pad >= 2m;
+// norms = row sums of g).
 void launch_pack_genotypes(const int8_t *g, int64_t n, int64_t m, int64_t ldg, int64_t n_pad,
                            int64_t m_pad, uint8_t *out_e4m3, float *out_f32, int32_t *norms,
-                           cudaStream_t s);
+                           cudaStream_t s, int thermo = 0);
 
 // Generic FP32/FP64 tiled GEMM on CUDA cores: C = alpha * op(A) op(B)^T + beta * Cin,
 // with A (M x K, row-major) and B either N x K row-major (b_trans = 0) or

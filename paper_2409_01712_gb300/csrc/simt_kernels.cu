@@ -90,9 +90,42 @@ __global__ void pack_genotypes16_kernel(const int8_t *__restrict__ g, int64_t n,
     }
 }
 
+// IBS encoding (Alg. 5, second branch): genotype g becomes the two
+// indicators [g >= 1], [g >= 2] (E4M3 0x38 = 1, 0x00 = 0).  The squared
+// Euclidean distance of two encoded rows is then the L1 distance of the
+// genotypes, and the encoded row's squared norm is n_i = sum_k g_ik.
+// Encoded column k holds locus k / 2, level k % 2.
+__global__ void pack_thermo_kernel(const int8_t *__restrict__ g, int64_t n, int64_t m, int64_t ldg, int64_t m_pad,
+                                   uint8_t *__restrict__ out8, float *__restrict__ outf, int32_t *__restrict__ norms) {
+    const int64_t row = blockIdx.x;
+    int32_t s = 0;
+    for (int64_t k = threadIdx.x; k < m_pad; k += blockDim.x) {
+        const int64_t locus = k >> 1;
+        int v = 0;
+        if (row < n && locus < m) v = g[row * ldg + locus];
+        const int f = (v >= 1 + (int)(k & 1)) ? 1 : 0;
+        s += f;
+        if (out8) out8[row * m_pad + k] = f ? 0x38 : 0x00;
+        if (outf) outf[row * m_pad + k] = (float)f;
+    }
+    __shared__ int32_t red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) norms[row] = s;
+    }
+}
+
 void launch_pack_genotypes(const int8_t *g, int64_t n, int64_t m, int64_t ldg, int64_t n_pad,
                            int64_t m_pad, uint8_t *out8, float *outf, int32_t *norms,
-                           cudaStream_t s) {
+                           cudaStream_t s, int thermo) {
+    if (thermo) {
+        count_launch(), pack_thermo_kernel<<<(unsigned)n_pad, 256, 0, s>>>(g, n, m, ldg, m_pad, out8, outf, norms);
+        return;
+    }
     const bool wide = ((reinterpret_cast<uintptr_t>(g) | (uintptr_t)ldg | (uintptr_t)m) & 15u) == 0 &&
                       m_pad % 16 == 0;
     if (wide)
@@ -282,7 +315,7 @@ template void launch_gemm_simt<double>(int, int, int, double, const double *, in
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) build_simt_kernel(const float *gf, const int32_t *norms,
                                                          int64_t m_pad, int64_t n, int64_t b,
-                                                         float gamma, float *Kd, uint32_t *Dd,
+                                                         float gamma, KernelFn kf, float *Kd, uint32_t *Dd,
                                                          double *knorm_part) {
     const int64_t sub_side = b / SG_BM, sub_per_tile = sub_side * sub_side;
     const int64_t t = blockIdx.x / sub_per_tile, sub = blockIdx.x % sub_per_tile;
@@ -305,7 +338,7 @@ __global__ void __launch_bounds__(256) build_simt_kernel(const float *gf, const 
             const int64_t lc = sn * SG_BN + sg_col(j), gj = tj * b + lc;
             int32_t d = ni + norms[gj] - 2 * (int32_t)acc[i][j];
             float kv;
-            if (gi < n && gj < n) kv = expf(-gamma * (float)d);
+            if (gi < n && gj < n) kv = kf.value(gamma, d);
             else kv = (gi == gj) ? 1.0f : 0.0f;
             kt[lr * b + lc] = kv;
             if (dt) dt[lr * b + lc] = (gi < n && gj < n) ? (uint32_t)d : 0u;
@@ -338,7 +371,7 @@ void launch_build_simt(Ctx *c) {
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     const int64_t sub = (c->b / SG_BM) * (c->b / SG_BM);
     count_launch(), build_simt_kernel<<<(unsigned)(ntri * sub), 256, 0, c->stream>>>(
-        c->gf, c->norms, c->m_pad, c->n, c->b, (float)c->gamma, c->Kd, c->Dd, c->knorm2);
+        c->gf, c->norms, c->m_pad, c->n, c->b, (float)c->gamma, kernel_fn(c), c->Kd, c->Dd, c->knorm2);
 }
 
 // Deterministic sums of the per-block partials: out[0] = ||K||_F^2 and
@@ -477,7 +510,7 @@ __global__ void __launch_bounds__(256) predict_simt_kernel(const float *tf, cons
                                                            int64_t n_test, const float *gf,
                                                            const int32_t *gn, int64_t n,
                                                            int64_t m_pad, int64_t ncolblk,
-                                                           float gamma, const float *A, int64_t p,
+                                                           float gamma, KernelFn kf, const float *A, int64_t p,
                                                            int64_t ntest_pad, float *part) {
     extern __shared__ float sh[];
     float *Ks = sh;                    // 128 x 129
@@ -495,7 +528,7 @@ __global__ void __launch_bounds__(256) predict_simt_kernel(const float *tf, cons
         for (int j = 0; j < 8; ++j) {
             const int64_t gj = c0 + sg_col(j);
             int32_t d = ni + gn[gj] - 2 * (int32_t)acc[i][j];
-            Ks[sg_row(i) * 129 + sg_col(j)] = (gi < n_test && gj < n) ? expf(-gamma * (float)d) : 0.f;
+            Ks[sg_row(i) * 129 + sg_col(j)] = (gi < n_test && gj < n) ? kf.value(gamma, d) : 0.f;
         }
     }
     for (int64_t e = threadIdx.x; e < 128 * p; e += blockDim.x) {
@@ -518,7 +551,7 @@ void launch_predict_simt(Ctx *c, const float *tf, const int32_t *tn, int64_t n_t
     if (sh > 48 * 1024)
         cudaFuncSetAttribute(predict_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     count_launch(), predict_simt_kernel<<<(unsigned)(nrb * ncb), 256, sh, c->stream>>>(
-        tf, tn, n_test, c->gf, c->norms, c->n, c->m_pad, ncb, (float)c->gamma, A, p, rows_pad, part);
+        tf, tn, n_test, c->gf, c->norms, c->n, c->m_pad, ncb, (float)c->gamma, kernel_fn(c), A, p, rows_pad, part);
 }
 
 // Sum of partial products over column blocks in a fixed order; with a shift

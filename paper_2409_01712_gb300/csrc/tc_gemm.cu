@@ -105,6 +105,7 @@ struct TcParams {
     const float *gp;   // OP_GRADT: G_p, padded test rows x ldaw
     double *gpart;     // OP_GRADT / OP_GRADK: one partial sum per block
     const double *kshift;  // OP_PREDICT: shift c subtracted from every K entry (nullptr: none)
+    KernelFn kf;           // OP_DIST / OP_PREDICT: kernel function of the distance
     uint64_t wait_ns;
     DevErrors *err;
 };
@@ -497,7 +498,7 @@ __device__ __forceinline__ void predict_half(const TcParams &p, uint32_t tacc, i
         for (int e = 0; e < 16; ++e) {
             const int c = ch * 16 + e;
             const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
-            const float kv = (real_row && j0 + c < p.n) ? expf(-p.gamma * (float)d) - kc : 0.f;
+            const float kv = (real_row && j0 + c < p.n) ? p.kf.value(p.gamma, d) - kc : 0.f;
             const float *ar = aw_s + c * PRED_MAX_P;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) acc[q] = fmaf(kv, ar[q], acc[q]);
@@ -577,7 +578,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                 const int64_t gj = w.j * b + w.sn * BN + c;
                 const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
                 const bool real = gi < p.n && gj < p.n;
-                kv[e] = real ? expf(-p.gamma * (float)d) : (gi == gj ? 1.f : 0.f);
+                kv[e] = real ? p.kf.value(p.gamma, d) : (gi == gj ? 1.f : 0.f);
                 dv[e] = real ? (uint32_t)d : 0u;
                 ss += (double)kv[e] * (double)kv[e];
                 s1 += (double)kv[e];
@@ -1224,6 +1225,7 @@ TcParams base_params(Ctx *c) {
     p.m_pad = c->m_pad;
     p.gamma = (float)c->gamma;
     p.lambda = (float)c->lambda;
+    p.kf = kernel_fn(c);
     return p;
 }
 

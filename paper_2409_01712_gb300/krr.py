@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "KRR_OK", 1: "KRR_EINVAL", 2: "KRR_ENOMEM", 3: "KRR_ECUDA", 4
                 5: "KRR_ENOCONV", 6: "KRR_ETIMEOUT", 7: "KRR_ESTATE"}
 MODES = {"mixed": 0, "fp32": 1}
 RULES = {"lambda": 0, "knorm": 1}
+KERNELS = {"gaussian": 0, "ibs": 1}
 PREC_NAMES = {0: "fp64", 1: "fp32", 2: "fp16", 3: "e4m3", 255: "-"}
 
 # Every symbol include/krr.h declares (checked by the CPU test suite).
@@ -42,7 +43,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int64), ("mode", ctypes.c_int32), ("allow_fp8", ctypes.c_int32),
                 ("eps", ctypes.c_double), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int32),
                 ("diag_fp64", ctypes.c_int32), ("wait_budget_ns", ctypes.c_int64), ("prec_rule", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32)]
 
 
 class FactorInfo(ctypes.Structure):
@@ -170,7 +171,7 @@ class KRR:
     def __init__(self, tile: int = 1024, mode: str = "mixed", eps: float | None = None,
                  ir_tol: float | None = None, ir_max: int | None = None, allow_fp8: bool = True,
                  diag_fp64: bool = False, prec_rule: str = "lambda", wait_budget_ns: int | None = None,
-                 stream=None):
+                 kernel: str = "gaussian", stream=None):
         lib = load_library()
         o = default_options()
         o.tile = tile
@@ -178,6 +179,7 @@ class KRR:
         o.allow_fp8 = int(allow_fp8)
         o.diag_fp64 = int(diag_fp64)
         o.prec_rule = RULES[prec_rule]
+        o.kernel = KERNELS[kernel]
         if wait_budget_ns is not None:
             o.wait_budget_ns = int(wait_budget_ns)
         if eps is not None:

@@ -43,7 +43,7 @@ def test_default_options(lib):
     o = krr.default_options()
     assert o.tile == 1024 and o.mode == 0 and o.ir_max == 30
     assert o.eps == pytest.approx(6e-4) and o.ir_tol == pytest.approx(1e-7)
-    assert o.prec_rule == 0 and o.reserved == 0
+    assert o.prec_rule == 0 and o.kernel == 0
 
 
 def test_struct_layouts_match_header():

@@ -95,8 +95,9 @@ def test_fit_predict_matches_oracle(mode, n, m, p, tile):
         assert sinfo["rel_residual"] <= 1e-5, sinfo
         assert err_yt <= 1e-4, (err_yt, err_a, sinfo)
         # forward error in A: at most cond(K + lambda I) times the residual
-        # (cond <= (0.5 n + lambda) / lambda, about 1e4 here); stated bound 1e-3
-        assert err_a <= 1e-3, (err_a, sinfo)
+        # (cond <= (0.5 n + lambda) / lambda, about 1e4 here); measured 2e-6 to
+        # 3e-6 on these cases, stated bound 1e-4
+        assert err_a <= 1e-4, (err_a, sinfo)
         assert finfo["tiles_fp32"] + finfo["tiles_fp16"] + finfo["tiles_e4m3"] == nt * (nt - 1) // 2
     else:
         assert err_yt <= 1e-3, (err_yt, err_a)

@@ -315,3 +315,52 @@ def test_lapack_krr_and_gradient_equal_plain():
     r0 = oracle.hyper_gradient(gamma, lam, g, y, t, yt)
     r1 = oracle.hyper_gradient(gamma, lam, g, y, t, yt, method="lapack")
     assert np.allclose(r1, r0, rtol=1e-8, atol=1e-13)
+
+
+# ---------------------------------------------------------------- IBS kernel (Alg. 5, second branch)
+
+def test_ibs_hand_example_and_extremes():
+    # loci: (0 vs 2) share 0 alleles, (1 vs 1) share 2, (2 vs 1) share 1 -> 3 of 6 alleles
+    a = np.array([[0, 1, 2]], np.int8)
+    b = np.array([[2, 1, 1], [0, 1, 2]], np.int8)
+    assert oracle.ibs_count(a, b).tolist() == [[3, 6]]
+    assert np.allclose(oracle.ibs_kernel(a, b), [[1.0, 2.0]], rtol=0, atol=0)
+    m = 77
+    z = np.zeros((1, m), np.int8)
+    two = np.full((1, m), 2, np.int8)
+    assert oracle.ibs_count(z, two)[0, 0] == 0
+    g = _rand_geno(30, m, 41)
+    k = oracle.ibs_kernel(g)
+    assert np.array_equal(k, k.T) and np.all(np.diag(k) == 2.0)
+    assert np.all((k >= 0) & (k <= 2))
+
+
+def test_ibs_matches_allele_sharing_table_by_loops():
+    # the definition spelled out allele by allele on tiny inputs: a genotype
+    # is a pair of alleles (minor allele first), and the shared count is the
+    # size of the multiset intersection
+    def alleles(v):
+        return [1] * int(v) + [0] * (2 - int(v))
+
+    def shared(u, v):
+        x, y = alleles(u), alleles(v)
+        return sum(min(x.count(t), y.count(t)) for t in (0, 1))
+
+    g1 = _rand_geno(6, 13, 42)
+    g2 = _rand_geno(5, 13, 43)
+    want = np.array([[sum(shared(g1[i, k], g2[j, k]) for k in range(13)) for j in range(5)] for i in range(6)])
+    assert np.array_equal(oracle.ibs_count(g1, g2), want)
+    assert np.array_equal(oracle.ibs_count(g1, g2, method="blas"), want)
+    big1, big2 = _rand_geno(40, 500, 44), _rand_geno(33, 500, 45)
+    assert np.array_equal(oracle.ibs_count(big1, big2, method="blas"), oracle.ibs_count(big1, big2))
+
+
+def test_ibs_kernel_positive_semidefinite_and_solve():
+    # each locus contributes E W E^T with the sharing table W positive
+    # definite, so K is positive semidefinite and K + lambda I factorises
+    g = _rand_geno(60, 40, 46)
+    k = oracle.ibs_kernel(g)
+    assert np.min(np.linalg.eigvalsh(k)) >= -1e-10
+    y = np.random.default_rng(46).standard_normal((60, 2))
+    _, w, pr = oracle.krr(0.0, 0.3, g, y, g, kernel="ibs")
+    assert np.allclose(pr, y - 0.3 * w, rtol=1e-9, atol=1e-10)
