@@ -83,10 +83,11 @@ def make_problem(cfg, n, m, p, n_test, seed, device="cpu"):
 
 
 PREC_CHARS = {0: "D", 1: "S", 2: "h", 3: "8", 255: " "}
+PREC_LEGEND = "D FP64, S FP32 (diagonal tiles: their factorisation precision), h FP16, 8 E4M3; row i = tiles (i, 0..i)"
 
 
 def heatmap_rows(pmap):
-    """The precision mosaic as text rows: D = FP64 diagonal, S = FP32 class,
+    """The precision mosaic as text rows: D = FP64, S = FP32 (FP32 class),
     h = FP16, 8 = E4M3 (row i lists tiles (i, 0..i))."""
     return ["".join(PREC_CHARS.get(int(v), "?") for v in pmap[i, : i + 1]) for i in range(pmap.shape[0])]
 
@@ -381,7 +382,7 @@ def run_ours(args):
             "phases": phases,
             "factor": {k: fi[k] for k in ("tiles_fp32", "tiles_fp16", "tiles_e4m3", "factor_bytes",
                                           "min_pivot")},
-            "precision_map": ({"legend": "D FP64/FP32 diagonal, S FP32 class, h FP16, 8 E4M3; row i = tiles (i, 0..i)",
+            "precision_map": ({"legend": PREC_LEGEND,
                                "rows": heatmap_rows(model.precision_map())} if fi["nt"] <= 32 else
                               {"note": f"{fi['nt']} x {fi['nt']} tiles: counts under factor"}),
             "solve": {"iterations": si["iterations"], "rel_residual": si["rel_residual"],

@@ -145,6 +145,24 @@ krr_status krr_build_kernel(krr_ctx *ctx, const int8_t *G, int64_t n, int64_t m,
                             double gamma);
 
 /*
+ * Build with confounders (Sec. IV-B, distance section: squared distances of
+ * the real-valued confounder columns -- age, sex, principal components, ...
+ * -- are accumulated in floating point and added to the integer genotype
+ * distances before the exponential of the Gaussian kernel):
+ *   K_ij = exp(-gamma (||g_i - g_j||^2 + ||c_i - c_j||^2)).
+ *   C  : n x nc FP32 confounders, leading dimension ldc >= nc, host or device;
+ *        0 <= nc <= 16 (nc = 0 is krr_build_kernel).
+ * The confounder distance is summed term by term in FP32 in the same
+ * epilogue that forms the genotype distance (no N x N buffer).  Predict on
+ * such a context needs the held-out rows' confounders: krr_predict_conf().
+ * Gaussian kernel only; krr_grad_hyper() and krr_predict_noalloc() reject
+ * a context with confounders.
+ * Errors: as krr_build_kernel, and KRR_EINVAL for a bad nc, ldc or kernel.
+ */
+krr_status krr_build_kernel_conf(krr_ctx *ctx, const int8_t *G, int64_t n, int64_t m, int64_t ldg,
+                                 const float *C, int64_t nc, int64_t ldc, double gamma);
+
+/*
  * Phase 2a (Alg. 3, Factorize): tile Cholesky L L^T = K + lambda I.
  * Diagonal tiles are factorised in FP32 or FP64 (options.diag_fp64); each
  * off-diagonal factor tile is stored in the lowest precision the adaptive
@@ -187,6 +205,16 @@ krr_status krr_solve(krr_ctx *ctx, const float *Y, int64_t p, int64_t ldy, float
  */
 krr_status krr_predict(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt, const float *A,
                        int64_t lda, int64_t p, float *Yt, int64_t ldyt);
+
+/*
+ * Predict (Alg. 4) on a kernel built with confounders: K_test from the
+ * held-out genotypes T and their confounders Ct (n_test x nc FP32, leading
+ * dimension ldct >= nc, host or device) against the training rows' genotypes
+ * and confounders.  Other arguments and errors as krr_predict(); KRR_EINVAL
+ * when the kernel has no confounders.
+ */
+krr_status krr_predict_conf(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt, const float *Ct,
+                            int64_t ldct, const float *A, int64_t lda, int64_t p, float *Yt, int64_t ldyt);
 
 /*
  * Copies the per-tile precision map of the current factor (the "mosaic" of

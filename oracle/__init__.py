@@ -91,6 +91,9 @@ def _load():
             lib.oracle_ibs_count.restype = None
             lib.oracle_ibs_count.argtypes = [_i8p, ctypes.c_int64, ctypes.c_int64, _i8p, ctypes.c_int64,
                                              ctypes.c_int64, ctypes.c_int64, _i64p]
+            lib.oracle_conf_sqdist.restype = None
+            lib.oracle_conf_sqdist.argtypes = [_f64p, ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_int64, _f64p]
             lib.oracle_kernel_rows.restype = None
             lib.oracle_kernel_rows.argtypes = [_i8p, ctypes.c_int64, _i64p, ctypes.c_int64, _i8p,
                                                ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
@@ -189,11 +192,30 @@ def ibs_kernel(g1, g2=None, method: str = "bruteforce") -> np.ndarray:
     return ibs_count(g1, g2, method=method).astype(np.float64) / float(m)
 
 
-def build_kernel(gamma: float, g1, g2=None, method: str = "bruteforce", kernel: str = "gaussian") -> np.ndarray:
+def conf_sqdist(c1, c2=None) -> np.ndarray:
+    """Squared distances of real confounder rows, term by term in double."""
+    a = np.ascontiguousarray(np.asarray(c1), dtype=np.float64)
+    b = a if c2 is None else np.ascontiguousarray(np.asarray(c2), dtype=np.float64)
+    if a.ndim != 2 or b.ndim != 2 or a.shape[1] != b.shape[1]:
+        raise ValueError("confounder matrices must be 2-D with the same number of columns")
+    out = np.empty((a.shape[0], b.shape[0]), dtype=np.float64)
+    _load().oracle_conf_sqdist(_ptr(a, _f64p), a.shape[0], a.shape[1], _ptr(b, _f64p), b.shape[0], b.shape[1],
+                               a.shape[1], _ptr(out, _f64p))
+    return out
+
+
+def build_kernel(gamma: float, g1, g2=None, method: str = "bruteforce", kernel: str = "gaussian",
+                 c1=None, c2=None) -> np.ndarray:
     """Alg. 2: ``K[i, j] = KernelMatrix(type, gamma, G1[i, :], G2[j, :])`` (type
-    ``"gaussian"`` or ``"ibs"``; gamma unused for IBS)."""
+    ``"gaussian"`` or ``"ibs"``; gamma unused for IBS).  With confounders
+    ``c1`` (and ``c2`` for the second set), their squared distances join the
+    genotype distances before the exponential:
+    ``K_ij = exp(-gamma (||g_i - g_j||^2 + ||c_i - c_j||^2))``."""
     if kernel == "ibs":
         return ibs_kernel(g1, g2, method="blas" if method in ("blas", "lapack") else "bruteforce")
+    if c1 is not None:
+        d = sqdist(g1, g2, method=method).astype(np.float64) + conf_sqdist(c1, c2 if g2 is not None else None)
+        return np.exp(-gamma * d)
     return gaussian_kernel(sqdist(g1, g2, method=method), gamma)
 
 
@@ -281,21 +303,23 @@ def associate(alpha: float, k: np.ndarray, y: np.ndarray, return_factor: bool = 
     return (w, l) if return_factor else w
 
 
-def predict(gamma: float, g, t, w: np.ndarray, method: str = "bruteforce", kernel: str = "gaussian") -> np.ndarray:
+def predict(gamma: float, g, t, w: np.ndarray, method: str = "bruteforce", kernel: str = "gaussian",
+            conf=None, conf_t=None) -> np.ndarray:
     """Alg. 4: ``K = Build(gamma, T, G)`` (N_P2 x N_P1), ``P_r = K W``."""
-    return matmul(build_kernel(gamma, t, g, method=_dist(method), kernel=kernel), w)
+    return matmul(build_kernel(gamma, t, g, method=_dist(method), kernel=kernel, c1=conf_t, c2=conf), w)
 
 
-def krr(gamma: float, alpha: float, g, y, t, method: str = "plain", kernel: str = "gaussian"):
+def krr(gamma: float, alpha: float, g, y, t, method: str = "plain", kernel: str = "gaussian", conf=None,
+        conf_t=None):
     """Alg. 1: Build, Associate, Predict.  Returns (K, W, P_r).
 
     ``method="lapack"``: Gram product and factorisation by library routines
     (see the module docstring); the same definitions otherwise.  ``kernel``:
     the Alg. 5 kernel type, ``"gaussian"`` or ``"ibs"``."""
     dm = "bruteforce" if method == "plain" else _dist(method)
-    k = build_kernel(gamma, g, method=dm, kernel=kernel)
+    k = build_kernel(gamma, g, method=dm, kernel=kernel, c1=conf)
     w = associate(alpha, k, y, method=method)
-    return k, w, predict(gamma, g, t, w, method=dm, kernel=kernel)
+    return k, w, predict(gamma, g, t, w, method=dm, kernel=kernel, conf=conf, conf_t=conf_t)
 
 
 def kernel_rows(gamma: float, g1, rows, g2) -> np.ndarray:

@@ -219,3 +219,26 @@ void oracle_ibs_count(const int8_t *g1, int64_t n1, int64_t ld1,
         }
     }
 }
+
+/*
+ * Squared Euclidean distances between real-valued confounder rows (age,
+ * sex, principal components, ...), term by term in double:
+ * dc_ij = sum_q (c1_iq - c2_jq)^2.  The paper adds these to the integer
+ * genotype distances before the exponential of the Gaussian kernel
+ * (Sec. IV-B, distance section).
+ */
+void oracle_conf_sqdist(const double *c1, int64_t n1, int64_t ld1,
+                        const double *c2, int64_t n2, int64_t ld2,
+                        int64_t nc, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n1; ++i) {
+        for (int64_t j = 0; j < n2; ++j) {
+            double s = 0.0;
+            for (int64_t q = 0; q < nc; ++q) {
+                double t = c1[i * ld1 + q] - c2[j * ld2 + q];
+                s += t * t;
+            }
+            out[i * n2 + j] = s;
+        }
+    }
+}

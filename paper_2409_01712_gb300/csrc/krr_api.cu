@@ -161,6 +161,21 @@ krr_status load_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, int6
     return check_launch(c, "copy rows");
 }
 
+// Confounders (n x nc, leading dimension ld, host or device) into the
+// context's dense n_pad x CONF_MAX layout with zero padding.
+krr_status load_conf(Ctx *c, const float *src, int64_t n, int64_t nc, int64_t ld, int64_t rows_pad, float *dst) {
+    const float *dsrc = src;
+    KRR_CUDA_TRY(c, cudaMemsetAsync(dst, 0, (size_t)rows_pad * CONF_MAX * sizeof(float), c->stream));
+    if (!is_device_ptr(src)) {
+        KRR_TRY(stage(c, (size_t)n * ld * sizeof(float)));
+        KRR_CUDA_TRY(c, cudaMemcpyAsync(c->stage, src, (size_t)n * ld * sizeof(float), cudaMemcpyHostToDevice,
+                                        c->stream));
+        dsrc = (const float *)c->stage;
+    }
+    launch_copy_rows(dsrc, ld, dst, CONF_MAX, n, nc, n, c->stream);
+    return check_launch(c, "copy confounders");
+}
+
 // Copies the first n rows of a dense device matrix to a caller matrix.
 krr_status store_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, float *dst,
                           int64_t ld) {
@@ -477,6 +492,8 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->g_scal);
     dev_free(&c->t8);
     dev_free(&c->tnorms);
+    dev_free(&c->conf);
+    dev_free(&c->tconf);
     if (c->stage) cudaFree(c->stage);
     tc_free(c);
     if (c->prof) {
@@ -508,9 +525,14 @@ krr_status krr_set_keep_distances(krr_ctx *c, int32_t keep) {
     return KRR_OK;
 }
 
-krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, int64_t ldg,
-                            double gamma) {
+static krr_status build_common(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, int64_t ldg, const float *C,
+                        int64_t nc, int64_t ldc, double gamma) {
     if (!c) return KRR_EINVAL;
+    if (nc < 0 || nc > CONF_MAX || (nc > 0 && (!C || ldc < nc || is_ibs(c)))) {
+        c->last_error = "krr_build_kernel_conf: need 0 <= nc <= 16, C != NULL and ldc >= nc when nc > 0, "
+                        "and the Gaussian kernel";
+        return KRR_EINVAL;
+    }
     if (!G || n < 1 || m < 1 || m > (int64_t(1) << (is_ibs(c) ? 21 : 22)) || ldg < m ||
         (!is_ibs(c) && (!(gamma > 0.0) || !isfinite(gamma)))) {
         c->last_error = "krr_build_kernel: need G != NULL, n >= 1, 1 <= m <= 2^22 (IBS: 2^21), ldg >= m, "
@@ -566,6 +588,16 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
     int pr = prof_begin(c, KRR_PROF_PACK);
     KRR_TRY(pack(c, G, n, m, ldg, n_pad, c->g8, c->gf, c->norms));
     prof_end(c, pr, 0.0, (double)n * m + (double)g_bytes);
+    c->nconf = 0;
+    if (nc > 0) {
+        const size_t cnt = (size_t)n_pad * CONF_MAX;
+        if (c->conf_cap < cnt) {
+            KRR_TRY(dev_alloc(c, &c->conf, cnt, "confounders"));
+            c->conf_cap = cnt;
+        }
+        KRR_TRY(load_conf(c, C, n, nc, ldc, n_pad, c->conf));
+        c->nconf = nc;
+    }
     pr = prof_begin(c, KRR_PROF_BUILD);
     if (mixed(c)) {
         KRR_TRY(tc_build(c));
@@ -581,6 +613,15 @@ krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, i
     KRR_TRY(check_launch(c, "kernel norm"));
     c->built = true;
     return KRR_OK;
+}
+
+krr_status krr_build_kernel(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, int64_t ldg, double gamma) {
+    return build_common(c, G, n, m, ldg, nullptr, 0, 0, gamma);
+}
+
+krr_status krr_build_kernel_conf(krr_ctx *c, const int8_t *G, int64_t n, int64_t m, int64_t ldg, const float *C,
+                                 int64_t nc, int64_t ldc, double gamma) {
+    return build_common(c, G, n, m, ldg, C, nc, ldc, gamma);
 }
 
 krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
@@ -720,8 +761,8 @@ krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *
     return st;
 }
 
-krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt, const float *A,
-                       int64_t lda, int64_t p, float *Yt, int64_t ldyt) {
+static krr_status predict_common(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt, const float *Ct, int64_t ldct,
+                          const float *A, int64_t lda, int64_t p, float *Yt, int64_t ldyt) {
     if (!c) return KRR_EINVAL;
     if (!c->built) {
         c->last_error = "krr_predict: no kernel built";
@@ -729,6 +770,12 @@ krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt,
     }
     if (!T || !A || !Yt || n_test < 1 || ldt < c->m || p < 1 || p > 256 || lda < p || ldyt < p) {
         c->last_error = "krr_predict: bad arguments (need 1 <= p <= 256, ldt >= m, lda, ldyt >= p)";
+        return KRR_EINVAL;
+    }
+    if ((c->nconf > 0) != (Ct != nullptr) || (Ct && ldct < c->nconf)) {
+        c->last_error = c->nconf > 0 ? "krr_predict: the kernel has confounders: use krr_predict_conf with the "
+                                       "held-out rows' confounders (ldct >= nc)"
+                                     : "krr_predict_conf: the kernel was built without confounders";
         return KRR_EINVAL;
     }
     const bool mx = mixed(c);
@@ -765,6 +812,16 @@ krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt,
                  mx ? nullptr : (float *)c->t8, c->tnorms));
     float *aw = c->dabuf;  // padded copy of the weights
     KRR_TRY(load_rows_f32(c, A, c->n, p, lda, c->n_pad, aw));
+    const float *tconf = nullptr;
+    if (c->nconf > 0) {
+        const size_t cnt = (size_t)rows_pad * CONF_MAX;
+        if (c->tconf_cap < cnt) {
+            KRR_TRY(dev_alloc(c, &c->tconf, cnt, "held-out confounders"));
+            c->tconf_cap = cnt;
+        }
+        KRR_TRY(load_conf(c, Ct, n_test, c->nconf, ldct, rows_pad, c->tconf));
+        tconf = c->tconf;
+    }
     float *out = c->pred_out;
     if (mx && c->colsum_cap < p) {
         KRR_TRY(dev_alloc(c, &c->colsum, (size_t)p, "column sums"));
@@ -775,21 +832,38 @@ krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt,
         // products of the shifted kernel K - c, then + c (1^T A) in FP64
         const double *shift = c->red + RED_KSHIFT;
         launch_colsum(aw, c->n_pad, p, c->colsum, c->stream);
-        // the tensor-core epilogue holds at most 32 weight columns: chunk p
-        for (int64_t q0 = 0; q0 < p; q0 += 32) {
-            const int64_t pc = std::min<int64_t>(32, p - q0);
-            KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows_pad, aw + q0, p, pc, c->pred_part, shift));
+        // the tensor-core epilogue holds at most 32 weight columns (16 with
+        // confounders, which take the other 16 slots of a staged row): chunk p
+        const int64_t chunk = c->nconf ? 16 : 32;
+        for (int64_t q0 = 0; q0 < p; q0 += chunk) {
+            const int64_t pc = std::min<int64_t>(chunk, p - q0);
+            KRR_TRY(tc_predict(c, c->t8, c->tnorms, n_test, rows_pad, aw + q0, p, pc, c->pred_part, shift, tconf));
             launch_predict_reduce(c->pred_part, nblk, rows_pad, n_test, pc, out + q0, p, c->stream, shift,
                                   c->colsum + q0);
         }
     } else {
         launch_predict_simt(c, (const float *)c->t8, c->tnorms, n_test, rows_pad, aw, p,
-                            c->pred_part);
+                            c->pred_part, tconf);
         launch_predict_reduce(c->pred_part, nblk, rows_pad, n_test, p, out, p, c->stream);
     }
     prof_end(c, pr, 2.0 * (double)n_test * c->n * encoded_width(c, c->m) + 2.0 * (double)n_test * c->n * p, 0.0);
     KRR_TRY(check_launch(c, "predict"));
     return store_rows_f32(c, out, n_test, p, Yt, ldyt);
+}
+
+krr_status krr_predict(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt, const float *A, int64_t lda,
+                       int64_t p, float *Yt, int64_t ldyt) {
+    return predict_common(c, T, n_test, ldt, nullptr, 0, A, lda, p, Yt, ldyt);
+}
+
+krr_status krr_predict_conf(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt, const float *Ct,
+                            int64_t ldct, const float *A, int64_t lda, int64_t p, float *Yt, int64_t ldyt) {
+    if (!c) return KRR_EINVAL;
+    if (!Ct) {
+        c->last_error = "krr_predict_conf: Ct is NULL";
+        return KRR_EINVAL;
+    }
+    return predict_common(c, T, n_test, ldt, Ct, ldct, A, lda, p, Yt, ldyt);
 }
 
 krr_status krr_get_precision_map(krr_ctx *c, uint8_t *map, int64_t cap, int64_t *nt) {
@@ -939,8 +1013,9 @@ extern "C" krr_status krr_grad_hyper(krr_ctx *c, const int8_t *T, int64_t n_test
         c->last_error = "krr_grad_hyper: no factorisation";
         return KRR_ESTATE;
     }
-    if (!mixed(c) || !c->tc || is_ibs(c)) {
-        c->last_error = "krr_grad_hyper: needs a context in KRR_MODE_MIXED with the Gaussian kernel";
+    if (!mixed(c) || !c->tc || is_ibs(c) || c->nconf > 0) {
+        c->last_error = "krr_grad_hyper: needs a context in KRR_MODE_MIXED with the Gaussian kernel and no "
+                        "confounders";
         return KRR_EINVAL;
     }
     if (!T || !Yt || !A || !out || n_test < 1 || ldt < c->m || p < 1 || p > 16 || ldy < p || lda < p) {

@@ -36,13 +36,33 @@ __host__ __device__ inline void tri_decode(int64_t t, int64_t *i, int64_t *j) {
 // encoded rows: Gaussian exp(-gamma d) on the squared Euclidean distance, or
 // IBS (2M - d) / M on the L1 distance (the encoded rows' squared distance),
 // one correctly rounded division of exact integers.
+// dc: the squared distance of the two rows' confounders (FP32; 0 without
+// confounders), added to the exact genotype distance before the exponential.
 struct KernelFn {
     int ibs;
     float two_m, m;
-    __device__ __forceinline__ float value(float gamma, int32_t d) const {
-        return ibs ? __fdiv_rn(two_m - (float)d, m) : expf(-gamma * (float)d);
+    __device__ __forceinline__ float value(float gamma, int32_t d, float dc = 0.f) const {
+        return ibs ? __fdiv_rn(two_m - (float)d, m) : expf(-gamma * ((float)d + dc));
     }
 };
+
+// Confounders (real-valued covariates) per row: at most CONF_MAX, stored
+// n_pad x CONF_MAX FP32 with zero padding.
+constexpr int CONF_MAX = 16;
+
+// Squared distance of two confounder rows, term by term in FP32 (no
+// cancellation): ci in registers, cj in memory, nc <= CONF_MAX.
+__device__ __forceinline__ float conf_dist(const float (&ci)[CONF_MAX], const float *cj, int nc) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < CONF_MAX; ++q) {
+        if (q < nc) {
+            const float t = ci[q] - cj[q];
+            s = fmaf(t, t, s);
+        }
+    }
+    return s;
+}
 
 // Slots of the small FP64 reduction buffer Ctx::red.
 constexpr int RED_RNORM = 0;     // [0] ||R||_F^2, [1] ||Y||_F^2 of the last residual
@@ -145,6 +165,11 @@ struct Ctx {
     float *g_yt = nullptr, *g_gp = nullptr, *g_aw = nullptr, *g_part = nullptr;
     double *g_sq = nullptr, *g_tpart = nullptr, *g_kpart = nullptr, *g_scal = nullptr;
     size_t g_rows_cap = 0, g_aw_cap = 0, g_part_cap = 0, g_tpart_cap = 0, g_kpart_cap = 0;
+    // confounders of the training rows (krr_build_kernel_conf), n_pad x
+    // CONF_MAX, and of the held-out rows of the current predict
+    float *conf = nullptr, *tconf = nullptr;
+    size_t conf_cap = 0, tconf_cap = 0;
+    int64_t nconf = 0;
     uint8_t *t8 = nullptr;                   // packed test genotypes (E4M3 / FP32 bytes)
     size_t t_cap = 0;
     int32_t *tnorms = nullptr;
@@ -246,7 +271,8 @@ void launch_trsm_simt(Ctx *c, int64_t k);
 // number of packed test rows (a multiple of 128); part is
 // (n_pad / 128) x rows_pad x p.
 void launch_predict_simt(Ctx *c, const float *tf, const int32_t *tn, int64_t n_test,
-                         int64_t rows_pad, const float *A, int64_t p, float *part);
+                         int64_t rows_pad, const float *A, int64_t p, float *part,
+                         const float *tconf = nullptr);
 
 // Diagonal-step dataflow kernel (diag.cu): FP32 factor of tile W, inverse X,
 // its transpose XT and FP16 split hi/lo (optional); ctr holds
@@ -329,9 +355,10 @@ krr_status tc_update(Ctx *c, int64_t k);     // trailing update of step k
 // dimension lda): part is (n_pad / 128) x rows_pad x p.
 // With kshift the partials are of (K - c) A, c = *kshift (the reduction adds
 // c (1^T A) back).
+// With confounders (c->nconf > 0) tconf holds the held-out rows' and p <= 16.
 krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
                       int64_t rows_pad, const float *A, int64_t lda, int64_t p, float *part,
-                      const double *kshift = nullptr);
+                      const double *kshift = nullptr, const float *tconf = nullptr);
 // B = K_test^T G_p (roles swapped): part is (2 * test_rows256 / 256) x n_pad x p.
 krr_status tc_predict_t(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
                         int64_t test_rows256, const float *gp, int64_t ldgp, int64_t p, float *part);

@@ -315,8 +315,8 @@ template void launch_gemm_simt<double>(int, int, int, double, const double *, in
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) build_simt_kernel(const float *gf, const int32_t *norms,
                                                          int64_t m_pad, int64_t n, int64_t b,
-                                                         float gamma, KernelFn kf, float *Kd, uint32_t *Dd,
-                                                         double *knorm_part) {
+                                                         float gamma, KernelFn kf, const float *conf, int nc,
+                                                         float *Kd, uint32_t *Dd, double *knorm_part) {
     const int64_t sub_side = b / SG_BM, sub_per_tile = sub_side * sub_side;
     const int64_t t = blockIdx.x / sub_per_tile, sub = blockIdx.x % sub_per_tile;
     int64_t ti, tj;
@@ -333,12 +333,16 @@ __global__ void __launch_bounds__(256) build_simt_kernel(const float *gf, const 
     for (int i = 0; i < 8; ++i) {
         const int64_t lr = sm * SG_BM + sg_row(i), gi = ti * b + lr;
         const int32_t ni = norms[gi];
+        float ci[CONF_MAX];
+#pragma unroll
+        for (int q = 0; q < CONF_MAX; ++q) ci[q] = (q < nc) ? conf[gi * CONF_MAX + q] : 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int64_t lc = sn * SG_BN + sg_col(j), gj = tj * b + lc;
             int32_t d = ni + norms[gj] - 2 * (int32_t)acc[i][j];
+            const float dc = nc ? conf_dist(ci, conf + gj * CONF_MAX, nc) : 0.f;
             float kv;
-            if (gi < n && gj < n) kv = kf.value(gamma, d);
+            if (gi < n && gj < n) kv = kf.value(gamma, d, dc);
             else kv = (gi == gj) ? 1.0f : 0.0f;
             kt[lr * b + lc] = kv;
             if (dt) dt[lr * b + lc] = (gi < n && gj < n) ? (uint32_t)d : 0u;
@@ -371,7 +375,8 @@ void launch_build_simt(Ctx *c) {
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     const int64_t sub = (c->b / SG_BM) * (c->b / SG_BM);
     count_launch(), build_simt_kernel<<<(unsigned)(ntri * sub), 256, 0, c->stream>>>(
-        c->gf, c->norms, c->m_pad, c->n, c->b, (float)c->gamma, kernel_fn(c), c->Kd, c->Dd, c->knorm2);
+        c->gf, c->norms, c->m_pad, c->n, c->b, (float)c->gamma, kernel_fn(c), c->conf, (int)c->nconf, c->Kd, c->Dd,
+        c->knorm2);
 }
 
 // Deterministic sums of the per-block partials: out[0] = ||K||_F^2 and
@@ -510,7 +515,8 @@ __global__ void __launch_bounds__(256) predict_simt_kernel(const float *tf, cons
                                                            int64_t n_test, const float *gf,
                                                            const int32_t *gn, int64_t n,
                                                            int64_t m_pad, int64_t ncolblk,
-                                                           float gamma, KernelFn kf, const float *A, int64_t p,
+                                                           float gamma, KernelFn kf, const float *tconf,
+                                                           const float *gconf, int nc, const float *A, int64_t p,
                                                            int64_t ntest_pad, float *part) {
     extern __shared__ float sh[];
     float *Ks = sh;                    // 128 x 129
@@ -524,11 +530,15 @@ __global__ void __launch_bounds__(256) predict_simt_kernel(const float *tf, cons
     for (int i = 0; i < 8; ++i) {
         const int64_t gi = r0 + sg_row(i);
         const int32_t ni = tn[gi];
+        float ci[CONF_MAX];
+#pragma unroll
+        for (int q = 0; q < CONF_MAX; ++q) ci[q] = (q < nc) ? tconf[gi * CONF_MAX + q] : 0.f;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int64_t gj = c0 + sg_col(j);
             int32_t d = ni + gn[gj] - 2 * (int32_t)acc[i][j];
-            Ks[sg_row(i) * 129 + sg_col(j)] = (gi < n_test && gj < n) ? kf.value(gamma, d) : 0.f;
+            const float dc = nc ? conf_dist(ci, gconf + gj * CONF_MAX, nc) : 0.f;
+            Ks[sg_row(i) * 129 + sg_col(j)] = (gi < n_test && gj < n) ? kf.value(gamma, d, dc) : 0.f;
         }
     }
     for (int64_t e = threadIdx.x; e < 128 * p; e += blockDim.x) {
@@ -545,13 +555,14 @@ __global__ void __launch_bounds__(256) predict_simt_kernel(const float *tf, cons
 }
 
 void launch_predict_simt(Ctx *c, const float *tf, const int32_t *tn, int64_t n_test,
-                         int64_t rows_pad, const float *A, int64_t p, float *part) {
+                         int64_t rows_pad, const float *A, int64_t p, float *part, const float *tconf) {
     const int64_t nrb = rows_pad / SG_BM, ncb = c->n_pad / SG_BN;
     size_t sh = (128 * 129 + 128 * p) * sizeof(float);
     if (sh > 48 * 1024)
         cudaFuncSetAttribute(predict_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
     count_launch(), predict_simt_kernel<<<(unsigned)(nrb * ncb), 256, sh, c->stream>>>(
-        tf, tn, n_test, c->gf, c->norms, c->n, c->m_pad, ncb, (float)c->gamma, kernel_fn(c), A, p, rows_pad, part);
+        tf, tn, n_test, c->gf, c->norms, c->n, c->m_pad, ncb, (float)c->gamma, kernel_fn(c), tconf, c->conf,
+        (int)c->nconf, A, p, rows_pad, part);
 }
 
 // Sum of partial products over column blocks in a fixed order; with a shift

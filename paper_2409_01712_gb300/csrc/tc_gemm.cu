@@ -106,6 +106,10 @@ struct TcParams {
     double *gpart;     // OP_GRADT / OP_GRADK: one partial sum per block
     const double *kshift;  // OP_PREDICT: shift c subtracted from every K entry (nullptr: none)
     KernelFn kf;           // OP_DIST / OP_PREDICT: kernel function of the distance
+    // OP_DIST / OP_PREDICT: confounders of the A rows and the B rows
+    // (rows x CONF_MAX), nconf of them (0: none)
+    const float *conf_a, *conf_b;
+    int nconf;
     uint64_t wait_ns;
     DevErrors *err;
 };
@@ -488,6 +492,10 @@ __device__ __forceinline__ void predict_half(const TcParams &p, uint32_t tacc, i
                                              const int32_t *nb_s, const float *aw_s, float kc, float *dst) {
     const int32_t ni = p.norms_a[gi];
     const bool real_row = gi < p.n_test;
+    const int nc = p.nconf;
+    float ci[CONF_MAX];
+#pragma unroll
+    for (int q = 0; q < CONF_MAX; ++q) ci[q] = (q < nc) ? p.conf_a[gi * CONF_MAX + q] : 0.f;
     float acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.f;
@@ -498,8 +506,10 @@ __device__ __forceinline__ void predict_half(const TcParams &p, uint32_t tacc, i
         for (int e = 0; e < 16; ++e) {
             const int c = ch * 16 + e;
             const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
-            const float kv = (real_row && j0 + c < p.n) ? p.kf.value(p.gamma, d) - kc : 0.f;
             const float *ar = aw_s + c * PRED_MAX_P;
+            // confounders of the training row: slots [16, 32) of its staged row (p <= 16 then)
+            const float dc = nc ? conf_dist(ci, ar + 16, nc) : 0.f;
+            const float kv = (real_row && j0 + c < p.n) ? p.kf.value(p.gamma, d, dc) - kc : 0.f;
 #pragma unroll
             for (int q = 0; q < NQ; ++q) acc[q] = fmaf(kv, ar[q], acc[q]);
         }
@@ -563,6 +573,10 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
     if (OP == OP_DIST) {
         const int64_t gi = w.i * b + w.sm * BM + row;
         const int32_t ni = p.norms_a[gi];
+        const int nc = p.nconf;
+        float ci[CONF_MAX];
+#pragma unroll
+        for (int q = 0; q < CONF_MAX; ++q) ci[q] = (q < nc) ? p.conf_a[gi * CONF_MAX + q] : 0.f;
         const int64_t tidx = tri_index(w.i, w.j);
         float *krow = p.Kd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN;
         uint32_t *drow = p.Dd ? p.Dd + tidx * b * b + (w.sm * BM + row) * b + w.sn * BN : nullptr;
@@ -578,7 +592,9 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                 const int64_t gj = w.j * b + w.sn * BN + c;
                 const int32_t d = ni + nb_s[c] - 2 * (int32_t)v[e];
                 const bool real = gi < p.n && gj < p.n;
-                kv[e] = real ? p.kf.value(p.gamma, d) : (gi == gj ? 1.f : 0.f);
+                // confounders of column c: slots [16, 32) of its staged row
+                const float dc = nc ? conf_dist(ci, aw_s + c * PRED_MAX_P + 16, nc) : 0.f;
+                kv[e] = real ? p.kf.value(p.gamma, d, dc) : (gi == gj ? 1.f : 0.f);
                 dv[e] = real ? (uint32_t)d : 0u;
                 ss += (double)kv[e] * (double)kv[e];
                 s1 += (double)kv[e];
@@ -773,7 +789,14 @@ template <int OP>
 __device__ __forceinline__ void epilogue_stage(const TcParams &p, const Work &w, int row,
                                                int32_t *nb_s, float *aw_s) {
     if (OP == OP_DIST) {
-        for (int c = row; c < BN; c += EPI_THREADS) nb_s[c] = p.norms_b[w.j * p.b + w.sn * BN + c];
+        const int64_t j0 = w.j * p.b + w.sn * BN;
+        for (int c = row; c < BN; c += EPI_THREADS) nb_s[c] = p.norms_b[j0 + c];
+        if (p.nconf) {  // confounders of the block's columns: slots [16, 32) of each staged row
+            for (int e = row; e < BN * CONF_MAX; e += EPI_THREADS) {
+                const int c = e / CONF_MAX, q = e % CONF_MAX;
+                aw_s[c * PRED_MAX_P + 16 + q] = p.conf_b[(j0 + c) * CONF_MAX + q];
+            }
+        }
     } else if (OP == OP_GRADK) {
         // columns j of the block: norms, A_j in slots [0, 16), Z_j in [16, 32)
         const int64_t j0 = w.j * p.b + w.sn * BN;
@@ -800,6 +823,8 @@ __device__ __forceinline__ void epilogue_stage(const TcParams &p, const Work &w,
         for (int k = 0; k < PER; ++k) {
             const int c = row / PRED_MAX_P + k * (EPI_THREADS / PRED_MAX_P);
             v[k] = (q < p.p) ? __ldg(p.aw + (w.j * BN + c) * p.ldaw + q) : 0.f;
+            // with confounders (p <= 16) slots [16, 32) hold the training row's confounders
+            if (OP == OP_PREDICT && p.nconf && q >= 16) v[k] = __ldg(p.conf_b + (w.j * BN + c) * CONF_MAX + (q - 16));
         }
 #pragma unroll
         for (int k = 0; k < PER; ++k) aw_s[row + k * EPI_THREADS] = v[k];
@@ -1285,6 +1310,8 @@ krr_status tc_build(Ctx *c) {
     p.Kd = c->Kd;
     p.Dd = c->Dd;
     p.knorm_part = c->knorm2;
+    p.conf_a = p.conf_b = c->conf;
+    p.nconf = (int)c->nconf;
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     p.items = ntri * (c->b / BM) * (c->b / BN);
     return launch<KIND_F8, OP_DIST>(c, st->g_map, st->g_map, st->g_map, st->g_map, p);
@@ -1397,10 +1424,10 @@ krr_status tc_grad_terms(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n
 
 krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_test,
                       int64_t rows_pad, const float *A, int64_t lda, int64_t p_cols, float *part,
-                      const double *kshift) {
+                      const double *kshift, const float *tconf) {
     TcState *st = (TcState *)c->tc;
-    if (p_cols < 1 || p_cols > PRED_MAX_P) {
-        c->last_error = "tc_predict: at most 32 weight columns per launch";
+    if (p_cols < 1 || p_cols > (c->nconf ? 16 : PRED_MAX_P) || (c->nconf && !tconf)) {
+        c->last_error = "tc_predict: at most 32 weight columns per launch (16 with confounders)";
         return KRR_EINVAL;
     }
     CUtensorMap t_map;
@@ -1416,6 +1443,9 @@ krr_status tc_predict(Ctx *c, const uint8_t *t8, const int32_t *tn, int64_t n_te
     p.p = p_cols;
     p.part = part;
     p.kshift = kshift;
+    p.conf_a = tconf;
+    p.conf_b = c->conf;
+    p.nconf = (int)c->nconf;
     p.items = (rows_pad / BM) * (c->n_pad / BN);
     return launch<KIND_F8, OP_PREDICT>(c, t_map, t_map, st->g_map, st->g_map, p);
 }

@@ -134,3 +134,11 @@ def structured_problem(n: int, m: int, n_pheno: int, n_test: int, seed: int, pop
     y_all = phenotypes(g_all, n_pheno, seed)
     return {"G": g_all[:n].contiguous(), "Y": y_all[:n].contiguous(),
             "T": g_all[n:].contiguous(), "Yt": y_all[n:].contiguous(), "pop": pop, "pop_test": pop_t}
+
+
+def confounders(n: int, nc: int, seed: int, scale: float = 1.0) -> torch.Tensor:
+    """n x nc FP32 real-valued covariates (stand-ins for age, sex, ancestry
+    principal components): independent N(0, scale^2) draws from a CPU
+    generator seeded with ``seed + 4``."""
+    g = torch.Generator().manual_seed(int(seed) + 4)
+    return (torch.randn((n, nc), generator=g, dtype=torch.float64) * scale).to(torch.float32)

@@ -32,7 +32,7 @@ PREC_NAMES = {0: "fp64", 1: "fp32", 2: "fp16", 3: "e4m3", 255: "-"}
 
 # Every symbol include/krr.h declares (checked by the CPU test suite).
 EXPORTED = ["krr_default_options", "krr_create", "krr_build_kernel", "krr_factor", "krr_solve",
-            "krr_predict", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
+            "krr_predict", "krr_build_kernel_conf", "krr_predict_conf", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
             "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_sync", "krr_last_error",
             "krr_destroy", "krr_batch_create", "krr_batch_run", "krr_batch_last_error", "krr_batch_destroy"]
@@ -101,6 +101,8 @@ def load_library(path: str = LIB_PATH):
     lib.krr_factor.argtypes = [vp, dbl, ctypes.POINTER(FactorInfo)]
     lib.krr_solve.argtypes = [vp, vp, i64, i64, vp, i64, ctypes.POINTER(SolveInfo)]
     lib.krr_predict.argtypes = [vp, vp, i64, i64, vp, i64, i64, vp, i64]
+    lib.krr_build_kernel_conf.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64, dbl]
+    lib.krr_predict_conf.argtypes = [vp, vp, i64, i64, vp, i64, vp, i64, i64, vp, i64]
     lib.krr_get_precision_map.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     lib.krr_set_keep_distances.argtypes = [vp, i32]
     lib.krr_get_distances.argtypes = [vp, vp, i64]
@@ -125,6 +127,7 @@ def load_library(path: str = LIB_PATH):
     lib.krr_destroy.argtypes = [vp]
     lib.krr_destroy.restype = None
     for name in ("krr_create", "krr_build_kernel", "krr_factor", "krr_solve", "krr_predict",
+                 "krr_build_kernel_conf", "krr_predict_conf",
                  "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
                  "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_sync"):
@@ -221,10 +224,17 @@ class KRR:
             pass
 
     # -- Alg. 2 ---------------------------------------------------------------
-    def build_kernel(self, g, gamma: float, keep_distances: bool = False):
+    def build_kernel(self, g, gamma: float, keep_distances: bool = False, conf=None):
+        """Alg. 2; ``conf``: n x nc FP32 confounders whose squared distances join
+        the genotype distances before the exponential (nc <= 16)."""
         n, m = g.shape
         self._check(self._lib.krr_set_keep_distances(self._ctx, int(keep_distances)))
-        self._check(self._lib.krr_build_kernel(self._ctx, ctypes.c_void_p(_ptr(g)), n, m, _ld(g), gamma))
+        if conf is None:
+            self._check(self._lib.krr_build_kernel(self._ctx, ctypes.c_void_p(_ptr(g)), n, m, _ld(g), gamma))
+        else:
+            self._check(self._lib.krr_build_kernel_conf(self._ctx, ctypes.c_void_p(_ptr(g)), n, m, _ld(g),
+                                                        ctypes.c_void_p(_ptr(conf)), conf.shape[1], _ld(conf),
+                                                        gamma))
         self.n, self.m = n, m
 
     # -- Alg. 3 ---------------------------------------------------------------
@@ -247,12 +257,19 @@ class KRR:
         return a, d
 
     # -- Alg. 4 ---------------------------------------------------------------
-    def predict(self, t, a, out=None):
+    def predict(self, t, a, out=None, conf=None):
+        """Alg. 4; ``conf``: the held-out rows' confounders (kernels built with them)."""
         nt_, p = t.shape[0], a.shape[1]
         yt = _empty_like_rows(a, nt_, p) if out is None else out
-        self._check(self._lib.krr_predict(self._ctx, ctypes.c_void_p(_ptr(t)), nt_, _ld(t),
-                                          ctypes.c_void_p(_ptr(a)), _ld(a), p, ctypes.c_void_p(_ptr(yt)),
-                                          _ld(yt)))
+        if conf is None:
+            self._check(self._lib.krr_predict(self._ctx, ctypes.c_void_p(_ptr(t)), nt_, _ld(t),
+                                              ctypes.c_void_p(_ptr(a)), _ld(a), p, ctypes.c_void_p(_ptr(yt)),
+                                              _ld(yt)))
+        else:
+            self._check(self._lib.krr_predict_conf(self._ctx, ctypes.c_void_p(_ptr(t)), nt_, _ld(t),
+                                                   ctypes.c_void_p(_ptr(conf)), _ld(conf),
+                                                   ctypes.c_void_p(_ptr(a)), _ld(a), p, ctypes.c_void_p(_ptr(yt)),
+                                                   _ld(yt)))
         return yt
 
     # -- hyperparameter gradient (adjoint reusing the factor) ----------------

@@ -89,10 +89,10 @@ def test_c3_subproblem_matches_fp64_oracle():
 
     Gates: squared distances bit-exact on a sample of tiles; the predictions
     ||Yt - Yt*||_F / ||Yt*||_F <= 1e-4 (the end-to-end target).  Reported and
-    gated loosely: ||A - A*||_F / ||A*||_F <= 1e-3 (the forward error in A
-    grows with the condition number of K + lambda I, up to ||K|| / lambda,
-    about 8e4 here), and the FP64 relative residual of the GPU's A
-    ||Y - (K + lambda I) A||_F / ||Y||_F <= 2e-5.
+    gated: ||A - A*||_F / ||A*||_F <= 1e-4 (the forward error in A grows with
+    the condition number of K + lambda I, up to ||K|| / lambda, about 8e4
+    here; measured 4.8e-6), and the FP64 relative residual of the GPU's A
+    ||Y - (K + lambda I) A||_F / ||Y||_F <= 2e-5 (measured 3.7e-6).
     """
     gamma = 1.0 / M
     prob = inputs.problem(N, M, P, N_TEST, seed=SEED, device=DEV)
@@ -128,4 +128,4 @@ def test_c3_subproblem_matches_fp64_oracle():
     assert sinfo["converged"] in (1, 2), sinfo
     assert err_yt <= 1e-4, err_yt
     assert rel_res <= 2e-5, rel_res
-    assert err_a <= 1e-3, err_a
+    assert err_a <= 1e-4, err_a

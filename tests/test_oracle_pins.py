@@ -364,3 +364,29 @@ def test_ibs_kernel_positive_semidefinite_and_solve():
     y = np.random.default_rng(46).standard_normal((60, 2))
     _, w, pr = oracle.krr(0.0, 0.3, g, y, g, kernel="ibs")
     assert np.allclose(pr, y - 0.3 * w, rtol=1e-9, atol=1e-10)
+
+
+# ---------------------------------------------------------------- confounders (Sec. IV-B, distance section)
+
+def test_confounder_distances_by_hand_and_identity():
+    c1 = np.array([[1.0, -2.0, 0.5]])
+    c2 = np.array([[0.0, 1.0, 0.5], [1.0, -2.0, 0.5]])
+    assert np.allclose(oracle.conf_sqdist(c1, c2), [[1.0 + 9.0, 0.0]], rtol=0, atol=0)
+    rng = np.random.default_rng(51)
+    a, b = rng.standard_normal((20, 7)), rng.standard_normal((11, 7))
+    gram = (a * a).sum(1)[:, None] + (b * b).sum(1)[None, :] - 2 * a @ b.T
+    assert np.allclose(oracle.conf_sqdist(a, b), gram, rtol=1e-12, atol=1e-12)
+    # a common shift of every row leaves the distances unchanged
+    assert np.allclose(oracle.conf_sqdist(a + 3.0, b + 3.0), oracle.conf_sqdist(a, b), rtol=1e-12, atol=1e-12)
+
+
+def test_kernel_with_confounders_adds_before_exponential():
+    g = _rand_geno(25, 30, 52)
+    c = np.random.default_rng(52).standard_normal((25, 4))
+    gamma = 1 / 30
+    k0 = oracle.build_kernel(gamma, g)
+    kc = oracle.build_kernel(gamma, g, c1=c)
+    # exp(-gamma (d + dc)) = exp(-gamma d) exp(-gamma dc)
+    assert np.allclose(kc, k0 * np.exp(-gamma * oracle.conf_sqdist(c)), rtol=1e-13, atol=0)
+    assert np.allclose(oracle.build_kernel(gamma, g, c1=np.zeros((25, 4))), k0, rtol=4e-16, atol=0)
+    assert np.all(np.diag(kc) == 1.0)
