@@ -217,6 +217,39 @@ krr_status krr_predict_conf(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64
                             int64_t ldct, const float *A, int64_t lda, int64_t p, float *Yt, int64_t ldyt);
 
 /*
+ * Ridge regression (Sec. IV-A, Eq. 2): beta = (X^T X + lambda I)^-1 X^T Y with
+ * X = [G C], G the n x m genotypes and C the n x nc real confounders of the
+ * training patients.  Three calls around the same factor and solve:
+ *   1. krr_rr_build: the context's matrix becomes the Gram matrix X^T X of
+ *      order m + nc (genotype columns first), by the paper's mixed-precision
+ *      SYRK: G^T G on the tensor cores from exact E4M3 operands with FP32
+ *      accumulation (entries below 4n, so exact: n <= 2^22), the columns with
+ *      confounders in FP32 products summed in FP64;
+ *   2. krr_rr_rhs: B = X^T Y (m + nc rows, p columns), FP32 products summed in
+ *      FP64 over patient chunks;
+ *   3. krr_factor(ctx, lambda, ...) and krr_solve(ctx, B, ...) -> beta, the
+ *      same adaptive-precision Cholesky, substitution and refinement as KRR;
+ *   4. krr_rr_predict: Yt = T beta_g + Ct beta_c for held-out patients.
+ *   X  : n x m int8 genotypes {0, 1, 2}, leading dimension ldx >= m, host or
+ *        device; C: n x nc FP32 (ldc >= nc), 0 <= nc <= 16 (C may be NULL
+ *        when nc = 0).
+ *   Y  : n x p FP32 phenotypes (ldy >= p); B: (m + nc) x p FP32 output
+ *        (ldb >= p); T: n_test x m int8 (ldt >= m); Ct: n_test x nc FP32
+ *        (ldct >= nc); beta: (m + nc) x p FP32 (ldbeta >= p); Yt: n_test x p
+ *        FP32 output (ldyt >= p).  Any of them host or device.
+ * krr_build_kernel / krr_build_kernel_conf replace the Gram matrix with a KRR
+ * kernel again; krr_predict, krr_predict_conf, krr_grad_hyper and
+ * krr_predict_noalloc reject a context that holds a Gram matrix.
+ * Errors: KRR_EINVAL (shapes), KRR_ESTATE (rhs / predict before build),
+ * KRR_ENOMEM, KRR_ECUDA.
+ */
+krr_status krr_rr_build(krr_ctx *ctx, const int8_t *X, int64_t n, int64_t m, int64_t ldx, const float *C,
+                        int64_t nc, int64_t ldc);
+krr_status krr_rr_rhs(krr_ctx *ctx, const float *Y, int64_t p, int64_t ldy, float *B, int64_t ldb);
+krr_status krr_rr_predict(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t ldt, const float *Ct,
+                          int64_t ldct, const float *beta, int64_t ldbeta, int64_t p, float *Yt, int64_t ldyt);
+
+/*
  * Copies the per-tile precision map of the current factor (the "mosaic" of
  * the paper's adaptive-precision Cholesky) to host memory: map[i * nt + j]
  * for tile row i >= tile column j holds a KRR_PREC_* value (diagonal tiles

@@ -379,3 +379,33 @@ def hyper_gradient(gamma: float, lam: float, g, y, t, y_t, method: str = "plain"
     ga = matmul(g_p, a.T)
     dgamma = float((d * k * za).sum()) - float((d_t * k_t * ga).sum())
     return loss, gamma * dgamma, dlog_lam
+
+
+def ridge_design(g, c=None) -> np.ndarray:
+    """X = [G C]: genotype columns, then the real confounder columns (double)."""
+    x = _geno(g).astype(np.float64)
+    if c is not None:
+        x = np.concatenate([x, np.asarray(c, dtype=np.float64).reshape(len(x), -1)], axis=1)
+    return x
+
+
+def ridge(lam: float, g, y, c=None, method: str = "plain"):
+    """Ridge regression (Sec. IV-A, Eq. 2): ``beta = (X^T X + lambda I)^-1 X^T Y``
+    with X = [G C].  The Gram matrix and X^T Y are plain double products
+    (``method="lapack"``: library products and factorisation); the system is
+    solved by the Cholesky factorisation and substitutions of Alg. 3.
+    Returns (X^T X, X^T Y, beta)."""
+    x = ridge_design(g, c)
+    yy = np.asarray(y, dtype=np.float64).reshape(len(x), -1)
+    xt = np.ascontiguousarray(x.T)
+    if method == "lapack":
+        gram, rhs = xt @ x, xt @ yy
+    else:
+        gram, rhs = matmul(xt, x), matmul(xt, yy)
+    beta = associate(lam, gram, rhs, method=method)
+    return gram, rhs, beta
+
+
+def ridge_predict(t, beta, ct=None) -> np.ndarray:
+    """Predictions ``[T Ct] beta`` of held-out patients."""
+    return matmul(ridge_design(t, ct), beta)

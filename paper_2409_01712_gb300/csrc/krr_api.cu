@@ -72,31 +72,7 @@ void prof_end(Ctx *c, int idx, double flops, double bytes) {
 
 }  // namespace
 
-namespace {
-
-template <typename T>
-krr_status dev_alloc(Ctx *c, T **p, size_t count, const char *what) {
-    if (*p) {
-        cudaFree(*p);
-        *p = nullptr;
-    }
-    if (count == 0) return KRR_OK;
-    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        c->last_error = std::string("cudaMalloc failed for ") + what + " (" +
-                        std::to_string(count * sizeof(T)) + " bytes): " + cudaGetErrorString(e);
-        return KRR_ENOMEM;
-    }
-    return KRR_OK;
-}
-
-template <typename T>
-void dev_free(T **p) {
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-}
+namespace krr {
 
 // Device address of page-locked host memory (the GPU reads it over the host
 // link, no staging copy), or nullptr for anything else.
@@ -254,7 +230,7 @@ void free_build(Ctx *c) {
 
 bool mixed(const Ctx *c) { return c->opt.mode == KRR_MODE_MIXED; }
 
-}  // namespace
+}  // namespace krr
 
 namespace {
 // Scratch of the residual-norm reduction: the last norm_partial_count()
@@ -378,6 +354,56 @@ krr_status solve_device(Ctx *c, int64_t p, krr_solve_info *info) {
 }
 }  // namespace
 
+namespace krr {
+// Buffers of a build over an n x n lower-triangle tile grid (tile edge from
+// the options) with packed operand rows of m_pad columns; sets the shape
+// fields of the context.
+krr_status prepare_build(Ctx *c, int64_t n, int64_t m_pad, int keep_d) {
+    const int64_t b = c->opt.tile;
+    const int64_t nt = (n + b - 1) / b;
+    if (nt != c->nt || b != c->b) free_factor(c);  // factor buffers depend on the tile grid
+    const int64_t n_pad = nt * b;
+    const size_t g_bytes = (size_t)n_pad * m_pad * (mixed(c) ? 1 : 4);
+    const int64_t ntri = nt * (nt + 1) / 2;
+    const size_t kd_bytes = (size_t)ntri * b * b * sizeof(float);
+    if (c->g_bytes != g_bytes || c->kd_bytes != kd_bytes || c->b != b || c->nt != nt) {
+        free_build(c);
+        if (mixed(c)) KRR_TRY(dev_alloc(c, &c->g8, g_bytes, "packed genotypes"));
+        else KRR_TRY(dev_alloc(c, &c->gf, g_bytes / 4, "FP32 genotypes"));
+        KRR_TRY(dev_alloc(c, &c->norms, (size_t)n_pad, "row norms"));
+        KRR_TRY(dev_alloc(c, &c->Kd, (size_t)ntri * b * b, "kernel tiles"));
+        // per-tile partial sums of K^2: one per 128 x 256 (tensor-core) or
+        // 128 x 128 (CUDA-core) block
+        const size_t per_tile = mixed(c) ? (size_t)(b / 128) * (b / 256) : (size_t)(b / 128) * (b / 128);
+        KRR_TRY(dev_alloc(c, &c->knorm2, (size_t)2 * ntri * per_tile, "tile norms"));
+        c->g_bytes = g_bytes;
+        c->kd_bytes = kd_bytes;
+    }
+    const size_t dd_bytes = keep_d ? (size_t)ntri * b * b * sizeof(uint32_t) : 0;
+    if (dd_bytes != c->dd_bytes) {
+        KRR_TRY(dev_alloc(c, &c->Dd, dd_bytes / sizeof(uint32_t), "distance tiles"));
+        c->dd_bytes = dd_bytes;
+    }
+    c->n = n;
+    c->m_pad = m_pad;
+    c->b = b;
+    c->nt = nt;
+    c->n_pad = n_pad;
+    const size_t red_count = RED_MINPIV + (size_t)nt * (b / 64) + (size_t)nt + 16 + (size_t)norm_partial_count();
+    if (c->red_cap < red_count) {
+        KRR_TRY(dev_alloc(c, &c->red, red_count, "reduction buffer"));
+        c->red_cap = red_count;
+    }
+    if (!c->hred && cudaMallocHost((void **)&c->hred, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->hred = nullptr;
+        c->last_error = "pinned allocation failed";
+        return KRR_ENOMEM;
+    }
+    return KRR_OK;
+}
+}  // namespace krr
+
 extern "C" {
 
 void krr_default_options(krr_options *opt) {
@@ -496,6 +522,7 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->tconf);
     if (c->stage) cudaFree(c->stage);
     tc_free(c);
+    rr_free(c);
     if (c->prof) {
         ProfState *ps = (ProfState *)c->prof;
         for (const ProfRec &r : ps->recs) {
@@ -541,50 +568,16 @@ static krr_status build_common(krr_ctx *c, const int8_t *G, int64_t n, int64_t m
     }
     c->built = false;
     c->factored = false;
+    c->rr = 0;
+    c->rr_m = c->rr_nc = 0;
     const int64_t b = c->opt.tile;
     const int64_t nt = (n + b - 1) / b;
-    if (nt != c->nt || b != c->b) free_factor(c);  // factor buffers depend on the tile grid
     const int64_t n_pad = nt * b;
     const int64_t m_pad = (encoded_width(c, m) + 127) / 128 * 128;
     const size_t g_bytes = (size_t)n_pad * m_pad * (mixed(c) ? 1 : 4);
-    const int64_t ntri = nt * (nt + 1) / 2;
-    const size_t kd_bytes = (size_t)ntri * b * b * sizeof(float);
-    if (c->g_bytes != g_bytes || c->kd_bytes != kd_bytes || c->b != b || c->nt != nt) {
-        free_build(c);
-        if (mixed(c)) KRR_TRY(dev_alloc(c, &c->g8, g_bytes, "packed genotypes"));
-        else KRR_TRY(dev_alloc(c, &c->gf, g_bytes / 4, "FP32 genotypes"));
-        KRR_TRY(dev_alloc(c, &c->norms, (size_t)n_pad, "row norms"));
-        KRR_TRY(dev_alloc(c, &c->Kd, (size_t)ntri * b * b, "kernel tiles"));
-        // per-tile partial sums of K^2: one per 128 x 256 (tensor-core) or
-        // 128 x 128 (CUDA-core) block
-        const size_t per_tile = mixed(c) ? (size_t)(b / 128) * (b / 256) : (size_t)(b / 128) * (b / 128);
-        KRR_TRY(dev_alloc(c, &c->knorm2, (size_t)2 * ntri * per_tile, "tile norms"));
-        c->g_bytes = g_bytes;
-        c->kd_bytes = kd_bytes;
-    }
-    const size_t dd_bytes = c->keep_distances ? (size_t)ntri * b * b * sizeof(uint32_t) : 0;
-    if (dd_bytes != c->dd_bytes) {
-        KRR_TRY(dev_alloc(c, &c->Dd, dd_bytes / sizeof(uint32_t), "distance tiles"));
-        c->dd_bytes = dd_bytes;
-    }
-    c->n = n;
     c->m = m;  // set before packing: the IBS encoding and kernel function read it
-    c->m_pad = m_pad;
-    c->b = b;
-    c->nt = nt;
-    c->n_pad = n_pad;
     c->gamma = gamma;
-    const size_t red_count = RED_MINPIV + (size_t)nt * (b / 64) + (size_t)nt + 16 + (size_t)norm_partial_count();
-    if (c->red_cap < red_count) {
-        KRR_TRY(dev_alloc(c, &c->red, red_count, "reduction buffer"));
-        c->red_cap = red_count;
-    }
-    if (!c->hred && cudaMallocHost((void **)&c->hred, 64 * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
-        c->hred = nullptr;
-        c->last_error = "pinned allocation failed";
-        return KRR_ENOMEM;
-    }
+    KRR_TRY(prepare_build(c, n, m_pad, c->keep_distances));
     int pr = prof_begin(c, KRR_PROF_PACK);
     KRR_TRY(pack(c, G, n, m, ldg, n_pad, c->g8, c->gf, c->norms));
     prof_end(c, pr, 0.0, (double)n * m + (double)g_bytes);
@@ -607,7 +600,8 @@ static krr_status build_common(krr_ctx *c, const int8_t *G, int64_t n, int64_t m
     // algorithmic work: 2 M multiply-adds per entry of the lower-triangle
     // tiles (2 x 2M for the IBS encoding); compulsory bytes: the K tiles
     // written once (FP32)
-    prof_end(c, pr, 2.0 * (double)ntri * b * b * (double)encoded_width(c, m), (double)kd_bytes);
+    const double ntri = (double)nt * (nt + 1) / 2;
+    prof_end(c, pr, 2.0 * ntri * b * b * (double)encoded_width(c, m), (double)c->kd_bytes);
     KRR_TRY(check_launch(c, "build"));
     launch_kernel_sumsq(c, c->red + RED_KNORM2);
     KRR_TRY(check_launch(c, "kernel norm"));
@@ -770,6 +764,10 @@ static krr_status predict_common(krr_ctx *c, const int8_t *T, int64_t n_test, in
     }
     if (!T || !A || !Yt || n_test < 1 || ldt < c->m || p < 1 || p > 256 || lda < p || ldyt < p) {
         c->last_error = "krr_predict: bad arguments (need 1 <= p <= 256, ldt >= m, lda, ldyt >= p)";
+        return KRR_EINVAL;
+    }
+    if (c->rr) {
+        c->last_error = "krr_predict: the context holds a ridge-regression Gram matrix: use krr_rr_predict";
         return KRR_EINVAL;
     }
     if ((c->nconf > 0) != (Ct != nullptr) || (Ct && ldct < c->nconf)) {
@@ -1013,7 +1011,7 @@ extern "C" krr_status krr_grad_hyper(krr_ctx *c, const int8_t *T, int64_t n_test
         c->last_error = "krr_grad_hyper: no factorisation";
         return KRR_ESTATE;
     }
-    if (!mixed(c) || !c->tc || is_ibs(c) || c->nconf > 0) {
+    if (!mixed(c) || !c->tc || is_ibs(c) || c->nconf > 0 || c->rr) {
         c->last_error = "krr_grad_hyper: needs a context in KRR_MODE_MIXED with the Gaussian kernel and no "
                         "confounders";
         return KRR_EINVAL;

@@ -38,8 +38,9 @@ __host__ __device__ inline void tri_decode(int64_t t, int64_t *i, int64_t *j) {
 // one correctly rounded division of exact integers.
 // dc: the squared distance of the two rows' confounders (FP32; 0 without
 // confounders), added to the exact genotype distance before the exponential.
+// gram = 1 (ridge regression): the kernel is the Gram product S itself.
 struct KernelFn {
-    int ibs;
+    int ibs, gram;
     float two_m, m;
     __device__ __forceinline__ float value(float gamma, int32_t d, float dc = 0.f) const {
         return ibs ? __fdiv_rn(two_m - (float)d, m) : expf(-gamma * ((float)d + dc));
@@ -184,6 +185,13 @@ struct Ctx {
     void *prof = nullptr;
     int prof_on = 0;
 
+    // ridge regression (ridge.cu): the context's matrix is the Gram matrix
+    // X^T X of order n = rr_m genotype columns + rr_nc confounder columns;
+    // m is then the number of patients (the contraction length)
+    int rr = 0;
+    int64_t rr_m = 0, rr_nc = 0;
+    void *rr_state = nullptr;
+
     // graph mode: no host synchronisation or readback inside build / factor /
     // solve / predict, fixed refinement count (used by the batch runner)
     int graph_mode = 0;
@@ -194,10 +202,18 @@ inline bool is_ibs(const Ctx *c) { return c->opt.kernel == KRR_KERNEL_IBS; }
 inline KernelFn kernel_fn(const Ctx *c) {
     KernelFn f;
     f.ibs = is_ibs(c) ? 1 : 0;
+    f.gram = c->rr;
     f.two_m = (float)(2 * c->m);
     f.m = (float)c->m;
     return f;
 }
+// Rows whose kernel entries are real (the rest is padding with K = I): the
+// training rows, or the genotype columns of a ridge-regression Gram matrix
+// (its confounder rows are written afterwards).
+inline int64_t real_rows(const Ctx *c) { return c->rr ? c->rr_m : c->n; }
+// Ridge regression buffers (ridge.cu), released with the context.
+void rr_free(Ctx *c);
+
 // Width of the packed operand rows before padding: M, or 2M for IBS.
 inline int64_t encoded_width(const Ctx *c, int64_t m) { return is_ibs(c) ? 2 * m : m; }
 
@@ -220,6 +236,55 @@ struct PerDevice {
         done[dev].store(1, std::memory_order_release);
     }
 };
+
+// Device buffers owned by a context: (re)allocation with the failure message
+// recorded in the context (KRR_ENOMEM), and release.
+template <typename T>
+krr_status dev_alloc(Ctx *c, T **p, size_t count, const char *what) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    if (count == 0) return KRR_OK;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        c->last_error = std::string("cudaMalloc failed for ") + what + " (" +
+                        std::to_string(count * sizeof(T)) + " bytes): " + cudaGetErrorString(e);
+        return KRR_ENOMEM;
+    }
+    return KRR_OK;
+}
+
+template <typename T>
+void dev_free(T **p) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+// Host-side helpers of the driver (krr_api.cu), shared by the entry points of
+// the other translation units.
+bool is_device_ptr(const void *p);
+const void *pinned_host_alias(const void *p);
+// Makes the context's device staging buffer for host arguments at least `bytes`.
+krr_status stage(Ctx *c, size_t bytes);
+// KRR_ECUDA with the message of the last launch error, if any.
+krr_status check_launch(Ctx *c, const char *where);
+// n x cols caller matrix (host or device, leading dimension ld) -> dense device
+// matrix of rows_pad rows (zero padded).
+krr_status load_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, int64_t ld, int64_t rows_pad,
+                         float *dst);
+// First n rows of a dense device matrix -> caller matrix (host or device).
+krr_status store_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, float *dst, int64_t ld);
+// Confounders (n x nc) -> dense rows_pad x CONF_MAX device layout.
+krr_status load_conf(Ctx *c, const float *src, int64_t n, int64_t nc, int64_t ld, int64_t rows_pad, float *dst);
+void free_factor(Ctx *c);
+void free_build(Ctx *c);
+// Buffers and shape fields of a build over n rows, packed operand rows of
+// m_pad columns (keep_d: keep the exact distances as well).
+krr_status prepare_build(Ctx *c, int64_t n, int64_t m_pad, int keep_d);
+bool mixed(const Ctx *c);
 
 // Kernel launch counter of the whole library (reported by krr_get_profile).
 void count_launch();

@@ -87,7 +87,7 @@ extern "C" krr_status krr_predict_noalloc(krr_ctx *ctx, const int8_t *T, int64_t
         c->last_error = "krr_predict_noalloc: no kernel built";
         return KRR_ESTATE;
     }
-    if (c->opt.mode != KRR_MODE_MIXED || !c->tc || c->opt.kernel != KRR_KERNEL_GAUSSIAN || c->nconf > 0) {
+    if (c->opt.mode != KRR_MODE_MIXED || !c->tc || c->opt.kernel != KRR_KERNEL_GAUSSIAN || c->nconf > 0 || c->rr) {
         c->last_error = "krr_predict_noalloc: needs a context in KRR_MODE_MIXED with the Gaussian kernel and no "
                         "confounders";
         return KRR_EINVAL;

@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(256) build_simt_kernel(const float *gf, const 
             int32_t d = ni + norms[gj] - 2 * (int32_t)acc[i][j];
             const float dc = nc ? conf_dist(ci, conf + gj * CONF_MAX, nc) : 0.f;
             float kv;
-            if (gi < n && gj < n) kv = kf.value(gamma, d, dc);
+            if (gi < n && gj < n) kv = kf.gram ? acc[i][j] : kf.value(gamma, d, dc);
             else kv = (gi == gj) ? 1.0f : 0.0f;
             kt[lr * b + lc] = kv;
             if (dt) dt[lr * b + lc] = (gi < n && gj < n) ? (uint32_t)d : 0u;
@@ -375,8 +375,8 @@ void launch_build_simt(Ctx *c) {
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     const int64_t sub = (c->b / SG_BM) * (c->b / SG_BM);
     count_launch(), build_simt_kernel<<<(unsigned)(ntri * sub), 256, 0, c->stream>>>(
-        c->gf, c->norms, c->m_pad, c->n, c->b, (float)c->gamma, kernel_fn(c), c->conf, (int)c->nconf, c->Kd, c->Dd,
-        c->knorm2);
+        c->gf, c->norms, c->m_pad, real_rows(c), c->b, (float)c->gamma, kernel_fn(c), c->conf, (int)c->nconf, c->Kd,
+        c->Dd, c->knorm2);
 }
 
 // Deterministic sums of the per-block partials: out[0] = ||K||_F^2 and

@@ -594,7 +594,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
                 const bool real = gi < p.n && gj < p.n;
                 // confounders of column c: slots [16, 32) of its staged row
                 const float dc = nc ? conf_dist(ci, aw_s + c * PRED_MAX_P + 16, nc) : 0.f;
-                kv[e] = real ? p.kf.value(p.gamma, d, dc) : (gi == gj ? 1.f : 0.f);
+                kv[e] = real ? (p.kf.gram ? v[e] : p.kf.value(p.gamma, d, dc)) : (gi == gj ? 1.f : 0.f);
                 dv[e] = real ? (uint32_t)d : 0u;
                 ss += (double)kv[e] * (double)kv[e];
                 s1 += (double)kv[e];
@@ -1312,6 +1312,7 @@ krr_status tc_build(Ctx *c) {
     p.knorm_part = c->knorm2;
     p.conf_a = p.conf_b = c->conf;
     p.nconf = (int)c->nconf;
+    p.n = real_rows(c);
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     p.items = ntri * (c->b / BM) * (c->b / BN);
     return launch<KIND_F8, OP_DIST>(c, st->g_map, st->g_map, st->g_map, st->g_map, p);

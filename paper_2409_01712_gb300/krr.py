@@ -32,7 +32,8 @@ PREC_NAMES = {0: "fp64", 1: "fp32", 2: "fp16", 3: "e4m3", 255: "-"}
 
 # Every symbol include/krr.h declares (checked by the CPU test suite).
 EXPORTED = ["krr_default_options", "krr_create", "krr_build_kernel", "krr_factor", "krr_solve",
-            "krr_predict", "krr_build_kernel_conf", "krr_predict_conf", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
+            "krr_predict", "krr_build_kernel_conf", "krr_predict_conf", "krr_rr_build", "krr_rr_rhs",
+            "krr_rr_predict", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
             "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_sync", "krr_last_error",
             "krr_destroy", "krr_batch_create", "krr_batch_run", "krr_batch_last_error", "krr_batch_destroy"]
@@ -103,6 +104,9 @@ def load_library(path: str = LIB_PATH):
     lib.krr_predict.argtypes = [vp, vp, i64, i64, vp, i64, i64, vp, i64]
     lib.krr_build_kernel_conf.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64, dbl]
     lib.krr_predict_conf.argtypes = [vp, vp, i64, i64, vp, i64, vp, i64, i64, vp, i64]
+    lib.krr_rr_build.argtypes = [vp, vp, i64, i64, i64, vp, i64, i64]
+    lib.krr_rr_rhs.argtypes = [vp, vp, i64, i64, vp, i64]
+    lib.krr_rr_predict.argtypes = [vp, vp, i64, i64, vp, i64, vp, i64, i64, vp, i64]
     lib.krr_get_precision_map.argtypes = [vp, vp, i64, ctypes.POINTER(i64)]
     lib.krr_set_keep_distances.argtypes = [vp, i32]
     lib.krr_get_distances.argtypes = [vp, vp, i64]
@@ -127,7 +131,7 @@ def load_library(path: str = LIB_PATH):
     lib.krr_destroy.argtypes = [vp]
     lib.krr_destroy.restype = None
     for name in ("krr_create", "krr_build_kernel", "krr_factor", "krr_solve", "krr_predict",
-                 "krr_build_kernel_conf", "krr_predict_conf",
+                 "krr_build_kernel_conf", "krr_predict_conf", "krr_rr_build", "krr_rr_rhs", "krr_rr_predict",
                  "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
                  "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_sync"):
@@ -270,6 +274,34 @@ class KRR:
                                                    ctypes.c_void_p(_ptr(conf)), _ld(conf),
                                                    ctypes.c_void_p(_ptr(a)), _ld(a), p, ctypes.c_void_p(_ptr(yt)),
                                                    _ld(yt)))
+        return yt
+
+    # -- ridge regression (Sec. IV-A): Gram matrix, X^T Y, predictions --------
+    def rr_build(self, x, conf=None):
+        """The context's matrix becomes X^T X, X = [x conf] (x: n x m int8)."""
+        n, m = x.shape
+        nc = 0 if conf is None else conf.shape[1]
+        self._check(self._lib.krr_rr_build(self._ctx, ctypes.c_void_p(_ptr(x)), n, m, _ld(x),
+                                           ctypes.c_void_p(_ptr(conf) if conf is not None else 0), nc,
+                                           _ld(conf) if conf is not None else max(nc, 1)))
+        self.n, self.m, self.rr_m, self.rr_nc = m + nc, n, m, nc
+
+    def rr_rhs(self, y, out=None):
+        """X^T Y ((m + nc) x p)."""
+        p = y.shape[1]
+        b = _empty_like_rows(y, self.n, p) if out is None else out
+        self._check(self._lib.krr_rr_rhs(self._ctx, ctypes.c_void_p(_ptr(y)), p, _ld(y), ctypes.c_void_p(_ptr(b)),
+                                         _ld(b)))
+        return b
+
+    def rr_predict(self, t, beta, conf=None, out=None):
+        """T beta_g + Ct beta_c for held-out patients."""
+        n_t, p = t.shape[0], beta.shape[1]
+        yt = _empty_like_rows(beta, n_t, p) if out is None else out
+        self._check(self._lib.krr_rr_predict(self._ctx, ctypes.c_void_p(_ptr(t)), n_t, _ld(t),
+                                             ctypes.c_void_p(_ptr(conf) if conf is not None else 0),
+                                             _ld(conf) if conf is not None else 1, ctypes.c_void_p(_ptr(beta)),
+                                             _ld(beta), p, ctypes.c_void_p(_ptr(yt)), _ld(yt)))
         return yt
 
     # -- hyperparameter gradient (adjoint reusing the factor) ----------------

@@ -390,3 +390,31 @@ def test_kernel_with_confounders_adds_before_exponential():
     assert np.allclose(kc, k0 * np.exp(-gamma * oracle.conf_sqdist(c)), rtol=1e-13, atol=0)
     assert np.allclose(oracle.build_kernel(gamma, g, c1=np.zeros((25, 4))), k0, rtol=4e-16, atol=0)
     assert np.all(np.diag(kc) == 1.0)
+
+
+# ---------------------------------------------------------------- ridge regression (Sec. IV-A, Eq. 2)
+
+def test_ridge_gram_is_integer_sum_and_optimality():
+    g = _rand_geno(70, 40, 61)
+    c = np.random.default_rng(61).standard_normal((70, 3))
+    y = np.random.default_rng(62).standard_normal((70, 2))
+    lam = 0.7
+    gram, rhs, beta = oracle.ridge(lam, g, y, c)
+    gi = g.astype(np.int64)
+    # genotype block: exact integer sums over the patients
+    assert np.array_equal(gram[:40, :40], np.einsum("pi,pj->ij", gi, gi).astype(np.float64))
+    x = np.concatenate([g.astype(np.float64), c], axis=1)
+    # first-order optimality of the ridge objective: X^T (Y - X beta) = lambda beta
+    assert np.allclose(x.T @ (y - x @ beta), lam * beta, rtol=1e-9, atol=1e-9)
+    assert np.allclose(beta, np.linalg.solve(x.T @ x + lam * np.eye(43), x.T @ y), rtol=1e-9, atol=1e-10)
+    # lambda -> infinity: lambda beta -> X^T Y
+    big = 1e9
+    _, _, b2 = oracle.ridge(big, g, y, c)
+    assert np.allclose(big * b2, rhs, rtol=1e-4, atol=1e-4)
+    # library path = plain loops
+    _, _, b3 = oracle.ridge(lam, g, y, c, method="lapack")
+    assert np.allclose(b3, beta, rtol=1e-9, atol=1e-11)
+    t = _rand_geno(9, 40, 63)
+    ct = np.random.default_rng(63).standard_normal((9, 3))
+    assert np.allclose(oracle.ridge_predict(t, beta, ct), np.concatenate([t, ct], axis=1) @ beta, rtol=1e-12,
+                       atol=1e-12)
