@@ -70,6 +70,7 @@ constexpr int RED_RNORM = 0;     // [0] ||R||_F^2, [1] ||Y||_F^2 of the last res
 constexpr int RED_KNORM2 = 2;    // ||K||_F^2
 constexpr int RED_KSUM = 3;      // sum of the entries of K
 constexpr int RED_KSHIFT = 4;    // mean off-diagonal entry of K (residual shift)
+constexpr int RED_KBOUND = 5;    // max_i K_ii: bounds every |K_ij| (K is positive semidefinite)
 constexpr int RED_MINPIV = 64;   // nt * (b / 64) block minimum pivots, then nt max|L_kk| bounds
 
 // Storage precision of an off-diagonal factor tile (values of the

@@ -227,14 +227,15 @@ krr_status copy_in(Ctx *c, void *dst, const void *src, int64_t rows, size_t row_
 }
 
 // Split of a contraction of length K for `rows` output rows: enough CTAs to
-// fill the GPU twice over.
+// fill the GPU twice over, and at most RG_KMAX terms summed in FP32 per chunk.
+constexpr int64_t RG_KMAX = 2048;
 void split(const Ctx *c, int64_t rows, int64_t K, int64_t *nchunk, int64_t *kchunk) {
     const int64_t rb = (rows + RG_R - 1) / RG_R;
     int64_t want = std::max<int64_t>(1, (4 * (int64_t)c->num_sms + rb - 1) / rb);
     want = std::min<int64_t>(want, std::max<int64_t>(1, (K + RG_K - 1) / RG_K));
     int64_t kc = (K + want - 1) / want;
     kc = (kc + RG_K - 1) / RG_K * RG_K;
-    *kchunk = std::max<int64_t>(kc, RG_K);
+    *kchunk = std::min<int64_t>(std::max<int64_t>(kc, RG_K), RG_KMAX);
     *nchunk = (K + *kchunk - 1) / *kchunk;
 }
 

@@ -940,11 +940,30 @@ void launch_column_cast(Ctx *c, int64_t k) {
                                                                       (__half *)c->W);
 }
 
+// Largest diagonal entry of K over the diagonal tiles (padding included):
+// K is positive semidefinite, so it bounds every |K_ij|.
+__global__ void kernel_bound_kernel(const float *Kd, int64_t nt, int64_t b, double *out) {
+    __shared__ float red[32];
+    float mx = 0.f;
+    for (int64_t e = threadIdx.x; e < nt * b; e += blockDim.x) {
+        const int64_t t = e / b, r = e % b;
+        mx = fmaxf(mx, fabsf(Kd[tri_index(t, t) * b * b + r * b + r]));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+        *out = (double)mx;
+    }
+}
+
 void launch_kernel_sumsq(Ctx *c, double *out) {
     const int64_t ntri = c->nt * (c->nt + 1) / 2;
     const int64_t per = (c->opt.mode == KRR_MODE_FP32) ? (c->b / SG_BM) * (c->b / SG_BM)
                                                        : (c->b / 128) * (c->b / 256);
     count_launch(), kernel_sumsq_kernel<<<1, 1024, 0, c->stream>>>(c->knorm2, ntri, per, c->n_pad, out);
+    count_launch(), kernel_bound_kernel<<<1, 1024, 0, c->stream>>>(c->Kd, c->nt, c->b, c->red + RED_KBOUND);
 }
 
 // x (n_pad x p) <- (L L^T)^-1 x.  tmp is n_pad x p scratch (ends as Z).

@@ -211,7 +211,17 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int 
                  "r"(x), "r"(y), "r"(smem_u32(src))
                  : "memory");
 }
+// Element-wise add of a shared-memory box into global memory (the L2 performs
+// the read-modify-write; the element type is the tensor map's, here FP16).
+__device__ __forceinline__ void tma_reduce_add_2d(const CUtensorMap *map, int x, int y, const void *src) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// All but the most recent bulk group have finished reading shared memory.
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -332,6 +342,33 @@ __device__ __forceinline__ TileDesc col_tile(const TcParams &p, const TileDesc *
     return col_desc ? col_desc[e] : p.ltab[off_index(p.k + 1 + e, p.k)];
 }
 
+// Order of the trailing-update target tiles (ii, jj), jj <= ii, of one step:
+// bands of UPD_BAND tile rows, and within a band blocks of UPD_BAND tile
+// columns (row by row inside a block), so the tiles in flight at any time
+// read the factor tiles of at most two bands' worth of rows and columns
+// (about 32 MB at b = 1024) and these stay in L2 while they are reused.  A
+// band covers the same tile indices as in plain row order, so the band of
+// index t is found from the row-major decoding.
+constexpr int64_t UPD_BAND = 8;
+__device__ __forceinline__ void update_tile_order(int64_t t, int64_t u, int64_t *ii, int64_t *jj) {
+    int64_t r, c;
+    tri_decode(t, &r, &c);
+    const int64_t r0 = r / UPD_BAND * UPD_BAND;
+    const int64_t h = (u - r0 < UPD_BAND) ? u - r0 : UPD_BAND;  // rows of the band (the last may be short)
+    const int64_t l = t - r0 * (r0 + 1) / 2;                    // index inside the band
+    const int64_t full = h * r0;  // tiles of the band left of its diagonal block
+    if (l < full) {
+        const int64_t cb = l / (h * UPD_BAND), l2 = l % (h * UPD_BAND);
+        *ii = r0 + l2 / UPD_BAND;
+        *jj = cb * UPD_BAND + l2 % UPD_BAND;
+    } else {
+        int64_t a, bb;
+        tri_decode(l - full, &a, &bb);
+        *ii = r0 + a;
+        *jj = r0 + bb;
+    }
+}
+
 template <int OP>
 __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, const TileDesc *col_desc) {
     const int64_t b = p.b;
@@ -402,7 +439,7 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
         const int64_t k = p.k;
         const int64_t tile = t / sub_per_tile, sub = t % sub_per_tile;
         int64_t ii, jj;
-        tri_decode(tile, &ii, &jj);
+        update_tile_order(tile, p.nt - k - 1, &ii, &jj);
         w.i = k + 1 + ii;
         w.j = k + 1 + jj;
         w.sm = sub / sub_cols;
@@ -756,32 +793,41 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
     }
 }
 
-// Trailing update, FP16 target: box bx (columns [64 bx, 64 bx + 64)) of the
-// block, staged 128-byte swizzled in `box` (128 rows of 128 bytes), is
-// updated in place from the accumulator: thread `row` takes columns
-// [32 hh, 32 hh + 32) of the box.
-__device__ __forceinline__ void update_box(uint32_t tacc, int row, int hh, int bx, uint8_t *box, float sc) {
+// Trailing update, FP16 target: the update of box bx (columns [64 bx,
+// 64 bx + 64)) of the block, -scale * accumulator rounded to FP16, written
+// 128-byte swizzled into `box` (128 rows of 128 bytes) for a TMA reduce-add
+// into the target: thread `row` takes columns [32 hh, 32 hh + 32) of the box.
+__device__ __forceinline__ void delta_box(uint32_t tacc, int row, int hh, int bx, uint8_t *box, float nsc) {
 #pragma unroll
     for (int cc = 0; cc < 2; ++cc) {
         const int col = hh * 32 + cc * 16, u0 = col >> 3;
         float v[16];
         tmem_ld16(tacc + bx * 64 + col, v);
         uint8_t *rp = box + row * 128;
-        uint4 *q0 = reinterpret_cast<uint4 *>(rp + ((u0 ^ (row & 7)) << 4));
-        uint4 *q1 = reinterpret_cast<uint4 *>(rp + (((u0 + 1) ^ (row & 7)) << 4));
-        uint4 u[2] = {*q0, *q1};
+        uint4 u[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
             __half2 *h2 = reinterpret_cast<__half2 *>(&u[e]);
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-                const float2 f = __half22float2(h2[qq]);
-                h2[qq] = __floats2half2_rn(f.x - v[8 * e + 2 * qq] * sc, f.y - v[8 * e + 2 * qq + 1] * sc);
-            }
+            for (int qq = 0; qq < 4; ++qq)
+                h2[qq] = __floats2half2_rn(v[8 * e + 2 * qq] * nsc, v[8 * e + 2 * qq + 1] * nsc);
         }
-        *q0 = u[0];
-        *q1 = u[1];
+        *reinterpret_cast<uint4 *>(rp + ((u0 ^ (row & 7)) << 4)) = u[0];
+        *reinterpret_cast<uint4 *>(rp + (((u0 + 1) ^ (row & 7)) << 4)) = u[1];
     }
+}
+
+// Named barrier 1 of the 256 epilogue threads with the OR of `fail` over
+// them: all threads get the same answer, so they leave their loops together.
+__device__ __forceinline__ bool epi_any(bool fail) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\tbar.red.or.pred q, 1, 256, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)fail)
+        : "memory");
+    return r != 0;
 }
 
 // Per-block epilogue inputs staged in shared memory by the epilogue warps.
@@ -1019,64 +1065,51 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int half = (warp - 2) >> 2;          // column half of the block
         const int hh = (warp - 2) >> 2;            // 32-column half of a target box
         int acc = 0;
-        uint32_t aph = 0, cph = 0;                 // cph: phases of the two box buffers
-        uint32_t cload_pending = 0;  // thread 64: box buffers with a load issued and not waited for
+        uint32_t aph = 0;
         for (int64_t u = ustart; u < nunits; u += ustep) {
             Work w;
             decode<OP>(p, unit_item(u), w, col_desc);
             if (w.nph * w.nkb == 0) continue;
-            // pair mode, FP16 target: the block goes through shared memory box by
-            // box; the first two boxes load while the MMAs run (once the previous
-            // block's stores have read the buffers), the other two are prefetched
-            // into L2
+            // pair mode, FP16 target: the update goes back box by box as a TMA
+            // reduce-add of its FP16 value (the L2 adds it to the target; the
+            // target is never loaded into the SM); the target boxes are
+            // prefetched into L2 while the MMAs run
             const bool cstage = (PAIR == 2 && OP == OP_UPDATE) && p.k > 0 && w.i != w.j;
             const int ybox = (int)(off_index(w.i, w.j) * p.b + w.sm * BM);
-            if (cstage && threadIdx.x == 64) {
-                bulk_wait_read();
-                for (int bx = 0; bx < 2; ++bx) {
-                    mbar_arrive_expect_tx(&cfull[bx], (uint32_t)BOX_BYTES);
-                    tma_load_2d(cbuf + bx * BOX_BYTES, &mB1, (int)(w.sn * BN + bx * 64), ybox, &cfull[bx]);
-                }
-                for (int bx = 2; bx < BN / 64; ++bx) tma_prefetch_2d(&mB1, (int)(w.sn * BN + bx * 64), ybox);
-                cload_pending = 3u;
-            }
+            if (cstage && threadIdx.x == 64)
+                for (int bx = 0; bx < BN / 64; ++bx) tma_prefetch_2d(&mB1, (int)(w.sn * BN + bx * 64), ybox);
             epi_bar();
             epilogue_stage<OP>(p, w, threadIdx.x - 64, nb_s, aw_s);
             if (!cstage) epilogue_prefetch<OP>(p, w, row, half);
             epi_bar();
-            if (!wait_bar(&tfull[acc], aph, budget, abort_flag, p.err)) break;
+            // a collective decision: a wait that ran out in any thread ends the
+            // loop in all of them
+            const bool got = wait_bar(&tfull[acc], aph, budget, abort_flag, p.err);
+            if (epi_any(!got)) break;
             tmem_fence_after();
             const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * BN);
             if (cstage) {
-                const float sc = 1.f / (col_tile(p, col_desc, w.i - p.k - 1).scale *
-                                        col_tile(p, col_desc, w.j - p.k - 1).scale);
-                bool ok = true;
+                const float nsc = -1.f / (col_tile(p, col_desc, w.i - p.k - 1).scale *
+                                          col_tile(p, col_desc, w.j - p.k - 1).scale);
                 for (int bx = 0; bx < BN / 64; ++bx) {
                     const int bi = bx & 1;
-                    // every thread reaches the barrier, then all take the same
-                    // decision (a wait that ran out set the abort flag)
-                    wait_bar(&cfull[bi], (cph >> bi) & 1u, budget, abort_flag, p.err);
+                    // buffer bi is free once the reduce that last used it has
+                    // read it: at box 0 every earlier group (the previous
+                    // block's boxes), later all but the newest (box bx - 1)
+                    if (threadIdx.x == 64) {
+                        if (bx == 0) bulk_wait_read();
+                        else if (bx >= 2) bulk_wait_read1();
+                    }
                     epi_bar();
-                    if (*abort_flag) { ok = false; break; }
-                    cph ^= 1u << bi;
-                    if (threadIdx.x == 64) cload_pending &= ~(1u << bi);
-                    update_box(tacc, row, hh, bx, cbuf + bi * BOX_BYTES, sc);
-                    // generic-proxy writes become visible to the TMA store
+                    delta_box(tacc, row, hh, bx, cbuf + bi * BOX_BYTES, nsc);
+                    // generic-proxy writes become visible to the TMA reduce
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     epi_bar();
                     if (threadIdx.x == 64) {
-                        tma_store_2d(&mB1, (int)(w.sn * BN + bx * 64), ybox, cbuf + bi * BOX_BYTES);
+                        tma_reduce_add_2d(&mB1, (int)(w.sn * BN + bx * 64), ybox, cbuf + bi * BOX_BYTES);
                         bulk_commit();
-                        if (bx + 2 < BN / 64) {
-                            bulk_wait_read();  // the store has read the buffer
-                            mbar_arrive_expect_tx(&cfull[bi], (uint32_t)BOX_BYTES);
-                            tma_load_2d(cbuf + bi * BOX_BYTES, &mB1, (int)(w.sn * BN + (bx + 2) * 64), ybox,
-                                        &cfull[bi]);
-                            cload_pending |= 1u << bi;
-                        }
                     }
                 }
-                if (!ok) break;
             } else {
                 epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc);
             }
@@ -1088,15 +1121,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             if (++acc == 2) { acc = 0; aph ^= 1; }
         }
-        if (PAIR == 2 && threadIdx.x == 64) {
-            bulk_wait_all();  // stores finished before the CTA leaves
-            for (int bi = 0; bi < 2; ++bi) {
-                if (cload_pending & (1u << bi)) {  // aborted with a box load in flight
-                    const uint64_t t0 = globaltimer();
-                    while (!mbar_try_wait(&cfull[bi], (cph >> bi) & 1u) && globaltimer() - t0 < budget) {}
-                }
-            }
-        }
+        if (PAIR == 2 && threadIdx.x == 64) bulk_wait_all();  // reduces finished before the CTA leaves
     }
     tmem_fence_before();
     __syncthreads();

@@ -914,7 +914,14 @@ constexpr int RS_THREADS = 320;
 constexpr int RS_STG = 32768;      // FP32 chunk: 128 x 64 or 64 x 128
 constexpr int RS_NSTG = 5;         // staging ring (FP32 K chunks by TMA, converted in place)
 constexpr int RS_NB = 3;           // B ring (FP16 terms of a, TMA): loads run ahead of the A ring
-constexpr float RS_KSCALE = 4096.f;  // (K - c) * 2^12 in FP16 (|K - c| <= 1)
+// (K - c) s in FP16 with the power of two s = 2^(e - 1) <= 8192 / (max|K| + |c|):
+// |(K - c) s| <= 8192, far below the FP16 maximum (s = 2^12 for the Gaussian
+// kernel, whose entries lie in (0, 1]).
+__device__ __forceinline__ float rs_kscale(const double *kbound, const double *shift) {
+    int e;
+    frexpf(8192.f / (float)(*kbound + fabs(*shift)), &e);
+    return ldexpf(1.f, e - 1);
+}
 
 struct RsParams {
     int64_t b, nt, S, KC, items, n_pad;
@@ -923,6 +930,7 @@ struct RsParams {
     const float *y, *a;
     double *r;
     const double *shift, *colsum;
+    const double *kbound;   // max |K_ij| (the residual operand's scale follows from it)
     float lambda;
     const float *sa;        // scales of the FP16 pair of a, [nt][np]
     int *flags;             // [0] item counter, [1] abort
@@ -1128,6 +1136,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
         // ------------------------------ converters ------------------------------
         const int ct = threadIdx.x - 192;
         const float c = (float)*p.shift;
+        const float kscale = rs_kscale(p.kbound, p.shift);
         int ss = 0, slot = 0;
         uint32_t sph = 0, iph = 0;
         bool ok = true;
@@ -1167,7 +1176,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                         __half2 *hh = reinterpret_cast<__half2 *>(&hv), *ll = reinterpret_cast<__half2 *>(&lv);
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const float x0 = (v[8 * u + 2 * e] - c) * RS_KSCALE, x1 = (v[8 * u + 2 * e + 1] - c) * RS_KSCALE;
+                            const float x0 = (v[8 * u + 2 * e] - c) * kscale, x1 = (v[8 * u + 2 * e + 1] - c) * kscale;
                             const __half2 hx = __floats2half2_rn(x0, x1);
                             const float2 hf = __half22float2(hx);
                             hh[e] = hx;
@@ -1210,10 +1219,11 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 alo_s[q * 128 + et] = 0.f;
             }
             bool ok = true;
-            float mlane = 0.f;  // lane q: 1 / (2^12 * scale of column q of a_j)
+            const float kscale = rs_kscale(p.kbound, p.shift);
+            float mlane = 0.f;  // lane q: 1 / (kscale * scale of column q of a_j)
             for (int64_t jc = 0; jc < nt * KC; ++jc) {
                 const int64_t j = jc / KC;
-                if (jc % KC == 0) mlane = (lane < pc) ? 1.f / (RS_KSCALE * __ldg(p.sa + j * np + lane)) : 0.f;
+                if (jc % KC == 0) mlane = (lane < pc) ? 1.f / (kscale * __ldg(p.sa + j * np + lane)) : 0.f;
                 if (!__all_sync(0xffffffffu, rs_wait(&tfull[acc], aph, p))) { ok = false; break; }
                 tmem_fence_after();
                 const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * 3 * np);
@@ -1575,6 +1585,7 @@ krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_
         rp.a = a;
         rp.r = r;
         rp.shift = c->red + RED_KSHIFT;
+        rp.kbound = c->red + RED_KBOUND;
         rp.colsum = c->colsum;
         rp.lambda = (float)c->lambda;
         rp.sa = sbase;
