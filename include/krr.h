@@ -40,7 +40,7 @@ typedef enum krr_status {
     KRR_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
     KRR_ENOTPD = 4,   /* a pivot of the Cholesky factorisation was not positive */
     KRR_ENOCONV = 5,  /* iterative refinement did not reach the requested residual */
-    KRR_ETIMEOUT = 6, /* a bounded device-side wait ran out */
+    KRR_ETIMEOUT = 6, /* a bounded device-side wait ran out (see krr_set_wait_budget) */
     KRR_ESTATE = 7    /* calls out of order (e.g. solve before factor) */
 } krr_status;
 
@@ -414,6 +414,16 @@ krr_status krr_set_profiling(krr_ctx *ctx, int32_t on);
 /* Synchronises the stream and sums the timed regions into *out; reset = 1
  * clears the records and the launch counter afterwards. */
 krr_status krr_get_profile(krr_ctx *ctx, krr_profile *out, int32_t reset);
+
+/*
+ * Changes the limit of every bounded device wait of the context's later
+ * launches (krr_options.wait_budget_ns; ns >= 1).  A wait that runs out ends
+ * its kernel early, after the kernel's own copies and MMAs in flight have
+ * finished, and the call that launched it returns KRR_ETIMEOUT (krr_factor,
+ * krr_solve); the context stays usable, and a later call with a sufficient
+ * budget recomputes what was cut short.  Errors: KRR_EINVAL.
+ */
+krr_status krr_set_wait_budget(krr_ctx *ctx, int64_t ns);
 
 /* Waits for all work issued by the context. */
 krr_status krr_sync(krr_ctx *ctx);

@@ -748,11 +748,35 @@ krr_status krr_solve(krr_ctx *c, const float *Y, int64_t p, int64_t ldy, float *
         return KRR_EINVAL;
     }
     KRR_TRY(ensure_vectors(c, p));
+    // the sweep and residual kernels record an expired wait in the error
+    // record (the factor stays valid: they do not write it)
+    KRR_CUDA_TRY(c, cudaMemsetAsync(&c->derr->code, 0, sizeof(int32_t), c->stream));
     KRR_TRY(load_rows_f32(c, Y, c->n, p, ldy, c->n_pad, c->ybuf));
     krr_status st = solve_device(c, p, info);
     if (st != KRR_OK && st != KRR_ENOCONV) return st;
     KRR_TRY(store_rows_f32(c, c->abuf, c->n, p, A, lda));
+    if (!c->graph_mode) {
+        KRR_CUDA_TRY(c, cudaMemcpyAsync(&c->herr->code, &c->derr->code, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                        c->stream));
+        KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        const int32_t code = c->herr->code;
+        if (code != 0) {
+            c->last_error = "krr_solve: device error " + std::to_string(code) +
+                            (code == KRR_ETIMEOUT ? " (a bounded device wait ran out)" : "");
+            return (krr_status)code;
+        }
+    }
     return st;
+}
+
+krr_status krr_set_wait_budget(krr_ctx *c, int64_t ns) {
+    if (!c) return KRR_EINVAL;
+    if (ns < 1) {
+        c->last_error = "krr_set_wait_budget: the budget must be positive";
+        return KRR_EINVAL;
+    }
+    c->opt.wait_budget_ns = ns;
+    return KRR_OK;
 }
 
 static krr_status predict_common(krr_ctx *c, const int8_t *T, int64_t n_test, int64_t ldt, const float *Ct, int64_t ldct,

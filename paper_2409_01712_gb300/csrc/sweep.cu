@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1)
             for (int e = 0; e < n; ++e) {
                 if (--ss < 0) { ss = NS - 1; pp ^= 1; }
                 const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < p.wait_ns) {}
+                while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < drain_limit(p.wait_ns)) {}
             }
         }
     } else {

@@ -1005,7 +1005,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 for (int e = 0; e < n; ++e) {
                     if (--ss < 0) { ss = NST - 1; pp ^= 1; }
                     const uint64_t t0 = globaltimer();
-                    while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < budget) {}
+                    while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < drain_limit(budget)) {}
                 }
             }
         }
@@ -1056,7 +1056,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 if (PAIR == 2) mma_commit_pair(drain);
                 else mma_commit(drain);
                 const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < budget) {}
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < drain_limit(budget)) {}
             }
         }
     } else {

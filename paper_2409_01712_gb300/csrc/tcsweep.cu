@@ -672,7 +672,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
                 for (int e = 0; e < n; ++e) {
                     if (--ss < 0) { ss = NS - 1; pp ^= 1; }
                     const uint64_t t0 = globaltimer();
-                    while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < p.wait_ns) {}
+                    while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < drain_limit(p.wait_ns)) {}
                 }
             }
         }
@@ -718,7 +718,7 @@ __global__ void __launch_bounds__(TS_THREADS, 1)
             if (!ok && any) {
                 mma_commit(drain);
                 const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < p.wait_ns) {}
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < drain_limit(p.wait_ns)) {}
             }
         }
     } else {
@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 for (int e = 0; e < n; ++e) {
                     if (--q < 0) { q = RS_NSTG - 1; pp ^= 1; }
                     const uint64_t t0 = globaltimer();
-                    while (!mbar_try_wait(&sfull[q], pp) && globaltimer() - t0 < p.wait_ns) {}
+                    while (!mbar_try_wait(&sfull[q], pp) && globaltimer() - t0 < drain_limit(p.wait_ns)) {}
                 }
                 n = issued_o < RS_NB ? issued_o : RS_NB;
                 q = os;
@@ -1076,7 +1076,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
                 for (int e = 0; e < n; ++e) {
                     if (--q < 0) { q = RS_NB - 1; pp ^= 1; }
                     const uint64_t t0 = globaltimer();
-                    while (!mbar_try_wait(&bfull[q], pp) && globaltimer() - t0 < p.wait_ns) {}
+                    while (!mbar_try_wait(&bfull[q], pp) && globaltimer() - t0 < drain_limit(p.wait_ns)) {}
                 }
             }
         }
@@ -1129,7 +1129,7 @@ __global__ void __launch_bounds__(RS_THREADS, 1)
             if (!ok && any) {
                 mma_commit(drain);
                 const uint64_t t0 = globaltimer();
-                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < p.wait_ns) {}
+                while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < drain_limit(p.wait_ns)) {}
             }
         }
     } else if (warp >= 6) {

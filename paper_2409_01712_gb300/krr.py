@@ -35,7 +35,7 @@ EXPORTED = ["krr_default_options", "krr_create", "krr_build_kernel", "krr_factor
             "krr_predict", "krr_build_kernel_conf", "krr_predict_conf", "krr_rr_build", "krr_rr_rhs",
             "krr_rr_predict", "krr_get_precision_map", "krr_set_keep_distances", "krr_get_distances",
             "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
-            "krr_get_profile", "krr_sync", "krr_last_error",
+            "krr_get_profile", "krr_set_wait_budget", "krr_sync", "krr_last_error",
             "krr_destroy", "krr_batch_create", "krr_batch_run", "krr_batch_last_error", "krr_batch_destroy"]
 PROF_CLASSES = ["pack", "build", "diag", "trsm", "cast", "update", "solve", "residual", "predict"]
 
@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH):
     lib.krr_batch_last_error.restype = ctypes.c_char_p
     lib.krr_batch_destroy.argtypes = [vp]
     lib.krr_batch_destroy.restype = None
+    lib.krr_set_wait_budget.argtypes = [vp, i64]
+    lib.krr_set_wait_budget.restype = ctypes.c_int
     lib.krr_sync.argtypes = [vp]
     lib.krr_last_error.argtypes = [vp]
     lib.krr_last_error.restype = ctypes.c_char_p
@@ -358,6 +360,10 @@ class KRR:
         out = np.zeros((self.n, self.n), dtype=np.float32)
         self._check(self._lib.krr_get_factor(self._ctx, ctypes.c_void_p(out.ctypes.data), self.n))
         return out
+
+    def set_wait_budget(self, ns: int):
+        """Limit (ns) of every bounded device wait of later launches."""
+        self._check(self._lib.krr_set_wait_budget(self._ctx, int(ns)))
 
     def sync(self):
         self._check(self._lib.krr_sync(self._ctx))
