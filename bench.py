@@ -544,6 +544,57 @@ def run_batch(args):
     return 0
 
 
+def run_peaks(args):
+    """Dense tensor-core peaks of this GPU for the dtypes the path uses, by
+    library GEMMs (cuBLAS / cuBLASLt through torch) timed with CUDA events:
+    FP16 (torch.matmul) and E4M3 with FP32 accumulation (torch._scaled_mm),
+    n x n x n with n = 8192; burst = best of 10 single products, sustained =
+    back-to-back products for about 4 s; SM clocks sampled meanwhile."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    n = 8192
+    flops = 2.0 * n ** 3
+    a16 = torch.randn((n, n), device=dev, dtype=torch.float16)
+    b16 = torch.randn((n, n), device=dev, dtype=torch.float16)
+    a8 = a16.to(torch.float8_e4m3fn)
+    b8 = b16.t().contiguous().to(torch.float8_e4m3fn).t()  # column-major second operand
+    one = torch.ones((), device=dev, dtype=torch.float32)
+    cases = {"fp16": lambda: torch.matmul(a16, b16),
+             "e4m3": lambda: torch._scaled_mm(a8, b8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)}
+    out = {"metric": "dense tensor-core peaks (library GEMM, n=8192)", "n": n, "unit": "TFLOP/s"}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for name, fn in cases.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        best = 0.0
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+        reps, t_total = 0, 0.0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        w0 = time.perf_counter()
+        while time.perf_counter() - w0 < 4.0:
+            for _ in range(20):
+                fn()
+            reps += 20
+            torch.cuda.synchronize()
+        e1.record()
+        torch.cuda.synchronize()
+        t_total = e0.elapsed_time(e1) / 1e3
+        out[name] = {"burst": best, "sustained": flops * reps / t_total / 1e12, "reps": reps}
+    out["clocks"] = clocks.stop()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -564,7 +615,10 @@ def main():
     ap.add_argument("--fp32-warmup", type=int, default=1)
     ap.add_argument("--fp32-steps", type=int, default=2)
     ap.add_argument("--check-rows", type=int, default=32, help="rows of the sampled oracle residual")
+    ap.add_argument("--peaks", action="store_true", help="measure the dense FP16 / E4M3 library GEMM peaks")
     args = ap.parse_args()
+    if args.peaks:
+        return run_peaks(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.config == "c4":

@@ -67,11 +67,11 @@ __device__ __forceinline__ float conf_dist(const float (&ci)[CONF_MAX], const fl
 
 // Limit of the waits that drain a kernel's own copies and MMAs in flight
 // after another wait ran out: those complete in microseconds, so the limit
-// only bounds the wait; it is never shorter than 0.2 s, whatever the
+// only bounds the wait; it is never shorter than 20 ms, whatever the
 // context's wait budget, so that no CTA leaves with a copy into its shared
 // memory or an MMA into its tensor memory still pending.
 __host__ __device__ inline uint64_t drain_limit(uint64_t wait_ns) {
-    return wait_ns > 200000000ull ? wait_ns : 200000000ull;
+    return wait_ns > 20000000ull ? wait_ns : 20000000ull;
 }
 
 // Slots of the small FP64 reduction buffer Ctx::red.

@@ -59,6 +59,7 @@ constexpr int NUM_THREADS = 320;        // 2 control warps + 8 epilogue warps
 constexpr int EPI_THREADS = 256;
 constexpr int TMEM_COLS = 512;          // two 256-column FP32 accumulators
 constexpr int PRED_MAX_P = 32;
+constexpr uint64_t DRAIN_GRACE_NS = 200000;  // 0.2 ms
 
 // Instruction descriptor (kind::f16 with F16 operands, kind::f8f6f4 with
 // E4M3 operands -- both formats encode as 0): D = F32, A and B K-major,
@@ -969,6 +970,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int s = 0;
             uint32_t ph = 0;
             int issued = 0;
+            uint64_t last_issue = 0;
             bool ok = true;
             for (int64_t u = ustart; u < nunits && ok; u += ustep) {
                 Work w;
@@ -992,6 +994,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             tma_load_2d(sb + A_BYTES, maps[w.bmap[q]], x, w.brow[q] + BM, &full[s]);
                         }
                         ++issued;
+                        last_issue = globaltimer();
                         if (++s == NST) { s = 0; ph ^= 1; }
                     }
                 }
@@ -1007,6 +1010,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const uint64_t t0 = globaltimer();
                     while (!mbar_try_wait(&full[ss], pp) && globaltimer() - t0 < drain_limit(budget)) {}
                 }
+            } else if (PAIR == 2 && issued > 0 && (!ok || atomicAdd(&p.err->code, 0) != 0)) {
+                // pair mode, rank 1, after a wait ran out anywhere: its loads
+                // complete on rank 0's barriers, which it cannot poll, and near
+                // the abort it may have issued a stage rank 0 no longer waits
+                // for.  Such a copy lands within microseconds: give it a grace
+                // period far beyond that before the CTA leaves.
+                while (globaltimer() - last_issue < DRAIN_GRACE_NS) __nanosleep(1000);
             }
         }
     } else if (warp == 1) {
