@@ -218,6 +218,15 @@ void free_factor(Ctx *c) {
 }
 
 void free_build(Ctx *c) {
+    if (c->build_borrowed) {  // another context owns these buffers
+        c->g8 = nullptr;
+        c->gf = nullptr;
+        c->norms = nullptr;
+        c->Kd = nullptr;
+        c->Dd = nullptr;
+        c->knorm2 = nullptr;
+        c->build_borrowed = 0;
+    }
     dev_free(&c->g8);
     dev_free(&c->gf);
     dev_free(&c->norms);
@@ -226,6 +235,57 @@ void free_build(Ctx *c) {
     dev_free(&c->knorm2);
     c->g_bytes = c->kd_bytes = c->dd_bytes = 0;
     c->built = false;
+}
+
+// dst reads the build products of src (same device, same tile edge): the
+// packed genotypes, norms and kernel tiles are shared read-only -- nothing
+// after the build writes them -- and the kernel statistics (||K||, the
+// shift, the bound on |K|) are copied on dst's stream, after work that
+// dst's stream already waits for.  src must outlive dst's use of them.
+krr_status adopt_build(Ctx *dst, const Ctx *src) {
+    if (!src->built || src->opt.tile != dst->opt.tile || src->opt.mode != dst->opt.mode ||
+        src->opt.kernel != dst->opt.kernel || src->rr) {
+        dst->last_error = "adopt_build: incompatible source context";
+        return KRR_EINVAL;
+    }
+    if (dst->nt != src->nt || dst->b != src->b) free_factor(dst);
+    free_build(dst);
+    dst->g8 = src->g8;
+    dst->gf = src->gf;
+    dst->norms = src->norms;
+    dst->Kd = src->Kd;
+    dst->knorm2 = src->knorm2;
+    dst->Dd = nullptr;
+    dst->build_borrowed = 1;
+    dst->g_bytes = src->g_bytes;
+    dst->kd_bytes = src->kd_bytes;
+    dst->dd_bytes = 0;
+    dst->n = src->n;
+    dst->m = src->m;
+    dst->m_pad = src->m_pad;
+    dst->b = src->b;
+    dst->nt = src->nt;
+    dst->n_pad = src->n_pad;
+    dst->gamma = src->gamma;
+    dst->nconf = 0;
+    dst->rr = 0;
+    const size_t red_count = src->red_cap;
+    if (dst->red_cap < red_count) {
+        KRR_TRY(dev_alloc(dst, &dst->red, red_count, "reduction buffer"));
+        dst->red_cap = red_count;
+    }
+    if (!dst->hred && cudaMallocHost((void **)&dst->hred, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        dst->hred = nullptr;
+        dst->last_error = "pinned allocation failed";
+        return KRR_ENOMEM;
+    }
+    KRR_CUDA_TRY(dst, cudaMemcpyAsync(dst->red + RED_KNORM2, src->red + RED_KNORM2,
+                                      (RED_KBOUND - RED_KNORM2 + 1) * sizeof(double), cudaMemcpyDeviceToDevice,
+                                      dst->stream));
+    dst->built = true;
+    dst->factored = false;
+    return KRR_OK;
 }
 
 bool mixed(const Ctx *c) { return c->opt.mode == KRR_MODE_MIXED; }
@@ -366,7 +426,7 @@ krr_status prepare_build(Ctx *c, int64_t n, int64_t m_pad, int keep_d) {
     const size_t g_bytes = (size_t)n_pad * m_pad * (mixed(c) ? 1 : 4);
     const int64_t ntri = nt * (nt + 1) / 2;
     const size_t kd_bytes = (size_t)ntri * b * b * sizeof(float);
-    if (c->g_bytes != g_bytes || c->kd_bytes != kd_bytes || c->b != b || c->nt != nt) {
+    if (c->g_bytes != g_bytes || c->kd_bytes != kd_bytes || c->b != b || c->nt != nt || c->build_borrowed) {
         free_build(c);
         if (mixed(c)) KRR_TRY(dev_alloc(c, &c->g8, g_bytes, "packed genotypes"));
         else KRR_TRY(dev_alloc(c, &c->gf, g_bytes / 4, "FP32 genotypes"));

@@ -5,7 +5,10 @@
 // captured once into one CUDA graph with a fork/join over the problem
 // streams, so independent problems overlap on the GPU and a run is a single
 // graph launch.  An autotuner picks the tile edge per problem size from
-// timed trial runs.
+// timed trial runs.  Problems that differ only in lambda (the same genotype
+// matrix, gamma and tile) share one Build: the first of them builds the
+// kernel matrix, the others wait for it on their streams and factorise the
+// same tiles (K does not depend on lambda; nothing after the Build writes it).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -29,6 +32,8 @@ struct krr_batch {
     std::vector<krr_ctx *> ctx;
     std::vector<cudaStream_t> streams;
     std::vector<int32_t> tiles;
+    std::vector<int32_t> owner;       // problem whose Build this one reads (itself when it builds)
+    std::vector<cudaEvent_t> built;   // recorded after an owner's Build
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
     cudaGraph_t graph = nullptr;
@@ -40,8 +45,19 @@ namespace {
 
 thread_local std::string g_batch_create_error;
 
-krr_status issue(krr_ctx *c, const krr_batch_problem &pr, int64_t m, int64_t p) {
-    KRR_TRY(krr_build_kernel(c, pr.G, pr.n, m, pr.ldg, pr.gamma));
+// Build (or, with src != NULL, wait for src's Build and read it), Factor,
+// Solve and Predict of one problem on c's stream; `done` is recorded after
+// an own Build.
+krr_status issue(krr_ctx *c, const krr_batch_problem &pr, int64_t m, int64_t p, krr_ctx *src = nullptr,
+                 cudaEvent_t src_built = nullptr, cudaEvent_t done = nullptr) {
+    krr::Ctx *cc = reinterpret_cast<krr::Ctx *>(c);
+    if (src) {
+        if (cudaStreamWaitEvent(cc->stream, src_built, 0) != cudaSuccess) return KRR_ECUDA;
+        KRR_TRY(krr::adopt_build(cc, reinterpret_cast<krr::Ctx *>(src)));
+    } else {
+        KRR_TRY(krr_build_kernel(c, pr.G, pr.n, m, pr.ldg, pr.gamma));
+        if (done && cudaEventRecord(done, cc->stream) != cudaSuccess) return KRR_ECUDA;
+    }
     KRR_TRY(krr_factor(c, pr.lambda, nullptr));
     krr_status st = krr_solve(c, pr.Y, p, pr.ldy, pr.A, pr.lda, nullptr);
     if (st != KRR_OK) return st;
@@ -136,23 +152,40 @@ extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, 
             bt->tiles[i] = (int32_t)best_b[qbest];
         }
     }
+    // ---- problems sharing a Build: same genotypes, shape, gamma and tile
+    bt->owner.assign(count, -1);
+    for (int32_t i = 0; i < count; ++i) {
+        bt->owner[i] = i;
+        for (int32_t j = 0; j < i; ++j) {
+            const krr_batch_problem &a = problems[i], &b2 = problems[j];
+            if (bt->owner[j] == j && a.G == b2.G && a.n == b2.n && a.ldg == b2.ldg && a.gamma == b2.gamma &&
+                bt->tiles[i] == bt->tiles[j]) {
+                bt->owner[i] = j;
+                break;
+            }
+        }
+    }
     // ---- one context and stream per problem, warm-up run (allocations)
     bt->ctx.assign(count, nullptr);
     bt->streams.assign(count, nullptr);
     bt->join.assign(count, nullptr);
+    bt->built.assign(count, nullptr);
     if (cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&bt->capture, cudaStreamNonBlocking) != cudaSuccess)
         return fail(KRR_ECUDA, "event / stream creation failed");
     for (int32_t i = 0; i < count; ++i) {
         if (cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&bt->join[i], cudaEventDisableTiming) != cudaSuccess)
+            cudaEventCreateWithFlags(&bt->join[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&bt->built[i], cudaEventDisableTiming) != cudaSuccess)
             return fail(KRR_ECUDA, "stream creation failed");
         krr_options o = bt->opt;
         o.tile = bt->tiles[i];
         krr_status st = krr_create(&bt->ctx[i], &o, bt->streams[i]);
         if (st != KRR_OK) return fail(st, std::string("krr_batch_create: ") + krr_last_error(nullptr));
         reinterpret_cast<krr::Ctx *>(bt->ctx[i])->graph_mode = 1;
-        st = issue(bt->ctx[i], problems[i], m, p);
+        const int32_t ow = bt->owner[i];
+        st = (ow == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
+                       : issue(bt->ctx[i], problems[i], m, p, bt->ctx[ow], bt->built[ow]);
         if (st != KRR_OK)
             return fail(st, std::string("krr_batch_create: warm-up of problem ") + std::to_string(i) + ": " +
                                 krr_last_error(bt->ctx[i]));
@@ -172,7 +205,9 @@ extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, 
     std::string cmsg;
     for (int32_t i = 0; i < count && cst == KRR_OK; ++i) {
         cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
-        cst = issue(bt->ctx[i], problems[i], m, p);
+        const int32_t o = bt->owner[i];
+        cst = (o == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
+                       : issue(bt->ctx[i], problems[i], m, p, bt->ctx[o], bt->built[o]);
         if (cst != KRR_OK) cmsg = "problem " + std::to_string(i) + ": " + krr_last_error(bt->ctx[i]);
         cudaEventRecord(bt->join[i], bt->streams[i]);
         cudaStreamWaitEvent(bt->capture, bt->join[i], 0);
@@ -236,7 +271,13 @@ extern "C" void krr_batch_destroy(krr_batch *bt) {
     if (bt->capture) cudaStreamDestroy(bt->capture);
     if (bt->exec) cudaGraphExecDestroy(bt->exec);
     if (bt->graph) cudaGraphDestroy(bt->graph);
-    for (krr_ctx *c : bt->ctx) krr_destroy(c);
+    // contexts that read another's Build go first
+    for (size_t i = 0; i < bt->ctx.size(); ++i)
+        if (i < bt->owner.size() && bt->owner[i] != (int32_t)i) krr_destroy(bt->ctx[i]);
+    for (size_t i = 0; i < bt->ctx.size(); ++i)
+        if (i >= bt->owner.size() || bt->owner[i] == (int32_t)i) krr_destroy(bt->ctx[i]);
+    for (cudaEvent_t e : bt->built)
+        if (e) cudaEventDestroy(e);
     for (cudaStream_t s : bt->streams)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : bt->join)

@@ -201,6 +201,8 @@ struct Ctx {
     int rr = 0;
     int64_t rr_m = 0, rr_nc = 0;
     void *rr_state = nullptr;
+    // build products read from another context (adopt_build), not owned
+    int build_borrowed = 0;
 
     // graph mode: no host synchronisation or readback inside build / factor /
     // solve / predict, fixed refinement count (used by the batch runner)
@@ -291,6 +293,9 @@ krr_status store_rows_f32(Ctx *c, const float *src, int64_t n, int64_t cols, flo
 krr_status load_conf(Ctx *c, const float *src, int64_t n, int64_t nc, int64_t ld, int64_t rows_pad, float *dst);
 void free_factor(Ctx *c);
 void free_build(Ctx *c);
+// Shares src's build (genotypes, norms, kernel tiles, kernel statistics) with
+// dst, read-only, for several factorisations of one kernel matrix.
+krr_status adopt_build(Ctx *dst, const Ctx *src);
 // Buffers and shape fields of a build over n rows, packed operand rows of
 // m_pad columns (keep_d: keep the exact distances as well).
 krr_status prepare_build(Ctx *c, int64_t n, int64_t m_pad, int keep_d);

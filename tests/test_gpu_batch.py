@@ -1,7 +1,8 @@
 """Batched problems under one captured CUDA graph (cross-validation style:
 cohorts x lambdas of uneven size) against the CPU oracle, and run-to-run
-identity of the graph replays.  Y_test tolerance 1e-4 (as the other parity
-tests)."""
+identity of the graph replays.  Problems that pass the same genotype tensor
+with the same gamma share one Build (the kernel matrix does not depend on
+lambda).  Y_test tolerance 1e-4 (as the other parity tests)."""
 import numpy as np
 import pytest
 import torch
@@ -15,15 +16,17 @@ DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
 
 def test_batch_matches_oracle_and_replays():
     m, p = 300, 2
-    sizes = [(700, 0.1), (700, 1.0), (1300, 0.1), (1300, 0.01), (300, 0.1)]
-    problems, refs = [], []
+    sizes = [(700, 0.1), (700, 1.0), (1300, 0.1), (1300, 0.01), (1300, 1.0), (300, 0.1)]
+    problems, refs, cohorts = [], [], {}
     for idx, (n, lam) in enumerate(sizes):
         prob = inputs.problem(n, m, p, 120, seed=900 + n)  # same n -> same cohort data
         g, y, t = prob["G"].numpy(), prob["Y"].numpy(), prob["T"].numpy()
         _, a_ref, yt_ref = oracle.krr(1.0 / m, lam, g, y.astype(np.float64), t)
         refs.append((a_ref, yt_ref))
-        problems.append({"G": prob["G"].to(DEV), "Y": prob["Y"].to(DEV), "T": prob["T"].to(DEV),
-                         "gamma": 1.0 / m, "lam": lam})
+        if n not in cohorts:  # one device copy per cohort: its lambdas share the Build
+            cohorts[n] = {k: prob[k].to(DEV) for k in ("G", "Y", "T")}
+        c = cohorts[n]
+        problems.append({"G": c["G"], "Y": c["Y"], "T": c["T"], "gamma": 1.0 / m, "lam": lam})
     with KRRBatch(problems, ir_iters=3, autotune=True) as bt:
         res = bt.run()
         first = [yt.clone() for yt in bt.Yt]
