@@ -283,6 +283,8 @@ krr_status adopt_build(Ctx *dst, const Ctx *src) {
     KRR_CUDA_TRY(dst, cudaMemcpyAsync(dst->red + RED_KNORM2, src->red + RED_KNORM2,
                                       (RED_KBOUND - RED_KNORM2 + 1) * sizeof(double), cudaMemcpyDeviceToDevice,
                                       dst->stream));
+    // the tensor map of the shared genotypes, which this context's Predict reads
+    if (mixed(dst)) KRR_TRY(tc_bind_genotypes(dst));
     dst->built = true;
     dst->factored = false;
     return KRR_OK;

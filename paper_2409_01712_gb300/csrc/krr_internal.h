@@ -429,6 +429,9 @@ void launch_dot_f32(const float *a, const float *b, int64_t n, double *out, cuda
 krr_status tc_init(Ctx *c);
 void tc_free(Ctx *c);
 krr_status tc_build(Ctx *c);                 // distance GEMM + exp epilogue (E4M3)
+// (Re)makes the tensor map of the packed training genotypes (c->g8), which
+// Predict and the gradient read; tc_build does it itself.
+krr_status tc_bind_genotypes(Ctx *c);
 krr_status tc_trsm(Ctx *c, int64_t k);       // panel TRSM of column k (FP16 split)
 krr_status tc_update(Ctx *c, int64_t k);     // trailing update of step k
 // Predict partial products for weight columns A[:, 0:p] (p <= 32, leading

@@ -1336,9 +1336,14 @@ void tc_invalidate_factor_maps(Ctx *c) {
     if (c->tc) ((TcState *)c->tc)->factor_maps = false;
 }
 
+krr_status tc_bind_genotypes(Ctx *c) {
+    TcState *st = (TcState *)c->tc;
+    return make_map(c, &st->g_map, c->g8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, c->n_pad, c->m_pad);
+}
+
 krr_status tc_build(Ctx *c) {
     TcState *st = (TcState *)c->tc;
-    KRR_TRY(make_map(c, &st->g_map, c->g8, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, c->n_pad, c->m_pad));
+    KRR_TRY(tc_bind_genotypes(c));
     TcParams p = base_params(c);
     p.norms_a = c->norms;
     p.norms_b = c->norms;
