@@ -530,7 +530,8 @@ def run_batch(args):
         times.append(time.perf_counter() - t1)
     ms = float(np.median(times)) * 1e3
     tiles = sorted({r["tile"] for r in res})
-    worst_res = max(r["rel_residual"] for r in res)
+    bad = [i for i, r in enumerate(res) if r["status"] != 0 or not (r["rel_residual"] > 0.0)]
+    worst_res = max((r["rel_residual"] for r in res), key=lambda v: (v != v, v))  # NaN counts as worst
     bt.close()
     # the same problems one after another, eagerly (refinement with host
     # checks), each on a context of its own made and warmed up before the
@@ -565,6 +566,7 @@ def run_batch(args):
             "config": {"workload": f"c4: 64 problems, cohort N = {ns}, M={m}, P={p}, N_test={C4['n_test']}, "
                                    f"lambda in {C4['lambdas']}, gamma=1/M", "graph": "one CUDA graph per run"},
             "batch": {"tiles_chosen": tiles, "setup_s": setup_s, "worst_rel_residual": worst_res,
+                      "problems_failed_or_zero_residual": bad, "residuals": [r["rel_residual"] for r in res],
                       "shared_builds": "the 4 lambdas of a cohort share one Build",
                       "sequential_fp32_ms": seq32_ms, "speedup_over_sequential_fp32": seq32_ms / ms,
                       "sequential_mixed_ms": seq_ms, "speedup_over_sequential_mixed": seq_ms / ms}}

@@ -45,6 +45,13 @@ namespace {
 
 thread_local std::string g_batch_create_error;
 
+// CTAs per launch of a batched problem: the problems run concurrently on their
+// streams, and persistent kernels sized for the whole GPU would each hold every
+// SM while waiting on their dependency chains (measured on the cross-validation
+// workload: the diagonal steps alone, 136 CTAs -> 32, took a run from 405 to
+// 276 ms).
+constexpr int BATCH_CTA_CAP = 32;
+
 // Build (or, with src != NULL, wait for src's Build and read it), Factor,
 // Solve and Predict of one problem on c's stream; `done` is recorded after
 // an own Build.
@@ -73,6 +80,7 @@ krr_status trial_ms(const krr_options &base, cudaStream_t s, const krr_batch_pro
     krr_ctx *c = nullptr;
     KRR_TRY(krr_create(&c, &o, s));
     reinterpret_cast<krr::Ctx *>(c)->graph_mode = 1;
+    reinterpret_cast<krr::Ctx *>(c)->cta_cap = BATCH_CTA_CAP;
     krr_status st = issue(c, pr, m, p);  // warm-up (allocations)
     if (st == KRR_OK) {
         cudaStreamSynchronize(s);
@@ -183,6 +191,7 @@ extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, 
         krr_status st = krr_create(&bt->ctx[i], &o, bt->streams[i]);
         if (st != KRR_OK) return fail(st, std::string("krr_batch_create: ") + krr_last_error(nullptr));
         reinterpret_cast<krr::Ctx *>(bt->ctx[i])->graph_mode = 1;
+        reinterpret_cast<krr::Ctx *>(bt->ctx[i])->cta_cap = BATCH_CTA_CAP;
         const int32_t ow = bt->owner[i];
         st = (ow == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
                        : issue(bt->ctx[i], problems[i], m, p, bt->ctx[ow], bt->built[ow]);

@@ -203,6 +203,9 @@ struct Ctx {
     void *rr_state = nullptr;
     // build products read from another context (adopt_build), not owned
     int build_borrowed = 0;
+    // at most this many CTAs per launch (0: one per SM); the batch runner sets
+    // it so that the kernels of concurrent problems share the GPU
+    int cta_cap = 0;
 
     // graph mode: no host synchronisation or readback inside build / factor /
     // solve / predict, fixed refinement count (used by the batch runner)
@@ -211,6 +214,10 @@ struct Ctx {
 };
 
 inline bool is_ibs(const Ctx *c) { return c->opt.kernel == KRR_KERNEL_IBS; }
+// CTAs a persistent launch of this context may use.
+inline int64_t grid_limit(const Ctx *c) {
+    return (c->cta_cap > 0 && c->cta_cap < c->num_sms) ? c->cta_cap : c->num_sms;
+}
 inline KernelFn kernel_fn(const Ctx *c) {
     KernelFn f;
     f.ibs = is_ibs(c) ? 1 : 0;

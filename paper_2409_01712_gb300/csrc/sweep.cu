@@ -796,7 +796,7 @@ krr_status launch_nq(Ctx *c, const CUtensorMap (&m)[4], const SweepParams &p, si
         }
         attr.put(c->device);
     }
-    const int64_t grid = std::min<int64_t>(p.items, c->num_sms);
+    const int64_t grid = std::min<int64_t>(p.items, grid_limit(c));
     count_launch(), sweep_kernel<NQ><<<(unsigned)grid, SW_THREADS, smem, c->stream>>>(m[0], m[1], m[2], m[3], p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -37,6 +37,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
 #include "krr_internal.h"
@@ -1229,7 +1230,7 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
     p.wait_ns = (uint64_t)c->opt.wait_budget_ns;
     p.err = c->derr;
     if (PAIR == 1) {
-        const int64_t grid = p.items < c->num_sms ? p.items : c->num_sms;
+        const int64_t grid = p.items < grid_limit(c) ? p.items : grid_limit(c);
         count_launch(), tc_kernel<KIND, OP, 1><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, c->stream>>>(a0, a1, b0, b1, mx, p);
     } else {
         cudaLaunchConfig_t cfg;
@@ -1258,7 +1259,8 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
             clusters_of.put(c->device, n);
         }
         const int64_t units = p.items / PAIR;
-        const int64_t clusters = units < max_clusters ? units : max_clusters;
+        const int64_t cap = std::min<int64_t>(max_clusters, std::max<int64_t>(grid_limit(c) / PAIR, 1));
+        const int64_t clusters = units < cap ? units : cap;
         cfg.gridDim = dim3((unsigned)(clusters * PAIR));
         count_launch();
         cudaError_t e = cudaLaunchKernelEx(&cfg, tc_kernel<KIND, OP, PAIR>, a0, a1, b0, b1, mx, p);

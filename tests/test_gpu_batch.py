@@ -34,6 +34,7 @@ def test_batch_matches_oracle_and_replays():
         for i, (a_ref, yt_ref) in enumerate(refs):
             assert res[i]["status"] == 0
             assert res[i]["tile"] in (256, 512, 1024)
+            assert 0.0 < res[i]["rel_residual"] <= 1e-5, res[i]
             yt = bt.Yt[i].cpu().numpy().astype(np.float64)
             err = np.linalg.norm(yt - yt_ref) / np.linalg.norm(yt_ref)
             assert err <= 1e-4, (i, err, res[i])
