@@ -92,6 +92,7 @@ struct TcParams {
     // real / padded test rows; p / ldaw: weight columns in this launch and the
     // leading dimension of the weights.
     int64_t n, n_pad, n_test, test_rows, b, nt, k, m_pad, items, p, ldaw;
+    int lb;  // log2 b (the tile edge is a power of two)
     float gamma, lambda;
     const int32_t *norms_a, *norms_b;
     float *Kd;
@@ -360,9 +361,10 @@ __device__ __forceinline__ void update_tile_order(int64_t t, int64_t u, int64_t 
     const int64_t l = t - r0 * (r0 + 1) / 2;                    // index inside the band
     const int64_t full = h * r0;  // tiles of the band left of its diagonal block
     if (l < full) {
-        const int64_t cb = l / (h * UPD_BAND), l2 = l % (h * UPD_BAND);
+        const uint32_t hb = (uint32_t)(h * UPD_BAND);
+        const uint32_t cb = (uint32_t)l / hb, l2 = (uint32_t)l % hb;
         *ii = r0 + l2 / UPD_BAND;
-        *jj = cb * UPD_BAND + l2 % UPD_BAND;
+        *jj = (int64_t)cb * UPD_BAND + l2 % UPD_BAND;
     } else {
         int64_t a, bb;
         tri_decode(l - full, &a, &bb);
@@ -373,15 +375,21 @@ __device__ __forceinline__ void update_tile_order(int64_t t, int64_t u, int64_t 
 
 template <int OP>
 __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, const TileDesc *col_desc) {
+    // Every role decodes every item, so this runs in 32-bit shifts and masks
+    // (the tile edge b is a power of two; item counts stay below 2^31): a
+    // 64-bit division costs about a hundred dependent instructions.
     const int64_t b = p.b;
-    const int64_t sub_cols = b / BN, sub_per_tile = (b / BM) * sub_cols;
+    const int lsc = p.lb - 8, lst = 2 * p.lb - 15;  // log2 (b / BN), log2 ((b / BM) (b / BN))
+    const uint32_t ut = (uint32_t)t;
+    const int64_t t_tile = ut >> lst;
+    const uint32_t t_sub = ut & ((1u << lst) - 1u);
+    const int64_t t_sm = t_sub >> lsc, t_sn = t_sub & ((1u << lsc) - 1u);
     w.t = t;
     w.kind8 = 0;
     if (OP == OP_DIST || OP == OP_GRADK) {
-        const int64_t tile = t / sub_per_tile, sub = t % sub_per_tile;
-        tri_decode(tile, &w.i, &w.j);
-        w.sm = sub / sub_cols;
-        w.sn = sub % sub_cols;
+        tri_decode(t_tile, &w.i, &w.j);
+        w.sm = t_sm;
+        w.sn = t_sn;
         w.nph = 1;
         w.nkb = (int)(p.m_pad / SLAB);
         w.amap[0] = 0;
@@ -393,13 +401,13 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
         // the B rows (training rows).  The larger operand's block index varies
         // slowest, so the smaller operand is reused from L2 while each block of
         // the larger one is read from HBM once.
-        const int64_t nab = p.test_rows / BM, ncb = p.n_pad / BN;
+        const uint32_t nab = (uint32_t)(p.test_rows / BM), ncb = (uint32_t)(p.n_pad / BN);
         if (p.n_pad >= p.test_rows) {
-            w.j = t / nab;
-            w.i = t % nab;
+            w.j = ut / nab;
+            w.i = ut % nab;
         } else {
-            w.i = t / ncb;
-            w.j = t % ncb;
+            w.i = ut / ncb;
+            w.j = ut % ncb;
         }
         w.sm = w.sn = 0;
         w.nph = 1;
@@ -410,11 +418,10 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
         w.brow[0] = (int)(w.j * BN);
     } else if (OP == OP_TRSM) {
         const int64_t k = p.k;
-        w.i = k + 1 + t / sub_per_tile;
+        w.i = k + 1 + t_tile;
         w.j = k;
-        const int64_t sub = t % sub_per_tile;
-        w.sm = sub / sub_cols;
-        w.sn = sub % sub_cols;
+        w.sm = t_sm;
+        w.sn = t_sn;
         // Linv_kk is lower triangular: output columns < (sn + 1) * 256 need
         // K < (sn + 1) * 256 only.
         w.nkb = (int)((w.sn + 1) * BN * 2 / SLAB);
@@ -439,13 +446,12 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
         }
     } else {  // OP_UPDATE
         const int64_t k = p.k;
-        const int64_t tile = t / sub_per_tile, sub = t % sub_per_tile;
         int64_t ii, jj;
-        update_tile_order(tile, p.nt - k - 1, &ii, &jj);
+        update_tile_order(t_tile, p.nt - k - 1, &ii, &jj);
         w.i = k + 1 + ii;
         w.j = k + 1 + jj;
-        w.sm = sub / sub_cols;
-        w.sn = sub % sub_cols;
+        w.sm = t_sm;
+        w.sn = t_sn;
         w.nkb = (int)(b * 2 / SLAB);
         if (w.i == w.j && w.sn * BN >= (w.sm + 1) * BM) {
             w.nph = 0;  // strictly above the diagonal of a diagonal tile
@@ -464,15 +470,15 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
             w.nph = 1;
             w.nkb = (int)(b / SLAB);
             w.amap[0] = 4;
-            w.arow[0] = (int)(di.offset / b + w.sm * BM);
+            w.arow[0] = (int)((di.offset >> p.lb) + w.sm * BM);
             w.bmap[0] = 4;
-            w.brow[0] = (int)(dj.offset / b + w.sn * BN);
+            w.brow[0] = (int)((dj.offset >> p.lb) + w.sn * BN);
             return;
         }
         const int ahi_map = (di.prec == KRR_PREC_FP16) ? 0 : 1;
         const int bhi_map = (dj.prec == KRR_PREC_FP16) ? 0 : 1;
-        const int ahi_row = (int)((di.prec == KRR_PREC_FP16 ? di.offset / (2 * b) : (w.i - k - 1) * b) + w.sm * BM);
-        const int bhi_row = (int)((dj.prec == KRR_PREC_FP16 ? dj.offset / (2 * b) : (w.j - k - 1) * b) + w.sn * BN);
+        const int ahi_row = (int)((di.prec == KRR_PREC_FP16 ? di.offset >> (p.lb + 1) : (w.i - k - 1) * b) + w.sm * BM);
+        const int bhi_row = (int)((dj.prec == KRR_PREC_FP16 ? dj.offset >> (p.lb + 1) : (w.j - k - 1) * b) + w.sn * BN);
         const int alo_row = (int)((w.i - k - 1) * b + w.sm * BM);
         const int blo_row = (int)((w.j - k - 1) * b + w.sn * BN);
         int q = 0;
@@ -488,10 +494,11 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
 // one tile; CTA `rank` of the pair takes block 2 pm + rank.  Both CTAs of a
 // pair decode the same tile, phases and B rows.
 __device__ __forceinline__ int64_t pair_item(const TcParams &p, int64_t u, uint32_t rank) {
-    const int64_t sub_cols = p.b / BN, sub_per_tile = (p.b / BM) * sub_cols, pairs_per_tile = sub_per_tile / 2;
-    const int64_t tile = u / pairs_per_tile, pu = u % pairs_per_tile;
-    const int64_t sn = pu % sub_cols, pm = pu / sub_cols;
-    return tile * sub_per_tile + (2 * pm + rank) * sub_cols + sn;
+    const int lsc = p.lb - 8, lpt = 2 * p.lb - 16;  // log2 (b / BN), log2 (pairs per tile)
+    const uint32_t uu = (uint32_t)u;
+    const uint32_t tile = uu >> lpt, pu = uu & ((1u << lpt) - 1u);
+    const uint32_t sn = pu & ((1u << lsc) - 1u), pm = pu >> lsc;
+    return ((int64_t)tile << (lpt + 1)) + (int64_t)(((2u * pm + rank) << lsc) + sn);
 }
 
 // ---------------------------------------------------------------------------
@@ -1283,6 +1290,8 @@ TcParams base_params(Ctx *c) {
     memset(&p, 0, sizeof(p));
     p.n = c->n;
     p.b = c->b;
+    p.lb = 0;
+    while ((int64_t)1 << p.lb < c->b) ++p.lb;
     p.nt = c->nt;
     p.m_pad = c->m_pad;
     p.gamma = (float)c->gamma;
