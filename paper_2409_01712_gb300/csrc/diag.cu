@@ -680,7 +680,7 @@ krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT
     cudaStream_t s = c->stream;
     KRR_CUDA_TRY(c, cudaMemsetAsync(ctr, 0, (size_t)diag_counter_count(b) * sizeof(int), s));
     KRR_CUDA_TRY(c, cudaMemsetAsync(X, 0, (size_t)b * b * sizeof(float), s));
-    const int64_t grid = std::min<int64_t>(grid_limit(c), std::max<int64_t>(p.NB * (p.NB + 1) / 2, 1));
+    const int64_t grid = std::min<int64_t>(grid_limit(c, GL_DIAG), std::max<int64_t>(p.NB * (p.NB + 1) / 2, 1));
     count_launch(), diag_kernel<<<(unsigned)grid, DT, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -47,10 +47,22 @@ thread_local std::string g_batch_create_error;
 
 // CTAs per launch of a batched problem: the problems run concurrently on their
 // streams, and persistent kernels sized for the whole GPU would each hold every
-// SM while waiting on their dependency chains (measured on the cross-validation
-// workload: the diagonal steps alone, 136 CTAs -> 32, took a run from 405 to
-// 276 ms).
+// SM while waiting on their dependency chains.  Measured on the
+// cross-validation workload (64 problems, N up to 16384): no cap 408 ms per
+// run; 32 CTAs for every kernel 220 ms; per class as below 183-185 ms (the
+// diagonal step, mostly waiting CTAs, at 12; the sweeps at 16; the tensor-core
+// kernels, which keep their CTAs busy, at 64).
 constexpr int BATCH_CTA_CAP = 32;
+constexpr int BATCH_CAP_DIAG = 12, BATCH_CAP_SWEEP = 16, BATCH_CAP_PAIR = 64, BATCH_CAP_SINGLE = 64;
+
+void set_batch_caps(krr_ctx *c) {
+    krr::Ctx *cc = reinterpret_cast<krr::Ctx *>(c);
+    cc->cta_cap = BATCH_CTA_CAP;
+    cc->cta_caps[krr::GL_DIAG] = BATCH_CAP_DIAG;
+    cc->cta_caps[krr::GL_SWEEP] = BATCH_CAP_SWEEP;
+    cc->cta_caps[krr::GL_PAIR] = BATCH_CAP_PAIR;
+    cc->cta_caps[krr::GL_SINGLE] = BATCH_CAP_SINGLE;
+}
 
 // Build (or, with src != NULL, wait for src's Build and read it), Factor,
 // Solve and Predict of one problem on c's stream; `done` is recorded after
@@ -80,7 +92,7 @@ krr_status trial_ms(const krr_options &base, cudaStream_t s, const krr_batch_pro
     krr_ctx *c = nullptr;
     KRR_TRY(krr_create(&c, &o, s));
     reinterpret_cast<krr::Ctx *>(c)->graph_mode = 1;
-    reinterpret_cast<krr::Ctx *>(c)->cta_cap = BATCH_CTA_CAP;
+    set_batch_caps(c);
     krr_status st = issue(c, pr, m, p);  // warm-up (allocations)
     if (st == KRR_OK) {
         cudaStreamSynchronize(s);
@@ -191,7 +203,7 @@ extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, 
         krr_status st = krr_create(&bt->ctx[i], &o, bt->streams[i]);
         if (st != KRR_OK) return fail(st, std::string("krr_batch_create: ") + krr_last_error(nullptr));
         reinterpret_cast<krr::Ctx *>(bt->ctx[i])->graph_mode = 1;
-        reinterpret_cast<krr::Ctx *>(bt->ctx[i])->cta_cap = BATCH_CTA_CAP;
+        set_batch_caps(bt->ctx[i]);
         const int32_t ow = bt->owner[i];
         st = (ow == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
                        : issue(bt->ctx[i], problems[i], m, p, bt->ctx[ow], bt->built[ow]);

@@ -203,9 +203,11 @@ struct Ctx {
     void *rr_state = nullptr;
     // build products read from another context (adopt_build), not owned
     int build_borrowed = 0;
-    // at most this many CTAs per launch (0: one per SM); the batch runner sets
-    // it so that the kernels of concurrent problems share the GPU
+    // at most this many CTAs per launch (0: one per SM), in general and per
+    // kernel class (GL_*; 0: the general cap); the batch runner sets them so
+    // that the kernels of concurrent problems share the GPU
     int cta_cap = 0;
+    int cta_caps[6] = {0, 0, 0, 0, 0, 0};
 
     // graph mode: no host synchronisation or readback inside build / factor /
     // solve / predict, fixed refinement count (used by the batch runner)
@@ -214,9 +216,15 @@ struct Ctx {
 };
 
 inline bool is_ibs(const Ctx *c) { return c->opt.kernel == KRR_KERNEL_IBS; }
-// CTAs a persistent launch of this context may use.
-inline int64_t grid_limit(const Ctx *c) {
-    return (c->cta_cap > 0 && c->cta_cap < c->num_sms) ? c->cta_cap : c->num_sms;
+// Kernel classes with a CTA cap of their own: the diagonal step (a dependency
+// chain: most of its CTAs wait), the substitution sweeps, the refinement
+// residual, the CTA-pair kernels (panel solve, trailing update) and the other
+// tensor-core kernels (build, predict, gradient).
+enum GridClass { GL_DEFAULT = 0, GL_DIAG = 1, GL_SWEEP = 2, GL_RESIDUAL = 3, GL_PAIR = 4, GL_SINGLE = 5 };
+// CTAs a persistent launch of this class may use.
+inline int64_t grid_limit(const Ctx *c, int cls = GL_DEFAULT) {
+    const int cap = c->cta_caps[cls] > 0 ? c->cta_caps[cls] : c->cta_cap;
+    return (cap > 0 && cap < c->num_sms) ? cap : c->num_sms;
 }
 inline KernelFn kernel_fn(const Ctx *c) {
     KernelFn f;

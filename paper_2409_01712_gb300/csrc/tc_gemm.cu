@@ -339,10 +339,10 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
 // Every role calls this with the same arguments, so all agree on the number
 // of slabs of every block (zero for skipped blocks).
 // ---------------------------------------------------------------------------
-// Descriptor of factor tile (k + 1 + e, k): staged in shared memory, or read
-// from the global table (pair mode, whose shared memory holds a fifth stage).
-__device__ __forceinline__ TileDesc col_tile(const TcParams &p, const TileDesc *col_desc, int64_t e) {
-    return col_desc ? col_desc[e] : p.ltab[off_index(p.k + 1 + e, p.k)];
+// Descriptor of factor tile (k + 1 + e, k) (the trailing update runs in pair
+// mode only, whose shared memory has no room to stage the column's table).
+__device__ __forceinline__ TileDesc col_tile(const TcParams &p, int64_t e) {
+    return p.ltab[off_index(p.k + 1 + e, p.k)];
 }
 
 // Order of the trailing-update target tiles (ii, jj), jj <= ii, of one step:
@@ -374,7 +374,7 @@ __device__ __forceinline__ void update_tile_order(int64_t t, int64_t u, int64_t 
 }
 
 template <int OP>
-__device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, const TileDesc *col_desc) {
+__device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w) {
     // Every role decodes every item, so this runs in 32-bit shifts and masks
     // (the tile edge b is a power of two; item counts stay below 2^31): a
     // 64-bit division costs about a hundred dependent instructions.
@@ -463,8 +463,8 @@ __device__ __forceinline__ void decode(const TcParams &p, int64_t t, Work &w, co
         // phase on their stored bytes (a stage holds 128 of their columns);
         // otherwise FP16 tiles are read from the pool directly, FP32 tiles
         // use the hi/lo split, E4M3 tiles their FP16 shadow in the hi panel.
-        const TileDesc di = col_tile(p, col_desc, w.i - k - 1);
-        const TileDesc dj = col_tile(p, col_desc, w.j - k - 1);
+        const TileDesc di = col_tile(p, w.i - k - 1);
+        const TileDesc dj = col_tile(p, w.j - k - 1);
         if (di.prec == KRR_PREC_E4M3 && dj.prec == KRR_PREC_E4M3) {
             w.kind8 = 1;
             w.nph = 1;
@@ -612,8 +612,7 @@ __device__ __forceinline__ double grad_half(const TcParams &p, const Work &w, ui
 
 template <int OP>
 __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint32_t tacc, int row, int half,
-                                         int32_t *nb_s, float *aw_s, double *red_s,
-                                         const TileDesc *col_desc) {
+                                         int32_t *nb_s, float *aw_s, double *red_s) {
     const int64_t b = p.b;
     const int ch0 = half * CH_PER_HALF;
     if (OP == OP_DIST) {
@@ -738,7 +737,7 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const Work &w, uint3
         }
     } else {  // OP_UPDATE
         const int64_t k = p.k;
-        const float sc = 1.f / (col_tile(p, col_desc, w.i - k - 1).scale * col_tile(p, col_desc, w.j - k - 1).scale);
+        const float sc = 1.f / (col_tile(p, w.i - k - 1).scale * col_tile(p, w.j - k - 1).scale);
         const int64_t lr = w.sm * BM + row;
         const bool diag = (w.i == w.j);
         const float *cin32 = nullptr;
@@ -910,10 +909,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     double *red_s = reinterpret_cast<double *>(tmem_slot + 2);
     int32_t *nb_s = reinterpret_cast<int32_t *>(red_s + 16);
     float *aw_s = reinterpret_cast<float *>(nb_s + BN);
-    // trailing update: descriptors of factor column k, staged once (aw_s is
-    // unused by that op; 32 KB hold 2048 descriptors); pair mode reads them
-    // from the global table instead
-    TileDesc *col_desc = (PAIR == 2) ? nullptr : reinterpret_cast<TileDesc *>(aw_s);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = (PAIR == 2) ? cluster_rank() : 0u;
@@ -960,10 +955,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (OP == OP_UPDATE)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mX)) : "memory");
     }
-    if (OP == OP_UPDATE && col_desc) {
-        const int64_t ncol = p.nt - p.k - 1;
-        for (int64_t e = threadIdx.x; e < ncol; e += blockDim.x) col_desc[e] = p.ltab[off_index(p.k + 1 + e, p.k)];
-    }
     tmem_fence_before();
     __syncthreads();
     if (PAIR == 2) cluster_sync();  // both CTAs' barriers and TMEM are ready before any pair traffic
@@ -982,7 +973,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int64_t u = ustart; u < nunits && ok; u += ustep) {
                 Work w;
-                decode<OP>(p, unit_item(u), w, col_desc);
+                decode<OP>(p, unit_item(u), w);
                 for (int q = 0; q < w.nph && ok; ++q) {
                     for (int kb = 0; kb < w.nkb; ++kb) {
                         if (!wait_bar(&empty[s], ph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
@@ -1038,7 +1029,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool any = false;
             for (int64_t u = ustart; u < nunits && ok; u += ustep) {
                 Work w;
-                decode<OP>(p, unit_item(u), w, col_desc);
+                decode<OP>(p, unit_item(u), w);
                 const int total = w.nph * w.nkb;
                 if (total == 0) continue;
                 if (!wait_bar(&tempty[acc], aph ^ 1, budget, abort_flag, p.err)) { ok = false; break; }
@@ -1086,7 +1077,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         uint32_t aph = 0;
         for (int64_t u = ustart; u < nunits; u += ustep) {
             Work w;
-            decode<OP>(p, unit_item(u), w, col_desc);
+            decode<OP>(p, unit_item(u), w);
             if (w.nph * w.nkb == 0) continue;
             // pair mode, FP16 target: the update goes back box by box as a TMA
             // reduce-add of its FP16 value (the L2 adds it to the target; the
@@ -1107,8 +1098,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             tmem_fence_after();
             const uint32_t tacc = tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(acc * BN);
             if (cstage) {
-                const float nsc = -1.f / (col_tile(p, col_desc, w.i - p.k - 1).scale *
-                                          col_tile(p, col_desc, w.j - p.k - 1).scale);
+                const float nsc = -1.f / (col_tile(p, w.i - p.k - 1).scale * col_tile(p, w.j - p.k - 1).scale);
                 for (int bx = 0; bx < BN / 64; ++bx) {
                     const int bi = bx & 1;
                     // buffer bi is free once the reduce that last used it has
@@ -1129,7 +1119,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                 }
             } else {
-                epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s, col_desc);
+                epilogue<OP>(p, w, tacc, row, half, nb_s, aw_s, red_s);
             }
             tmem_fence_before();
             __syncwarp();
@@ -1237,7 +1227,8 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
     p.wait_ns = (uint64_t)c->opt.wait_budget_ns;
     p.err = c->derr;
     if (PAIR == 1) {
-        const int64_t grid = p.items < grid_limit(c) ? p.items : grid_limit(c);
+        const int64_t gl = grid_limit(c, GL_SINGLE);
+        const int64_t grid = p.items < gl ? p.items : gl;
         count_launch(), tc_kernel<KIND, OP, 1><<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, c->stream>>>(a0, a1, b0, b1, mx, p);
     } else {
         cudaLaunchConfig_t cfg;
@@ -1266,7 +1257,7 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
             clusters_of.put(c->device, n);
         }
         const int64_t units = p.items / PAIR;
-        const int64_t cap = std::min<int64_t>(max_clusters, std::max<int64_t>(grid_limit(c) / PAIR, 1));
+        const int64_t cap = std::min<int64_t>(max_clusters, std::max<int64_t>(grid_limit(c, GL_PAIR) / PAIR, 1));
         const int64_t clusters = units < cap ? units : cap;
         cfg.gridDim = dim3((unsigned)(clusters * PAIR));
         count_launch();

@@ -1473,7 +1473,7 @@ krr_status run_ts(Ctx *c, int job, float *rhs, float *out, int64_t p) {
         KRR_TRY(map_f16(c, &mvo, c->ts_v1, 2 * sp.np, c->n_pad, 2 * sp.np));
         KRR_CUDA_TRY(c, cudaMemsetAsync(flags, 0, (size_t)ts_flag_count(c) * sizeof(int), c->stream));
         const size_t smem = ts_smem_bytes(stages, sp.stage_bytes);
-        const int64_t grid = std::min<int64_t>(sp.items, grid_limit(c));
+        const int64_t grid = std::min<int64_t>(sp.items, grid_limit(c, GL_SWEEP));
         count_launch(), tcsweep_kernel<<<(unsigned)grid, TS_THREADS, smem, c->stream>>>(mp, mw, mlh, mll, mvi, mvo, sp);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
@@ -1599,7 +1599,7 @@ krr_status tc_residual(Ctx *c, const float *y, const float *a, double *r, int64_
         rp.err = c->derr;
         KRR_CUDA_TRY(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
         const size_t smem = rs_smem_bytes(rp.b_bytes);
-        const int64_t grid = std::min<int64_t>(rp.items, grid_limit(c));
+        const int64_t grid = std::min<int64_t>(rp.items, grid_limit(c, GL_RESIDUAL));
         count_launch(), tcres_kernel<<<(unsigned)grid, RS_THREADS, smem, c->stream>>>(mk128, mk64, ma, rp);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) {
