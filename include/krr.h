@@ -92,6 +92,10 @@ typedef struct krr_options {
     int32_t prec_rule;       /* KRR_RULE_LAMBDA (default) or KRR_RULE_KNORM; eps is the
                                 threshold of either rule */
     int32_t kernel;          /* KRR_KERNEL_GAUSSIAN (default) or KRR_KERNEL_IBS */
+    int32_t lookahead;       /* 1: the diagonal step of column k + 1 overlaps the trailing
+                                update of step k on a second stream (mixed mode, FP32
+                                diagonal step; default 1), 0: strictly in sequence */
+    int32_t reserved;        /* must be 0 */
 } krr_options;
 
 /* Per-call reports; valid when the call returns. */

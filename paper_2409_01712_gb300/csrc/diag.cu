@@ -649,7 +649,7 @@ int64_t diag_counter_count(int64_t b) {
 // the FP16 split of Linv when present).  The counters `ctr` hold
 // diag_counter_count(b) ints.
 krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT, __half *hi, __half *lo,
-                                float *tmp, int *ctr, double *minpiv) {
+                                float *tmp, int *ctr, double *minpiv, cudaStream_t s, int64_t cta_cap) {
     const int64_t b = c->b;
     if (b % DB != 0 || b / DB > DMAX_NB) {
         c->last_error = "diagonal step: tile edge must be a multiple of 64 and at most 4096";
@@ -677,10 +677,11 @@ krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT
     p.minpiv = minpiv;
     p.err = c->derr;
     p.wait_ns = (uint64_t)c->opt.wait_budget_ns;
-    cudaStream_t s = c->stream;
     KRR_CUDA_TRY(c, cudaMemsetAsync(ctr, 0, (size_t)diag_counter_count(b) * sizeof(int), s));
     KRR_CUDA_TRY(c, cudaMemsetAsync(X, 0, (size_t)b * b * sizeof(float), s));
-    const int64_t grid = std::min<int64_t>(grid_limit(c, GL_DIAG), std::max<int64_t>(p.NB * (p.NB + 1) / 2, 1));
+    int64_t gl = grid_limit(c, GL_DIAG);
+    if (cta_cap > 0 && cta_cap < gl) gl = cta_cap;
+    const int64_t grid = std::min<int64_t>(gl, std::max<int64_t>(p.NB * (p.NB + 1) / 2, 1));
     count_launch(), diag_kernel<<<(unsigned)grid, DT, 0, s>>>(p);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

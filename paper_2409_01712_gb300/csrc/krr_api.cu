@@ -3,6 +3,7 @@
 // (Alg. 3: tile Cholesky + solves + refinement) and Predict (Alg. 4).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -47,8 +48,9 @@ struct ProfState {
     }
 };
 
-// Opens a timed region of class cls; returns its index or -1 when off.
-int prof_begin(Ctx *c, int cls) {
+// Opens a timed region of class cls on stream s (nullptr: the context's
+// stream); returns its index or -1 when off.
+int prof_begin(Ctx *c, int cls, cudaStream_t s = nullptr) {
     if (!c->prof_on || !c->prof) return -1;
     ProfState *ps = (ProfState *)c->prof;
     ProfRec r;
@@ -56,18 +58,18 @@ int prof_begin(Ctx *c, int cls) {
     r.a = ps->take();
     r.b = ps->take();
     r.flops = r.bytes = 0.0;
-    cudaEventRecord(r.a, c->stream);
+    cudaEventRecord(r.a, s ? s : c->stream);
     ps->recs.push_back(r);
     return (int)ps->recs.size() - 1;
 }
 
-void prof_end(Ctx *c, int idx, double flops, double bytes) {
+void prof_end(Ctx *c, int idx, double flops, double bytes, cudaStream_t s = nullptr) {
     if (idx < 0 || !c->prof) return;
     ProfState *ps = (ProfState *)c->prof;
     ProfRec &r = ps->recs[idx];
     r.flops = flops;
     r.bytes = bytes;
-    cudaEventRecord(r.b, c->stream);
+    cudaEventRecord(r.b, s ? s : c->stream);
 }
 
 }  // namespace
@@ -480,6 +482,8 @@ void krr_default_options(krr_options *opt) {
     opt->wait_budget_ns = 2000000000LL;
     opt->prec_rule = KRR_RULE_LAMBDA;
     opt->kernel = KRR_KERNEL_GAUSSIAN;
+    opt->lookahead = 1;
+    opt->reserved = 0;
 }
 
 krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
@@ -511,6 +515,10 @@ krr_status krr_create(krr_ctx **out, const krr_options *opt, void *stream) {
     }
     if (o.kernel != KRR_KERNEL_GAUSSIAN && o.kernel != KRR_KERNEL_IBS) {
         g_create_error = "unknown kernel function";
+        return KRR_EINVAL;
+    }
+    if ((o.lookahead != 0 && o.lookahead != 1) || o.reserved != 0) {
+        g_create_error = "lookahead must be 0 or 1 and reserved 0";
         return KRR_EINVAL;
     }
     krr_ctx *c = new (std::nothrow) krr_ctx();
@@ -583,6 +591,12 @@ void krr_destroy(krr_ctx *c) {
     dev_free(&c->conf);
     dev_free(&c->tconf);
     if (c->stage) cudaFree(c->stage);
+    if (c->la_stream) {
+        cudaStreamSynchronize(c->la_stream);
+        cudaStreamDestroy(c->la_stream);
+    }
+    for (cudaEvent_t &e : c->la_ev)
+        if (e) cudaEventDestroy(e);
     tc_free(c);
     rr_free(c);
     if (c->prof) {
@@ -680,6 +694,73 @@ krr_status krr_build_kernel_conf(krr_ctx *c, const int8_t *G, int64_t n, int64_t
     return build_common(c, G, n, m, ldg, C, nc, ldc, gamma);
 }
 
+namespace {
+
+// Lookahead of the factorisation (mixed mode, outside graph capture, FP32
+// diagonal step).  Per step, the diagonal step of the next column runs on
+// `ctas` CTAs beside the first `tiles` target tiles of the update (after its
+// diagonal target) on the other SMs.  The choice comes from a model of the
+// two kernels measured on GB300 (152 SMs) while they share the GPU:
+//   diagonal step on R CTAs: T(R) = a + c / R, a chain of b / 64 block
+//     factorisations (a = 600 us at b = 1024, proportional to b) plus work
+//     spread over the CTAs (c = 13 CTA-ms at b = 1024, proportional to b^3);
+//     on 16 / 24 / 32 / 48 CTAs it took 1.42 / 1.11 / 0.95 / 0.81 ms, on 136
+//     alone 0.59 ms;
+//   trailing update: about 8.3 TF/s per SM (2 b^3 per off-diagonal target).
+// The plan minimises the step's time: T(R) while the update fits beside the
+// diagonal step, else T(R) plus the rest of the update on every SM.  The
+// update part beside it is sized 30 % above T(R): if it ended first, the
+// other SMs would idle until the diagonal step ends, while if it ends last
+// only the diagonal step's R SMs wait.  At N = 131072 the factorisation
+// takes 660 ms this way and 697 ms in sequence; fixed R = 24 and R = 48 gave
+// the same 658-662 ms, R = 8 690 ms.
+struct LookaheadPlan {
+    bool on = false;
+    int64_t ctas = 0, tiles = 0;
+};
+
+bool lookahead_enabled(const Ctx *c) {
+    return c->opt.lookahead && mixed(c) && !c->graph_mode && !c->opt.diag_fp64 && c->nt >= 3 && c->num_sms >= 32;
+}
+
+LookaheadPlan lookahead_plan(const Ctx *c, int64_t k) {
+    LookaheadPlan pl;
+    const int64_t u = c->nt - k - 1;
+    const int64_t tiles = u * (u + 1) / 2;
+    if (tiles < 2) return pl;
+    const double bd = (double)c->b, rel = bd / 1024.0;
+    const double a_us = 600.0 * rel, c_us = 13000.0 * rel * rel * rel;
+    const double tile_sm_us = 2.0 * bd * bd * bd / 8.3e12 * 1e6;  // SM-microseconds per target tile
+    const double work = (double)(tiles - 1) * tile_sm_us;
+    const int64_t sms = c->num_sms;
+    static const int64_t cand[] = {16, 20, 24, 32, 48, 64, 96, 128};
+    double best = 1e300;
+    for (int64_t r : cand) {
+        if (r + 16 > sms) break;
+        const double td = a_us + c_us / (double)r;
+        const double beside = (double)(sms - r) * td;  // SM-us of update beside the diagonal step
+        const double t = (work <= beside) ? td : td + (work - beside) / (double)sms;
+        if (t < best) {
+            best = t;
+            pl.ctas = r;
+            pl.tiles = std::min<int64_t>(tiles - 1, (int64_t)std::ceil(1.3 * beside / tile_sm_us));
+        }
+    }
+    pl.on = pl.ctas > 0 && pl.tiles > 0;
+    return pl;
+}
+
+krr_status ensure_lookahead_stream(Ctx *c) {
+    if (c->la_stream) return KRR_OK;
+    int lo = 0, hi = 0;
+    KRR_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    KRR_CUDA_TRY(c, cudaStreamCreateWithPriority(&c->la_stream, cudaStreamNonBlocking, hi));
+    for (cudaEvent_t &e : c->la_ev) KRR_CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return KRR_OK;
+}
+
+}  // namespace
+
 krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
     if (!c) return KRR_EINVAL;
     if (!c->built) {
@@ -734,11 +815,22 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
     launch_factor_init(c);
     KRR_TRY(check_launch(c, "factor init"));
     const double bd = (double)b;
+    // Lookahead: the diagonal step of column k + 1 needs only the diagonal
+    // target of step k's trailing update.  That tile is updated first; the
+    // diagonal step then runs on a second stream on la_ctas CTAs while the
+    // update goes on with the other SMs, and the rest of the update takes
+    // every SM again once the diagonal step is done.
+    const bool la_on = mx && lookahead_enabled(c);
+    if (la_on) KRR_TRY(ensure_lookahead_stream(c));
+    bool diag_ahead = false;  // diagonal step k already issued by step k - 1
     for (int64_t k = 0; k < nt; ++k) {
-        int pr = prof_begin(c, KRR_PROF_DIAG);
-        KRR_TRY(diag_step(c, k));
-        prof_end(c, pr, 2.0 * bd * bd * bd / 3.0, 0.0);
-        KRR_TRY(check_launch(c, "diagonal step"));
+        if (!diag_ahead) {
+            int pr = prof_begin(c, KRR_PROF_DIAG);
+            KRR_TRY(diag_step(c, k));
+            prof_end(c, pr, 2.0 * bd * bd * bd / 3.0, 0.0);
+            KRR_TRY(check_launch(c, "diagonal step"));
+        }
+        diag_ahead = false;
         if (k + 1 >= nt) break;
         const double u = (double)(nt - k - 1);
         // algorithmic work: triangular solve b^3 per panel tile; update 2 b^3
@@ -746,18 +838,44 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
         const double trsm_flops = u * bd * bd * bd;
         const double upd_flops = (u * (u - 1) / 2.0) * 2.0 * bd * bd * bd + u * bd * bd * bd;
         if (mx) {
-            pr = prof_begin(c, KRR_PROF_TRSM);
+            int pr = prof_begin(c, KRR_PROF_TRSM);
             KRR_TRY(tc_trsm(c, k));
             prof_end(c, pr, trsm_flops, 0.0);
             pr = prof_begin(c, KRR_PROF_CAST);
             launch_column_cast(c, k);
             prof_end(c, pr, 0.0, u * bd * bd * (4.0 + 2.0));
             KRR_TRY(check_launch(c, "column cast"));
-            pr = prof_begin(c, KRR_PROF_UPDATE);
-            KRR_TRY(tc_update(c, k));
-            prof_end(c, pr, upd_flops, 0.0);
+            const int64_t tiles = (nt - k - 1) * (nt - k) / 2;
+            const LookaheadPlan la = la_on ? lookahead_plan(c, k) : LookaheadPlan();
+            if (la.on) {
+                // the diagonal target (k + 1, k + 1), b^3 flops
+                pr = prof_begin(c, KRR_PROF_UPDATE);
+                KRR_TRY(tc_update(c, k, 0, 1, 0));
+                prof_end(c, pr, bd * bd * bd, 0.0);
+                KRR_CUDA_TRY(c, cudaEventRecord(c->la_ev[0], s));
+                KRR_CUDA_TRY(c, cudaStreamWaitEvent(c->la_stream, c->la_ev[0], 0));
+                pr = prof_begin(c, KRR_PROF_DIAG, c->la_stream);
+                KRR_TRY(diag_step(c, k + 1, c->la_stream, la.ctas));
+                prof_end(c, pr, 2.0 * bd * bd * bd / 3.0, 0.0, c->la_stream);
+                KRR_TRY(check_launch(c, "diagonal step"));
+                KRR_CUDA_TRY(c, cudaEventRecord(c->la_ev[1], c->la_stream));
+                // the targets that run beside the diagonal step, then the
+                // rest (one timed region: it includes any wait for the
+                // diagonal step)
+                const int64_t side = std::min<int64_t>(tiles - 1, la.tiles);
+                pr = prof_begin(c, KRR_PROF_UPDATE);
+                KRR_TRY(tc_update(c, k, 1, side, c->num_sms - la.ctas));
+                KRR_CUDA_TRY(c, cudaStreamWaitEvent(s, c->la_ev[1], 0));
+                if (1 + side < tiles) KRR_TRY(tc_update(c, k, 1 + side, tiles - 1 - side, 0));
+                prof_end(c, pr, upd_flops - bd * bd * bd, 0.0);
+                diag_ahead = true;
+            } else {
+                pr = prof_begin(c, KRR_PROF_UPDATE);
+                KRR_TRY(tc_update(c, k));
+                prof_end(c, pr, upd_flops, 0.0);
+            }
         } else {
-            pr = prof_begin(c, KRR_PROF_TRSM);
+            int pr = prof_begin(c, KRR_PROF_TRSM);
             launch_trsm_simt(c, k);
             prof_end(c, pr, trsm_flops, 0.0);
             KRR_TRY(check_launch(c, "trsm"));

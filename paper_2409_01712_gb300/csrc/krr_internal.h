@@ -209,6 +209,12 @@ struct Ctx {
     int cta_cap = 0;
     int cta_caps[6] = {0, 0, 0, 0, 0, 0};
 
+    // lookahead of the factorisation: the diagonal step of column k + 1 runs
+    // on this second stream while the trailing update of step k continues
+    // (created on the first factorisation that uses it)
+    cudaStream_t la_stream = nullptr;
+    cudaEvent_t la_ev[2] = {nullptr, nullptr};
+
     // graph mode: no host synchronisation or readback inside build / factor /
     // solve / predict, fixed refinement count (used by the batch runner)
     int graph_mode = 0;
@@ -374,10 +380,12 @@ void launch_predict_simt(Ctx *c, const float *tf, const int32_t *tn, int64_t n_t
 // diag_counter_count(b) ints, minpiv b / 64 doubles.
 int64_t diag_counter_count(int64_t b);
 krr_status launch_diag_dataflow(Ctx *c, int64_t k, float *W, float *X, float *XT, __half *hi, __half *lo,
-                                float *tmp, int *ctr, double *minpiv);
+                                float *tmp, int *ctr, double *minpiv, cudaStream_t s, int64_t cta_cap);
 
 // Diagonal step: in-place Cholesky of Wd tile k and its inverse into Linv.
-krr_status diag_step(Ctx *c, int64_t k);
+// Factor and inverse of diagonal tile k, on stream s (nullptr: the context's
+// stream) with at most cta_cap CTAs for the dataflow kernel (0: class limit).
+krr_status diag_step(Ctx *c, int64_t k, cudaStream_t s = nullptr, int64_t cta_cap = 0);
 
 // Number of max |L_ik| partials per panel tile written by the tensor-core
 // panel solve (one per 128 x 256 output block).
@@ -448,7 +456,10 @@ krr_status tc_build(Ctx *c);                 // distance GEMM + exp epilogue (E4
 // Predict and the gradient read; tc_build does it itself.
 krr_status tc_bind_genotypes(Ctx *c);
 krr_status tc_trsm(Ctx *c, int64_t k);       // panel TRSM of column k (FP16 split)
-krr_status tc_update(Ctx *c, int64_t k);     // trailing update of step k
+// Trailing update of step k over target tiles [tile0, tile0 + tiles) of the
+// step's order (tile 0 is the diagonal target (k + 1, k + 1); tiles < 0: to
+// the end), on at most cta_cap CTAs (0: the class limit).
+krr_status tc_update(Ctx *c, int64_t k, int64_t tile0 = 0, int64_t tiles = -1, int64_t cta_cap = 0);
 // Predict partial products for weight columns A[:, 0:p] (p <= 32, leading
 // dimension lda): part is (n_pad / 128) x rows_pad x p.
 // With kshift the partials are of (K - c) A, c = *kshift (the reduction adds

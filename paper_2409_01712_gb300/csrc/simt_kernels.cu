@@ -781,9 +781,9 @@ __global__ void min_pivot_kernel(const double *mp, int n, DevErrors *err) {
     err->min_pivot = m;
 }
 
-krr_status diag_step(Ctx *c, int64_t k) {
+krr_status diag_step(Ctx *c, int64_t k, cudaStream_t s, int64_t cta_cap) {
     const int64_t b = c->b, bb = b * b;
-    cudaStream_t s = c->stream;
+    if (!s) s = c->stream;
     float *wd = c->Wd + k * bb;
     float *linv = c->Linv + k * bb;
     const int nq = (int)(b / DNB);
@@ -805,7 +805,7 @@ krr_status diag_step(Ctx *c, int64_t k) {
         // one dataflow launch: factor, inverse, transpose and FP16 split
         KRR_TRY(launch_diag_dataflow(c, k, wd, linv, c->LinvT + k * bb, c->Linv_hi ? c->Linv_hi + k * bb : nullptr,
                                      c->Linv_lo ? c->Linv_lo + k * bb : nullptr, (float *)c->diag64, c->diag_ctr,
-                                     minpiv + k * nq));
+                                     minpiv + k * nq, s, cta_cap));
     }
     count_launch(), min_pivot_kernel<<<1, 1, 0, s>>>(minpiv + k * nq, nq, c->derr);
     return KRR_OK;

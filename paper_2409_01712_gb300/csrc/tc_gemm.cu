@@ -92,6 +92,9 @@ struct TcParams {
     // real / padded test rows; p / ldaw: weight columns in this launch and the
     // leading dimension of the weights.
     int64_t n, n_pad, n_test, test_rows, b, nt, k, m_pad, items, p, ldaw;
+    // index of the launch's first item (a whole number of tiles): a launch
+    // covers items [item0, item0 + items) of its operation
+    int64_t item0;
     int lb;  // log2 b (the tile edge is a power of two)
     float gamma, lambda;
     const int32_t *norms_a, *norms_b;
@@ -915,7 +918,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     // work units: blocks (PAIR = 1) or pairs of blocks (PAIR = 2)
     const int64_t nunits = p.items / PAIR;
     const int64_t ustart = blockIdx.x / PAIR, ustep = gridDim.x / PAIR;
-    auto unit_item = [&](int64_t u) -> int64_t { return (PAIR == 2) ? pair_item(p, u, rank) : u; };
+    auto unit_item = [&](int64_t u) -> int64_t { return p.item0 + ((PAIR == 2) ? pair_item(p, u, rank) : u); };
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
@@ -1209,9 +1212,10 @@ krr_status make_map(Ctx *c, CUtensorMap *map, const void *base, CUtensorMapDataT
     return KRR_OK;
 }
 
+// cta_cap > 0 bounds the CTAs of this launch below the class limit.
 template <int KIND, int OP, int PAIR = 1>
 krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CUtensorMap &b0,
-                  const CUtensorMap &b1, TcParams &p, const CUtensorMap *x = nullptr) {
+                  const CUtensorMap &b1, TcParams &p, const CUtensorMap *x = nullptr, int64_t cta_cap = 0) {
     const CUtensorMap &mx = x ? *x : a0;  // fifth map: only the trailing update reads one
     if (p.items <= 0) return KRR_OK;
     static PerDevice attr, clusters_of;  // per device: smem opt-in done; clusters that fit at once
@@ -1257,7 +1261,9 @@ krr_status launch(Ctx *c, const CUtensorMap &a0, const CUtensorMap &a1, const CU
             clusters_of.put(c->device, n);
         }
         const int64_t units = p.items / PAIR;
-        const int64_t cap = std::min<int64_t>(max_clusters, std::max<int64_t>(grid_limit(c, GL_PAIR) / PAIR, 1));
+        int64_t gl = grid_limit(c, GL_PAIR);
+        if (cta_cap > 0 && cta_cap < gl) gl = cta_cap;
+        const int64_t cap = std::min<int64_t>(max_clusters, std::max<int64_t>(gl / PAIR, 1));
         const int64_t clusters = units < cap ? units : cap;
         cfg.gridDim = dim3((unsigned)(clusters * PAIR));
         count_launch();
@@ -1378,21 +1384,30 @@ krr_status tc_trsm(Ctx *c, int64_t k) {
     return launch<KIND_F16, OP_TRSM, 2>(c, a0, st->lo_map, st->linv_hi_map, st->linv_lo_map, p);
 }
 
-krr_status tc_update(Ctx *c, int64_t k) {
+krr_status tc_update(Ctx *c, int64_t k, int64_t tile0, int64_t tiles, int64_t cta_cap) {
     TcState *st = (TcState *)c->tc;
     KRR_TRY(ensure_factor_maps(c));
     const int64_t b = c->b, nt = c->nt;
     const int64_t u = nt - k - 1;
+    const int64_t total = u * (u + 1) / 2;  // target tiles of the step
+    if (tiles < 0) tiles = total - tile0;
+    if (tile0 < 0 || tile0 + tiles > total) {
+        c->last_error = "trailing update: target tile range out of bounds";
+        return KRR_EINVAL;
+    }
     TcParams p = base_params(c);
     p.k = k;
     p.Kd = c->Kd;
     p.W = (__half *)c->W;
     p.Wd = c->Wd;
     p.ltab = c->ltab;
-    p.items = u * (u + 1) / 2 * (b / BM) * (b / BN);
+    const int64_t per_tile = (b / BM) * (b / BN);
+    p.item0 = tile0 * per_tile;
+    p.items = tiles * per_tile;
     // mB1 = the FP16 trailing tiles: staged target blocks (TMA load and store);
     // the fifth map reads E4M3 tiles for kind::f8f6f4 blocks
-    return launch<KIND_F16, OP_UPDATE, 2>(c, st->pool_map, st->hi_map, st->lo_map, st->w_map, p, &st->pool8_map);
+    return launch<KIND_F16, OP_UPDATE, 2>(c, st->pool_map, st->hi_map, st->lo_map, st->w_map, p, &st->pool8_map,
+                                          cta_cap);
 }
 
 // B = K_test^T G_p: the predict kernel with the roles of the two genotype

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int64), ("mode", ctypes.c_int32), ("allow_fp8", ctypes.c_int32),
                 ("eps", ctypes.c_double), ("ir_tol", ctypes.c_double), ("ir_max", ctypes.c_int32),
                 ("diag_fp64", ctypes.c_int32), ("wait_budget_ns", ctypes.c_int64), ("prec_rule", ctypes.c_int32),
-                ("kernel", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("lookahead", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class FactorInfo(ctypes.Structure):
@@ -180,7 +180,7 @@ class KRR:
     def __init__(self, tile: int = 1024, mode: str = "mixed", eps: float | None = None,
                  ir_tol: float | None = None, ir_max: int | None = None, allow_fp8: bool = True,
                  diag_fp64: bool = False, prec_rule: str = "lambda", wait_budget_ns: int | None = None,
-                 kernel: str = "gaussian", stream=None):
+                 kernel: str = "gaussian", lookahead: bool = True, stream=None):
         lib = load_library()
         o = default_options()
         o.tile = tile
@@ -189,6 +189,7 @@ class KRR:
         o.diag_fp64 = int(diag_fp64)
         o.prec_rule = RULES[prec_rule]
         o.kernel = KERNELS[kernel]
+        o.lookahead = int(lookahead)
         if wait_budget_ns is not None:
             o.wait_budget_ns = int(wait_budget_ns)
         if eps is not None:

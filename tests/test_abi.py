@@ -43,13 +43,13 @@ def test_default_options(lib):
     o = krr.default_options()
     assert o.tile == 1024 and o.mode == 0 and o.ir_max == 30
     assert o.eps == pytest.approx(6e-4) and o.ir_tol == pytest.approx(1e-7)
-    assert o.prec_rule == 0 and o.kernel == 0
+    assert o.prec_rule == 0 and o.kernel == 0 and o.lookahead == 1 and o.reserved == 0
 
 
 def test_struct_layouts_match_header():
     import ctypes
 
-    # int64 + 2 int32 + 2 double + 2 int32 + int64 + 2 int32 = 56 bytes, no padding
-    assert ctypes.sizeof(krr.Options) == 56
+    # int64 + 2 int32 + 2 double + 2 int32 + int64 + 4 int32 = 64 bytes, no padding
+    assert ctypes.sizeof(krr.Options) == 64
     assert ctypes.sizeof(krr.FactorInfo) == 8 * 8
     assert ctypes.sizeof(krr.SolveInfo) == 8 + 8 + 32 * 8
