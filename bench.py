@@ -346,7 +346,10 @@ def run_ours(args):
     fi, si = infos[-1]
 
     pk, pk_kind = peaks()
-    upd = prof["update"]
+    # every launch of the trailing-update kernel: those with the whole GPU
+    # and those beside the next column's diagonal step (lookahead)
+    full, shared = prof["update"], prof.get("update_shared", {"count": 0, "ms": 0.0, "flops": 0.0})
+    upd = {k: full[k] + shared[k] for k in ("count", "ms", "flops")}
     roof = None
     if upd["count"] > 0 and upd["ms"] > 0:
         ach = upd["flops"] / (upd["ms"] / 1e3) / 1e12
@@ -360,6 +363,13 @@ def run_ours(args):
                 "peak_source": f"{pk_kind}: bf16 dense sustained (FP16 dense runs at the same rate)",
                 "traffic": traffic, "launches": upd["count"],
                 "avg_launch_ms": upd["ms"] / upd["count"]}
+        if shared["count"] > 0 and full["ms"] > 0:
+            ach_full = full["flops"] / (full["ms"] / 1e3) / 1e12
+            roof["lookahead"] = {
+                "note": "launches beside the next column's diagonal step run on the SMs it leaves free",
+                "shared_launches": shared["count"], "shared_ms_per_step": shared["ms"] / args.steps,
+                "shared_tflops": shared["flops"] / (shared["ms"] / 1e3) / 1e12 if shared["ms"] > 0 else None,
+                "full_gpu_launches": full["count"], "full_gpu_tflops": ach_full, "full_gpu_frac": ach_full / peak}
     bld = prof["build"]
     if bld["count"] > 0 and bld["ms"] > 0 and args.mode == "mixed":
         # the distance GEMM on E4M3 operands: its peak is the measured BF16
@@ -392,6 +402,8 @@ def run_ours(args):
             "gpu_launches": int(prof["launches"]),
             "clocks": clk,
             "phases": phases,
+            "phases_note": "CUDA-event time per class; diagonal steps of the lookahead run on a second stream "
+                           "at the same time as update_shared, so the classes add up to more than the step",
             "factor": {k: fi[k] for k in ("tiles_fp32", "tiles_fp16", "tiles_e4m3", "factor_bytes",
                                           "min_pivot")},
             "precision_map": ({"legend": PREC_LEGEND,

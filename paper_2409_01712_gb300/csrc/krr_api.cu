@@ -860,14 +860,18 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
                 KRR_TRY(check_launch(c, "diagonal step"));
                 KRR_CUDA_TRY(c, cudaEventRecord(c->la_ev[1], c->la_stream));
                 // the targets that run beside the diagonal step, then the
-                // rest (one timed region: it includes any wait for the
-                // diagonal step)
+                // rest on every SM (each launch timed on its own: the wait
+                // for the diagonal step lies between them)
                 const int64_t side = std::min<int64_t>(tiles - 1, la.tiles);
-                pr = prof_begin(c, KRR_PROF_UPDATE);
+                pr = prof_begin(c, KRR_PROF_UPDATE_SHARED);
                 KRR_TRY(tc_update(c, k, 1, side, c->num_sms - la.ctas));
+                prof_end(c, pr, update_flops(c, k, 1, side), 0.0);
                 KRR_CUDA_TRY(c, cudaStreamWaitEvent(s, c->la_ev[1], 0));
-                if (1 + side < tiles) KRR_TRY(tc_update(c, k, 1 + side, tiles - 1 - side, 0));
-                prof_end(c, pr, upd_flops - bd * bd * bd, 0.0);
+                if (1 + side < tiles) {
+                    pr = prof_begin(c, KRR_PROF_UPDATE);
+                    KRR_TRY(tc_update(c, k, 1 + side, tiles - 1 - side, 0));
+                    prof_end(c, pr, update_flops(c, k, 1 + side, tiles - 1 - side), 0.0);
+                }
                 diag_ahead = true;
             } else {
                 pr = prof_begin(c, KRR_PROF_UPDATE);
@@ -1159,6 +1163,7 @@ extern "C" krr_status krr_get_profile(krr_ctx *c, krr_profile *out, int32_t rese
     if (!c || !out) return KRR_EINVAL;
     memset(out, 0, sizeof(*out));
     KRR_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (c->la_stream) KRR_CUDA_TRY(c, cudaStreamSynchronize(c->la_stream));
     out->launches = (int64_t)g_launches.load();
     if (c->prof) {
         ProfState *ps = (ProfState *)c->prof;

@@ -460,6 +460,9 @@ krr_status tc_trsm(Ctx *c, int64_t k);       // panel TRSM of column k (FP16 spl
 // step's order (tile 0 is the diagonal target (k + 1, k + 1); tiles < 0: to
 // the end), on at most cta_cap CTAs (0: the class limit).
 krr_status tc_update(Ctx *c, int64_t k, int64_t tile0 = 0, int64_t tiles = -1, int64_t cta_cap = 0);
+// Algorithmic flops of those target tiles: 2 b^3 per off-diagonal target,
+// b^3 per diagonal target.
+double update_flops(const Ctx *c, int64_t k, int64_t tile0, int64_t tiles);
 // Predict partial products for weight columns A[:, 0:p] (p <= 32, leading
 // dimension lda): part is (n_pad / 128) x rows_pad x p.
 // With kshift the partials are of (K - c) A, c = *kshift (the reduction adds

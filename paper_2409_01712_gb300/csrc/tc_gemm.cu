@@ -1384,6 +1384,22 @@ krr_status tc_trsm(Ctx *c, int64_t k) {
     return launch<KIND_F16, OP_TRSM, 2>(c, a0, st->lo_map, st->linv_hi_map, st->linv_lo_map, p);
 }
 
+double update_flops(const Ctx *c, int64_t k, int64_t tile0, int64_t tiles) {
+    // diagonal target (r0 + a, r0 + a) of the band starting at tile row r0
+    // sits after the band's h * r0 tiles left of its diagonal block, at
+    // triangle index a (a + 1) / 2 + a (the order of update_tile_order)
+    const int64_t u = c->nt - k - 1;
+    int64_t ndiag = 0;
+    for (int64_t d = 0; d < u; ++d) {
+        const int64_t r0 = d / UPD_BAND * UPD_BAND, a = d - r0;
+        const int64_t h = (u - r0 < UPD_BAND) ? u - r0 : UPD_BAND;
+        const int64_t pos = r0 * (r0 + 1) / 2 + h * r0 + a * (a + 1) / 2 + a;
+        if (pos >= tile0 && pos < tile0 + tiles) ++ndiag;
+    }
+    const double b3 = (double)c->b * (double)c->b * (double)c->b;
+    return (double)(tiles - ndiag) * 2.0 * b3 + (double)ndiag * b3;
+}
+
 krr_status tc_update(Ctx *c, int64_t k, int64_t tile0, int64_t tiles, int64_t cta_cap) {
     TcState *st = (TcState *)c->tc;
     KRR_TRY(ensure_factor_maps(c));

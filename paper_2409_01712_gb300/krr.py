@@ -37,7 +37,7 @@ EXPORTED = ["krr_default_options", "krr_create", "krr_build_kernel", "krr_factor
             "krr_get_kernel", "krr_get_factor", "krr_predict_noalloc", "krr_grad_hyper", "krr_set_profiling",
             "krr_get_profile", "krr_set_wait_budget", "krr_sync", "krr_last_error",
             "krr_destroy", "krr_batch_create", "krr_batch_run", "krr_batch_last_error", "krr_batch_destroy"]
-PROF_CLASSES = ["pack", "build", "diag", "trsm", "cast", "update", "solve", "residual", "predict"]
+PROF_CLASSES = ["pack", "build", "diag", "trsm", "cast", "update", "solve", "residual", "predict", "update_shared"]
 
 
 class Options(ctypes.Structure):
@@ -60,8 +60,9 @@ class SolveInfo(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64), ("count", ctypes.c_int64 * 9), ("ms", ctypes.c_double * 9),
-                ("flops", ctypes.c_double * 9), ("bytes", ctypes.c_double * 9)]
+    _fields_ = [("launches", ctypes.c_int64), ("count", ctypes.c_int64 * len(PROF_CLASSES)),
+                ("ms", ctypes.c_double * len(PROF_CLASSES)), ("flops", ctypes.c_double * len(PROF_CLASSES)),
+                ("bytes", ctypes.c_double * len(PROF_CLASSES))]
 
 
 class BatchProblem(ctypes.Structure):
