@@ -569,8 +569,8 @@ def run_batch(args):
         torch.cuda.empty_cache()
         return dt
 
-    seq_ms = sequential("mixed")
-    seq32_ms = sequential("fp32")
+    seq_ms = sequential("mixed") if not args.no_compare else None
+    seq32_ms = sequential("fp32") if not args.no_compare else None
     line = {"metric": "batched KRR: 64 CV problems (16 cohorts x 4 lambdas, N~U[1024,16384]) TOp/s",
             "value": ops / (ms / 1e3) / 1e12, "unit": "TOp/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -580,8 +580,10 @@ def run_batch(args):
             "batch": {"tiles_chosen": tiles, "setup_s": setup_s, "worst_rel_residual": worst_res,
                       "problems_failed_or_zero_residual": bad, "residuals": [r["rel_residual"] for r in res],
                       "shared_builds": "the 4 lambdas of a cohort share one Build",
-                      "sequential_fp32_ms": seq32_ms, "speedup_over_sequential_fp32": seq32_ms / ms,
-                      "sequential_mixed_ms": seq_ms, "speedup_over_sequential_mixed": seq_ms / ms}}
+                      "sequential_fp32_ms": seq32_ms,
+                      "speedup_over_sequential_fp32": seq32_ms / ms if seq32_ms else None,
+                      "sequential_mixed_ms": seq_ms,
+                      "speedup_over_sequential_mixed": seq_ms / ms if seq_ms else None}}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -466,6 +466,20 @@ krr_status prepare_build(Ctx *c, int64_t n, int64_t m_pad, int keep_d) {
     }
     return KRR_OK;
 }
+krr_status ensure_lookahead_stream(Ctx *c) {
+    if (c->la_stream) return KRR_OK;
+    if (c->graph_mode) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        KRR_CUDA_TRY(c, cudaStreamIsCapturing(c->stream, &cs));
+        if (cs != cudaStreamCaptureStatusNone) return KRR_OK;  // made before the capture, or not at all
+    }
+    int lo = 0, hi = 0;
+    KRR_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    KRR_CUDA_TRY(c, cudaStreamCreateWithPriority(&c->la_stream, cudaStreamNonBlocking, hi));
+    for (cudaEvent_t &e : c->la_ev) KRR_CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return KRR_OK;
+}
+
 }  // namespace krr
 
 extern "C" {
@@ -714,13 +728,22 @@ namespace {
 // only the diagonal step's R SMs wait.  At N = 131072 the factorisation
 // takes 660 ms this way and 697 ms in sequence; fixed R = 24 and R = 48 gave
 // the same 658-662 ms, R = 8 690 ms.
+//
+// A context of a batch (graph mode) shares the GPU with the other problems
+// and its kernels are capped per class: there the diagonal step keeps its
+// class cap and the whole rest of the update runs beside it (on the
+// cross-validation workload, 64 problems: 170.4-171.8 ms per run against
+// 172.9-175.4 ms in sequence).
 struct LookaheadPlan {
     bool on = false;
-    int64_t ctas = 0, tiles = 0;
+    int64_t ctas = 0, tiles = 0;  // 0 CTAs: the class limit
+    int64_t upd_ctas = 0;         // CTAs of the update launch beside it (0: class limit)
 };
 
 bool lookahead_enabled(const Ctx *c) {
-    return c->opt.lookahead && mixed(c) && !c->graph_mode && !c->opt.diag_fp64 && c->nt >= 3 && c->num_sms >= 32;
+    // in graph mode the second stream must exist before the capture began
+    if (c->graph_mode && !c->la_stream) return false;
+    return c->opt.lookahead && mixed(c) && !c->opt.diag_fp64 && c->nt >= 3 && c->num_sms >= 32;
 }
 
 LookaheadPlan lookahead_plan(const Ctx *c, int64_t k) {
@@ -728,6 +751,11 @@ LookaheadPlan lookahead_plan(const Ctx *c, int64_t k) {
     const int64_t u = c->nt - k - 1;
     const int64_t tiles = u * (u + 1) / 2;
     if (tiles < 2) return pl;
+    if (c->graph_mode) {
+        pl.on = true;
+        pl.tiles = tiles - 1;
+        return pl;
+    }
     const double bd = (double)c->b, rel = bd / 1024.0;
     const double a_us = 600.0 * rel, c_us = 13000.0 * rel * rel * rel;
     const double tile_sm_us = 2.0 * bd * bd * bd / 8.3e12 * 1e6;  // SM-microseconds per target tile
@@ -743,20 +771,12 @@ LookaheadPlan lookahead_plan(const Ctx *c, int64_t k) {
         if (t < best) {
             best = t;
             pl.ctas = r;
+            pl.upd_ctas = sms - r;
             pl.tiles = std::min<int64_t>(tiles - 1, (int64_t)std::ceil(1.3 * beside / tile_sm_us));
         }
     }
     pl.on = pl.ctas > 0 && pl.tiles > 0;
     return pl;
-}
-
-krr_status ensure_lookahead_stream(Ctx *c) {
-    if (c->la_stream) return KRR_OK;
-    int lo = 0, hi = 0;
-    KRR_CUDA_TRY(c, cudaDeviceGetStreamPriorityRange(&lo, &hi));
-    KRR_CUDA_TRY(c, cudaStreamCreateWithPriority(&c->la_stream, cudaStreamNonBlocking, hi));
-    for (cudaEvent_t &e : c->la_ev) KRR_CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    return KRR_OK;
 }
 
 }  // namespace
@@ -864,7 +884,7 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
                 // for the diagonal step lies between them)
                 const int64_t side = std::min<int64_t>(tiles - 1, la.tiles);
                 pr = prof_begin(c, KRR_PROF_UPDATE_SHARED);
-                KRR_TRY(tc_update(c, k, 1, side, c->num_sms - la.ctas));
+                KRR_TRY(tc_update(c, k, 1, side, la.upd_ctas));
                 prof_end(c, pr, update_flops(c, k, 1, side), 0.0);
                 KRR_CUDA_TRY(c, cudaStreamWaitEvent(s, c->la_ev[1], 0));
                 if (1 + side < tiles) {

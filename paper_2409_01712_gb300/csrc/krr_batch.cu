@@ -51,7 +51,12 @@ thread_local std::string g_batch_create_error;
 // cross-validation workload (64 problems, N up to 16384): no cap 408 ms per
 // run; 32 CTAs for every kernel 220 ms; per class as below 183-185 ms (the
 // diagonal step, mostly waiting CTAs, at 12; the sweeps at 16; the tensor-core
-// kernels, which keep their CTAs busy, at 64).
+// kernels, which keep their CTAs busy, at 64).  Later re-measured around
+// these caps (172-176 ms): the diagonal step at 4 / 6 CTAs 204 / 185 ms,
+// at 16 / 24 (with the lookahead) 175 / 187 ms; diagonal step and sweeps
+// both at 8 195 ms; the pair kernels at 48 (sweeps 12) 194 ms: the chain of
+// the diagonal steps of the largest problems needs their CTAs, and more
+// CTAs crowd out the other problems.
 constexpr int BATCH_CTA_CAP = 32;
 constexpr int BATCH_CAP_DIAG = 12, BATCH_CAP_SWEEP = 16, BATCH_CAP_PAIR = 64, BATCH_CAP_SINGLE = 64;
 
@@ -93,6 +98,10 @@ krr_status trial_ms(const krr_options &base, cudaStream_t s, const krr_batch_pro
     KRR_TRY(krr_create(&c, &o, s));
     reinterpret_cast<krr::Ctx *>(c)->graph_mode = 1;
     set_batch_caps(c);
+    if (krr::ensure_lookahead_stream(reinterpret_cast<krr::Ctx *>(c)) != KRR_OK) {
+        krr_destroy(c);
+        return KRR_ECUDA;
+    }
     krr_status st = issue(c, pr, m, p);  // warm-up (allocations)
     if (st == KRR_OK) {
         cudaStreamSynchronize(s);
@@ -204,6 +213,8 @@ extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, 
         if (st != KRR_OK) return fail(st, std::string("krr_batch_create: ") + krr_last_error(nullptr));
         reinterpret_cast<krr::Ctx *>(bt->ctx[i])->graph_mode = 1;
         set_batch_caps(bt->ctx[i]);
+        st = krr::ensure_lookahead_stream(reinterpret_cast<krr::Ctx *>(bt->ctx[i]));
+        if (st != KRR_OK) return fail(st, "krr_batch_create: lookahead stream");
         const int32_t ow = bt->owner[i];
         st = (ow == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
                        : issue(bt->ctx[i], problems[i], m, p, bt->ctx[ow], bt->built[ow]);

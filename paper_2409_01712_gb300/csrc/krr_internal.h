@@ -460,6 +460,9 @@ krr_status tc_trsm(Ctx *c, int64_t k);       // panel TRSM of column k (FP16 spl
 // step's order (tile 0 is the diagonal target (k + 1, k + 1); tiles < 0: to
 // the end), on at most cta_cap CTAs (0: the class limit).
 krr_status tc_update(Ctx *c, int64_t k, int64_t tile0 = 0, int64_t tiles = -1, int64_t cta_cap = 0);
+// Second stream and events of the factorisation lookahead (made once; in
+// graph mode it must be made before the capture).
+krr_status ensure_lookahead_stream(Ctx *c);
 // Algorithmic flops of those target tiles: 2 b^3 per off-diagonal target,
 // b^3 per diagonal target.
 double update_flops(const Ctx *c, int64_t k, int64_t tile0, int64_t tiles);
