@@ -366,7 +366,8 @@ def run_ours(args):
         if shared["count"] > 0 and full["ms"] > 0:
             ach_full = full["flops"] / (full["ms"] / 1e3) / 1e12
             roof["lookahead"] = {
-                "note": "launches beside the next column's diagonal step run on the SMs it leaves free",
+                "note": "lookahead launches: the diagonal target alone, then targets beside the next column's "
+                        "diagonal step on the SMs it leaves free; full_gpu = the other update launches",
                 "shared_launches": shared["count"], "shared_ms_per_step": shared["ms"] / args.steps,
                 "shared_tflops": shared["flops"] / (shared["ms"] / 1e3) / 1e12 if shared["ms"] > 0 else None,
                 "full_gpu_launches": full["count"], "full_gpu_tflops": ach_full, "full_gpu_frac": ach_full / peak}

@@ -391,8 +391,9 @@ enum {
     KRR_PROF_SOLVE = 6,    /* forward + backward substitution */
     KRR_PROF_RESIDUAL = 7, /* refinement residual */
     KRR_PROF_PREDICT = 8,  /* predict (distance GEMM + exp + weights) */
-    KRR_PROF_UPDATE_SHARED = 9, /* trailing-update launches that share the GPU with the
-                                   diagonal step of the next column (lookahead) */
+    KRR_PROF_UPDATE_SHARED = 9, /* trailing-update launches of the lookahead: the diagonal
+                                   target alone, and the targets that share the GPU with
+                                   the diagonal step of the next column */
     KRR_PROF_CLASSES = 10
 };
 

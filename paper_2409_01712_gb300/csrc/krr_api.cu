@@ -722,7 +722,10 @@ namespace {
 //     alone 0.59 ms;
 //   trailing update: about 8.3 TF/s per SM (2 b^3 per off-diagonal target).
 // The plan minimises the step's time: T(R) while the update fits beside the
-// diagonal step, else T(R) plus the rest of the update on every SM.  The
+// diagonal step, else T(R) plus the rest of the update on every SM; the
+// launch of the diagonal target alone adds about 25 us.  When the update is
+// small (the last steps, small problems) the plain sequence is faster: the
+// diagonal step alone on 136 CTAs, 0.59 ms at b = 1024, then the update.  The
 // update part beside it is sized 30 % above T(R): if it ended first, the
 // other SMs would idle until the diagonal step ends, while if it ends last
 // only the diagonal step's R SMs wait.  At N = 131072 the factorisation
@@ -761,13 +764,16 @@ LookaheadPlan lookahead_plan(const Ctx *c, int64_t k) {
     const double tile_sm_us = 2.0 * bd * bd * bd / 8.3e12 * 1e6;  // SM-microseconds per target tile
     const double work = (double)(tiles - 1) * tile_sm_us;
     const int64_t sms = c->num_sms;
+    // in sequence: the diagonal step alone on 136 CTAs (0.59 ms at b = 1024),
+    // then the whole update on every SM
+    double best = 590.0 * rel + (work + tile_sm_us) / (double)sms;
     static const int64_t cand[] = {16, 20, 24, 32, 48, 64, 96, 128};
-    double best = 1e300;
     for (int64_t r : cand) {
         if (r + 16 > sms) break;
         const double td = a_us + c_us / (double)r;
         const double beside = (double)(sms - r) * td;  // SM-us of update beside the diagonal step
-        const double t = (work <= beside) ? td : td + (work - beside) / (double)sms;
+        // plus the launch of the diagonal target alone (about 25 us)
+        const double t = 25.0 + ((work <= beside) ? td : td + (work - beside) / (double)sms);
         if (t < best) {
             best = t;
             pl.ctas = r;
@@ -869,7 +875,7 @@ krr_status krr_factor(krr_ctx *c, double lambda, krr_factor_info *info) {
             const LookaheadPlan la = la_on ? lookahead_plan(c, k) : LookaheadPlan();
             if (la.on) {
                 // the diagonal target (k + 1, k + 1), b^3 flops
-                pr = prof_begin(c, KRR_PROF_UPDATE);
+                pr = prof_begin(c, KRR_PROF_UPDATE_SHARED);
                 KRR_TRY(tc_update(c, k, 0, 1, 0));
                 prof_end(c, pr, bd * bd * bd, 0.0);
                 KRR_CUDA_TRY(c, cudaEventRecord(c->la_ev[0], s));
