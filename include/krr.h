@@ -18,7 +18,11 @@
  *    tiles, factor tiles, precision map) and frees them in krr_destroy().
  *  - Work is issued on the stream given to krr_create().  A call that returns
  *    host-visible results (info structs, host output buffers) synchronises
- *    that stream before it returns.
+ *    that stream before it returns.  krr_factor() with options.lookahead also
+ *    uses a second stream of the context's own (made on first use); every
+ *    piece of work on it is joined back into the context's stream by an
+ *    event before the call returns, so ordering on the caller's stream is
+ *    unchanged.
  *  - A context is not thread safe; use one context per host thread.
  *
  * Notation: N training patients, M SNPs, P phenotypes, N_t held-out patients,
