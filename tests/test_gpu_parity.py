@@ -239,3 +239,28 @@ def test_single_row_closed_form(mode):
     assert np.allclose(a.cpu().numpy(), y / (1 + lam), rtol=1e-6, atol=1e-7)
     # predicting the training row: K A = Y - lambda A
     assert np.allclose(yt.cpu().numpy(), y - lam * y / (1 + lam), rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n,m,p,tile", [(5000, 700, 2, 2048), (9000, 512, 2, 4096)])
+def test_largest_tile_edges_match_oracle(n, m, p, tile):
+    """The two largest tile edges the API accepts (2048, 4096: 32 and 64
+    blocks of 64 in the diagonal step, 16 x 8 and 32 x 16 tensor-core blocks
+    per tile), ragged N over three tiles, mixed mode with the lookahead,
+    against the FP64 oracle (library Gram product and LAPACK factorisation)."""
+    prob = _problem(n, m, p, 300, seed=11 + tile)
+    gamma, lam = 1.0 / m, 0.1
+    _, a_ref, yt_ref = oracle.krr(gamma, lam, prob["G"], prob["Y"].astype(np.float64), prob["T"], method="lapack")
+    with KRR(tile=tile, mode="mixed") as model:
+        model.build_kernel(_to(prob["G"]), gamma)
+        finfo = model.factor(lam)
+        a, sinfo = model.solve(_to(prob["Y"]))
+        yt = model.predict(_to(prob["T"]), a)
+    a = a.cpu().numpy().astype(np.float64)
+    yt = yt.cpu().numpy().astype(np.float64)
+    err_yt = np.linalg.norm(yt - yt_ref) / np.linalg.norm(yt_ref)
+    err_a = np.linalg.norm(a - a_ref) / np.linalg.norm(a_ref)
+    print(f"\nmixed n={n} tile={tile}: err_Yt={err_yt:.3e} err_A={err_a:.3e} residual={sinfo['rel_residual']:.3e}")
+    assert finfo["nt"] == -(-n // tile)
+    assert sinfo["converged"] in (1, 2), sinfo
+    assert err_yt <= 1e-4, (err_yt, err_a, sinfo)
+    assert err_a <= 1e-4, (err_a, sinfo)
