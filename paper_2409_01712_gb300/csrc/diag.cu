@@ -289,9 +289,14 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
         const int o = 16 * q;
         if (warp == 0) {
             const int l = lane & 15;
-            float v[16], ivs[16];
+            float v[16], xr[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] = (j <= l) ? a[o + l][o + j] : 0.f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) xr[k] = (k == l) ? 1.f : 0.f;
+            // column c of the factor, then column c of the inverse (it needs
+            // only columns 0 .. c of L): one loop, so the inverse step of
+            // column c fills the latency of column c + 1's pivot chain
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 float d = __shfl_sync(FULL, v[c], c);
@@ -304,7 +309,6 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
                 float inv = rsqrtf(d);
                 inv = inv * fmaf(-0.5f * d * inv, inv, 1.5f);
                 const float lcc = d * inv;
-                ivs[c] = inv;
                 mpiv = fminf(mpiv, lcc);
                 if (l == c) {
                     v[c] = lcc;
@@ -320,16 +324,10 @@ __device__ void chol_inv_64(float (*a)[65], float (*x)[65], float (*tmp)[16][17]
                         if (l >= j) v[j] = fmaf(-v[c], ljc, v[j]);
                     }
                 }
-            }
-            float xr[16];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) xr[k] = (k == l) ? 1.f : 0.f;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const float invc = ivs[c];  // 1 / L[c][c] from the factorisation
+                // inverse: row c of X is final once scaled by 1 / L[c][c]
                 if (l == c) {
 #pragma unroll
-                    for (int k = 0; k <= c; ++k) xr[k] *= invc;
+                    for (int k = 0; k <= c; ++k) xr[k] *= inv;
                 }
 #pragma unroll
                 for (int k = 0; k <= c; ++k) {
