@@ -531,7 +531,7 @@ def run_batch(args):
             problems.append({"G": prob["G"], "Y": prob["Y"], "T": prob["T"], "gamma": 1.0 / m, "lam": lam})
     ops = sum(metric_ops(pr["G"].shape[0], m, p) for pr in problems)
     t0 = time.perf_counter()
-    bt = KRRBatch(problems, ir_iters=3, autotune=True)
+    bt = KRRBatch(problems, ir_iters=3, autotune=2)
     setup_s = time.perf_counter() - t0
     for _ in range(args.warmup):
         bt.run()
@@ -578,7 +578,9 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "e4m3+f16 tensor, f32/f64 refine", "data": "synthetic",
             "config": {"workload": f"c4: 64 problems, cohort N = {ns}, M={m}, P={p}, N_test={C4['n_test']}, "
                                    f"lambda in {C4['lambdas']}, gamma=1/M", "graph": "one CUDA graph per run"},
-            "batch": {"tiles_chosen": tiles, "setup_s": setup_s, "worst_rel_residual": worst_res,
+            "batch": {"tiles_chosen": tiles, "setup_s": setup_s,
+                      "autotune": "per-size trial runs, then the whole batch timed for that choice and every uniform "
+                                  "tile edge (256 / 512 / 1024); the fastest kept", "worst_rel_residual": worst_res,
                       "problems_failed_or_zero_residual": bad, "residuals": [r["rel_residual"] for r in res],
                       "shared_builds": "the 4 lambdas of a cohort share one Build",
                       "sequential_fp32_ms": seq32_ms,

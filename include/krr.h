@@ -343,9 +343,8 @@ krr_status krr_grad_hyper(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t
  * uneven size -- the paper picks gamma and alpha by cross-validation (Sec.
  * III), i.e. by solving many such problems.  krr_batch_create() gives every
  * problem its own context and stream, picks each problem's tile edge with an
- * autotuner (timed trial runs of the smallest, median and largest problem
- * with tile edges 256 / 512 / 1024) when autotune != 0, runs every pipeline
- * once to allocate, and captures Build -> Factor -> Solve (with
+ * autotuner, runs every pipeline once to allocate, and captures Build ->
+ * Factor -> Solve (with
  * options->ir_max refinement steps, no host decisions) -> Predict of all
  * problems into one CUDA graph with a fork/join over the problem streams.
  * krr_batch_run() launches that graph once and reports per-problem status,
@@ -354,6 +353,12 @@ krr_status krr_grad_hyper(krr_ctx *ctx, const int8_t *T, int64_t n_test, int64_t
  * stream).  All pointers are device pointers and are read at every run
  * (update the data in place between runs).  krr_batch_last_error(NULL) gives
  * the message of the calling thread's last failed krr_batch_create().
+ *   autotune : 0 = every problem at options->tile; 1 = timed trial runs of
+ *              the smallest, median and largest problem with tile edges
+ *              256 / 512 / 1024, each problem taking the edge of the measured
+ *              problem nearest to it in log N; 2 = that choice and every
+ *              uniform edge, each captured and timed as the whole batch (a
+ *              few graph runs per candidate), the fastest kept.
  * Errors: KRR_EINVAL, KRR_ENOMEM, KRR_ECUDA, and the first per-problem error.
  */
 typedef struct krr_batch_problem {

@@ -38,6 +38,7 @@ struct krr_batch {
     std::vector<cudaEvent_t> join;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<double> tune_ms;      // autotune level 2: ms per run of each candidate assignment
     std::string last_error;
 };
 
@@ -115,6 +116,149 @@ krr_status trial_ms(const krr_options &base, cudaStream_t s, const krr_batch_pro
     return st;
 }
 
+// Contexts, streams and the captured graph of the current tile assignment
+// bt->tiles: problems sharing a Build (same genotypes, shape, gamma and
+// tile) are found, every pipeline runs once eagerly (allocations), then all
+// are captured into one graph with a fork / join over the problem streams.
+krr_status instantiate(krr_batch *bt, std::string *msg) {
+    const int32_t count = (int32_t)bt->probs.size();
+    const krr_batch_problem *problems = bt->probs.data();
+    const int64_t m = bt->m, p = bt->p;
+    bt->owner.assign(count, -1);
+    for (int32_t i = 0; i < count; ++i) {
+        bt->owner[i] = i;
+        for (int32_t j = 0; j < i; ++j) {
+            const krr_batch_problem &a = problems[i], &b2 = problems[j];
+            if (bt->owner[j] == j && a.G == b2.G && a.n == b2.n && a.ldg == b2.ldg && a.gamma == b2.gamma &&
+                bt->tiles[i] == bt->tiles[j]) {
+                bt->owner[i] = j;
+                break;
+            }
+        }
+    }
+    bt->ctx.assign(count, nullptr);
+    bt->streams.assign(count, nullptr);
+    bt->join.assign(count, nullptr);
+    bt->built.assign(count, nullptr);
+    for (int32_t i = 0; i < count; ++i) {
+        if (cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&bt->join[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&bt->built[i], cudaEventDisableTiming) != cudaSuccess) {
+            *msg = "stream creation failed";
+            return KRR_ECUDA;
+        }
+        krr_options o = bt->opt;
+        o.tile = bt->tiles[i];
+        krr_status st = krr_create(&bt->ctx[i], &o, bt->streams[i]);
+        if (st != KRR_OK) {
+            *msg = std::string("krr_batch_create: ") + krr_last_error(nullptr);
+            return st;
+        }
+        reinterpret_cast<krr::Ctx *>(bt->ctx[i])->graph_mode = 1;
+        set_batch_caps(bt->ctx[i]);
+        st = krr::ensure_lookahead_stream(reinterpret_cast<krr::Ctx *>(bt->ctx[i]));
+        if (st != KRR_OK) {
+            *msg = "krr_batch_create: lookahead stream";
+            return st;
+        }
+        const int32_t ow = bt->owner[i];
+        st = (ow == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
+                       : issue(bt->ctx[i], problems[i], m, p, bt->ctx[ow], bt->built[ow]);
+        if (st != KRR_OK) {
+            *msg = std::string("krr_batch_create: warm-up of problem ") + std::to_string(i) + ": " +
+                   krr_last_error(bt->ctx[i]);
+            return st;
+        }
+    }
+    {
+        const cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            *msg = std::string("warm-up failed: ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+    }
+    {
+        const cudaError_t e = cudaStreamBeginCapture(bt->capture, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            *msg = std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e);
+            return KRR_ECUDA;
+        }
+    }
+    cudaEventRecord(bt->fork, bt->capture);
+    krr_status cst = KRR_OK;
+    std::string cmsg;
+    for (int32_t i = 0; i < count && cst == KRR_OK; ++i) {
+        cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
+        const int32_t o = bt->owner[i];
+        cst = (o == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
+                       : issue(bt->ctx[i], problems[i], m, p, bt->ctx[o], bt->built[o]);
+        if (cst != KRR_OK) cmsg = "problem " + std::to_string(i) + ": " + krr_last_error(bt->ctx[i]);
+        cudaEventRecord(bt->join[i], bt->streams[i]);
+        cudaStreamWaitEvent(bt->capture, bt->join[i], 0);
+    }
+    const cudaError_t ce = cudaStreamEndCapture(bt->capture, &bt->graph);
+    if (cst != KRR_OK || ce != cudaSuccess || !bt->graph) {
+        cudaGetLastError();
+        *msg = "graph capture failed: " + (cst != KRR_OK ? cmsg : std::string(cudaGetErrorString(ce)));
+        return cst != KRR_OK ? cst : KRR_ECUDA;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *msg = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        return KRR_ECUDA;
+    }
+    return KRR_OK;
+}
+
+// Frees what instantiate() made; the batch can be instantiated again.
+void release(krr_batch *bt) {
+    if (bt->exec) cudaStreamSynchronize(bt->main);
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    bt->exec = nullptr;
+    bt->graph = nullptr;
+    // contexts that read another's Build go first
+    for (size_t i = 0; i < bt->ctx.size(); ++i)
+        if (i < bt->owner.size() && bt->owner[i] != (int32_t)i) krr_destroy(bt->ctx[i]);
+    for (size_t i = 0; i < bt->ctx.size(); ++i)
+        if (i >= bt->owner.size() || bt->owner[i] == (int32_t)i) krr_destroy(bt->ctx[i]);
+    for (cudaEvent_t e : bt->built)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t st : bt->streams)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t e : bt->join)
+        if (e) cudaEventDestroy(e);
+    bt->ctx.clear();
+    bt->owner.clear();
+    bt->built.clear();
+    bt->streams.clear();
+    bt->join.clear();
+}
+
+// Median wall time of `runs` graph launches after one more (untimed); any
+// per-problem error is returned.
+krr_status time_graph(krr_batch *bt, int runs, double *ms) {
+    std::vector<double> t;
+    for (int r = 0; r <= runs; ++r) {
+        const auto t0 = std::chrono::steady_clock::now();
+        if (cudaGraphLaunch(bt->exec, bt->main) != cudaSuccess || cudaStreamSynchronize(bt->main) != cudaSuccess) {
+            cudaGetLastError();
+            return KRR_ECUDA;
+        }
+        if (r > 0) t.push_back(std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    }
+    for (krr_ctx *c : bt->ctx) {
+        krr::DevErrors e;
+        if (cudaMemcpy(&e, reinterpret_cast<krr::Ctx *>(c)->derr, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return KRR_ECUDA;
+        if (e.code) return (krr_status)e.code;
+    }
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return KRR_OK;
+}
+
 }  // namespace
 
 extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, void *stream, int64_t m,
@@ -181,81 +325,45 @@ extern "C" krr_status krr_batch_create(krr_batch **out, const krr_options *opt, 
             bt->tiles[i] = (int32_t)best_b[qbest];
         }
     }
-    // ---- problems sharing a Build: same genotypes, shape, gamma and tile
-    bt->owner.assign(count, -1);
-    for (int32_t i = 0; i < count; ++i) {
-        bt->owner[i] = i;
-        for (int32_t j = 0; j < i; ++j) {
-            const krr_batch_problem &a = problems[i], &b2 = problems[j];
-            if (bt->owner[j] == j && a.G == b2.G && a.n == b2.n && a.ldg == b2.ldg && a.gamma == b2.gamma &&
-                bt->tiles[i] == bt->tiles[j]) {
-                bt->owner[i] = j;
-                break;
-            }
-        }
-    }
-    // ---- one context and stream per problem, warm-up run (allocations)
-    bt->ctx.assign(count, nullptr);
-    bt->streams.assign(count, nullptr);
-    bt->join.assign(count, nullptr);
-    bt->built.assign(count, nullptr);
     if (cudaEventCreateWithFlags(&bt->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&bt->capture, cudaStreamNonBlocking) != cudaSuccess)
         return fail(KRR_ECUDA, "event / stream creation failed");
-    for (int32_t i = 0; i < count; ++i) {
-        if (cudaStreamCreateWithFlags(&bt->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&bt->join[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&bt->built[i], cudaEventDisableTiming) != cudaSuccess)
-            return fail(KRR_ECUDA, "stream creation failed");
-        krr_options o = bt->opt;
-        o.tile = bt->tiles[i];
-        krr_status st = krr_create(&bt->ctx[i], &o, bt->streams[i]);
-        if (st != KRR_OK) return fail(st, std::string("krr_batch_create: ") + krr_last_error(nullptr));
-        reinterpret_cast<krr::Ctx *>(bt->ctx[i])->graph_mode = 1;
-        set_batch_caps(bt->ctx[i]);
-        st = krr::ensure_lookahead_stream(reinterpret_cast<krr::Ctx *>(bt->ctx[i]));
-        if (st != KRR_OK) return fail(st, "krr_batch_create: lookahead stream");
-        const int32_t ow = bt->owner[i];
-        st = (ow == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
-                       : issue(bt->ctx[i], problems[i], m, p, bt->ctx[ow], bt->built[ow]);
-        if (st != KRR_OK)
-            return fail(st, std::string("krr_batch_create: warm-up of problem ") + std::to_string(i) + ": " +
-                                krr_last_error(bt->ctx[i]));
-    }
-    {
-        const cudaError_t e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return fail(KRR_ECUDA, std::string("warm-up failed: ") + cudaGetErrorString(e));
-    }
-    // ---- capture every problem's pipeline into one graph (fork / join)
-    {
-        const cudaError_t e = cudaStreamBeginCapture(bt->capture, cudaStreamCaptureModeRelaxed);
-        if (e != cudaSuccess)
-            return fail(KRR_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
-    }
-    cudaEventRecord(bt->fork, bt->capture);
-    krr_status cst = KRR_OK;
-    std::string cmsg;
-    for (int32_t i = 0; i < count && cst == KRR_OK; ++i) {
-        cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
-        const int32_t o = bt->owner[i];
-        cst = (o == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
-                       : issue(bt->ctx[i], problems[i], m, p, bt->ctx[o], bt->built[o]);
-        if (cst != KRR_OK) cmsg = "problem " + std::to_string(i) + ": " + krr_last_error(bt->ctx[i]);
-        cudaEventRecord(bt->join[i], bt->streams[i]);
-        cudaStreamWaitEvent(bt->capture, bt->join[i], 0);
-    }
-    const cudaError_t ce = cudaStreamEndCapture(bt->capture, &bt->graph);
-    if (cst != KRR_OK || ce != cudaSuccess || !bt->graph) {
-        cudaGetLastError();
-        return fail(cst != KRR_OK ? cst : KRR_ECUDA,
-                    "graph capture failed: " + (cst != KRR_OK ? cmsg : std::string(cudaGetErrorString(ce))));
-    }
-    {
-        const cudaError_t e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(KRR_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    // ---- autotune level 2: the whole batch, captured and timed, with the
+    // per-size choice above and with every uniform tile edge; the fastest
+    // assignment is kept (the per-size trials time one problem alone, while
+    // the batch runs them all at once, sharing the SMs)
+    if (autotune >= 2) {
+        std::vector<std::vector<int32_t>> cands;
+        cands.push_back(bt->tiles);
+        int64_t nmax = 0;
+        for (int32_t i = 0; i < count; ++i) nmax = std::max<int64_t>(nmax, problems[i].n);
+        for (int32_t b : {256, 512, 1024}) {
+            if (b > 2 * nmax && b != 256) continue;
+            std::vector<int32_t> u(count, b);
+            if (std::find(cands.begin(), cands.end(), u) == cands.end()) cands.push_back(u);
         }
+        double best = INFINITY;
+        size_t best_c = 0;
+        for (size_t ci = 0; ci < cands.size(); ++ci) {
+            bt->tiles = cands[ci];
+            std::string msg;
+            krr_status st = instantiate(bt, &msg);
+            double ms = INFINITY;
+            if (st == KRR_OK) st = time_graph(bt, 3, &ms);
+            release(bt);
+            if (st != KRR_OK) return fail(st, "krr_batch_create: autotune of the batch: " + msg);
+            bt->tune_ms.push_back(ms);
+            if (ms < best) {
+                best = ms;
+                best_c = ci;
+            }
+        }
+        bt->tiles = cands[best_c];
+    }
+    {
+        std::string msg;
+        const krr_status st = instantiate(bt, &msg);
+        if (st != KRR_OK) return fail(st, msg);
     }
     *out = bt;
     return KRR_OK;
@@ -299,21 +407,8 @@ extern "C" const char *krr_batch_last_error(const krr_batch *bt) {
 
 extern "C" void krr_batch_destroy(krr_batch *bt) {
     if (!bt) return;
-    if (bt->exec) cudaStreamSynchronize(bt->main);
+    release(bt);
     if (bt->capture) cudaStreamDestroy(bt->capture);
-    if (bt->exec) cudaGraphExecDestroy(bt->exec);
-    if (bt->graph) cudaGraphDestroy(bt->graph);
-    // contexts that read another's Build go first
-    for (size_t i = 0; i < bt->ctx.size(); ++i)
-        if (i < bt->owner.size() && bt->owner[i] != (int32_t)i) krr_destroy(bt->ctx[i]);
-    for (size_t i = 0; i < bt->ctx.size(); ++i)
-        if (i >= bt->owner.size() || bt->owner[i] == (int32_t)i) krr_destroy(bt->ctx[i]);
-    for (cudaEvent_t e : bt->built)
-        if (e) cudaEventDestroy(e);
-    for (cudaStream_t s : bt->streams)
-        if (s) cudaStreamDestroy(s);
-    for (cudaEvent_t e : bt->join)
-        if (e) cudaEventDestroy(e);
     if (bt->fork) cudaEventDestroy(bt->fork);
     delete bt;
 }

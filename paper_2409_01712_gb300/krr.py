@@ -379,7 +379,7 @@ class KRRBatch:
     allocated here and refreshed by every run().
     """
 
-    def __init__(self, problems, ir_iters: int = 3, autotune: bool = True, tile: int = 1024, stream=None):
+    def __init__(self, problems, ir_iters: int = 3, autotune: int = 1, tile: int = 1024, stream=None):
         lib = load_library()
         self._lib = lib
         o = default_options()

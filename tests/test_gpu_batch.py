@@ -14,7 +14,8 @@ pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0") if torch.cuda.is_available() else None
 
 
-def test_batch_matches_oracle_and_replays():
+@pytest.mark.parametrize("autotune", [1, 2])
+def test_batch_matches_oracle_and_replays(autotune):
     m, p = 300, 2
     sizes = [(700, 0.1), (700, 1.0), (1300, 0.1), (1300, 0.01), (1300, 1.0), (300, 0.1)]
     problems, refs, cohorts = [], [], {}
@@ -27,7 +28,9 @@ def test_batch_matches_oracle_and_replays():
             cohorts[n] = {k: prob[k].to(DEV) for k in ("G", "Y", "T")}
         c = cohorts[n]
         problems.append({"G": c["G"], "Y": c["Y"], "T": c["T"], "gamma": 1.0 / m, "lam": lam})
-    with KRRBatch(problems, ir_iters=3, autotune=True) as bt:
+    # autotune 2 also captures and times the whole batch for every candidate
+    # assignment of tile edges (instantiating and releasing the graph each time)
+    with KRRBatch(problems, ir_iters=3, autotune=autotune) as bt:
         res = bt.run()
         first = [yt.clone() for yt in bt.Yt]
         res2 = bt.run()
