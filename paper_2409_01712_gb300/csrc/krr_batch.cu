@@ -124,6 +124,15 @@ krr_status instantiate(krr_batch *bt, std::string *msg) {
     const int32_t count = (int32_t)bt->probs.size();
     const krr_batch_problem *problems = bt->probs.data();
     const int64_t m = bt->m, p = bt->p;
+    // problems are captured by decreasing N (stable: the first problem of a
+    // shared Build stays ahead of the others), so the longest dependency
+    // chains start first: 168-169 ms per run on the cross-validation
+    // workload against 168-173 ms in problem order (stream priorities by
+    // size on top of it changed nothing)
+    std::vector<int32_t> order(count);
+    for (int32_t i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b2) { return problems[a].n > problems[b2].n; });
     bt->owner.assign(count, -1);
     for (int32_t i = 0; i < count; ++i) {
         bt->owner[i] = i;
@@ -187,7 +196,8 @@ krr_status instantiate(krr_batch *bt, std::string *msg) {
     cudaEventRecord(bt->fork, bt->capture);
     krr_status cst = KRR_OK;
     std::string cmsg;
-    for (int32_t i = 0; i < count && cst == KRR_OK; ++i) {
+    for (int32_t r = 0; r < count && cst == KRR_OK; ++r) {
+        const int32_t i = order[r];
         cudaStreamWaitEvent(bt->streams[i], bt->fork, 0);
         const int32_t o = bt->owner[i];
         cst = (o == i) ? issue(bt->ctx[i], problems[i], m, p, nullptr, nullptr, bt->built[i])
